@@ -1,0 +1,105 @@
+"""Pins for the oracle's PRNG (Sec. 3.2, Fig. 5) and its counter-based seeding.
+
+The oracle writes the generator update as the textbook MLCG s' = a*s mod m and the output as
+fract(s0/m0 - s1/m1 + s2/m2 - s3/m3) in FP32. These tests pin it to things other than itself:
+the paper's float-only listing evaluated in float32 over every state, number theory of (a, m),
+exact rational arithmetic for the output, published SplitMix64 outputs, and uniformity.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+FIG5 = json.load(open(os.path.join(GOLD, "fig5_prng_constants.json")))
+
+
+def fig5_float_update(s, q, r, a, m):
+    """The paper's float-only state update (Fig. 5), evaluated in float32 with GLSL semantics:
+    mod(x, y) = x - y * floor(x / y), sign(0) = 0."""
+    f = np.float32
+    s = s.astype(f)
+    q, r, a, m = f(q), f(r), f(a), f(m)
+    beta = np.floor(s / q).astype(f)
+    modv = (s - q * np.floor(s / q)).astype(f)
+    p = (a * modv - beta * r).astype(f)
+    beta2 = ((np.sign(-p) + f(1)) * f(0.5) * m).astype(f)
+    return (p + beta2).astype(f), p
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_fig5_float_update_equals_mlcg_for_every_state(i):
+    q, r, a, m = (FIG5[k][i] for k in ("q", "r", "a", "m"))
+    s = np.arange(1, m, dtype=np.int64)
+    ref, p = fig5_float_update(s, q, r, a, m)
+    assert not np.any(p == 0), "p == 0 would give the m/2 branch of sign()"
+    got = O.mlcg_step_many(i, s)
+    assert np.array_equal(got, ref.astype(np.int64))
+    # textbook definition, independent of both
+    assert np.array_equal(got, (a * s) % m)
+
+
+@pytest.mark.parametrize("i", range(4))
+def test_mlcg_constants_give_full_period(i):
+    sympy = pytest.importorskip("sympy")
+    q, r, a, m = (FIG5[k][i] for k in ("q", "r", "a", "m"))
+    assert sympy.isprime(m)
+    assert (q, r) == (m // a, m % a)  # Schrage's decomposition
+    for p in sympy.factorint(m - 1):
+        assert pow(a, (m - 1) // p, m) != 1  # a is a primitive root: period m - 1
+    assert O.mlcg_step(i, 1) == a
+
+
+def test_output_is_fract_of_the_exact_weighted_sum():
+    rng = np.random.default_rng(0)
+    ms = FIG5["m"]
+    for _ in range(3000):
+        st = np.array([rng.integers(1, m) for m in ms], np.int64)
+        u = O.rng_next(st)  # advances st, then combines the advanced state
+        exact = (Fraction(int(st[0]), ms[0]) - Fraction(int(st[1]), ms[1]) +
+                 Fraction(int(st[2]), ms[2]) - Fraction(int(st[3]), ms[3]))
+        frac = exact - (exact.numerator // exact.denominator)
+        assert 0.0 <= u < 1.0
+        d = abs(float(frac) - u)
+        assert min(d, 1.0 - d) < 2.0 ** -22
+
+
+def test_splitmix64_published_outputs():
+    g = json.load(open(os.path.join(GOLD, "splitmix64_seed0.json")))
+    gamma = int(g["gamma"], 16)
+    for k, want in enumerate(g["outputs"]):
+        assert O.splitmix64((k * gamma) % 2 ** 64) == int(want, 16)
+
+
+def test_seeded_states_in_range_and_distinct():
+    ms = np.array(FIG5["m"])
+    states = np.array([O.rng_seed(7, 0, 1, 3, i) for i in range(20000)])
+    assert np.all(states >= 1) and np.all(states < ms[None, :])
+    assert len({tuple(s) for s in states}) == len(states)
+    # every coordinate of the key changes the stream
+    base = O.rng_seed(7, 0, 1, 3, 5)
+    for args in [(8, 0, 1, 3, 5), (7, 1, 1, 3, 5), (7, 0, 0, 3, 5), (7, 0, 1, 4, 5), (7, 0, 1, 3, 6)]:
+        assert not np.array_equal(O.rng_seed(*args), base)
+
+
+def test_uniformity_and_independence():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    u = O.rng_draws(1, 0, 1, 0, np.arange(1 << 14), 64).astype(np.float64)  # 2^20 draws
+    assert np.all((u >= 0) & (u < 1))
+    flat = u.ravel()
+    n = flat.size
+    assert abs(flat.mean() - 0.5) < 5 * np.sqrt(1 / 12 / n)
+    assert abs(flat.var() - 1 / 12) < 5 * np.sqrt(1 / 180 / n)
+    counts = np.bincount((flat * 256).astype(int), minlength=256)
+    assert scipy_stats.chisquare(counts).pvalue > 1e-4
+    # lag-1 within streams, and first draws across consecutive stream ids
+    lag = np.corrcoef(u[:, :-1].ravel(), u[:, 1:].ravel())[0, 1]
+    cross = np.corrcoef(u[:-1, 0], u[1:, 0])[0, 1]
+    assert abs(lag) < 5 / np.sqrt(n) and abs(cross) < 5 / np.sqrt(u.shape[0])
+    # 2-D equidistribution of consecutive pairs on an 16x16 grid
+    pairs = (u[:, 0::2] * 16).astype(int) * 16 + (u[:, 1::2] * 16).astype(int)
+    assert scipy_stats.chisquare(np.bincount(pairs.ravel(), minlength=256)).pvalue > 1e-4
