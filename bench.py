@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark: closest-hit ray casting through the multiple-threaded BVH, plus an SPPM pass.
+
+Default workload (one line of JSON on rank 0):
+  * step = one gsp_trace_closest_hit call over 4,194,304 rays (2,097,152 coherent pinhole rays
+    + 2,097,152 uniform random rays) against a 1,003,520-triangle displaced icosphere
+    (SAH BVH, 16 bins, six hit/miss link sets). metric: closest-hit Mrays/s.
+  * "sppm_512": SPPM passes/s at 512x512 on a 247,234-triangle scene with 1M photons/pass.
+  * "e2e": the same ray casting through the C ABI with host buffers (host->device copy of the
+    rays and device->host copy of the hits inside the timed region).
+Multi-GPU: every rank casts its own 4M rays (independent work, no collective on the data
+path); the value is all rays of all ranks over the slowest rank's time.
+
+--impl reference times the CPU oracle (FP64, all host cores) on a bounded sample of the same
+workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# FP32 instructions of the traversal kernel, counted from its source: per node visit 6 FSUB,
+# 6 FMUL, 6 FMIN/FMAX per axis, 3 FMAX + 2 FMIN for the interval, 1 FMUL + 1 FMIN for the
+# conservative far plane, 1 compare; per triangle test (Moller-Trumbore) about 40.
+OPS_PER_NODE = 26
+OPS_PER_TRI = 40
+BYTES_PER_NODE = 32
+BYTES_PER_TRI = 48
+BYTES_PER_RAY_IO = 32 + 8
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def traversal_workload():
+    from paper_1505_06022_gb300 import inputs as I
+    sc = I.traversal_sphere(n=224, seed=2)
+    rays = I.traversal_rays(2048, 1024, seed=2)
+    return sc, rays
+
+
+def stratified(n, k, seed=11):
+    rng = np.random.default_rng(seed)
+    half = n // 2
+    return np.sort(np.concatenate([rng.choice(half, k // 2, replace=False),
+                                   half + rng.choice(n - half, k - k // 2, replace=False)]))
+
+
+def cpu_oracle_rays(sc, rays, sample_rays, steps=1, warmup=0):
+    """Times the FP64 oracle's closest-hit query on `sample_rays` rays per step, all cores."""
+    import oracle as O
+    mesh = O.Mesh(sc.verts, sc.tris)
+    idx = stratified(len(rays), sample_rays)
+    sub = np.ascontiguousarray(rays[idx])
+    cores = O.nthreads_default()
+    for _ in range(warmup):
+        mesh.closest_hit(sub, classify=False, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        mesh.closest_hit(sub, classify=False, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return sample_rays * steps / dt / 1e6, cores, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    sc, rays = traversal_workload()
+    sample = 1 << 19
+    mrays, cores, dt = cpu_oracle_rays(sc, rays, sample, steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": "closest-hit Mrays/s", "value": round(mrays, 4), "unit": "Mrays/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000 * dt / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "closest-hit traversal: 1,003,520-triangle displaced icosphere, 4,194,304 rays "
+                               "(half coherent pinhole, half uniform random)",
+                   "sample_rays_per_step": sample, "parallelism": "host threads"},
+        "cpu_baseline": {"value": round(mrays, 4), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} stratified rays of the 4,194,304 per step, FP64 oracle BVH"},
+        "e2e": {"value": round(mrays, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1505_06022_gb300 import gsp, inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    gsp.lib()
+    ctx = gsp.Context(local)
+    sc, rays_h = traversal_workload()
+    scene = gsp.Scene(ctx, sc, bins=16, leaf_threshold=4, max_leaf=7, link_sets=6)
+    n = len(rays_h)
+    rays = torch.from_numpy(rays_h).to(dev)
+    tri = torch.empty(n, dtype=torch.int32, device=dev)
+    tt = torch.empty(n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        gsp.gsp_trace_closest_hit(scene.h, rays, tri, tt, None, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.sync()
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms_total = ev[0].elapsed_time(ev[1])
+    if pg:
+        tm = torch.tensor([ms_total], device=dev)
+        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
+        ms_total = float(tm.item())
+    ctx.sync()
+    ms_step = ms_total / args.steps
+    mrays = world * n / (ms_step / 1000.0) / 1e6
+
+    # ---- end to end through the C ABI with host buffers ----
+    rays_pin = torch.from_numpy(rays_h).pin_memory()
+    tri_pin = torch.empty(n, dtype=torch.int32).pin_memory()
+    t_pin = torch.empty(n, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        rays.copy_(rays_pin, non_blocking=True)
+        step()
+        tri_pin.copy_(tri, non_blocking=True)
+        t_pin.copy_(tt, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if pg:
+        tm = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
+        e2e_ms = float(tm.item())
+    # correctness of the timed results on a few rays (host walk of the same BVH)
+    chk = stratified(n, 4096, seed=5)
+    htri, _, vis, tests = scene.host_walk(rays_h[chk])
+    agree = float(np.mean(htri == tri_pin.numpy()[chk]))
+
+    # ---- roofline of the traversal kernel (FP32 ALU) ----
+    peaks = load_peaks()
+    wk = stratified(n, 65536, seed=6)
+    _, _, visw, testw = scene.host_walk(rays_h[wk])
+    v_node, v_tri = float(visw.mean()), float(testw.mean())
+    ops = (OPS_PER_NODE * v_node + OPS_PER_TRI * v_tri) * n
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
+    peak_tops = sm_count * 128 * sm_max * 1e6 / 1e12
+    achieved = ops / (ms_step / 1000.0) / 1e12
+    algo_bytes_ray = BYTES_PER_NODE * v_node + BYTES_PER_TRI * v_tri + BYTES_PER_RAY_IO
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tops, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak_tops, 4), "traffic": None,
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (measured max SM clock)",
+                "ops_per_ray": round(OPS_PER_NODE * v_node + OPS_PER_TRI * v_tri, 2),
+                "node_visits_per_ray": round(v_node, 3), "tri_tests_per_ray": round(v_tri, 3),
+                "algorithmic_bytes_per_ray": round(algo_bytes_ray, 1),
+                "algorithmic_GBps": round(algo_bytes_ray * n / (ms_step / 1000.0) / 1e9, 1),
+                "hbm_peak_GBps": (peaks or {}).get("hbm_gbs")}
+    traffic_file = os.path.join(ROOT, "profiles", "trace_traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            tf = json.load(open(traffic_file))
+            if tf.get("kernel_digest") == gsp_kernel_digest():
+                roofline["traffic"] = tf.get("dram_bytes_per_launch")
+        except Exception:
+            pass
+
+    # ---- SPPM pass at 512x512 ----
+    sppm = None
+    if not args.skip_sppm:
+        sppm = bench_sppm(args, ctx, dev, stream, pg)
+
+    # ---- CPU baseline: the oracle on the same workload ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        sample = 1 << 20
+        mr, cores, dt = cpu_oracle_rays(sc, rays_h, sample)
+        cpu = {"value": round(mr, 4), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+               "sample": f"{sample} stratified rays (half coherent, half random) of the 4,194,304-ray batch, "
+                         f"FP64 oracle BVH, {dt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": "closest-hit Mrays/s", "value": round(mrays, 2), "unit": "Mrays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "closest-hit traversal: 1,003,520-triangle displaced icosphere (SAH 16 bins, "
+                                   "6 link sets), 4,194,304 rays (2,097,152 coherent pinhole + 2,097,152 "
+                                   "uniform random)", "rays_per_rank": n, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (rays 134 MB per step); BVH resident",
+                       "bvh": scene.stats},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(world * n / (e2e_ms / 1000.0) / 1e6, 2), "unit": "Mrays/s",
+                    "h2d_bytes_per_step": int(rays_h.nbytes), "d2h_bytes_per_step": int(n * 8)},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "wall_s_timed": round(wall, 4),
+            "check": {"host_walk_agreement": round(agree, 5)},
+            "sppm_512": sppm,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def gsp_kernel_digest():
+    from paper_1505_06022_gb300 import build
+    return build._digest()[:16]
+
+
+def bench_sppm(args, ctx, dev, stream, pg):
+    import torch
+    from paper_1505_06022_gb300 import gsp, inputs as I
+    sc = I.full_scene(seed=3)
+    s = gsp.Scene(ctx, sc)
+    params = gsp.sppm_params(sc, 1 << 20, seed=3, r0_frac=0.004)
+    r = gsp.Renderer(s, params)
+    r.run(2, stream)
+    torch.cuda.synchronize()
+    k = args.sppm_passes
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r.run(k, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r.sync()
+    ms = e0.elapsed_time(e1) / k
+    if pg:
+        tm = torch.tensor([ms], device=dev)
+        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
+        ms = float(tm.item())
+    img = r.image(stream)
+    torch.cuda.synchronize()
+    out = {"passes_per_s": round(1000.0 / ms, 2), "ms_per_pass": round(ms, 3), "passes_timed": k,
+           "config": "512x512, 247,234 triangles (displaced plane, glass/mirror/diffuse icospheres, area light), "
+                     "1,048,576 photon paths/pass, alpha 0.7, r0 = 0.004 * diagonal, full paths + exact hash grid",
+           "image_mean": round(float(img.mean()), 5)}
+    r.close()
+    s.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sppm-passes", type=int, default=16)
+    ap.add_argument("--skip-sppm", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

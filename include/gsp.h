@@ -1,0 +1,235 @@
+/*
+ * gsp.h -- C ABI of the GB300 stackless-BVH ray caster and stochastic progressive photon
+ * mapping (SPPM) library.
+ *
+ * Method: T. Hachisuka, "Implementing a Photorealistic Rendering System using GLSL",
+ * EGSR 2015. Sec. 2 (three-stage SPPM iteration), Sec. 3.1 / Fig. 3 (multiple-threaded BVH
+ * traversal), Sec. 3.2 / Fig. 5 (PRNG), Sec. 3.3 (photon path regeneration), Sec. 3.4
+ * (stochastic spatial hashing with random depth).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns gsp_status: 0 on success, a negative code otherwise. Nothing
+ *    throws across the ABI. gsp_status_string() gives a static description.
+ *  - Handles (gsp_context, gsp_scene, gsp_sppm) are opaque, owned by the library, and freed by
+ *    the matching *_destroy call. A handle is not thread-safe; use one per host thread.
+ *  - Host arrays ("h_" or documented as host) are read during the call and not retained.
+ *  - Device arrays ("d_") are borrowed, caller-owned, contiguous, 16-byte aligned device
+ *    memory on the context's device. They must stay valid until the stream work that uses
+ *    them has completed.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream. Device
+ *    work is asynchronous on that stream. Kernels report faults they detect (a traversal that
+ *    exceeds its step limit, an overflowing buffer) in a device status word; the next
+ *    gsp_sppm_sync()/gsp_context_sync() returns the first such error.
+ *  - Memory the library allocates itself (scene, BVH, SPPM state) lives in device memory of
+ *    the context's device, sized at creation; no call allocates during a pass.
+ */
+#ifndef GSP_H_
+#define GSP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gsp_status;
+
+enum {
+    GSP_OK = 0,
+    GSP_ERR_INVALID_ARG = -1,     /* a pointer, size or parameter is out of range */
+    GSP_ERR_OOM = -2,             /* a device or host allocation failed */
+    GSP_ERR_CUDA = -3,            /* a CUDA runtime call failed */
+    GSP_ERR_TRAVERSAL_LIMIT = -4, /* a traversal exceeded 2 * nodes + 8 steps (corrupt links) */
+    GSP_ERR_TIMEOUT = -5,         /* a bounded device wait gave up */
+    GSP_ERR_NOT_BUILT = -6,       /* the scene has no BVH yet (call gsp_build_bvh) */
+    GSP_ERR_BAD_STATE = -7,       /* call order violated, e.g. render_grad before a forward */
+    GSP_ERR_IO = -8,              /* checkpoint file could not be read or written */
+    GSP_ERR_OVERFLOW = -9         /* a device buffer sized at creation overflowed */
+};
+
+typedef struct gsp_context gsp_context;
+typedef struct gsp_scene gsp_scene;
+typedef struct gsp_sppm gsp_sppm;
+
+/* Material types. DIFFUSE: two-sided Lambertian with reflectance `albedo`; if `emission` is
+ * non-zero it also emits Lambertian radiance `emission` from its front face (the side of
+ * (v1-v0) x (v2-v0)). MIRROR: perfect reflection scaled by `albedo`. DIELECTRIC: smooth
+ * interface of index `ior`, reflection or refraction picked with the exact unpolarised Fresnel
+ * probability. EMITTER: one-sided Lambertian emitter of radiance `emission` that absorbs
+ * everything it receives. */
+enum { GSP_DIFFUSE = 0, GSP_MIRROR = 1, GSP_DIELECTRIC = 2, GSP_EMITTER = 3 };
+
+typedef struct {
+    int32_t type;
+    float albedo[3];
+    float emission[3];
+    float ior;
+} gsp_material; /* 32 bytes */
+
+/* Pinhole camera: eye position, look-at point, up vector, full vertical field of view in
+ * degrees, image size in pixels. Pixel (0, 0) is the top-left corner. */
+typedef struct {
+    float eye[3], look[3], up[3];
+    float vfov_deg;
+    int32_t width, height;
+} gsp_camera; /* 48 bytes */
+
+/* BVH build parameters (Sec. 3.1: top-down SAH build and threading on the host).
+ *  bins           SAH bins per axis (default 16; 2..64)
+ *  leaf_threshold a node with at most this many triangles becomes a leaf (default 4)
+ *  max_leaf       hard cap on triangles per leaf (default 7, at most 7)
+ *  link_sets      6 = multiple-threaded BVH (one hit/miss link set per ray direction class
+ *                 +x,-x,+y,-y,+z,-z, Fig. 3); 1 = original threaded BVH (one fixed order). */
+typedef struct {
+    int32_t bins;
+    int32_t leaf_threshold;
+    int32_t max_leaf;
+    int32_t link_sets;
+} gsp_bvh_params;
+
+typedef struct {
+    int64_t nodes;        /* nodes in the tree (per link set) */
+    int64_t leaves;
+    int32_t depth;
+    int32_t link_sets;
+    double build_ms;      /* SAH build on the host */
+    double thread_ms;     /* writing the hit/miss links of every link set on the host */
+    int64_t device_bytes; /* node + triangle + shading bytes resident on the device */
+} gsp_bvh_stats;
+
+/* SPPM parameters.
+ *  photons_per_pass  photon paths traced per pass (FULL_PATH) or photon threads (REGEN)
+ *  table_size        hash table entries, a power of two; 0 = next_pow2(2 * photons_per_pass)
+ *  seed              stream seed of the counter-based PRNG
+ *  alpha             radius reduction parameter in (0, 1]
+ *  r0                initial gather radius (world units, > 0)
+ *  rr_continue       Russian-roulette continue probability at diffuse hits, in (0, 1]
+ *  cell_h            hash cell edge; 0 = 2 * r0. Must be >= 2 * r0 in STOCHASTIC mode.
+ *  eps               ray offset (tmin) of every secondary ray, world units
+ *  photon_mode       GSP_FULL_PATH: whole photon paths each pass; GSP_REGEN: one bounce per
+ *                    pass per thread, a thread starts a new path when its path ends (Sec. 3.3)
+ *  hash_mode         GSP_EXACT: every photon within R is gathered; GSP_STOCHASTIC: one photon
+ *                    survives per hash entry (minimum random depth), weighted by the entry's
+ *                    photon count (Sec. 3.4)
+ *  max_eye_depth     specular bounces followed by an eye path before it is dropped
+ *  max_photon_depth  rays per photon path, at most 32
+ *  scene_id          extra PRNG key so that batched scenes draw independent streams */
+enum { GSP_FULL_PATH = 0, GSP_REGEN = 1 };
+enum { GSP_EXACT = 0, GSP_STOCHASTIC = 1 };
+
+typedef struct {
+    int64_t photons_per_pass;
+    int64_t table_size;
+    uint64_t seed;
+    float alpha, r0, rr_continue, cell_h, eps;
+    int32_t photon_mode;
+    int32_t hash_mode;
+    int32_t max_eye_depth;
+    int32_t max_photon_depth;
+    uint32_t scene_id;
+} gsp_sppm_params;
+
+const char* gsp_status_string(gsp_status s);
+/* Text of the last host-side error on the calling thread (CUDA message, build error), or "". */
+const char* gsp_last_error_message(void);
+
+/* ---- context ---------------------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device` (the device is made current for the calling
+ * thread). Owns a device status word used by every kernel of its scenes. */
+gsp_status gsp_context_create(int32_t device, gsp_context** out);
+void gsp_context_destroy(gsp_context* ctx);
+/* Waits for all device work of the context and returns (then clears) the first device-side
+ * error recorded by its kernels. */
+gsp_status gsp_context_sync(gsp_context* ctx);
+
+/* ---- PRNG (Sec. 3.2, Fig. 5) ------------------------------------------------------------- */
+
+/* The renderer's random streams, written out: out[k * ndraw + j] = draw j of the stream keyed
+ * by (seed, scene, domain, pass, d_ids[k]). A stream's four MLCG states are derived from the key
+ * with SplitMix64 (s_i = 1 + 32-bit word i mod (m_i - 1)); each draw advances every state by
+ * s' = a s mod m and returns fract(s0/m0 - s1/m1 + s2/m2 - s3/m3) evaluated left to right in
+ * FP32 with round-to-nearest (1.0 is mapped to the largest float below 1). The renderer uses
+ * domain 0 for eye paths (id = pixel) and 1 for photon paths (id = path or thread).
+ * d_ids [n] uint64 device, d_out [n][ndraw] float device. */
+gsp_status gsp_rng_fill(gsp_context* ctx, uint64_t seed, uint32_t scene, uint32_t domain, uint32_t pass,
+                        const uint64_t* d_ids, int64_t n, int32_t ndraw, float* d_out, void* stream);
+
+/* ---- scene (Sec. 3.1) -------------------------------------------------------------------- */
+
+/* Uploads a triangle scene. Host inputs: verts [nv][3] float, tris [nt][3] int32 vertex
+ * indices, tri_mat [nt] int32 material indices (NULL = all 0), mats [nmat], cam (NULL allowed
+ * when only gsp_trace_closest_hit is used). Rejects non-finite vertices, out-of-range indices
+ * and nmat outside 1..64 with GSP_ERR_INVALID_ARG. Zero-area triangles are kept; the
+ * intersection test never reports them (determinant 0).
+ * ctx == NULL makes a host-only scene that touches no GPU: it accepts gsp_build_bvh (which then
+ * skips the upload), gsp_bvh_export and gsp_bvh_host_walk, and every device call rejects it. */
+gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, const int32_t* tris,
+                            int64_t nt, const int32_t* tri_mat, const gsp_material* mats,
+                            int32_t nmat, const gsp_camera* cam, gsp_scene** out);
+void gsp_scene_destroy(gsp_scene* scene);
+
+/* Builds the SAH BVH and its hit/miss links on the host (Sec. 3.1), packs them, and uploads
+ * them to the device (replacing any previous BVH). params NULL = defaults. stats may be NULL. */
+gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh_stats* stats);
+
+/* Closest-hit ray casting (Fig. 3): for each ray i, the triangle with the lexicographically
+ * smallest (t, triangle index) among tmin < t < tmax, Moller-Trumbore in FP32.
+ *  d_rays [n][8] float: ox, oy, oz, tmin, dx, dy, dz, tmax (d need not be unit length)
+ *  d_tri  [n] int32 out: triangle index in the uploaded order, -1 on a miss
+ *  d_t    [n] float out: hit distance (in units of |d|), +inf on a miss
+ *  d_uv   [n][2] float out or NULL: barycentrics (u, v) of the hit, 0 on a miss
+ * Returns GSP_ERR_NOT_BUILT if the scene has no BVH. n == 0 is a no-op. */
+gsp_status gsp_trace_closest_hit(gsp_scene* scene, const float* d_rays, int64_t n, int32_t* d_tri,
+                                 float* d_t, float* d_uv, void* stream);
+
+/* Instrumented host walk of the same threaded BVH (no GPU): per ray, the number of node
+ * visits and triangle tests that the device traversal performs, and its closest hit.
+ * Used to count the algorithmic bytes of a traversal. Host arrays; any output may be NULL. */
+gsp_status gsp_bvh_host_walk(gsp_scene* scene, const float* h_rays, int64_t n, int32_t* h_tri,
+                             float* h_t, int32_t* h_node_visits, int32_t* h_tri_tests);
+
+/* Copies the packed BVH of link set `set` (0..link_sets-1) to host arrays (no GPU needed):
+ *  h_nodes [nodes][8] float: min.xyz, miss link (int bits, -1 = none) | max.xyz, leaf word
+ *          (int bits: bit 31 set = internal node, hit link = index + 1; otherwise
+ *          triangle offset << 3 | triangle count, hit link = miss link)
+ *  h_tris  [nt][12] float: v0.xyz, triangle index (int bits) | e1.xyz, 0 | e2.xyz, 0
+ * Either pointer may be NULL; *nodes_out receives the node count. */
+gsp_status gsp_bvh_export(gsp_scene* scene, int32_t set, float* h_nodes, float* h_tris,
+                          int64_t* nodes_out);
+
+/* ---- SPPM (Sec. 2, 3.3, 3.4) ------------------------------------------------------------- */
+
+/* Creates a renderer over `scene` (which needs a camera, a BVH and at least one emitting
+ * triangle). Allocates every device buffer a pass needs (pixel state, hit points, photon
+ * records, hash table, sort scratch). */
+gsp_status gsp_sppm_create(gsp_scene* scene, const gsp_sppm_params* params, gsp_sppm** out);
+void gsp_sppm_destroy(gsp_sppm* r);
+
+/* Runs `npasses` SPPM iterations on `stream`: eye pass (first non-specular hit per pixel,
+ * emission seen directly), photon pass, hash-grid deposit, range query with the progressive
+ * update N' = N + alpha M, R' = R sqrt((N + alpha M) / (N + M)), tau' = (tau + Phi) R'^2/R^2. */
+gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
+
+/* Writes the current estimate L = direct / P + tau / (pi R^2 N_e) to d_rgb [h][w][3] float. */
+gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream);
+
+/* Copies the per-pixel state to caller device arrays (any may be NULL): d_N [h*w],
+ * d_R [h*w], d_tau [h*w][3], d_direct [h*w][3]. h_counts (host, may be NULL) receives
+ * {passes, emitted paths N_e} after synchronising the stream. */
+gsp_status gsp_sppm_state(gsp_sppm* r, float* d_N, float* d_R, float* d_tau, float* d_direct,
+                          double* h_counts, void* stream);
+
+/* Diagnostics of the last pass (host arrays, synchronises): number of photon deposits, and if
+ * h_ids is not NULL (capacity given by the previous return value) their ids in ascending
+ * order. Returns the count as a non-negative int64 or a negative gsp_status. */
+int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity);
+
+/* Waits for the renderer's stream work and returns the first recorded device error. */
+gsp_status gsp_sppm_sync(gsp_sppm* r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSP_H_ */

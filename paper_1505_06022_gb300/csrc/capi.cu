@@ -1,0 +1,329 @@
+// capi.cu -- context, scene, BVH and closest-hit entry points of the C ABI (include/gsp.h).
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "devcommon.cuh"
+#include "gsp_internal.h"
+#include "launch.h"
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void gsp_set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace gspd {
+
+// Closest-hit kernel (Fig. 3). Persistent grid; each warp takes batches of 32 rays from a
+// global counter and refills finished lanes, so lanes of long rays do not idle behind a warp
+// that is otherwise done.
+__global__ void __launch_bounds__(kTraceThreads)
+k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* __restrict__ tri,
+        float* __restrict__ tout, float2* __restrict__ uv, unsigned long long* __restrict__ next) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(next, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= (unsigned long long)n) break;
+        const int64_t i = (int64_t)base + lane;
+        if (i < n) {
+            const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
+            const Hit h = traverse(S, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z), a.w, b.w);
+            tri[i] = h.id;
+            tout[i] = h.id >= 0 ? h.t : __int_as_float(0x7f800000);
+            if (uv) uv[i] = make_float2(h.u, h.v);
+        }
+    }
+}
+
+__global__ void k_zero_u64(unsigned long long* p) { *p = 0ull; }
+
+// out[k * ndraw + j] = draw j of stream (seed, scene, domain, pass, ids[k])
+__global__ void k_rng_fill(uint64_t seed, uint32_t scene, uint32_t domain, uint32_t pass,
+                           const uint64_t* __restrict__ ids, int64_t n, int32_t ndraw, float* __restrict__ out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        Rng r = rng_seed(seed, scene, domain, pass, ids[k]);
+        for (int32_t j = 0; j < ndraw; ++j) out[k * ndraw + j] = rng_next(r);
+    }
+}
+
+}  // namespace gspd
+
+int gsp_trace_grid(int device) {
+    static int cached[64] = {0};
+    if (device >= 0 && device < 64 && cached[device]) return cached[device];
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gspd::k_trace, kTraceThreads, 0);
+    int g = std::max(1, sms) * std::max(1, per_sm);
+    if (device >= 0 && device < 64) cached[device] = g;
+    return g;
+}
+
+gspd::DevScene gsp_dev_scene(const gsp_scene* s) {
+    gspd::DevScene d;
+    d.nodes = s->d_nodes;
+    d.tris = s->d_tris;
+    d.shade = s->d_shade;
+    d.mats = s->d_mats;
+    d.nnodes = s->bvh.nnodes;
+    d.link_sets = s->bvh.link_sets;
+    d.status = s->ctx->d_status;
+    return d;
+}
+
+extern "C" {
+
+const char* gsp_status_string(gsp_status s) {
+    switch (s) {
+        case GSP_OK: return "ok";
+        case GSP_ERR_INVALID_ARG: return "invalid argument";
+        case GSP_ERR_OOM: return "out of memory";
+        case GSP_ERR_CUDA: return "CUDA runtime error";
+        case GSP_ERR_TRAVERSAL_LIMIT: return "traversal exceeded its step limit (corrupt BVH links)";
+        case GSP_ERR_TIMEOUT: return "bounded device wait timed out";
+        case GSP_ERR_NOT_BUILT: return "scene has no BVH";
+        case GSP_ERR_BAD_STATE: return "call order violated";
+        case GSP_ERR_IO: return "checkpoint I/O failed";
+        case GSP_ERR_OVERFLOW: return "device buffer overflow";
+        default: return "unknown status";
+    }
+}
+
+const char* gsp_last_error_message(void) { return g_last_error.c_str(); }
+
+gsp_status gsp_context_create(int32_t device, gsp_context** out) {
+    if (!out) return GSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    GSP_CUDA_TRY(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(device));
+    gsp_context* c = new (std::nothrow) gsp_context;
+    if (!c) return GSP_ERR_OOM;
+    c->device = device;
+    cudaError_t e = cudaMalloc(&c->d_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(e));
+        delete c;
+        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+    }
+    *out = c;
+    return GSP_OK;
+}
+
+void gsp_context_destroy(gsp_context* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+gsp_status gsp_context_sync(gsp_context* ctx) {
+    if (!ctx) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(ctx->device));
+    GSP_CUDA_TRY(cudaDeviceSynchronize());
+    int32_t st = 0;
+    GSP_CUDA_TRY(cudaMemcpy(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost));
+    if (st != 0) GSP_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(int32_t)));
+    return st;
+}
+
+static void scene_free_bvh(gsp_scene* s) {
+    cudaFree(s->d_nodes);
+    cudaFree(s->d_tris);
+    s->d_nodes = nullptr;
+    s->d_tris = nullptr;
+    s->built = false;
+}
+
+void gsp_scene_destroy(gsp_scene* s) {
+    if (!s) return;
+    if (s->ctx) {
+        cudaSetDevice(s->ctx->device);
+        scene_free_bvh(s);
+        cudaFree(s->d_shade);
+        cudaFree(s->d_mats);
+        cudaFree(s->d_counter);
+    }
+    delete s;
+}
+
+gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, const int32_t* tris,
+                            int64_t nt, const int32_t* tri_mat, const gsp_material* mats,
+                            int32_t nmat, const gsp_camera* cam, gsp_scene** out) {
+    if (!verts || !tris || !mats || !out || nv <= 0 || nt <= 0 || nmat < 1 || nmat > 64)
+        return GSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nt >= (int64_t(1) << 28) || nv >= (int64_t(1) << 31)) return GSP_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < 3 * nv; ++i)
+        if (!std::isfinite(verts[i])) return GSP_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < 3 * nt; ++i)
+        if (tris[i] < 0 || tris[i] >= nv) return GSP_ERR_INVALID_ARG;
+    if (tri_mat)
+        for (int64_t i = 0; i < nt; ++i)
+            if (tri_mat[i] < 0 || tri_mat[i] >= nmat) return GSP_ERR_INVALID_ARG;
+    for (int32_t m = 0; m < nmat; ++m) {
+        if (mats[m].type < GSP_DIFFUSE || mats[m].type > GSP_EMITTER) return GSP_ERR_INVALID_ARG;
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(mats[m].albedo[k]) || !std::isfinite(mats[m].emission[k]) ||
+                mats[m].emission[k] < 0.0f)
+                return GSP_ERR_INVALID_ARG;
+        if (mats[m].type == GSP_DIELECTRIC && !(mats[m].ior > 0.0f)) return GSP_ERR_INVALID_ARG;
+    }
+    if (cam && (cam->width <= 0 || cam->height <= 0 || !(cam->vfov_deg > 0.0f) ||
+                !(cam->vfov_deg < 180.0f)))
+        return GSP_ERR_INVALID_ARG;
+    if (ctx) GSP_CUDA_TRY(cudaSetDevice(ctx->device));
+    gsp_scene* s = new (std::nothrow) gsp_scene;
+    if (!s) return GSP_ERR_OOM;
+    s->ctx = ctx;
+    s->nv = nv;
+    s->nt = nt;
+    s->nmat = nmat;
+    s->verts.assign(verts, verts + 3 * nv);
+    s->tris.assign(tris, tris + 3 * nt);
+    s->tri_mat = tri_mat ? std::vector<int32_t>(tri_mat, tri_mat + nt) : std::vector<int32_t>(nt, 0);
+    s->mats.assign(mats, mats + nmat);
+    if (cam) { s->has_cam = true; s->cam = *cam; }
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nv; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], (double)verts[3 * i + k]);
+            hi[k] = std::max(hi[k], (double)verts[3 * i + k]);
+        }
+    s->extent = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                          (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    // shading record per triangle: unit geometric normal (computed in FP64) + material
+    std::vector<float4> shade(nt);
+    for (int64_t i = 0; i < nt; ++i) {
+        const float* a = verts + 3 * (int64_t)tris[3 * i];
+        const float* b = verts + 3 * (int64_t)tris[3 * i + 1];
+        const float* c = verts + 3 * (int64_t)tris[3 * i + 2];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) { e1[k] = (double)b[k] - a[k]; e2[k] = (double)c[k] - a[k]; }
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        double il = len > 0 ? 1.0 / len : 0.0;
+        int32_t m = s->tri_mat[i];
+        float mf;
+        std::memcpy(&mf, &m, 4);
+        shade[i] = float4{(float)(n[0] * il), (float)(n[1] * il), (float)(n[2] * il), mf};
+    }
+    std::vector<float4> mt(2 * nmat);
+    for (int32_t m = 0; m < nmat; ++m) {
+        float tf;
+        std::memcpy(&tf, &mats[m].type, 4);
+        mt[2 * m] = float4{mats[m].albedo[0], mats[m].albedo[1], mats[m].albedo[2], tf};
+        mt[2 * m + 1] = float4{mats[m].emission[0], mats[m].emission[1], mats[m].emission[2], mats[m].ior};
+    }
+    if (!ctx) {  // host-only scene: BVH build, export and host walk only
+        *out = s;
+        return GSP_OK;
+    }
+    cudaError_t e = cudaMalloc(&s->d_shade, nt * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_mats, 2 * nmat * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_shade, shade.data(), nt * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_mats, mt.data(), 2 * nmat * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(e));
+        gsp_scene_destroy(s);
+        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+    }
+    *out = s;
+    return GSP_OK;
+}
+
+gsp_status gsp_build_bvh(gsp_scene* s, const gsp_bvh_params* params, gsp_bvh_stats* stats) {
+    if (!s) return GSP_ERR_INVALID_ARG;
+    gsp_bvh_params p{16, 4, 7, 6};
+    if (params) p = *params;
+    if (p.bins < 2 || p.bins > 64 || p.max_leaf < 1 || p.max_leaf > 7 || p.leaf_threshold < 1 ||
+        p.leaf_threshold > p.max_leaf || (p.link_sets != 1 && p.link_sets != 6))
+        return GSP_ERR_INVALID_ARG;
+    HostBVH bvh;
+    std::string err = bvh_build_host(s->verts.data(), s->nv, s->tris.data(), s->nt, p, bvh);
+    if (!err.empty()) {
+        gsp_set_last_error(err);
+        return GSP_ERR_INVALID_ARG;
+    }
+    size_t nb = bvh.nodes.size() * sizeof(float4), tb = bvh.tris.size() * sizeof(float4);
+    if (s->ctx) {
+        GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+        scene_free_bvh(s);
+        GSP_CUDA_TRY(cudaMalloc(&s->d_nodes, nb));
+        GSP_CUDA_TRY(cudaMalloc(&s->d_tris, tb));
+        GSP_CUDA_TRY(cudaMemcpy(s->d_nodes, bvh.nodes.data(), nb, cudaMemcpyHostToDevice));
+        GSP_CUDA_TRY(cudaMemcpy(s->d_tris, bvh.tris.data(), tb, cudaMemcpyHostToDevice));
+    }
+    s->bvh = std::move(bvh);
+    s->built = true;
+    s->device_bytes = (int64_t)(nb + tb) + s->nt * (int64_t)sizeof(float4);
+    if (stats) {
+        stats->nodes = s->bvh.nnodes;
+        stats->leaves = s->bvh.nleaves;
+        stats->depth = s->bvh.depth;
+        stats->link_sets = s->bvh.link_sets;
+        stats->build_ms = s->bvh.build_ms;
+        stats->thread_ms = s->bvh.thread_ms;
+        stats->device_bytes = s->device_bytes;
+    }
+    return GSP_OK;
+}
+
+gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, int32_t* d_tri,
+                                 float* d_t, float* d_uv, void* stream) {
+    if (!s || n < 0) return GSP_ERR_INVALID_ARG;
+    if (!s->ctx) return GSP_ERR_INVALID_ARG;  // host-only scene
+    if (!s->built) return GSP_ERR_NOT_BUILT;
+    if (n == 0) return GSP_OK;
+    if (!d_rays || !d_tri || !d_t) return GSP_ERR_INVALID_ARG;
+    if (((uintptr_t)d_rays & 15) || ((uintptr_t)d_uv & 7)) return GSP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    unsigned long long* counter = s->d_counter;
+    gspd::k_zero_u64<<<1, 1, 0, st>>>(counter);
+    gspd::k_trace<<<gsp_trace_grid(s->ctx->device), kTraceThreads, 0, st>>>(
+        gsp_dev_scene(s), (const float4*)d_rays, n, d_tri, d_t, (float2*)d_uv, counter);
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+gsp_status gsp_rng_fill(gsp_context* ctx, uint64_t seed, uint32_t scene, uint32_t domain, uint32_t pass,
+                        const uint64_t* d_ids, int64_t n, int32_t ndraw, float* d_out, void* stream) {
+    if (!ctx || n < 0 || ndraw < 0 || (n > 0 && (!d_ids || !d_out))) return GSP_ERR_INVALID_ARG;
+    if (n == 0 || ndraw == 0) return GSP_OK;
+    GSP_CUDA_TRY(cudaSetDevice(ctx->device));
+    const int64_t nb = std::min<int64_t>((n + 255) / 256, 65535);
+    gspd::k_rng_fill<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(seed, scene, domain, pass, d_ids, n, ndraw, d_out);
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+gsp_status gsp_bvh_host_walk(gsp_scene* s, const float* h_rays, int64_t n, int32_t* h_tri,
+                             float* h_t, int32_t* h_visits, int32_t* h_tests) {
+    if (!s || n < 0 || (n > 0 && !h_rays)) return GSP_ERR_INVALID_ARG;
+    if (!s->built) return GSP_ERR_NOT_BUILT;
+    bvh_host_walk(s->bvh, h_rays, n, h_tri, h_t, h_visits, h_tests);
+    return GSP_OK;
+}
+
+gsp_status gsp_bvh_export(gsp_scene* s, int32_t set, float* h_nodes, float* h_tris, int64_t* nodes_out) {
+    if (!s) return GSP_ERR_INVALID_ARG;
+    if (!s->built) return GSP_ERR_NOT_BUILT;
+    if (set < 0 || set >= s->bvh.link_sets) return GSP_ERR_INVALID_ARG;
+    if (nodes_out) *nodes_out = s->bvh.nnodes;
+    if (h_nodes)
+        std::memcpy(h_nodes, s->bvh.nodes.data() + (size_t)set * s->bvh.nnodes * 2,
+                    s->bvh.nnodes * 2 * sizeof(float4));
+    if (h_tris) std::memcpy(h_tris, s->bvh.tris.data(), s->bvh.tris.size() * sizeof(float4));
+    return GSP_OK;
+}
+
+}  // extern "C"

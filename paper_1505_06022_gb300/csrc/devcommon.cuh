@@ -1,0 +1,189 @@
+// devcommon.cuh -- device-side building blocks: PRNG, ray/box and ray/triangle tests, and the
+// stackless multiple-threaded BVH traversal (Sec. 3.1-3.2, Fig. 3, Fig. 5).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gspd {
+
+// ----------------------------------------------------------------------------------------------
+// device status word: the first error a kernel detects (0 = none). Never traps.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ void report(int32_t* status, int32_t code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// ----------------------------------------------------------------------------------------------
+// PRNG (Sec. 3.2, Fig. 5): four MLCGs s' = a s mod m, advanced with Schrage's decomposition in
+// int32 (q = m div a, r = m mod a), combined as fract(s0/m0 - s1/m1 + s2/m2 - s3/m3) in FP32
+// with a fixed evaluation order and round-to-nearest operations (no contraction).
+// ----------------------------------------------------------------------------------------------
+struct Rng {
+    int32_t s[4];
+};
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    // SplitMix64 (Steele, Lea & Flood 2014) output function at x + golden gamma.
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Counter-based stream: (seed, scene, domain, pass, id) -> four states in [1, m_i - 1].
+__device__ __forceinline__ Rng rng_seed(uint64_t seed, uint32_t scene, uint32_t domain,
+                                        uint32_t pass, uint64_t id) {
+    uint64_t h = splitmix64(seed);
+    h = splitmix64(h ^ (uint64_t)scene);
+    h = splitmix64(h ^ (((uint64_t)domain << 32) | (uint64_t)pass));
+    uint64_t h3 = splitmix64(h ^ id);
+    uint64_t h4 = splitmix64(h3);
+    Rng r;
+    r.s[0] = 1 + (int32_t)((uint32_t)h3 % 4194286u);
+    r.s[1] = 1 + (int32_t)((uint32_t)(h3 >> 32) % 4194276u);
+    r.s[2] = 1 + (int32_t)((uint32_t)h4 % 4194190u);
+    r.s[3] = 1 + (int32_t)((uint32_t)(h4 >> 32) % 4194166u);
+    return r;
+}
+
+template <int A, int M, int Q, int R>
+__device__ __forceinline__ int32_t mlcg(int32_t s) {
+    int32_t hi = s / Q;
+    int32_t lo = s - hi * Q;
+    int32_t p = A * lo - R * hi;  // |p| < m, never 0 for 0 < s < m (m prime)
+    return p < 0 ? p + M : p;
+}
+
+__device__ __forceinline__ float rng_next(Rng& r) {
+    r.s[0] = mlcg<3423, 4194287, 1225, 1112>(r.s[0]);
+    r.s[1] = mlcg<2646, 4194277, 1585, 367>(r.s[1]);
+    r.s[2] = mlcg<1707, 4194191, 2457, 92>(r.s[2]);
+    r.s[3] = mlcg<1999, 4194167, 2098, 265>(r.s[3]);
+    float f0 = __fdiv_rn((float)r.s[0], 4194287.0f);
+    float f1 = __fdiv_rn((float)r.s[1], 4194277.0f);
+    float f2 = __fdiv_rn((float)r.s[2], 4194191.0f);
+    float f3 = __fdiv_rn((float)r.s[3], 4194167.0f);
+    float acc = __fsub_rn(f0, f1);
+    acc = __fadd_rn(acc, f2);
+    acc = __fsub_rn(acc, f3);
+    float u = __fsub_rn(acc, floorf(acc));
+    return u >= 1.0f ? 0x1.fffffep-1f : u;
+}
+
+// ----------------------------------------------------------------------------------------------
+// small float3 algebra
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 mul3(float3 a, float3 b) { return make_float3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+
+// ----------------------------------------------------------------------------------------------
+// scene as the kernels see it
+// ----------------------------------------------------------------------------------------------
+struct DevScene {
+    const float4* __restrict__ nodes;  // link_sets * nnodes * 2
+    const float4* __restrict__ tris;   // 3 per triangle, leaf order
+    const float4* __restrict__ shade;  // per triangle (upload order): normal xyz, material bits
+    const float4* __restrict__ mats;   // 2 per material
+    int64_t nnodes;
+    int32_t link_sets;
+    int32_t* status;
+};
+
+struct Hit {
+    int32_t id;  // triangle index in upload order, -1 = none
+    float t, u, v;
+};
+
+// Ray direction class for the multiple-threaded BVH (replaces Fig. 3's cubemap lookup):
+// principal axis = largest |d| component (ties x, y, z), sign = d_axis >= 0.
+__device__ __forceinline__ int ray_class(float3 d) {
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int a = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    float da = a == 0 ? d.x : (a == 1 ? d.y : d.z);
+    return 2 * a + (da >= 0.0f ? 0 : 1);
+}
+
+__device__ __forceinline__ float safe_inv(float d) {
+    return 1.0f / (fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d);
+}
+
+// 1 + 2 gamma_3 with gamma_n = n u / (1 - n u), u = 2^-24: the far-plane scale that makes the
+// FP32 slab test conservative (Ize 2013).
+#define GSP_ROBUST_FAR 1.0000003576278687f
+
+// Closest hit by the stackless traversal of Fig. 3: follow the hit link (index + 1) when the
+// node's box is hit, the miss link otherwise; leaves run Moller-Trumbore on their triangles.
+// The lexicographic (t, triangle index) minimum over tmin < t < tmax is kept.
+__device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, float tmin, float tmax) {
+    Hit h;
+    h.id = -1;
+    h.t = tmax;
+    h.u = h.v = 0.0f;
+    const float3 inv = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    const int c = S.link_sets == 6 ? ray_class(d) : 0;
+    const float4* __restrict__ nodes = S.nodes + (size_t)c * (size_t)S.nnodes * 2;
+    const int64_t cap = 2 * S.nnodes + 8;
+    int32_t node = 0;
+    int64_t steps = 0;
+    while (node >= 0) {
+        if (++steps > cap) {
+            report(S.status, -4);
+            break;
+        }
+        const float4 A = __ldg(nodes + 2 * node);
+        const float4 B = __ldg(nodes + 2 * node + 1);
+        float t0x = __fmul_rn(A.x - o.x, inv.x), t1x = __fmul_rn(B.x - o.x, inv.x);
+        float t0y = __fmul_rn(A.y - o.y, inv.y), t1y = __fmul_rn(B.y - o.y, inv.y);
+        float t0z = __fmul_rn(A.z - o.z, inv.z), t1z = __fmul_rn(B.z - o.z, inv.z);
+        float tn = fmaxf(tmin, fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z)));
+        float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
+        tf = fminf(h.t, tf * GSP_ROBUST_FAR);
+        const int32_t miss = __float_as_int(A.w);
+        const int32_t word = __float_as_int(B.w);
+        if (tn <= tf) {
+            if (word >= 0) {
+                const int32_t first = word >> 3, cnt = word & 7;
+                for (int32_t k = 0; k < cnt; ++k) {
+                    const float4 P = __ldg(S.tris + 3 * (first + k));
+                    const float4 E1 = __ldg(S.tris + 3 * (first + k) + 1);
+                    const float4 E2 = __ldg(S.tris + 3 * (first + k) + 2);
+                    const float3 e1 = f3(E1), e2 = f3(E2);
+                    const float3 p = cross3(d, e2);
+                    const float det = dot3(e1, p);
+                    if (det == 0.0f) continue;
+                    const float f = 1.0f / det;
+                    const float3 s = o - f3(P);
+                    const float u = f * dot3(s, p);
+                    const float3 q = cross3(s, e1);
+                    const float v = f * dot3(d, q);
+                    const float t = f * dot3(e2, q);
+                    const int32_t id = __float_as_int(P.w);
+                    if (u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t > tmin &&
+                        (t < h.t || (t == h.t && h.id >= 0 && id < h.id))) {
+                        h.t = t;
+                        h.id = id;
+                        h.u = u;
+                        h.v = v;
+                    }
+                }
+                node = miss;
+            } else {
+                node = node + 1;
+            }
+        } else {
+            node = miss;
+        }
+    }
+    return h;
+}
+
+}  // namespace gspd

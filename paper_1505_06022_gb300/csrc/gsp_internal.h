@@ -1,0 +1,69 @@
+// gsp_internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gsp.h"
+
+// Host copy of the packed BVH (Sec. 3.1): per link set, nodes in that set's preorder.
+// Node = 2 float4: {min.xyz, miss link}, {max.xyz, leaf word}; triangle = 3 float4:
+// {v0.xyz, triangle index}, {e1.xyz, 0}, {e2.xyz, 0}.
+struct HostBVH {
+    int64_t nnodes = 0;
+    int64_t nleaves = 0;
+    int32_t depth = 0;
+    int32_t link_sets = 0;
+    std::vector<float4> nodes;  // link_sets * nnodes * 2
+    std::vector<float4> tris;   // nt * 3, leaf order
+    double build_ms = 0, thread_ms = 0;
+};
+
+// Builds the binned-SAH tree and writes its hit/miss links (one set per ray direction
+// class when link_sets == 6). Returns an empty string on success, else an error message.
+std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                           const gsp_bvh_params& p, HostBVH& out);
+
+// Instrumented host walk of a packed BVH (same control flow as the device traversal).
+void bvh_host_walk(const HostBVH& bvh, const float* rays, int64_t n, int32_t* tri, float* t,
+                   int32_t* visits, int32_t* tests);
+
+struct gsp_context {
+    int32_t device = 0;
+    int32_t* d_status = nullptr;  // first device-side error (0 = none)
+};
+
+struct gsp_scene {
+    gsp_context* ctx = nullptr;
+    int64_t nv = 0, nt = 0;
+    int32_t nmat = 0;
+    std::vector<float> verts;
+    std::vector<int32_t> tris, tri_mat;
+    std::vector<gsp_material> mats;
+    bool has_cam = false;
+    gsp_camera cam{};
+    double extent = 0;  // diagonal of the vertex bounding box
+    // device copies
+    float4* d_shade = nullptr;  // per triangle (upload order): unit normal xyz, material (int bits)
+    float4* d_mats = nullptr;   // per material: {albedo.rgb, type bits}, {emission.rgb, ior}
+    float4* d_nodes = nullptr;
+    float4* d_tris = nullptr;
+    unsigned long long* d_counter = nullptr;  // work counter of the persistent trace kernel
+    bool built = false;
+    HostBVH bvh;
+    int64_t device_bytes = 0;
+};
+
+#define GSP_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) {                             \
+            gsp_set_last_error(cudaGetErrorString(e_));      \
+            return e_ == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA; \
+        }                                                    \
+    } while (0)
+
+void gsp_set_last_error(const std::string& msg);

@@ -1,0 +1,869 @@
+// sppm.cu -- stochastic progressive photon mapping on the device (Sec. 2, 3.3, 3.4).
+//
+// One pass = eye pass (first non-specular hit per pixel; emission seen directly is added to
+// the pixel's direct term), photon pass (whole paths, or one bounce per thread with path
+// regeneration), hash-grid deposit, and the fused range query + progressive update.
+//
+// Device layout (all library-owned, sized at creation):
+//   pixel state   st0[p] = {tau.rgb, N}, st1[p] = {direct.rgb, R}          32 B / pixel
+//   hit points    hx[p] = {x.xyz, material or -1}, hn[p] = {n_s.xyz, 0},
+//                 hf[p] = {w * albedo / pi, 0}                              48 B / pixel
+//   photon slots  slot s: {x.xyz, id}, {flux.rgb, octahedral direction}    32 B / deposit
+//                 path k owns slots [k*32, k*32+32) (one slot per thread in REGEN mode)
+//   exact grid    bucket-sorted SoA copies spos[], spay[] + bucket starts bstart[T+1]
+//   stochastic    entry[T] = min(random depth bits << 32 | slot), ecount[T]
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "devcommon.cuh"
+#include "gsp_internal.h"
+#include "launch.h"
+#include "scan_sort.h"
+
+namespace gspd {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr int kSlotsPerPath = 32;
+
+struct CamDev {
+    float3 eye, fwd, right, up;
+    float th, aspect;
+    int32_t w, h;
+};
+
+struct EmitDev {
+    const float4* __restrict__ geo;  // 5 per emitter: v0, e1, e2, n, flux
+    const float* __restrict__ cdf;
+    int32_t n;
+};
+
+struct PassDev {
+    uint64_t seed;
+    uint32_t scene_id, pass;
+    float alpha, rr, eps, inv_h;
+    int32_t max_eye, max_photon;
+    uint32_t tmask;
+    int64_t np;
+};
+
+struct Material {
+    float3 albedo, emission;
+    int32_t type;
+    float ior;
+};
+
+__device__ __forceinline__ Material load_mat(const DevScene& S, int32_t m) {
+    const float4 a = __ldg(S.mats + 2 * m), b = __ldg(S.mats + 2 * m + 1);
+    Material r;
+    r.albedo = f3(a);
+    r.type = __float_as_int(a.w);
+    r.emission = f3(b);
+    r.ior = b.w;
+    return r;
+}
+
+__device__ __forceinline__ bool emits(const Material& m) {
+    return (m.type == GSP_DIFFUSE || m.type == GSP_EMITTER) &&
+           fmaxf(m.emission.x, fmaxf(m.emission.y, m.emission.z)) > 0.0f;
+}
+
+// Orthonormal basis about a unit vector (Duff et al., JCGT 2017).
+__device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
+    const float sign = copysignf(1.0f, n.z);
+    const float a = -1.0f / (sign + n.z);
+    const float b = n.x * n.y * a;
+    t1 = make_float3(1.0f + sign * n.x * n.x * a, sign * b, -sign * n.x);
+    t2 = make_float3(b, sign + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float3 cosine_dir(float3 n, float ua, float ub) {
+    const float r = sqrtf(ua), phi = 2.0f * kPi * ub;
+    const float z = sqrtf(fmaxf(0.0f, 1.0f - ua));
+    float s, c;
+    sincosf(phi, &s, &c);
+    float3 t1, t2;
+    onb(n, t1, t2);
+    return t1 * (r * c) + t2 * (r * s) + n * z;
+}
+
+__device__ __forceinline__ float3 reflect3(float3 d, float3 n) { return d - n * (2.0f * dot3(d, n)); }
+
+// Smooth dielectric: reflection with the exact unpolarised Fresnel probability, else refraction.
+__device__ __forceinline__ float3 dielectric(float3 d, float3 n, float ior, float u) {
+    const bool front = dot3(d, n) < 0.0f;
+    const float3 nf = front ? n : n * -1.0f;
+    const float n1 = front ? 1.0f : ior, n2 = front ? ior : 1.0f;
+    const float eta = n1 / n2;
+    const float cosi = -dot3(d, nf);
+    const float k = 1.0f - eta * eta * (1.0f - cosi * cosi);
+    if (k < 0.0f) return reflect3(d, nf);
+    const float cost = sqrtf(k);
+    const float rs = (n1 * cosi - n2 * cost) / (n1 * cosi + n2 * cost);
+    const float rp = (n2 * cosi - n1 * cost) / (n2 * cosi + n1 * cost);
+    const float F = 0.5f * (rs * rs + rp * rp);
+    if (u < F) return reflect3(d, nf);
+    return d * eta + nf * (eta * cosi - cost);
+}
+
+// Octahedral unit-vector encoding, 2 x 16-bit snorm (Cigolle et al., JCGT 2014).
+__device__ __forceinline__ uint32_t oct_encode(float3 v) {
+    const float l1 = fabsf(v.x) + fabsf(v.y) + fabsf(v.z);
+    float px = v.x / l1, py = v.y / l1;
+    if (v.z < 0.0f) {
+        const float ox = (1.0f - fabsf(py)) * copysignf(1.0f, px);
+        const float oy = (1.0f - fabsf(px)) * copysignf(1.0f, py);
+        px = ox;
+        py = oy;
+    }
+    const int32_t qx = __float2int_rn(fminf(fmaxf(px, -1.0f), 1.0f) * 32767.0f);
+    const int32_t qy = __float2int_rn(fminf(fmaxf(py, -1.0f), 1.0f) * 32767.0f);
+    return ((uint32_t)(qx & 0xffff)) | ((uint32_t)(qy & 0xffff) << 16);
+}
+
+__device__ __forceinline__ float3 oct_decode(uint32_t e) {
+    const float px = (float)(int16_t)(e & 0xffff) * (1.0f / 32767.0f);
+    const float py = (float)(int16_t)(e >> 16) * (1.0f / 32767.0f);
+    float3 v = make_float3(px, py, 1.0f - fabsf(px) - fabsf(py));
+    const float t = fmaxf(-v.z, 0.0f);
+    v.x += v.x >= 0.0f ? -t : t;
+    v.y += v.y >= 0.0f ? -t : t;
+    return normalize3(v);
+}
+
+// Teschner et al. 2003 spatial hash of an integer cell, 32-bit wraparound.
+__device__ __forceinline__ uint32_t cell_hash(int32_t ix, int32_t iy, int32_t iz, uint32_t mask) {
+    return (((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u)) & mask;
+}
+
+__device__ __forceinline__ uint32_t bucket_of(float3 x, float inv_h, uint32_t mask) {
+    return cell_hash((int32_t)floorf(x.x * inv_h), (int32_t)floorf(x.y * inv_h),
+                     (int32_t)floorf(x.z * inv_h), mask);
+}
+
+// ------------------------------------------------------------------------------------------
+// eye pass: jittered pinhole ray, specular chain, first non-specular hit (Sec. 2)
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_eye(DevScene S, CamDev C, PassDev P, float4* __restrict__ hx, float4* __restrict__ hn,
+      float4* __restrict__ hf, float4* __restrict__ st1) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)C.w * C.h) return;
+    const int px = (int)(p % C.w), py = (int)(p / C.w);
+    Rng rng = rng_seed(P.seed, P.scene_id, 0u, P.pass, (uint64_t)p);
+    const float u0 = rng_next(rng), u1 = rng_next(rng);
+    const float sx = (((float)px + u0) / (float)C.w * 2.0f - 1.0f) * C.th * C.aspect;
+    const float sy = (1.0f - ((float)py + u1) / (float)C.h * 2.0f) * C.th;
+    float3 d = normalize3(C.fwd + C.right * sx + C.up * sy);
+    float3 o = C.eye;
+    float3 w = make_float3(1.0f, 1.0f, 1.0f);
+    float3 direct = make_float3(0.0f, 0.0f, 0.0f);
+    float tmin = 0.0f;
+    float4 rx = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), rn = make_float4(0, 0, 0, 0),
+           rf = make_float4(0, 0, 0, 0);
+    for (int depth = 0; depth <= P.max_eye; ++depth) {
+        const Hit h = traverse(S, o, d, tmin, __int_as_float(0x7f800000));
+        if (h.id < 0) break;
+        const float4 sh = __ldg(S.shade + h.id);
+        const float3 n = f3(sh);
+        const int32_t mid = __float_as_int(sh.w);
+        const Material m = load_mat(S, mid);
+        const bool front = dot3(d, n) < 0.0f;
+        if (front && emits(m)) direct = direct + mul3(w, m.emission);
+        if (m.type == GSP_EMITTER) break;
+        const float3 x = o + d * h.t;
+        if (m.type == GSP_DIFFUSE) {
+            const float3 ns = front ? n : n * -1.0f;
+            rx = make_float4(x.x, x.y, x.z, __int_as_float(mid));
+            rn = make_float4(ns.x, ns.y, ns.z, 0.0f);
+            const float3 f = mul3(w, m.albedo) * (1.0f / kPi);
+            rf = make_float4(f.x, f.y, f.z, 0.0f);
+            break;
+        }
+        if (m.type == GSP_MIRROR) {
+            w = mul3(w, m.albedo);
+            d = reflect3(d, n);
+        } else {
+            d = dielectric(d, n, m.ior, rng_next(rng));
+        }
+        o = x;
+        tmin = P.eps;
+    }
+    hx[p] = rx;
+    hn[p] = rn;
+    hf[p] = rf;
+    float4 s1 = st1[p];
+    s1.x += direct.x;
+    s1.y += direct.y;
+    s1.z += direct.z;
+    st1[p] = s1;
+}
+
+// ------------------------------------------------------------------------------------------
+// photon pass (Sec. 2 photon tracing; Sec. 3.3 one bounce per pass with regeneration)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void emit_photon(const EmitDev& E, Rng& rng, float3& o, float3& d, float3& phi) {
+    const float u0 = rng_next(rng);
+    int lo = 0, hi = E.n;  // first j with cdf[j] > u0
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(E.cdf + mid) > u0) hi = mid; else lo = mid + 1;
+    }
+    const int j = min(lo, E.n - 1);
+    const float3 v0 = f3(__ldg(E.geo + 5 * j)), e1 = f3(__ldg(E.geo + 5 * j + 1)),
+                 e2 = f3(__ldg(E.geo + 5 * j + 2)), n = f3(__ldg(E.geo + 5 * j + 3));
+    phi = f3(__ldg(E.geo + 5 * j + 4));
+    const float u1 = rng_next(rng), u2 = rng_next(rng);
+    const float su = sqrtf(u1);
+    o = v0 + e1 * (su * (1.0f - u2)) + e2 * (su * u2);
+    const float u3 = rng_next(rng), u4 = rng_next(rng);
+    d = cosine_dir(n, u3, u4);
+}
+
+struct DepositDev {
+    float4* __restrict__ slots;          // 2 float4 per slot
+    uint32_t* __restrict__ pcount;       // deposits per path / thread
+    unsigned long long* __restrict__ entry;  // stochastic: min key per bucket
+    uint32_t* __restrict__ ecount;       // stochastic: photons per bucket
+    int32_t stochastic;
+};
+
+// One photon interaction at a hit. Returns false when the path ends.
+__device__ __forceinline__ bool photon_bounce(const DevScene& S, const PassDev& P, const DepositDev& D,
+                                              Rng& rng, const Hit& h, float3& o, float3& d, float3& phi,
+                                              uint32_t id, uint32_t slot, uint32_t& ndep) {
+    const float4 sh = __ldg(S.shade + h.id);
+    const float3 n = f3(sh);
+    const Material m = load_mat(S, __float_as_int(sh.w));
+    if (m.type == GSP_EMITTER) return false;
+    const float3 x = o + d * h.t;
+    if (m.type == GSP_DIFFUSE) {
+        float4* rec = D.slots + 2 * (size_t)slot;
+        rec[0] = make_float4(x.x, x.y, x.z, __uint_as_float(id));
+        rec[1] = make_float4(phi.x, phi.y, phi.z, __uint_as_float(oct_encode(d)));
+        ++ndep;
+        if (D.stochastic) {
+            const float z = rng_next(rng);
+            const uint32_t b = bucket_of(x, P.inv_h, P.tmask);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | slot;
+            atomicMin(D.entry + b, key);
+            atomicAdd(D.ecount + b, 1u);
+        }
+        const float urr = rng_next(rng);
+        if (!(urr < P.rr)) return false;
+        phi = mul3(phi, m.albedo) * (1.0f / P.rr);
+        const float3 ns = dot3(d, n) < 0.0f ? n : n * -1.0f;
+        const float ua = rng_next(rng), ub = rng_next(rng);
+        d = cosine_dir(ns, ua, ub);
+    } else if (m.type == GSP_MIRROR) {
+        phi = mul3(phi, m.albedo);
+        d = reflect3(d, n);
+    } else {
+        d = dielectric(d, n, m.ior, rng_next(rng));
+    }
+    o = x;
+    return true;
+}
+
+__global__ void __launch_bounds__(128)
+k_photon_full(DevScene S, EmitDev E, PassDev P, DepositDev D) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.np) return;
+    Rng rng = rng_seed(P.seed, P.scene_id, 1u, P.pass, (uint64_t)k);
+    float3 o, d, phi;
+    emit_photon(E, rng, o, d, phi);
+    uint32_t ndep = 0;
+    for (int depth = 0; depth < P.max_photon; ++depth) {
+        const Hit h = traverse(S, o, d, P.eps, __int_as_float(0x7f800000));
+        if (h.id < 0) break;
+        const uint32_t id = (uint32_t)k * kSlotsPerPath + depth;
+        const uint32_t slot = (uint32_t)k * kSlotsPerPath + ndep;
+        if (!photon_bounce(S, P, D, rng, h, o, d, phi, id, slot, ndep)) break;
+    }
+    D.pcount[k] = ndep;
+}
+
+struct RegenDev {
+    float4* __restrict__ ro;    // {o.xyz, depth bits}
+    float4* __restrict__ rd;    // {d.xyz, alive bits}
+    float4* __restrict__ rphi;  // {flux.rgb, 0}
+    unsigned long long* __restrict__ started;
+};
+
+__global__ void __launch_bounds__(128)
+k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool start = false;
+    if (j < P.np) {
+        Rng rng = rng_seed(P.seed, P.scene_id, 1u, P.pass, (uint64_t)j);
+        float4 a = R.ro[j], b = R.rd[j], c = R.rphi[j];
+        float3 o = f3(a), d = f3(b), phi = f3(c);
+        int32_t depth = __float_as_int(a.w);
+        bool alive = __float_as_int(b.w) != 0;
+        if (!alive) {
+            emit_photon(E, rng, o, d, phi);
+            depth = 0;
+            alive = true;
+            start = true;
+        }
+        uint32_t ndep = 0;
+        const Hit h = traverse(S, o, d, P.eps, __int_as_float(0x7f800000));
+        if (h.id < 0) {
+            alive = false;
+        } else if (!photon_bounce(S, P, D, rng, h, o, d, phi, (uint32_t)j, (uint32_t)j, ndep)) {
+            alive = false;
+        } else if (++depth >= P.max_photon) {
+            alive = false;
+        }
+        D.pcount[j] = ndep;
+        R.ro[j] = make_float4(o.x, o.y, o.z, __int_as_float(depth));
+        R.rd[j] = make_float4(d.x, d.y, d.z, __int_as_float(alive ? 1 : 0));
+        R.rphi[j] = make_float4(phi.x, phi.y, phi.z, 0.0f);
+    }
+    const unsigned int starts = __popc(__ballot_sync(0xffffffffu, start));
+    if ((threadIdx.x & 31) == 0 && starts) atomicAdd(R.started, (unsigned long long)starts);
+}
+
+// ------------------------------------------------------------------------------------------
+// exact hash-grid deposit: compaction in id order, bucket keys, bucket counts
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_compact(const float4* __restrict__ slots, const uint32_t* __restrict__ pcount,
+          const uint32_t* __restrict__ poff, int64_t np, int32_t slots_per_path, float inv_h,
+          uint32_t tmask, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+          uint32_t* __restrict__ bcount) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const uint32_t c = pcount[k], off = poff[k];
+    for (uint32_t i = 0; i < c; ++i) {
+        const uint32_t slot = (uint32_t)k * slots_per_path + i;
+        const float4 a = slots[2 * (size_t)slot];
+        const uint32_t b = bucket_of(f3(a), inv_h, tmask);
+        keys[off + i] = b;
+        vals[off + i] = slot;
+        atomicAdd(bcount + b, 1u);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_permute(const float4* __restrict__ slots, const uint32_t* __restrict__ order,
+          const uint32_t* __restrict__ d_n, float4* __restrict__ spos, float4* __restrict__ spay) {
+    const int64_t n = *d_n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = order[i];
+        spos[i] = slots[2 * (size_t)s];
+        spay[i] = slots[2 * (size_t)s + 1];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// range query + progressive density estimation (fused)
+// ------------------------------------------------------------------------------------------
+struct GatherDev {
+    const float4* __restrict__ hx;
+    const float4* __restrict__ hn;
+    const float4* __restrict__ hf;
+    float4* __restrict__ st0;
+    float4* __restrict__ st1;
+    // exact
+    const float4* __restrict__ spos;
+    const float4* __restrict__ spay;
+    const uint32_t* __restrict__ bstart;
+    // stochastic
+    const float4* __restrict__ slots;
+    const unsigned long long* __restrict__ entry;
+    const uint32_t* __restrict__ ecount;
+    int64_t npix;
+};
+
+// Distinct buckets of the cells that overlap the ball of radius R about x. A photon within R
+// lies in one of these cells, so visiting each distinct bucket once finds every such photon
+// exactly once (photons of colliding cells fail the distance test).
+__device__ __forceinline__ int query_buckets(float3 x, float R, float inv_h, uint32_t mask, uint32_t* out) {
+    const float Rq = R * 1.00001f;
+    int32_t lo[3], hi[3];
+    const float xs[3] = {x.x, x.y, x.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (int32_t)floorf((xs[a] - Rq) * inv_h);
+        hi[a] = (int32_t)floorf((xs[a] + Rq) * inv_h);
+        hi[a] = min(hi[a], lo[a] + 2);
+    }
+    int nb = 0;
+    for (int32_t ix = lo[0]; ix <= hi[0]; ++ix)
+        for (int32_t iy = lo[1]; iy <= hi[1]; ++iy)
+            for (int32_t iz = lo[2]; iz <= hi[2]; ++iz) {
+                const uint32_t b = cell_hash(ix, iy, iz, mask);
+                bool dup = false;
+                for (int q = 0; q < nb; ++q) dup |= out[q] == b;
+                if (!dup) out[nb++] = b;
+            }
+    return nb;
+}
+
+__device__ __forceinline__ void progressive_update(float4& s0, float4& s1, float M, float3 Phi, float alpha) {
+    if (!(M > 0.0f)) return;
+    const float N = s0.w;
+    const float Nn = N + alpha * M;
+    const float ratio = Nn / (N + M);
+    s1.w = s1.w * sqrtf(ratio);
+    s0.x = (s0.x + Phi.x) * ratio;
+    s0.y = (s0.y + Phi.y) * ratio;
+    s0.z = (s0.z + Phi.z) * ratio;
+    s0.w = Nn;
+}
+
+template <bool STOCH>
+__global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= G.npix) return;
+    const float4 hxp = G.hx[p];
+    if (__float_as_int(hxp.w) < 0) return;
+    const float3 x = f3(hxp);
+    const float3 n = f3(G.hn[p]);
+    const float3 f = f3(G.hf[p]);
+    float4 s0 = G.st0[p], s1 = G.st1[p];
+    const float R = s1.w, R2 = R * R;
+    uint32_t buckets[27];
+    const int nb = query_buckets(x, R, P.inv_h, P.tmask, buckets);
+    float M = 0.0f;
+    float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+    for (int q = 0; q < nb; ++q) {
+        const uint32_t b = buckets[q];
+        if (STOCH) {
+            const uint32_t cnt = G.ecount[b];
+            if (cnt == 0) continue;
+            const uint32_t slot = (uint32_t)(G.entry[b] & 0xffffffffull);
+            const float4 a = __ldg(G.slots + 2 * (size_t)slot);
+            const float3 dx = f3(a) - x;
+            if (!(dot3(dx, dx) < R2)) continue;
+            const float4 c = __ldg(G.slots + 2 * (size_t)slot + 1);
+            if (!(dot3(oct_decode(__float_as_uint(c.w)), n) < 0.0f)) continue;
+            const float w = (float)cnt;
+            M += w;
+            acc = acc + f3(c) * w;
+        } else {
+            const uint32_t e = G.bstart[b + 1];
+            for (uint32_t i = G.bstart[b]; i < e; ++i) {
+                const float4 a = __ldg(G.spos + i);
+                const float3 dx = f3(a) - x;
+                if (!(dot3(dx, dx) < R2)) continue;
+                const float4 c = __ldg(G.spay + i);
+                if (!(dot3(oct_decode(__float_as_uint(c.w)), n) < 0.0f)) continue;
+                M += 1.0f;
+                acc = acc + f3(c);
+            }
+        }
+    }
+    progressive_update(s0, s1, M, mul3(f, acc), P.alpha);
+    G.st0[p] = s0;
+    G.st1[p] = s1;
+}
+
+__global__ void k_image(const float4* __restrict__ st0, const float4* __restrict__ st1, int64_t npix,
+                        float inv_passes, double ne_host, const unsigned long long* __restrict__ ne_dev,
+                        float* __restrict__ rgb) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const double ne = ne_dev ? (double)*ne_dev : ne_host;
+    const float4 a = st0[p], b = st1[p];
+    const float k = ne > 0.0 ? (float)(1.0 / ((double)kPi * (double)b.w * (double)b.w * ne)) : 0.0f;
+    rgb[3 * p] = b.x * inv_passes + a.x * k;
+    rgb[3 * p + 1] = b.y * inv_passes + a.y * k;
+    rgb[3 * p + 2] = b.z * inv_passes + a.z * k;
+}
+
+__global__ void k_state(const float4* __restrict__ st0, const float4* __restrict__ st1, int64_t npix,
+                        float* N, float* R, float* tau, float* direct) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const float4 a = st0[p], b = st1[p];
+    if (N) N[p] = a.w;
+    if (R) R[p] = b.w;
+    if (tau) { tau[3 * p] = a.x; tau[3 * p + 1] = a.y; tau[3 * p + 2] = a.z; }
+    if (direct) { direct[3 * p] = b.x; direct[3 * p + 1] = b.y; direct[3 * p + 2] = b.z; }
+}
+
+__global__ void k_init_state(float4* st0, float4* st1, int64_t npix, float r0) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    st0[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    st1[p] = make_float4(0.0f, 0.0f, 0.0f, r0);
+}
+
+__global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+}  // namespace gspd
+
+// ============================================================================================
+// host side
+// ============================================================================================
+using namespace gspd;
+
+struct gsp_sppm {
+    gsp_scene* scene = nullptr;
+    gsp_sppm_params P{};
+    int32_t w = 0, h = 0;
+    int64_t npix = 0, np = 0, T = 0, slot_cap = 0;
+    int32_t tbits = 0, slots_per_path = 0;
+    float inv_h = 0;
+    CamDev cam{};
+    int32_t nemit = 0;
+    float4* d_emit = nullptr;
+    float* d_cdf = nullptr;
+    float4 *st0 = nullptr, *st1 = nullptr, *hx = nullptr, *hn = nullptr, *hf = nullptr;
+    float4* slots = nullptr;
+    uint32_t *pcount = nullptr, *poff = nullptr, *counters = nullptr;
+    uint32_t *keys[2] = {nullptr, nullptr}, *vals[2] = {nullptr, nullptr};
+    uint32_t *hist = nullptr, *scan_tmp = nullptr, *bcount = nullptr, *bstart = nullptr;
+    float4 *spos = nullptr, *spay = nullptr;
+    unsigned long long* entry = nullptr;
+    uint32_t* ecount = nullptr;
+    float4 *ro = nullptr, *rd = nullptr, *rphi = nullptr;
+    unsigned long long* started = nullptr;
+    uint32_t* last_order = nullptr;  // sorted slot order of the last exact pass
+    int64_t passes = 0;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+template <class T>
+cudaError_t alloc(gsp_sppm* r, T** p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)p, (size_t)count * sizeof(T));
+    if (e == cudaSuccess) r->allocs.push_back((void*)*p);
+    return e;
+}
+
+void free_all(gsp_sppm* r) {
+    for (void* p : r->allocs) cudaFree(p);
+    r->allocs.clear();
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+extern "C" {
+
+gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm** out) {
+    if (!s || !params || !out) return GSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!s->ctx || !s->has_cam) return GSP_ERR_INVALID_ARG;
+    if (!s->built) return GSP_ERR_NOT_BUILT;
+    gsp_sppm_params P = *params;
+    if (P.photons_per_pass <= 0 || P.photons_per_pass > (int64_t(1) << 27)) return GSP_ERR_INVALID_ARG;
+    if (!(P.alpha > 0.0f && P.alpha <= 1.0f) || !(P.r0 > 0.0f) || !(P.rr_continue > 0.0f && P.rr_continue <= 1.0f) ||
+        !(P.eps >= 0.0f) || P.max_eye_depth < 0 || P.max_eye_depth > 64 || P.max_photon_depth < 1 ||
+        P.max_photon_depth > kSlotsPerPath || (P.photon_mode != GSP_FULL_PATH && P.photon_mode != GSP_REGEN) ||
+        (P.hash_mode != GSP_EXACT && P.hash_mode != GSP_STOCHASTIC))
+        return GSP_ERR_INVALID_ARG;
+    if (P.cell_h == 0.0f) P.cell_h = 2.0f * P.r0;
+    if (!(P.cell_h > 0.0f) || (P.hash_mode == GSP_STOCHASTIC && P.cell_h < 2.0f * P.r0)) return GSP_ERR_INVALID_ARG;
+    if (P.table_size == 0) {
+        P.table_size = 1;
+        while (P.table_size < 2 * P.photons_per_pass) P.table_size *= 2;
+    }
+    if (P.table_size < 1 || P.table_size > (int64_t(1) << 30) || (P.table_size & (P.table_size - 1)))
+        return GSP_ERR_INVALID_ARG;
+    // emitting triangles: probability proportional to area * mean emission
+    std::vector<int64_t> etri;
+    std::vector<double> cdf;
+    double acc = 0.0;
+    for (int64_t i = 0; i < s->nt; ++i) {
+        const gsp_material& m = s->mats[s->tri_mat[i]];
+        if (!(m.type == GSP_DIFFUSE || m.type == GSP_EMITTER)) continue;
+        if (!(std::max({m.emission[0], m.emission[1], m.emission[2]}) > 0.0f)) continue;
+        const float* a = &s->verts[3 * (int64_t)s->tris[3 * i]];
+        const float* b = &s->verts[3 * (int64_t)s->tris[3 * i + 1]];
+        const float* c = &s->verts[3 * (int64_t)s->tris[3 * i + 2]];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) { e1[k] = (double)b[k] - a[k]; e2[k] = (double)c[k] - a[k]; }
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double area = 0.5 * std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(area > 0.0)) continue;
+        acc += area * ((double)m.emission[0] + m.emission[1] + m.emission[2]) / 3.0;
+        cdf.push_back(acc);
+        etri.push_back(i);
+    }
+    if (etri.empty()) return GSP_ERR_INVALID_ARG;
+    const int32_t ne = (int32_t)etri.size();
+    std::vector<float4> emit(5 * (size_t)ne);
+    std::vector<float> cdff(ne);
+    for (int32_t j = 0; j < ne; ++j) {
+        const int64_t i = etri[j];
+        const gsp_material& m = s->mats[s->tri_mat[i]];
+        const float* a = &s->verts[3 * (int64_t)s->tris[3 * i]];
+        const float* b = &s->verts[3 * (int64_t)s->tris[3 * i + 1]];
+        const float* c = &s->verts[3 * (int64_t)s->tris[3 * i + 2]];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) { e1[k] = (double)b[k] - a[k]; e2[k] = (double)c[k] - a[k]; }
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        // flux of a path started here: Le * pi * sum(area * mean Le) / mean Le (the probability
+        // of picking the triangle times the density of its point cancels its own area)
+        double mean = ((double)m.emission[0] + m.emission[1] + m.emission[2]) / 3.0;
+        double scale = M_PI * acc / mean;
+        emit[5 * j] = float4{a[0], a[1], a[2], 0.0f};
+        emit[5 * j + 1] = float4{(float)e1[0], (float)e1[1], (float)e1[2], 0.0f};
+        emit[5 * j + 2] = float4{(float)e2[0], (float)e2[1], (float)e2[2], 0.0f};
+        emit[5 * j + 3] = float4{(float)(n[0] / len), (float)(n[1] / len), (float)(n[2] / len), 0.0f};
+        emit[5 * j + 4] = float4{(float)(m.emission[0] * scale), (float)(m.emission[1] * scale),
+                                 (float)(m.emission[2] * scale), 0.0f};
+        cdff[j] = (float)(cdf[j] / acc);
+    }
+    GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    gsp_sppm* r = new (std::nothrow) gsp_sppm;
+    if (!r) return GSP_ERR_OOM;
+    r->scene = s;
+    r->P = P;
+    r->w = s->cam.width;
+    r->h = s->cam.height;
+    r->npix = (int64_t)r->w * r->h;
+    r->np = P.photons_per_pass;
+    r->T = P.table_size;
+    while ((int64_t(1) << r->tbits) < r->T) ++r->tbits;
+    r->inv_h = 1.0f / P.cell_h;
+    r->slots_per_path = P.photon_mode == GSP_FULL_PATH ? kSlotsPerPath : 1;
+    r->slot_cap = r->np * r->slots_per_path;
+    r->nemit = ne;
+    {  // camera basis in FP64, rounded once
+        const gsp_camera& c = s->cam;
+        double eye[3] = {c.eye[0], c.eye[1], c.eye[2]}, f[3], rt[3], up[3];
+        for (int k = 0; k < 3; ++k) f[k] = (double)c.look[k] - eye[k];
+        double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+        for (int k = 0; k < 3; ++k) f[k] /= fl;
+        double u0[3] = {c.up[0], c.up[1], c.up[2]};
+        rt[0] = f[1] * u0[2] - f[2] * u0[1];
+        rt[1] = f[2] * u0[0] - f[0] * u0[2];
+        rt[2] = f[0] * u0[1] - f[1] * u0[0];
+        double rl = std::sqrt(rt[0] * rt[0] + rt[1] * rt[1] + rt[2] * rt[2]);
+        for (int k = 0; k < 3; ++k) rt[k] /= rl;
+        up[0] = rt[1] * f[2] - rt[2] * f[1];
+        up[1] = rt[2] * f[0] - rt[0] * f[2];
+        up[2] = rt[0] * f[1] - rt[1] * f[0];
+        r->cam.eye = make_float3((float)eye[0], (float)eye[1], (float)eye[2]);
+        r->cam.fwd = make_float3((float)f[0], (float)f[1], (float)f[2]);
+        r->cam.right = make_float3((float)rt[0], (float)rt[1], (float)rt[2]);
+        r->cam.up = make_float3((float)up[0], (float)up[1], (float)up[2]);
+        r->cam.th = (float)std::tan((double)c.vfov_deg * M_PI / 180.0 / 2.0);
+        r->cam.aspect = (float)((double)c.width / (double)c.height);
+        r->cam.w = c.width;
+        r->cam.h = c.height;
+    }
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, int64_t n) { if (e == cudaSuccess) e = alloc(r, p, n); };
+    A(&r->d_emit, 5 * (int64_t)ne);
+    A(&r->d_cdf, ne);
+    A(&r->st0, r->npix);
+    A(&r->st1, r->npix);
+    A(&r->hx, r->npix);
+    A(&r->hn, r->npix);
+    A(&r->hf, r->npix);
+    A(&r->slots, 2 * r->slot_cap);
+    A(&r->pcount, r->np);
+    A(&r->poff, r->np);
+    A(&r->counters, 8);
+    A(&r->started, 1);
+    const int64_t scan_tmp = std::max({gsp_scan_temp_elems(r->np), gsp_scan_temp_elems(r->T),
+                                       gsp_scan_temp_elems(gsp_sort_hist_elems())});
+    A(&r->scan_tmp, scan_tmp);
+    if (P.hash_mode == GSP_EXACT) {
+        for (int b = 0; b < 2; ++b) {
+            A(&r->keys[b], r->slot_cap);
+            A(&r->vals[b], r->slot_cap);
+        }
+        A(&r->hist, gsp_sort_hist_elems());
+        A(&r->bcount, r->T);
+        A(&r->bstart, r->T + 1);
+        A(&r->spos, r->slot_cap);
+        A(&r->spay, r->slot_cap);
+    } else {
+        A(&r->entry, r->T);
+        A(&r->ecount, r->T);
+    }
+    if (P.photon_mode == GSP_REGEN) {
+        A(&r->ro, r->np);
+        A(&r->rd, r->np);
+        A(&r->rphi, r->np);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_emit, emit.data(), emit.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_cdf, cdff.data(), cdff.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_init_state<<<blocks(r->npix, 256), 256>>>(r->st0, r->st1, r->npix, P.r0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemset(r->started, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(r->counters, 0, 8 * sizeof(uint32_t));
+    if (e == cudaSuccess && r->ro) {
+        e = cudaMemset(r->ro, 0, r->np * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMemset(r->rd, 0, r->np * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMemset(r->rphi, 0, r->np * sizeof(float4));
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(e));
+        free_all(r);
+        delete r;
+        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+    }
+    *out = r;
+    return GSP_OK;
+}
+
+void gsp_sppm_destroy(gsp_sppm* r) {
+    if (!r) return;
+    cudaSetDevice(r->scene->ctx->device);
+    free_all(r);
+    delete r;
+}
+
+static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
+    gsp_scene* s = r->scene;
+    const DevScene S = gsp_dev_scene(s);
+    PassDev P;
+    P.seed = r->P.seed;
+    P.scene_id = r->P.scene_id;
+    P.pass = (uint32_t)r->passes;
+    P.alpha = r->P.alpha;
+    P.rr = r->P.rr_continue;
+    P.eps = r->P.eps;
+    P.inv_h = r->inv_h;
+    P.max_eye = r->P.max_eye_depth;
+    P.max_photon = r->P.max_photon_depth;
+    P.tmask = (uint32_t)(r->T - 1);
+    P.np = r->np;
+    EmitDev E{r->d_emit, r->d_cdf, r->nemit};
+    const bool stoch = r->P.hash_mode == GSP_STOCHASTIC;
+    DepositDev D{r->slots, r->pcount, r->entry, r->ecount, stoch ? 1 : 0};
+
+    k_eye<<<blocks(r->npix, 128), 128, 0, st>>>(S, r->cam, P, r->hx, r->hn, r->hf, r->st1);
+    if (stoch) {
+        k_fill_u64<<<1024, 256, 0, st>>>(r->entry, r->T, ~0ull);
+        GSP_CUDA_TRY(cudaMemsetAsync(r->ecount, 0, r->T * sizeof(uint32_t), st));
+    }
+    if (r->P.photon_mode == GSP_FULL_PATH) {
+        k_photon_full<<<blocks(r->np, 128), 128, 0, st>>>(S, E, P, D);
+    } else {
+        RegenDev R{r->ro, r->rd, r->rphi, r->started};
+        k_photon_regen<<<blocks(r->np, 128), 128, 0, st>>>(S, E, P, D, R);
+    }
+    GatherDev G{};
+    G.hx = r->hx;
+    G.hn = r->hn;
+    G.hf = r->hf;
+    G.st0 = r->st0;
+    G.st1 = r->st1;
+    G.npix = r->npix;
+    if (stoch) {
+        G.slots = r->slots;
+        G.entry = r->entry;
+        G.ecount = r->ecount;
+        // deposit count for diagnostics
+        GSP_CUDA_TRY(gsp_scan_u32(r->pcount, r->poff, r->np, r->counters, r->scan_tmp, st));
+        k_gather<true><<<blocks(r->npix, 128), 128, 0, st>>>(G, P);
+    } else {
+        uint32_t* d_total = r->counters;  // deposits this pass
+        GSP_CUDA_TRY(gsp_scan_u32(r->pcount, r->poff, r->np, d_total, r->scan_tmp, st));
+        GSP_CUDA_TRY(cudaMemsetAsync(r->bcount, 0, r->T * sizeof(uint32_t), st));
+        k_compact<<<blocks(r->np, 256), 256, 0, st>>>(r->slots, r->pcount, r->poff, r->np, r->slots_per_path,
+                                                      r->inv_h, P.tmask, r->keys[0], r->vals[0], r->bcount);
+        GSP_CUDA_TRY(gsp_scan_u32(r->bcount, r->bstart, r->T, r->bstart + r->T, r->scan_tmp, st));
+        uint32_t *ko = nullptr, *vo = nullptr;
+        GSP_CUDA_TRY(gsp_radix_sort_u32(r->keys[0], r->vals[0], r->keys[1], r->vals[1], d_total, r->tbits,
+                                        r->hist, r->scan_tmp, st, &ko, &vo));
+        r->last_order = vo;
+        k_permute<<<1024, 256, 0, st>>>(r->slots, vo, d_total, r->spos, r->spay);
+        G.spos = r->spos;
+        G.spay = r->spay;
+        G.bstart = r->bstart;
+        k_gather<false><<<blocks(r->npix, 128), 128, 0, st>>>(G, P);
+    }
+    GSP_CUDA_TRY(cudaGetLastError());
+    r->passes += 1;
+    return GSP_OK;
+}
+
+gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream) {
+    if (!r || npasses < 0) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    for (int32_t i = 0; i < npasses; ++i) {
+        gsp_status s = sppm_one_pass(r, (cudaStream_t)stream);
+        if (s != GSP_OK) return s;
+    }
+    return GSP_OK;
+}
+
+gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream) {
+    if (!r || !d_rgb) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    const float inv_p = r->passes > 0 ? 1.0f / (float)r->passes : 0.0f;
+    const double ne_host = (double)r->passes * (double)r->np;
+    k_image<<<blocks(r->npix, 256), 256, 0, (cudaStream_t)stream>>>(
+        r->st0, r->st1, r->npix, inv_p, ne_host, r->P.photon_mode == GSP_REGEN ? r->started : nullptr, d_rgb);
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+gsp_status gsp_sppm_state(gsp_sppm* r, float* d_N, float* d_R, float* d_tau, float* d_direct,
+                          double* h_counts, void* stream) {
+    if (!r) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_N || d_R || d_tau || d_direct) {
+        k_state<<<blocks(r->npix, 256), 256, 0, st>>>(r->st0, r->st1, r->npix, d_N, d_R, d_tau, d_direct);
+        GSP_CUDA_TRY(cudaGetLastError());
+    }
+    if (h_counts) {
+        double ne = (double)r->passes * (double)r->np;
+        if (r->P.photon_mode == GSP_REGEN) {
+            unsigned long long v = 0;
+            GSP_CUDA_TRY(cudaMemcpyAsync(&v, r->started, sizeof v, cudaMemcpyDeviceToHost, st));
+            GSP_CUDA_TRY(cudaStreamSynchronize(st));
+            ne = (double)v;
+        }
+        h_counts[0] = (double)r->passes;
+        h_counts[1] = ne;
+    }
+    return GSP_OK;
+}
+
+int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity) {
+    if (!r) return GSP_ERR_INVALID_ARG;
+    if (cudaSetDevice(r->scene->ctx->device) != cudaSuccess) return GSP_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GSP_ERR_CUDA;
+    uint32_t total = 0;
+    if (cudaMemcpy(&total, r->counters, sizeof total, cudaMemcpyDeviceToHost) != cudaSuccess) return GSP_ERR_CUDA;
+    if (!h_ids) return (int64_t)total;
+    if (capacity < (int64_t)total) return GSP_ERR_INVALID_ARG;
+    // ids of every deposit: walk the per-path counts on the host
+    std::vector<uint32_t> cnt(r->np);
+    std::vector<float4> rec(2 * (size_t)r->slot_cap);
+    if (cudaMemcpy(cnt.data(), r->pcount, r->np * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(rec.data(), r->slots, rec.size() * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GSP_ERR_CUDA;
+    int64_t k = 0;
+    for (int64_t pth = 0; pth < r->np; ++pth)
+        for (uint32_t i = 0; i < cnt[pth]; ++i) {
+            const int64_t slot = pth * r->slots_per_path + i;
+            uint32_t id;
+            std::memcpy(&id, &rec[2 * slot].w, 4);
+            if (k < capacity) h_ids[k] = id;
+            ++k;
+        }
+    std::sort(h_ids, h_ids + k);
+    return k;
+}
+
+gsp_status gsp_sppm_sync(gsp_sppm* r) {
+    if (!r) return GSP_ERR_INVALID_ARG;
+    return gsp_context_sync(r->scene->ctx);
+}
+
+}  // extern "C"

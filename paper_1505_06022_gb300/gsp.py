@@ -1,0 +1,388 @@
+"""Python binding of the C ABI in include/gsp.h (ctypes; argument marshalling only).
+
+Every function named ``gsp_*`` here calls the C entry point of the same name in libgsp.so.
+Device arrays are torch CUDA tensors (contiguous, 16-byte aligned); host arrays are numpy.
+There is no fallback: if the CUDA library is missing or fails to load, calls raise.
+
+``Scene`` and ``Renderer`` are thin owners of the opaque handles for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgsp.so")
+_lock = threading.Lock()
+_lib = None
+
+GSP_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtime error",
+          -4: "traversal exceeded its step limit", -5: "bounded device wait timed out",
+          -6: "scene has no BVH", -7: "call order violated", -8: "checkpoint I/O failed",
+          -9: "device buffer overflow"}
+FULL_PATH, REGEN = 0, 1
+EXACT, STOCHASTIC = 0, 1
+
+# exported symbols of include/gsp.h
+ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp_context_destroy",
+       "gsp_context_sync", "gsp_scene_upload", "gsp_scene_destroy", "gsp_build_bvh",
+       "gsp_trace_closest_hit", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
+       "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
+       "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill"]
+
+
+class GspError(RuntimeError):
+    def __init__(self, fn, code):
+        msg = STATUS.get(code, f"status {code}")
+        detail = ""
+        if _lib is not None:
+            detail = _lib.gsp_last_error_message().decode(errors="replace")
+        super().__init__(f"{fn}: {msg}" + (f" ({detail})" if detail else ""))
+        self.code = code
+
+
+class BvhParams(C.Structure):
+    _fields_ = [("bins", C.c_int32), ("leaf_threshold", C.c_int32), ("max_leaf", C.c_int32),
+                ("link_sets", C.c_int32)]
+
+
+class BvhStats(C.Structure):
+    _fields_ = [("nodes", C.c_int64), ("leaves", C.c_int64), ("depth", C.c_int32),
+                ("link_sets", C.c_int32), ("build_ms", C.c_double), ("thread_ms", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class SppmParams(C.Structure):
+    _fields_ = [("photons_per_pass", C.c_int64), ("table_size", C.c_int64), ("seed", C.c_uint64),
+                ("alpha", C.c_float), ("r0", C.c_float), ("rr_continue", C.c_float),
+                ("cell_h", C.c_float), ("eps", C.c_float), ("photon_mode", C.c_int32),
+                ("hash_mode", C.c_int32), ("max_eye_depth", C.c_int32),
+                ("max_photon_depth", C.c_int32), ("scene_id", C.c_uint32)]
+
+
+def lib():
+    """Loads libgsp.so (building it first if the sources are newer). Raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            path = _build.build()
+            L = C.CDLL(path)
+            P, I64, I32 = C.c_void_p, C.c_int64, C.c_int32
+            for name in ABI:
+                getattr(L, name)  # every declared symbol must be exported
+            L.gsp_status_string.restype = C.c_char_p
+            L.gsp_status_string.argtypes = [I32]
+            L.gsp_last_error_message.restype = C.c_char_p
+            L.gsp_last_error_message.argtypes = []
+            L.gsp_context_create.argtypes = [I32, C.POINTER(P)]
+            L.gsp_context_destroy.argtypes = [P]
+            L.gsp_context_destroy.restype = None
+            L.gsp_context_sync.argtypes = [P]
+            L.gsp_scene_upload.argtypes = [P, P, I64, P, I64, P, P, I32, P, C.POINTER(P)]
+            L.gsp_scene_destroy.argtypes = [P]
+            L.gsp_scene_destroy.restype = None
+            L.gsp_build_bvh.argtypes = [P, P, P]
+            L.gsp_trace_closest_hit.argtypes = [P, P, I64, P, P, P, P]
+            L.gsp_bvh_host_walk.argtypes = [P, P, I64, P, P, P, P]
+            L.gsp_bvh_export.argtypes = [P, I32, P, P, C.POINTER(I64)]
+            L.gsp_sppm_create.argtypes = [P, P, C.POINTER(P)]
+            L.gsp_sppm_destroy.argtypes = [P]
+            L.gsp_sppm_destroy.restype = None
+            L.gsp_sppm_pass.argtypes = [P, I32, P]
+            L.gsp_sppm_image.argtypes = [P, P, P]
+            L.gsp_sppm_state.argtypes = [P, P, P, P, P, P, P]
+            L.gsp_sppm_last_deposits.restype = I64
+            L.gsp_sppm_last_deposits.argtypes = [P, P, I64]
+            L.gsp_sppm_sync.argtypes = [P]
+            L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
+            _lib = L
+    return _lib
+
+
+def _check(fn, code):
+    if code != GSP_OK:
+        raise GspError(fn, code)
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _dev(t):
+    """Device pointer of a torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(getattr(stream, "cuda_stream", stream) or 0)
+
+
+# ------------------------------------------------------------------------- C ABI mirrors
+def gsp_context_create(device: int = 0):
+    h = C.c_void_p()
+    _check("gsp_context_create", lib().gsp_context_create(device, C.byref(h)))
+    return h
+
+
+def gsp_context_destroy(ctx):
+    lib().gsp_context_destroy(ctx)
+
+
+def gsp_context_sync(ctx):
+    _check("gsp_context_sync", lib().gsp_context_sync(ctx))
+
+
+def gsp_rng_fill(ctx, seed, scene, domain, pass_, ids, ndraw, out=None, stream=None):
+    """ids: CUDA int64/uint64 tensor [n]; returns CUDA float32 [n, ndraw]."""
+    import torch
+    if out is None:
+        out = torch.empty((ids.shape[0], ndraw), dtype=torch.float32, device=ids.device)
+    rc = lib().gsp_rng_fill(ctx, seed, scene, domain, pass_, _dev(ids), ids.shape[0], ndraw, _dev(out),
+                            _stream(stream))
+    _check("gsp_rng_fill", rc)
+    return out
+
+
+def gsp_scene_upload(ctx, verts, tris, tri_mat=None, mats=None, camera=None):
+    """ctx None = host-only scene (BVH build, export, host walk; no GPU)."""
+    v, vp = _host(verts, np.float32)
+    t, tp = _host(tris, np.int32)
+    if tri_mat is None:
+        tm, tmp_ = None, None
+    else:
+        tm, tmp_ = _host(tri_mat, np.int32)
+    if mats is None:
+        mats = _inputs.material(_inputs.DIFFUSE, (0.5, 0.5, 0.5))
+    m = np.ascontiguousarray(mats, dtype=_inputs.MATERIAL_DTYPE)
+    cam = None if camera is None else np.ascontiguousarray(camera, dtype=_inputs.CAMERA_DTYPE)
+    h = C.c_void_p()
+    rc = lib().gsp_scene_upload(ctx, vp, len(v), tp, len(t), tmp_, m.ctypes.data_as(C.c_void_p), len(m),
+                                None if cam is None else cam.ctypes.data_as(C.c_void_p), C.byref(h))
+    _check("gsp_scene_upload", rc)
+    return h
+
+
+def gsp_scene_destroy(scene):
+    lib().gsp_scene_destroy(scene)
+
+
+def gsp_build_bvh(scene, bins=16, leaf_threshold=4, max_leaf=7, link_sets=6) -> dict:
+    p = BvhParams(bins, leaf_threshold, max_leaf, link_sets)
+    st = BvhStats()
+    _check("gsp_build_bvh", lib().gsp_build_bvh(scene, C.byref(p), C.byref(st)))
+    return st.as_dict()
+
+
+def gsp_trace_closest_hit(scene, rays, tri, t, uv=None, stream=None):
+    """rays: CUDA float32 [n, 8]; tri: CUDA int32 [n]; t: CUDA float32 [n]; uv: [n, 2] or None."""
+    n = rays.shape[0]
+    rc = lib().gsp_trace_closest_hit(scene, _dev(rays), n, _dev(tri), _dev(t), _dev(uv), _stream(stream))
+    _check("gsp_trace_closest_hit", rc)
+
+
+def gsp_bvh_host_walk(scene, rays):
+    r, rp = _host(rays, np.float32)
+    n = len(r)
+    tri, t = np.zeros(n, np.int32), np.zeros(n, np.float32)
+    vis, tests = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check("gsp_bvh_host_walk", lib().gsp_bvh_host_walk(scene, rp, n, p(tri), p(t), p(vis), p(tests)))
+    return tri, t, vis, tests
+
+
+def gsp_bvh_export(scene, link_set=0):
+    nn = C.c_int64()
+    _check("gsp_bvh_export", lib().gsp_bvh_export(scene, link_set, None, None, C.byref(nn)))
+    nodes = np.zeros((nn.value, 8), np.float32)
+    return nodes, nn.value
+
+
+def bvh_export_full(scene, ntris, link_set=0):
+    nodes, nn = gsp_bvh_export(scene, link_set)
+    tris = np.zeros((ntris, 12), np.float32)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    _check("gsp_bvh_export", lib().gsp_bvh_export(scene, link_set, p(nodes), p(tris), C.byref(C.c_int64())))
+    return nodes, tris
+
+
+def gsp_sppm_create(scene, params: dict):
+    p = SppmParams(**params)
+    h = C.c_void_p()
+    _check("gsp_sppm_create", lib().gsp_sppm_create(scene, C.byref(p), C.byref(h)))
+    return h
+
+
+def gsp_sppm_destroy(r):
+    lib().gsp_sppm_destroy(r)
+
+
+def gsp_sppm_pass(r, npasses=1, stream=None):
+    _check("gsp_sppm_pass", lib().gsp_sppm_pass(r, npasses, _stream(stream)))
+
+
+def gsp_sppm_image(r, rgb, stream=None):
+    _check("gsp_sppm_image", lib().gsp_sppm_image(r, _dev(rgb), _stream(stream)))
+
+
+def gsp_sppm_state(r, N=None, R=None, tau=None, direct=None, stream=None):
+    counts = np.zeros(2, np.float64)
+    rc = lib().gsp_sppm_state(r, _dev(N), _dev(R), _dev(tau), _dev(direct),
+                              counts.ctypes.data_as(C.c_void_p), _stream(stream))
+    _check("gsp_sppm_state", rc)
+    return int(counts[0]), float(counts[1])
+
+
+def gsp_sppm_last_deposits(r):
+    n = lib().gsp_sppm_last_deposits(r, None, 0)
+    if n < 0:
+        raise GspError("gsp_sppm_last_deposits", n)
+    ids = np.zeros(max(n, 1), np.uint32)
+    n2 = lib().gsp_sppm_last_deposits(r, ids.ctypes.data_as(C.c_void_p), len(ids))
+    if n2 < 0:
+        raise GspError("gsp_sppm_last_deposits", n2)
+    return ids[:n2]
+
+
+def gsp_sppm_sync(r):
+    _check("gsp_sppm_sync", lib().gsp_sppm_sync(r))
+
+
+# ------------------------------------------------------------------------- convenience owners
+class Context:
+    def __init__(self, device: int = 0):
+        self.h = gsp_context_create(device)
+        self.device = device
+
+    def sync(self):
+        gsp_context_sync(self.h)
+
+    def close(self):
+        if self.h:
+            gsp_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """Uploaded scene + BVH. `ctx` None makes a host-only scene."""
+
+    def __init__(self, ctx, scene: "_inputs.Scene", **bvh):
+        self.ctx = ctx
+        self.src = scene
+        self.h = gsp_scene_upload(None if ctx is None else ctx.h, scene.verts, scene.tris, scene.tri_mat,
+                                  scene.mats, scene.camera)
+        self.stats = gsp_build_bvh(self.h, **bvh) if bvh is not None else None
+
+    def trace(self, rays, stream=None, with_uv=False):
+        import torch
+        n = rays.shape[0]
+        tri = torch.empty(n, dtype=torch.int32, device=rays.device)
+        t = torch.empty(n, dtype=torch.float32, device=rays.device)
+        uv = torch.empty((n, 2), dtype=torch.float32, device=rays.device) if with_uv else None
+        gsp_trace_closest_hit(self.h, rays, tri, t, uv, stream)
+        return (tri, t, uv) if with_uv else (tri, t)
+
+    def host_walk(self, rays):
+        return gsp_bvh_host_walk(self.h, rays)
+
+    def close(self):
+        if self.h:
+            gsp_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Renderer:
+    """SPPM renderer over an uploaded scene."""
+
+    def __init__(self, scene: Scene, params: dict):
+        self.scene = scene
+        self.params = dict(params)
+        self.h = gsp_sppm_create(scene.h, self.params)
+        cam = scene.src.camera[0]
+        self.w, self.h_px = int(cam["width"]), int(cam["height"])
+
+    def run(self, npasses=1, stream=None):
+        gsp_sppm_pass(self.h, npasses, stream)
+
+    def image(self, stream=None):
+        import torch
+        img = torch.empty((self.h_px, self.w, 3), dtype=torch.float32, device=f"cuda:{self.scene.ctx.device}")
+        gsp_sppm_image(self.h, img, stream)
+        return img
+
+    def state(self, stream=None):
+        import torch
+        dev = f"cuda:{self.scene.ctx.device}"
+        n = self.w * self.h_px
+        N = torch.empty(n, device=dev)
+        R = torch.empty(n, device=dev)
+        tau = torch.empty((n, 3), device=dev)
+        direct = torch.empty((n, 3), device=dev)
+        passes, ne = gsp_sppm_state(self.h, N, R, tau, direct, stream)
+        hw = (self.h_px, self.w)
+        return dict(N=N.view(hw), R=R.view(hw), tau=tau.view(hw + (3,)), direct=direct.view(hw + (3,)),
+                    passes=passes, Ne=ne)
+
+    def last_deposits(self):
+        return gsp_sppm_last_deposits(self.h)
+
+    def sync(self):
+        gsp_sppm_sync(self.h)
+
+    def close(self):
+        if self.h:
+            gsp_sppm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sppm_params(scene, photons_per_pass, seed=1, alpha=0.7, r0=None, r0_frac=0.05, photon_mode=FULL_PATH,
+                hash_mode=EXACT, cell_h=None, table_size=None, rr_continue=0.8, eps_frac=1e-4,
+                max_eye_depth=16, max_photon_depth=32, scene_id=0) -> dict:
+    """SPPM parameters for a scene; radius and ray offset scale with the scene's diagonal."""
+    ext = scene.extent()
+    r0 = float(np.float32(r0 if r0 is not None else r0_frac * ext))
+    cell_h = float(np.float32(cell_h if cell_h is not None else 2.0 * r0))
+    if table_size is None:
+        table_size = 1
+        while table_size < 2 * photons_per_pass:
+            table_size *= 2
+    return dict(photons_per_pass=int(photons_per_pass), table_size=int(table_size), seed=int(seed),
+                alpha=float(np.float32(alpha)), r0=r0, rr_continue=float(np.float32(rr_continue)),
+                cell_h=cell_h, eps=float(np.float32(eps_frac * ext)), photon_mode=int(photon_mode),
+                hash_mode=int(hash_mode), max_eye_depth=int(max_eye_depth),
+                max_photon_depth=int(max_photon_depth), scene_id=int(scene_id))

@@ -1,0 +1,91 @@
+"""GPU SPPM pass (Sec. 2, 3.3, 3.4) against the FP64 oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1505_06022_gb300 import gsp, inputs as I
+from gpu_util import image_parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gsp.Context(0)
+    yield c
+    c.close()
+
+
+def render_both(ctx, sc, passes, **kw):
+    params = gsp.sppm_params(sc, **kw)
+    s = gsp.Scene(ctx, sc)
+    r = gsp.Renderer(s, params)
+    r.run(passes)
+    img = r.image().cpu().numpy()
+    r.sync()
+    st = r.state()
+    orc = O.Sppm(sc, O.default_params(sc, **kw))
+    orc.run(passes)
+    return img, orc, r, st
+
+
+def test_cornell_parity_exact_full_path(ctx):
+    """64x64, 16,384 photons/pass, 4 passes, alpha 0.7, r0 = 0.05 * diagonal, seed 1."""
+    sc = I.cornell_box(seed=1)
+    img, orc, r, st = render_both(ctx, sc, 4, photons_per_pass=16384, seed=1)
+    ref = orc.state()
+    assert st["passes"] == 4 and st["Ne"] == ref["Ne"]
+    image_parity(img, ref["image"])
+    image_parity(st["N"].cpu().numpy()[..., None], ref["N"][..., None])
+
+
+def test_cornell_deposit_ids_match(ctx):
+    sc = I.cornell_box(seed=1)
+    _, orc, r, _ = render_both(ctx, sc, 1, photons_per_pass=16384, seed=3)
+    gid = r.last_deposits()
+    oid = np.sort(orc.last_photons()["ids"])
+    diff = np.setxor1d(gid, oid)
+    assert len(diff) <= 2e-4 * len(oid), f"{len(diff)} of {len(oid)} deposit ids differ"
+
+
+@pytest.mark.parametrize("photon_mode,hash_mode", [(1, 0), (0, 1), (1, 1)])
+def test_cornell_parity_paper_modes(ctx, photon_mode, hash_mode):
+    sc = I.cornell_box(seed=1)
+    img, orc, r, st = render_both(ctx, sc, 4, photons_per_pass=16384, seed=1, photon_mode=photon_mode,
+                                  hash_mode=hash_mode)
+    ref = orc.state()
+    assert st["Ne"] == ref["Ne"]
+    image_parity(img, ref["image"])
+
+
+@pytest.mark.parametrize("rho", [0.5, 0.8])
+def test_white_furnace(ctx, rho):
+    sc = I.furnace_scene(n=32, albedo=rho, le=1.0, width=16, height=16)
+    params = gsp.sppm_params(sc, 200000, r0=0.15)
+    r = gsp.Renderer(gsp.Scene(ctx, sc), params)
+    r.run(4)
+    img = r.image().cpu().numpy()
+    assert img.mean() == pytest.approx(1.0 / (1.0 - rho), rel=0.01)
+
+
+def test_full_scene_one_pass_parity(ctx):
+    """512x512, 247,234 triangles (glass, mirror, diffuse spheres on a displaced plane),
+    1M photons/pass: one pass (two for the radius update) against the oracle."""
+    sc = I.full_scene()
+    kw = dict(photons_per_pass=1 << 20, seed=3, r0_frac=0.004)
+    img, orc, r, st = render_both(ctx, sc, 2, **kw)
+    image_parity(img, orc.state()["image"])
+
+
+def test_edge_cases(ctx):
+    # a 1x1 image, one photon per pass, alpha = 1 (no radius reduction)
+    sc = I.cornell_box(width=1, height=1)
+    img, orc, _, _ = render_both(ctx, sc, 3, photons_per_pass=1, seed=5, alpha=1.0)
+    np.testing.assert_allclose(img, orc.state()["image"], rtol=1e-4, atol=1e-12)
+    # a camera that sees nothing: the image stays zero
+    sc = I.cornell_box(width=8, height=8)
+    sc.camera["eye"] = (0.5, 0.5, 3.0)
+    sc.camera["look"] = (0.5, 0.5, 6.0)
+    img, orc, _, _ = render_both(ctx, sc, 2, photons_per_pass=64, seed=5)
+    assert np.all(img == 0) and np.all(orc.state()["image"] == 0)

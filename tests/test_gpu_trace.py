@@ -1,0 +1,123 @@
+"""GPU closest-hit traversal (Fig. 3, MTBVH and TBVH) against the oracle, through the C-ABI."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1505_06022_gb300 import gsp, inputs as I
+from gpu_util import parity_hits
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gsp.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_trace(ctx, sc, rays, **bvh):
+    s = gsp.Scene(ctx, sc, **bvh)
+    d = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
+    tri, t, uv = s.trace(d, with_uv=True)
+    torch.cuda.synchronize()
+    ctx.sync()
+    return tri.cpu().numpy(), t.cpu().numpy(), uv.cpu().numpy(), s
+
+
+def test_rng_streams_are_bit_exact():
+    c = gsp.Context(0)
+    ids = np.arange(1 << 22, dtype=np.uint64) * 7919 + 3
+    g = gsp.gsp_rng_fill(c.h, 12345, 2, 1, 9, torch.from_numpy(ids.view(np.int64)).cuda(), 24)
+    torch.cuda.synchronize()
+    got = g.cpu().numpy()
+    want = O.rng_draws(12345, 2, 1, 9, ids, 24)  # ~10^8 draws
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    c.close()
+
+
+def test_soup_against_brute_force(ctx):
+    sc = I.random_soup(300, seed=31, size=0.15)
+    rays = I.random_rays(20011, seed=32)  # ragged count
+    tri, t, uv, _ = gpu_trace(ctx, sc, rays)
+    ids, tt, uu, vv, nd = O.Mesh(sc.verts, sc.tris).closest_hit(rays, brute=True)
+    parity_hits(tri, t, ids, tt, nd)
+    hit = nd.astype(bool) & (ids >= 0)
+    np.testing.assert_allclose(uv[hit, 0], uu[hit], atol=1e-4)
+    np.testing.assert_allclose(uv[hit, 1], vv[hit], atol=1e-4)
+
+
+@pytest.mark.parametrize("link_sets", [1, 6])
+def test_sphere_both_link_sets(ctx, link_sets):
+    sc = I.traversal_sphere(n=40, seed=2)
+    rays = I.traversal_rays(128, 64, n_random=8192, seed=33)
+    tri, t, _, _ = gpu_trace(ctx, sc, rays, link_sets=link_sets)
+    ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(rays)
+    parity_hits(tri, t, ids, tt, nd)
+
+
+def test_link_sets_agree_bitwise(ctx):
+    sc = I.traversal_sphere(n=32, seed=5)
+    rays = I.traversal_rays(96, 48, n_random=6000, seed=34)
+    a = gpu_trace(ctx, sc, rays, link_sets=1)
+    b = gpu_trace(ctx, sc, rays, link_sets=6)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.int32), b[1].view(np.int32))
+
+
+def test_edge_cases(ctx):
+    sc = I.cornell_box()
+    s = gsp.Scene(ctx, sc)
+    # n == 0 is a no-op
+    empty = torch.zeros((0, 8), device="cuda")
+    gsp.gsp_trace_closest_hit(s.h, empty, torch.zeros(0, dtype=torch.int32, device="cuda"),
+                              torch.zeros(0, device="cuda"))
+    # axis-aligned directions (zero components), a finite tmax before the hit, tmin past it,
+    # origins outside pointing away, one ray alone and a ragged batch of 33
+    rays = np.array([[0.5, 0.5, 0.5, 0, 0, 0, -1, np.inf],
+                     [0.5, 0.5, 0.5, 0, 0, -1, 0, np.inf],
+                     [0.5, 0.5, 0.5, 0, 1, 0, 0, np.inf],
+                     [0.5, 0.5, 0.5, 0, 0, 0, -1, 0.1],
+                     [0.5, 0.5, 0.5, 5.0, 0, 0, -1, np.inf],
+                     [5, 5, 5, 0, 1, 0, 0, np.inf],
+                     [0.3, 0.2, 0.25, 0, 0.3, 0.9, -0.2, np.inf]], np.float32)
+    for batch in (rays[:1], rays, np.concatenate([rays] * 5)[:33]):
+        tri, t, _, _ = gpu_trace(ctx, sc, batch)
+        ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(batch, brute=True)
+        parity_hits(tri, t, ids, tt, nd, max_excluded=1.0)
+    assert gpu_trace(ctx, sc, rays[3:6])[0].tolist() == [-1, -1, -1]
+
+
+def test_matches_host_walk(ctx):
+    sc = I.traversal_sphere(n=24)
+    rays = I.traversal_rays(64, 32, n_random=4096, seed=35)
+    tri, t, _, s = gpu_trace(ctx, sc, rays)
+    htri, ht, _, _ = s.host_walk(rays)
+    ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(rays)
+    sel = nd.astype(bool)
+    assert np.array_equal(tri[sel], htri[sel])
+
+
+@pytest.fixture(scope="module")
+def full_size():
+    sc = I.traversal_sphere()  # 1,003,520 triangles
+    rays = I.traversal_rays()  # 4,194,304 rays: 2,097,152 coherent + 2,097,152 random
+    return sc, rays
+
+
+def test_full_size_traversal_sampled(ctx, full_size):
+    """The benchmark's workload and launch: all 4M rays in one call; the oracle checks a
+    stratified sample of 24,576 rays (both halves) with its FP64 BVH, and 256 by brute force."""
+    sc, rays = full_size
+    tri, t, _, _ = gpu_trace(ctx, sc, rays)
+    n = len(rays)
+    rng = np.random.default_rng(77)
+    sample = np.sort(np.concatenate([rng.choice(n // 2, 12288, replace=False),
+                                     n // 2 + rng.choice(n // 2, 12288, replace=False)]))
+    mesh = O.Mesh(sc.verts, sc.tris)
+    ids, tt, _, _, nd = mesh.closest_hit(rays[sample])
+    parity_hits(tri[sample], t[sample], ids, tt, nd)
+    sub = sample[::96]
+    bids, btt, _, _, bnd = mesh.closest_hit(rays[sub], brute=True)
+    parity_hits(tri[sub], t[sub], bids, btt, bnd)
+    assert (tri >= 0).mean() > 0.3
