@@ -174,7 +174,8 @@ void gsp_scene_destroy(gsp_scene* scene);
 gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh_stats* stats);
 
 /* Closest-hit ray casting (Fig. 3): for each ray i, the triangle with the lexicographically
- * smallest (t, triangle index) among tmin < t < tmax, Moller-Trumbore in FP32.
+ * smallest (t, triangle index) among tmin < t < tmax, Moller-Trumbore in FP32; the winner's
+ * t and (u, v) are then re-evaluated in FP64 from its exact vertices and rounded to FP32.
  *  d_rays [n][8] float: ox, oy, oz, tmin, dx, dy, dz, tmax (d need not be unit length)
  *  d_tri  [n] int32 out: triangle index in the uploaded order, -1 on a miss
  *  d_t    [n] float out: hit distance (in units of |d|), +inf on a miss
@@ -193,7 +194,7 @@ gsp_status gsp_bvh_host_walk(gsp_scene* scene, const float* h_rays, int64_t n, i
  *  h_nodes [nodes][8] float: min.xyz, miss link (int bits, -1 = none) | max.xyz, leaf word
  *          (int bits: bit 31 set = internal node, hit link = index + 1; otherwise
  *          triangle offset << 3 | triangle count, hit link = miss link)
- *  h_tris  [nt][12] float: v0.xyz, triangle index (int bits) | e1.xyz, 0 | e2.xyz, 0
+ *  h_tris  [nt][12] float: v0.xyz, triangle index (int bits) | v1.xyz, 0 | v2.xyz, 0
  * Either pointer may be NULL; *nodes_out receives the node count. */
 gsp_status gsp_bvh_export(gsp_scene* scene, int32_t set, float* h_nodes, float* h_tris,
                           int64_t* nodes_out);

@@ -683,7 +683,11 @@ struct CellHash {
     }
 };
 
-inline int64_t cell_of(double x, double h) { return (int64_t)std::floor(x / h); }
+// Hash-grid cell of a coordinate. Sec. 3.4 does not fix the lattice; it is shifted by 0.381966
+// of a cell so that axis-aligned walls at multiples of h (a scene's bounding planes are often at
+// 0) do not lie on cell boundaries, where rounding alone would pick the cell.
+const double kCellOffset = 0.381966;
+inline int64_t cell_of(double x, double h) { return (int64_t)std::floor(x / h + kCellOffset); }
 
 // Teschner et al. 2003 spatial hash, 32-bit wraparound, table size a power of two.
 inline uint32_t teschner(int64_t ix, int64_t iy, int64_t iz, uint64_t T) {

@@ -7,7 +7,8 @@
 //
 // Here every link set gets its own node array laid out in its own preorder, so the hit link
 // of an internal node is always index + 1 and only the miss link is stored. A node is two
-// float4 (32 bytes): {min.xyz, miss} and {max.xyz, leaf word}.
+// float4 (32 bytes): {min.xyz, miss} and {max.xyz, leaf word}. A triangle is three float4:
+// {v0.xyz, triangle index}, {v1.xyz, 0}, {v2.xyz, 0}.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -211,7 +212,7 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
     }
     auto t2 = clk::now();
 
-    // ---- triangles in leaf order: v0, e1 = v1 - v0, e2 = v2 - v0 (FP32) ----
+    // ---- triangles in leaf order: exact vertices v0, v1, v2 (edges are formed in the kernel) ----
     out.tris.resize((size_t)nt * 3);
     for (int64_t k = 0; k < nt; ++k) {
         int32_t t = perm[k];
@@ -219,8 +220,8 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
         const float* b = verts + 3 * (int64_t)tris[3 * t + 1];
         const float* c = verts + 3 * (int64_t)tris[3 * t + 2];
         out.tris[3 * k] = float4{a[0], a[1], a[2], as_float(t)};
-        out.tris[3 * k + 1] = float4{b[0] - a[0], b[1] - a[1], b[2] - a[2], 0.0f};
-        out.tris[3 * k + 2] = float4{c[0] - a[0], c[1] - a[1], c[2] - a[2], 0.0f};
+        out.tris[3 * k + 1] = float4{b[0], b[1], b[2], 0.0f};
+        out.tris[3 * k + 2] = float4{c[0], c[1], c[2], 0.0f};
     }
     out.nnodes = nn;
     out.nleaves = leaves;
@@ -280,8 +281,10 @@ void bvh_host_walk(const HostBVH& bvh, const float* rays, int64_t n, int32_t* ou
                     int32_t first = word >> 3, cnt = word & 7;
                     for (int32_t k = 0; k < cnt; ++k) {
                         ++nt;
-                        const float4 P = bvh.tris[3 * (first + k)], E1 = bvh.tris[3 * (first + k) + 1],
-                                     E2 = bvh.tris[3 * (first + k) + 2];
+                        const float4 P = bvh.tris[3 * (first + k)], V1 = bvh.tris[3 * (first + k) + 1],
+                                     V2 = bvh.tris[3 * (first + k) + 2];
+                        const float4 E1{V1.x - P.x, V1.y - P.y, V1.z - P.z, 0.0f};
+                        const float4 E2{V2.x - P.x, V2.y - P.y, V2.z - P.z, 0.0f};
                         float px = d[1] * E2.z - d[2] * E2.y, py = d[2] * E2.x - d[0] * E2.z,
                               pz = d[0] * E2.y - d[1] * E2.x;
                         float det = E1.x * px + E1.y * py + E1.z * pz;

@@ -287,6 +287,7 @@ gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, i
     if (((uintptr_t)d_rays & 15) || ((uintptr_t)d_uv & 7)) return GSP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
     unsigned long long* counter = s->d_counter;
     gspd::k_zero_u64<<<1, 1, 0, st>>>(counter);
     gspd::k_trace<<<gsp_trace_grid(s->ctx->device), kTraceThreads, 0, st>>>(
@@ -300,6 +301,7 @@ gsp_status gsp_rng_fill(gsp_context* ctx, uint64_t seed, uint32_t scene, uint32_
     if (!ctx || n < 0 || ndraw < 0 || (n > 0 && (!d_ids || !d_out))) return GSP_ERR_INVALID_ARG;
     if (n == 0 || ndraw == 0) return GSP_OK;
     GSP_CUDA_TRY(cudaSetDevice(ctx->device));
+    (void)cudaGetLastError();
     const int64_t nb = std::min<int64_t>((n + 255) / 256, 65535);
     gspd::k_rng_fill<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(seed, scene, domain, pass, d_ids, n, ndraw, d_out);
     GSP_CUDA_TRY(cudaGetLastError());

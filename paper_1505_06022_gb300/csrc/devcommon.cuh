@@ -120,6 +120,27 @@ __device__ __forceinline__ float safe_inv(float d) {
 // FP32 slab test conservative (Ize 2013).
 #define GSP_ROBUST_FAR 1.0000003576278687f
 
+// The triangle is chosen in FP32; its distance and barycentrics are then re-evaluated in FP64
+// from the exact vertices. FP32 Moller-Trumbore loses relative accuracy in t when the ray origin
+// is far from the vertex compared with t (cancellation in o - v0); one FP64 evaluation per ray
+// removes that without slowing the traversal loop.
+__device__ __forceinline__ void refine_hit(const float4* __restrict__ tri, float3 of, float3 df, Hit& h) {
+    const float4 A = __ldg(tri), B = __ldg(tri + 1), C = __ldg(tri + 2);
+    const double ax = A.x, ay = A.y, az = A.z;
+    const double e1x = (double)B.x - ax, e1y = (double)B.y - ay, e1z = (double)B.z - az;
+    const double e2x = (double)C.x - ax, e2y = (double)C.y - ay, e2z = (double)C.z - az;
+    const double dx = df.x, dy = df.y, dz = df.z;
+    const double px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
+    const double det = e1x * px + e1y * py + e1z * pz;
+    if (det == 0.0) return;
+    const double f = __drcp_rn(det);
+    const double sx = (double)of.x - ax, sy = (double)of.y - ay, sz = (double)of.z - az;
+    const double qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+    h.u = (float)(f * (sx * px + sy * py + sz * pz));
+    h.v = (float)(f * (dx * qx + dy * qy + dz * qz));
+    h.t = (float)(f * (e2x * qx + e2y * qy + e2z * qz));
+}
+
 // Closest hit by the stackless traversal of Fig. 3: follow the hit link (index + 1) when the
 // node's box is hit, the miss link otherwise; leaves run Moller-Trumbore on their triangles.
 // The lexicographic (t, triangle index) minimum over tmin < t < tmax is kept.
@@ -132,7 +153,7 @@ __device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, f
     const int c = S.link_sets == 6 ? ray_class(d) : 0;
     const float4* __restrict__ nodes = S.nodes + (size_t)c * (size_t)S.nnodes * 2;
     const int64_t cap = 2 * S.nnodes + 8;
-    int32_t node = 0;
+    int32_t node = 0, hit_slot = -1;
     int64_t steps = 0;
     while (node >= 0) {
         if (++steps > cap) {
@@ -154,14 +175,15 @@ __device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, f
                 const int32_t first = word >> 3, cnt = word & 7;
                 for (int32_t k = 0; k < cnt; ++k) {
                     const float4 P = __ldg(S.tris + 3 * (first + k));
-                    const float4 E1 = __ldg(S.tris + 3 * (first + k) + 1);
-                    const float4 E2 = __ldg(S.tris + 3 * (first + k) + 2);
-                    const float3 e1 = f3(E1), e2 = f3(E2);
+                    const float4 V1 = __ldg(S.tris + 3 * (first + k) + 1);
+                    const float4 V2 = __ldg(S.tris + 3 * (first + k) + 2);
+                    const float3 v0 = f3(P);
+                    const float3 e1 = f3(V1) - v0, e2 = f3(V2) - v0;
                     const float3 p = cross3(d, e2);
                     const float det = dot3(e1, p);
                     if (det == 0.0f) continue;
                     const float f = 1.0f / det;
-                    const float3 s = o - f3(P);
+                    const float3 s = o - v0;
                     const float u = f * dot3(s, p);
                     const float3 q = cross3(s, e1);
                     const float v = f * dot3(d, q);
@@ -173,6 +195,7 @@ __device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, f
                         h.id = id;
                         h.u = u;
                         h.v = v;
+                        hit_slot = first + k;
                     }
                 }
                 node = miss;
@@ -183,6 +206,7 @@ __device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, f
             node = miss;
         }
     }
+    if (hit_slot >= 0) refine_hit(S.tris + 3 * hit_slot, o, d, h);
     return h;
 }
 

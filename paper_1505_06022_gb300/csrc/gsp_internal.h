@@ -11,7 +11,7 @@
 
 // Host copy of the packed BVH (Sec. 3.1): per link set, nodes in that set's preorder.
 // Node = 2 float4: {min.xyz, miss link}, {max.xyz, leaf word}; triangle = 3 float4:
-// {v0.xyz, triangle index}, {e1.xyz, 0}, {e2.xyz, 0}.
+// {v0.xyz, triangle index}, {v1.xyz, 0}, {v2.xyz, 0}.
 struct HostBVH {
     int64_t nnodes = 0;
     int64_t nleaves = 0;

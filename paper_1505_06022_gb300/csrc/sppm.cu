@@ -29,8 +29,9 @@ constexpr float kPi = 3.14159265358979323846f;
 constexpr int kSlotsPerPath = 32;
 
 struct CamDev {
-    float3 eye, fwd, right, up;
-    float th, aspect;
+    float3 eye;
+    double3 fwd, right, up;
+    double th, aspect;
     int32_t w, h;
 };
 
@@ -80,10 +81,10 @@ __device__ __forceinline__ void onb(float3 n, float3& t1, float3& t2) {
 }
 
 __device__ __forceinline__ float3 cosine_dir(float3 n, float ua, float ub) {
-    const float r = sqrtf(ua), phi = 2.0f * kPi * ub;
+    const float r = sqrtf(ua);
     const float z = sqrtf(fmaxf(0.0f, 1.0f - ua));
     float s, c;
-    sincosf(phi, &s, &c);
+    sincospif(2.0f * ub, &s, &c);  // angle 2 pi ub without rounding 2 pi ub first
     float3 t1, t2;
     onb(n, t1, t2);
     return t1 * (r * c) + t2 * (r * s) + n * z;
@@ -138,9 +139,16 @@ __device__ __forceinline__ uint32_t cell_hash(int32_t ix, int32_t iy, int32_t iz
     return (((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u)) & mask;
 }
 
+// Cell lattice shifted by 0.381966 of a cell so that axis-aligned walls at multiples of the
+// cell size (e.g. a floor at 0) do not lie on cell boundaries.
+constexpr float kCellOffset = 0.381966f;
+
+__device__ __forceinline__ int32_t cell_of(float x, float inv_h) {
+    return (int32_t)floorf(fmaf(x, inv_h, kCellOffset));
+}
+
 __device__ __forceinline__ uint32_t bucket_of(float3 x, float inv_h, uint32_t mask) {
-    return cell_hash((int32_t)floorf(x.x * inv_h), (int32_t)floorf(x.y * inv_h),
-                     (int32_t)floorf(x.z * inv_h), mask);
+    return cell_hash(cell_of(x.x, inv_h), cell_of(x.y, inv_h), cell_of(x.z, inv_h), mask);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -154,9 +162,13 @@ k_eye(DevScene S, CamDev C, PassDev P, float4* __restrict__ hx, float4* __restri
     const int px = (int)(p % C.w), py = (int)(p / C.w);
     Rng rng = rng_seed(P.seed, P.scene_id, 0u, P.pass, (uint64_t)p);
     const float u0 = rng_next(rng), u1 = rng_next(rng);
-    const float sx = (((float)px + u0) / (float)C.w * 2.0f - 1.0f) * C.th * C.aspect;
-    const float sy = (1.0f - ((float)py + u1) / (float)C.h * 2.0f) * C.th;
-    float3 d = normalize3(C.fwd + C.right * sx + C.up * sy);
+    // primary ray in FP64 (once per pixel), rounded once
+    const double sx = (((double)px + u0) / (double)C.w * 2.0 - 1.0) * C.th * C.aspect;
+    const double sy = (1.0 - ((double)py + u1) / (double)C.h * 2.0) * C.th;
+    const double dx = C.fwd.x + C.right.x * sx + C.up.x * sy, dy = C.fwd.y + C.right.y * sx + C.up.y * sy,
+                 dz = C.fwd.z + C.right.z * sx + C.up.z * sy;
+    const double il = rsqrt(dx * dx + dy * dy + dz * dz);
+    float3 d = make_float3((float)(dx * il), (float)(dy * il), (float)(dz * il));
     float3 o = C.eye;
     float3 w = make_float3(1.0f, 1.0f, 1.0f);
     float3 direct = make_float3(0.0f, 0.0f, 0.0f);
@@ -216,8 +228,10 @@ __device__ __forceinline__ void emit_photon(const EmitDev& E, Rng& rng, float3& 
                  e2 = f3(__ldg(E.geo + 5 * j + 2)), n = f3(__ldg(E.geo + 5 * j + 3));
     phi = f3(__ldg(E.geo + 5 * j + 4));
     const float u1 = rng_next(rng), u2 = rng_next(rng);
-    const float su = sqrtf(u1);
-    o = v0 + e1 * (su * (1.0f - u2)) + e2 * (su * u2);
+    // point on the triangle in FP64 (once per path), rounded once
+    const double su = sqrt((double)u1), b1 = su * (1.0 - (double)u2), b2 = su * (double)u2;
+    o = make_float3((float)(v0.x + e1.x * b1 + e2.x * b2), (float)(v0.y + e1.y * b1 + e2.y * b2),
+                    (float)(v0.z + e1.z * b1 + e2.z * b2));
     const float u3 = rng_next(rng), u4 = rng_next(rng);
     d = cosine_dir(n, u3, u4);
 }
@@ -387,8 +401,8 @@ __device__ __forceinline__ int query_buckets(float3 x, float R, float inv_h, uin
     const float xs[3] = {x.x, x.y, x.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        lo[a] = (int32_t)floorf((xs[a] - Rq) * inv_h);
-        hi[a] = (int32_t)floorf((xs[a] + Rq) * inv_h);
+        lo[a] = cell_of(xs[a] - Rq, inv_h);
+        hi[a] = cell_of(xs[a] + Rq, inv_h);
         hi[a] = min(hi[a], lo[a] + 2);
     }
     int nb = 0;
@@ -649,11 +663,11 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         up[1] = rt[2] * f[0] - rt[0] * f[2];
         up[2] = rt[0] * f[1] - rt[1] * f[0];
         r->cam.eye = make_float3((float)eye[0], (float)eye[1], (float)eye[2]);
-        r->cam.fwd = make_float3((float)f[0], (float)f[1], (float)f[2]);
-        r->cam.right = make_float3((float)rt[0], (float)rt[1], (float)rt[2]);
-        r->cam.up = make_float3((float)up[0], (float)up[1], (float)up[2]);
-        r->cam.th = (float)std::tan((double)c.vfov_deg * M_PI / 180.0 / 2.0);
-        r->cam.aspect = (float)((double)c.width / (double)c.height);
+        r->cam.fwd = make_double3(f[0], f[1], f[2]);
+        r->cam.right = make_double3(rt[0], rt[1], rt[2]);
+        r->cam.up = make_double3(up[0], up[1], up[2]);
+        r->cam.th = std::tan((double)c.vfov_deg * M_PI / 180.0 / 2.0);
+        r->cam.aspect = (double)c.width / (double)c.height;
         r->cam.w = c.width;
         r->cam.h = c.height;
     }
@@ -793,6 +807,7 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
 gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream) {
     if (!r || npasses < 0) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
     for (int32_t i = 0; i < npasses; ++i) {
         gsp_status s = sppm_one_pass(r, (cudaStream_t)stream);
         if (s != GSP_OK) return s;
@@ -803,6 +818,7 @@ gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream) {
 gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream) {
     if (!r || !d_rgb) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    (void)cudaGetLastError();
     const float inv_p = r->passes > 0 ? 1.0f / (float)r->passes : 0.0f;
     const double ne_host = (double)r->passes * (double)r->np;
     k_image<<<blocks(r->npix, 256), 256, 0, (cudaStream_t)stream>>>(
@@ -815,6 +831,7 @@ gsp_status gsp_sppm_state(gsp_sppm* r, float* d_N, float* d_R, float* d_tau, flo
                           double* h_counts, void* stream) {
     if (!r) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    (void)cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
     if (d_N || d_R || d_tau || d_direct) {
         k_state<<<blocks(r->npix, 256), 256, 0, st>>>(r->st0, r->st1, r->npix, d_N, d_R, d_tau, d_direct);

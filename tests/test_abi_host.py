@@ -64,10 +64,10 @@ def check_threaded_tree(nodes, tris_packed, nt):
             assert 1 <= cnt <= 7
             covered[first:first + cnt] += 1
             v0 = tris_packed[first:first + cnt, 0:3]
-            v1 = v0 + tris_packed[first:first + cnt, 4:7]
-            v2 = v0 + tris_packed[first:first + cnt, 8:11]
-            for v in (v0, v1, v2):  # leaf box holds its triangles (up to FP32 edge rounding)
-                assert np.all(v >= nodes[i, 0:3] - 1e-6) and np.all(v <= nodes[i, 4:7] + 1e-6)
+            v1 = tris_packed[first:first + cnt, 4:7]
+            v2 = tris_packed[first:first + cnt, 8:11]
+            for v in (v0, v1, v2):  # leaf box holds its triangles exactly
+                assert np.all(v >= nodes[i, 0:3]) and np.all(v <= nodes[i, 4:7])
     assert np.all(covered == 1)  # leaves partition the triangles
 
 
