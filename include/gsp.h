@@ -229,6 +229,22 @@ int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity);
 /* Waits for the renderer's stream work and returns the first recorded device error. */
 gsp_status gsp_sppm_sync(gsp_sppm* r);
 
+/* ---- hash grid (the exact deposit of the SPPM pass as a standalone operation) ------------- */
+
+/* Exact hash grid of a point set: the index the exact-mode deposit builds over a pass's photons
+ * (Sec. 3.4 contrasts it with stochastic hashing). Per axis cell = floor(x / cell_h + 0.381966),
+ * bucket = (ix*73856093 ^ iy*19349663 ^ iz*83492791) mod table_size (Teschner et al. 2003, 32-bit
+ * wraparound; table_size a power of two <= 2^30). Points keep their input order inside a bucket.
+ *  d_pos    [n] float4 device: x, y, z, (ignored); n <= 2^31 - 1
+ *  d_order  [n] uint32 device out: point indices ordered by (bucket, input index)
+ *  d_bstart [table_size + 1] uint32 device out: first position of each bucket in d_order;
+ *           d_bstart[table_size] = n
+ * Scratch (16 n bytes + about 0.6 MiB) lives on the context; it is allocated on first use and
+ * reallocated (after synchronising `stream`) when a larger build needs more. */
+gsp_status gsp_hash_grid_build(gsp_context* ctx, const float* d_pos, int64_t n, float cell_h,
+                               int64_t table_size, uint32_t* d_order, uint32_t* d_bstart, void* stream);
+
+
 #ifdef __cplusplus
 }
 #endif

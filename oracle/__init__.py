@@ -97,6 +97,7 @@ def lib():
         L.orc_dielectric.argtypes = [P, P, C.c_double, C.c_float, P]
         L.orc_mlcg_step_many.argtypes = [I32, P, I64, P]
         L.orc_sppm_update.argtypes = [I64, C.c_double, P, P, P, P, P]
+        L.orc_hash_grid.argtypes = [P, I64, C.c_double, I64, P, P, P, P]
         _lib = L
     return _lib
 
@@ -285,6 +286,17 @@ class Sppm:
         lib().orc_sppm_last_gather(self.handle, _p(M), _p(Phi), _p(valid), _p(hx), _p(hn), _p(hw),
                                    _p(hm))
         return dict(M=M, Phi=Phi, valid=valid, x=hx, n=hn, w=hw, mat=hm)
+
+
+def hash_grid(xyz, h, T):
+    """Exact hash grid of float32 points: (bucket, order by (bucket, index), bucket starts,
+    near-boundary flags)."""
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    n = len(xyz)
+    b, order = np.zeros(n, np.uint32), np.zeros(n, np.uint32)
+    starts, near = np.zeros(T + 1, np.uint32), np.zeros(n, np.int32)
+    lib().orc_hash_grid(_p(xyz), n, float(h), int(T), _p(b), _p(order), _p(starts), _p(near))
+    return b, order, starts, near
 
 
 def sppm_update(alpha, M, Phi, N, R, tau):

@@ -957,6 +957,41 @@ void orc_dielectric(const double* d, const double* n, double ior, float u, doubl
     out[0] = r.x; out[1] = r.y; out[2] = r.z;
 }
 
+// Exact hash grid of a point set (the index the deposit builds, Sec. 3.4's regular hashing):
+// bucket of each point, points ordered by (bucket, input index), and bucket starts [T + 1].
+// near[i] = 1 when a coordinate lies within 1e-5 + 1e-6 |x/h| cells of a cell boundary: an FP32
+// evaluation of x/h + offset errs by up to about 1.2e-7 |x/h|, so FP32 and FP64 may then pick
+// different cells.
+void orc_hash_grid(const float* xyz, int64_t n, double h, int64_t T, uint32_t* bucket,
+                   uint32_t* order, uint32_t* bstart, int32_t* near) {
+    std::vector<std::pair<uint32_t, int64_t>> key(n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c[3];
+        bool nb = false;
+        for (int k = 0; k < 3; ++k) {
+            double q = (double)xyz[3 * i + k] / h + kCellOffset;
+            c[k] = (int64_t)std::floor(q);
+            double fr = q - std::floor(q);
+            const double tol = 1e-5 + 1e-6 * std::fabs(q);
+            nb = nb || fr < tol || fr > 1.0 - tol;
+        }
+        uint32_t b = teschner(c[0], c[1], c[2], (uint64_t)T);
+        key[i] = {b, i};
+        if (bucket) bucket[i] = b;
+        if (near) near[i] = nb ? 1 : 0;
+    }
+    std::stable_sort(key.begin(), key.end(),
+                     [](const std::pair<uint32_t, int64_t>& a, const std::pair<uint32_t, int64_t>& b) {
+                         return a.first < b.first;
+                     });
+    for (int64_t i = 0; i < n; ++i) order[i] = (uint32_t)key[i].second;
+    int64_t j = 0;
+    for (int64_t b = 0; b <= T; ++b) {
+        while (j < n && key[j].first < b) ++j;
+        bstart[b] = (uint32_t)j;
+    }
+}
+
 // The progressive update alone, for recurrence tests: applies one pass with counts M and
 // fluxes Phi to (N, R, tau) arrays in place.
 void orc_sppm_update(int64_t n, double alpha, const double* M, const double* Phi, double* N,

@@ -121,6 +121,7 @@ void gsp_context_destroy(gsp_context* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaFree(ctx->d_status);
+    cudaFree(ctx->grid_scratch);
     delete ctx;
 }
 

@@ -34,6 +34,8 @@ void bvh_host_walk(const HostBVH& bvh, const float* rays, int64_t n, int32_t* tr
 struct gsp_context {
     int32_t device = 0;
     int32_t* d_status = nullptr;  // first device-side error (0 = none)
+    uint32_t* grid_scratch = nullptr;  // scratch of gsp_hash_grid_build, grown on demand
+    int64_t grid_words = 0;
 };
 
 struct gsp_scene {

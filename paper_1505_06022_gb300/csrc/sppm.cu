@@ -507,6 +507,19 @@ __global__ void k_init_state(float4* st0, float4* st1, int64_t npix, float r0) {
     st1[p] = make_float4(0.0f, 0.0f, 0.0f, r0);
 }
 
+// Bucket key of each point of a standalone hash-grid build; counts per bucket.
+__global__ void k_grid_keys(const float4* __restrict__ pos, int64_t n, float inv_h, uint32_t mask,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ bcount) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = bucket_of(f3(pos[i]), inv_h, mask);
+        keys[i] = b;
+        vals[i] = (uint32_t)i;
+        atomicAdd(bcount + b, 1u);
+    }
+}
+
+__global__ void k_store_u32(uint32_t* p, uint32_t v) { *p = v; }
+
 __global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -876,6 +889,70 @@ int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity) {
         }
     std::sort(h_ids, h_ids + k);
     return k;
+}
+
+}  // extern "C"
+
+// Scratch (uint32 words) of a hash-grid build over n points with T buckets: key/value
+// ping-pong buffers, the radix histogram, scan partials and the device copy of n.
+int64_t gsp_grid_scratch_words(int64_t n, int64_t T) {
+    return 4 * n + gsp_sort_hist_elems() +
+           std::max(gsp_scan_temp_elems(T), gsp_scan_temp_elems(gsp_sort_hist_elems())) + 64;
+}
+
+// Exact hash grid of n points: keys -> counts -> in-place bucket scan -> stable radix sort.
+gsp_status gsp_grid_build_with(const float4* pos, int64_t n, float cell_h, int64_t T, uint32_t* order,
+                               uint32_t* bstart, uint32_t* scratch, cudaStream_t st) {
+    int tbits = 0;
+    while ((int64_t(1) << tbits) < T) ++tbits;
+    uint32_t* ka = scratch;
+    uint32_t* va = ka + n;
+    uint32_t* kb = va + n;
+    uint32_t* vb = kb + n;
+    uint32_t* hist = vb + n;
+    uint32_t* nbuf = hist + gsp_sort_hist_elems();
+    uint32_t* tmp = nbuf + 64;
+    GSP_CUDA_TRY(cudaMemsetAsync(bstart, 0, (size_t)T * sizeof(uint32_t), st));
+    k_store_u32<<<1, 1, 0, st>>>(nbuf, (uint32_t)n);
+    if (n > 0)
+        k_grid_keys<<<(unsigned)std::min<int64_t>(blocks(n, 256), 4096), 256, 0, st>>>(
+            pos, n, 1.0f / cell_h, (uint32_t)(T - 1), ka, va, bstart);
+    GSP_CUDA_TRY(gsp_scan_u32(bstart, bstart, T, bstart + T, tmp, st));
+    uint32_t *ko = nullptr, *vo = nullptr;
+    GSP_CUDA_TRY(gsp_radix_sort_u32(ka, va, kb, vb, nbuf, tbits, hist, tmp, st, &ko, &vo));
+    if (n > 0) GSP_CUDA_TRY(cudaMemcpyAsync(order, vo, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+static gsp_status grid_args_ok(const float* d_pos, int64_t n, float cell_h, int64_t T, const uint32_t* d_order,
+                               const uint32_t* d_bstart) {
+    if (n < 0 || n > INT32_MAX || !(cell_h > 0.0f) || !std::isfinite(cell_h) || T < 1 || T > (int64_t(1) << 30) ||
+        (T & (T - 1)) || !d_bstart || (n > 0 && (!d_pos || !d_order)) || ((uintptr_t)d_pos & 15))
+        return GSP_ERR_INVALID_ARG;
+    return GSP_OK;
+}
+
+extern "C" {
+
+gsp_status gsp_hash_grid_build(gsp_context* ctx, const float* d_pos, int64_t n, float cell_h, int64_t table_size,
+                               uint32_t* d_order, uint32_t* d_bstart, void* stream) {
+    if (!ctx) return GSP_ERR_INVALID_ARG;
+    gsp_status a = grid_args_ok(d_pos, n, cell_h, table_size, d_order, d_bstart);
+    if (a != GSP_OK) return a;
+    GSP_CUDA_TRY(cudaSetDevice(ctx->device));
+    (void)cudaGetLastError();
+    const int64_t words = gsp_grid_scratch_words(n, table_size);
+    if (words > ctx->grid_words) {  // grow the context's scratch (first use or a larger build)
+        GSP_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        cudaFree(ctx->grid_scratch);
+        ctx->grid_scratch = nullptr;
+        ctx->grid_words = 0;
+        GSP_CUDA_TRY(cudaMalloc(&ctx->grid_scratch, (size_t)words * sizeof(uint32_t)));
+        ctx->grid_words = words;
+    }
+    return gsp_grid_build_with((const float4*)d_pos, n, cell_h, table_size, d_order, d_bstart, ctx->grid_scratch,
+                               (cudaStream_t)stream);
 }
 
 gsp_status gsp_sppm_sync(gsp_sppm* r) {

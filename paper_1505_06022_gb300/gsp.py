@@ -34,7 +34,7 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_context_sync", "gsp_scene_upload", "gsp_scene_destroy", "gsp_build_bvh",
        "gsp_trace_closest_hit", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
-       "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill"]
+       "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build"]
 
 
 class GspError(RuntimeError):
@@ -104,6 +104,7 @@ def lib():
             L.gsp_sppm_last_deposits.restype = I64
             L.gsp_sppm_last_deposits.argtypes = [P, P, I64]
             L.gsp_sppm_sync.argtypes = [P]
+            L.gsp_hash_grid_build.argtypes = [P, P, I64, C.c_float, I64, P, P, P]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
             _lib = L
     return _lib
@@ -159,6 +160,20 @@ def gsp_rng_fill(ctx, seed, scene, domain, pass_, ids, ndraw, out=None, stream=N
                             _stream(stream))
     _check("gsp_rng_fill", rc)
     return out
+
+
+def gsp_hash_grid_build(ctx, pos, cell_h, table_size, order=None, bstart=None, stream=None):
+    """pos: CUDA float32 [n, 4]; returns (order uint32-as-int32 [n], bstart [table_size + 1])."""
+    import torch
+    n = pos.shape[0]
+    if order is None:
+        order = torch.empty(n, dtype=torch.int32, device=pos.device)
+    if bstart is None:
+        bstart = torch.empty(table_size + 1, dtype=torch.int32, device=pos.device)
+    rc = lib().gsp_hash_grid_build(ctx, _dev(pos), n, cell_h, table_size, _dev(order), _dev(bstart),
+                                   _stream(stream))
+    _check("gsp_hash_grid_build", rc)
+    return order, bstart
 
 
 def gsp_scene_upload(ctx, verts, tris, tri_mat=None, mats=None, camera=None):
