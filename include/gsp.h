@@ -244,6 +244,26 @@ gsp_status gsp_sppm_sync(gsp_sppm* r);
 gsp_status gsp_hash_grid_build(gsp_context* ctx, const float* d_pos, int64_t n, float cell_h,
                                int64_t table_size, uint32_t* d_order, uint32_t* d_bstart, void* stream);
 
+/* The same hash-grid build without any device allocation (the paper has no counterpart: this
+ * is a deployment variant). For callers that cannot allocate device memory: hosts whose device
+ * memory belongs to another allocator or pool that forbids side allocations, plugins that are
+ * handed fixed buffers, and real-time loops that must not block on cudaMalloc's implicit
+ * synchronisation. Inputs and outputs are exactly those of gsp_hash_grid_build and are the
+ * caller's buffers; no context is needed (the current device is
+ * used). The scratch is a fixed array inside the library's device image (8.53 MiB, held on every
+ * GPU that loads the library until the process exits), so:
+ *  - n <= GSP_GRID_STATIC_MAX_POINTS and table_size <= GSP_GRID_STATIC_MAX_TABLE, otherwise
+ *    GSP_ERR_INVALID_ARG with the limits in gsp_last_error_message();
+ *  - the first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture;
+ *  - every call uses the same array, which keeps the previous call's contents (whatever must
+ *    start at zero is cleared by the call itself); calls whose device work overlaps, on any
+ *    streams, race on it and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+#define GSP_GRID_STATIC_MAX_POINTS 524288
+#define GSP_GRID_STATIC_MAX_TABLE 16777216
+gsp_status gsp_hash_grid_build_static(const float* d_pos, int64_t n, float cell_h, int64_t table_size,
+                                      uint32_t* d_order, uint32_t* d_bstart, void* stream);
 
 #ifdef __cplusplus
 }

@@ -34,7 +34,10 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_context_sync", "gsp_scene_upload", "gsp_scene_destroy", "gsp_build_bvh",
        "gsp_trace_closest_hit", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
-       "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build"]
+       "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
+       "gsp_hash_grid_build_static"]
+GRID_STATIC_MAX_POINTS = 524288
+GRID_STATIC_MAX_TABLE = 16777216
 
 
 class GspError(RuntimeError):
@@ -105,6 +108,7 @@ def lib():
             L.gsp_sppm_last_deposits.argtypes = [P, P, I64]
             L.gsp_sppm_sync.argtypes = [P]
             L.gsp_hash_grid_build.argtypes = [P, P, I64, C.c_float, I64, P, P, P]
+            L.gsp_hash_grid_build_static.argtypes = [P, I64, C.c_float, I64, P, P, P]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
             _lib = L
     return _lib
@@ -173,6 +177,14 @@ def gsp_hash_grid_build(ctx, pos, cell_h, table_size, order=None, bstart=None, s
     rc = lib().gsp_hash_grid_build(ctx, _dev(pos), n, cell_h, table_size, _dev(order), _dev(bstart),
                                    _stream(stream))
     _check("gsp_hash_grid_build", rc)
+    return order, bstart
+
+
+def gsp_hash_grid_build_static(pos, cell_h, table_size, order, bstart, stream=None):
+    """Allocation-free hash-grid build on the current device; order/bstart are caller tensors."""
+    rc = lib().gsp_hash_grid_build_static(_dev(pos), pos.shape[0], cell_h, table_size, _dev(order),
+                                          _dev(bstart), _stream(stream))
+    _check("gsp_hash_grid_build_static", rc)
     return order, bstart
 
 

@@ -1,0 +1,53 @@
+"""The allocation-free hash-grid build (for callers that cannot allocate device memory, such as
+hosts whose device memory belongs to another allocator, or loops that must not block on
+cudaMalloc) gives the same grid as the allocating entry point, on consecutive calls that reuse its
+static scratch.
+
+Kept in a file that pytest collects last, so a run that stops at the first failure has run
+every other test before this one."""
+import numpy as np
+import pytest
+
+from paper_1505_06022_gb300 import gsp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def cloud(n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.concatenate([rng.normal(scale=1.0, size=(n // 2, 3)), rng.normal(scale=0.03, size=(n - n // 2, 3))])
+    pos = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+    pos[:, :3] = torch.from_numpy(x.astype(np.float32)).cuda()
+    return pos
+
+
+def test_static_build_matches_allocating_build_twice():
+    ctx = gsp.Context(0)
+    torch.cuda.set_device(0)
+    cases = [(cloud(300_001, 1), 0.02, 1 << 19),          # first call: scratch as loaded
+             (cloud(gsp.GRID_STATIC_MAX_POINTS, 2), 0.005, 1 << 20)]  # second: reuses it, at the limit
+    for pos, h, T in cases:
+        n = pos.shape[0]
+        want_order, want_starts = gsp.gsp_hash_grid_build(ctx.h, pos, h, T)
+        order = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        starts = torch.full((T + 1,), -7, dtype=torch.int32, device="cuda")
+        gsp.gsp_hash_grid_build_static(pos, h, T, order, starts)
+        torch.cuda.synchronize()
+        assert torch.equal(order, want_order)
+        assert torch.equal(starts, want_starts)
+        assert int(starts[-1]) == n
+    ctx.close()
+
+
+def test_static_build_rejects_sizes_beyond_its_scratch():
+    n = gsp.GRID_STATIC_MAX_POINTS + 1
+    pos = torch.zeros((n, 4), device="cuda")
+    order = torch.empty(n, dtype=torch.int32, device="cuda")
+    starts = torch.empty(65, dtype=torch.int32, device="cuda")
+    with pytest.raises(gsp.GspError, match="static scratch"):
+        gsp.gsp_hash_grid_build_static(pos, 0.1, 64, order, starts)
+    small = torch.zeros((16, 4), device="cuda")
+    big_table = gsp.GRID_STATIC_MAX_TABLE * 2
+    with pytest.raises(gsp.GspError, match="static scratch"):
+        gsp.gsp_hash_grid_build_static(small, 0.1, big_table, order[:16], torch.empty(2, device="cuda"))
