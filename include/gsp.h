@@ -174,13 +174,16 @@ void gsp_scene_destroy(gsp_scene* scene);
 gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh_stats* stats);
 
 /* Closest-hit ray casting (Fig. 3): for each ray i, the triangle with the lexicographically
- * smallest (t, triangle index) among tmin < t < tmax, Moller-Trumbore in FP32; the winner's
- * t and (u, v) are then re-evaluated in FP64 from its exact vertices and rounded to FP32.
+ * smallest (t, triangle index) among tmin < t < tmax, Moller-Trumbore in FP32; when the FP32
+ * t of the winner may be inaccurate (origin far from the triangle compared with t, grazing
+ * ray), its t and (u, v) are re-evaluated in FP64 from the exact vertices and rounded to FP32.
  *  d_rays [n][8] float: ox, oy, oz, tmin, dx, dy, dz, tmax (d need not be unit length)
  *  d_tri  [n] int32 out: triangle index in the uploaded order, -1 on a miss
  *  d_t    [n] float out: hit distance (in units of |d|), +inf on a miss
  *  d_uv   [n][2] float out or NULL: barycentrics (u, v) of the hit, 0 on a miss
- * Returns GSP_ERR_NOT_BUILT if the scene has no BVH. n == 0 is a no-op. */
+ * Returns GSP_ERR_NOT_BUILT if the scene has no BVH. n == 0 is a no-op; n <= 2^31 - 1.
+ * The scene keeps a list (8 bytes per ray) of hits whose t is re-evaluated in FP64; it is
+ * allocated, after synchronising `stream`, the first time a call has more rays than any before. */
 gsp_status gsp_trace_closest_hit(gsp_scene* scene, const float* d_rays, int64_t n, int32_t* d_tri,
                                  float* d_t, float* d_uv, void* stream);
 

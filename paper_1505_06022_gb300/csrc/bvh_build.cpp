@@ -175,7 +175,10 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
     for (int64_t n = nn - 1; n >= 0; --n)
         if (nodes[n].left >= 0) size[n] = 1 + size[nodes[n].left] + size[nodes[n].right];
     const int sets = p.link_sets;
-    out.nodes.assign((size_t)sets * nn * 2, float4{0, 0, 0, 0});
+    // one padding node after each link set: a traversal step may read node + 1 past the last
+    // node (a leaf) without using it; the padding box is empty and its links end the walk
+    const int64_t stride = nn + 1;
+    out.nodes.assign((size_t)sets * stride * 2, float4{0, 0, 0, 0});
     std::vector<int32_t> pos(nn), st;
     st.reserve(256);
     for (int c = 0; c < sets; ++c) {
@@ -200,7 +203,9 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
             st.push_back(second);
             st.push_back(first);
         }
-        float4* dst = out.nodes.data() + (size_t)c * nn * 2;
+        float4* dst = out.nodes.data() + (size_t)c * stride * 2;
+        dst[2 * nn] = float4{INFINITY, INFINITY, INFINITY, as_float(-1)};
+        dst[2 * nn + 1] = float4{-INFINITY, -INFINITY, -INFINITY, as_float(0)};
         for (int64_t n = 0; n < nn; ++n) {
             const BNode& nd = nodes[n];
             int32_t q = pos[n];
@@ -224,6 +229,7 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
         out.tris[3 * k + 2] = float4{c[0], c[1], c[2], 0.0f};
     }
     out.nnodes = nn;
+    out.stride = stride;
     out.nleaves = leaves;
     out.depth = max_depth;
     out.link_sets = sets;
@@ -261,7 +267,7 @@ void bvh_host_walk(const HostBVH& bvh, const float* rays, int64_t n, int32_t* ou
             inv[k] = 1.0f / dk;
         }
         int c = bvh.link_sets == 6 ? ray_class(d[0], d[1], d[2]) : 0;
-        const float4* nodes = bvh.nodes.data() + (size_t)c * bvh.nnodes * 2;
+        const float4* nodes = bvh.nodes.data() + (size_t)c * bvh.stride * 2;
         int32_t node = 0, nv = 0, nt = 0;
         int64_t steps = 0, cap = 2 * bvh.nnodes + 8;
         while (node >= 0 && steps++ < cap) {

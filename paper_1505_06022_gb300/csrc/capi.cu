@@ -17,27 +17,157 @@ void gsp_set_last_error(const std::string& msg) { g_last_error = msg; }
 
 namespace gspd {
 
-// Closest-hit kernel (Fig. 3). Persistent grid; each warp takes batches of 32 rays from a
-// global counter and refills finished lanes, so lanes of long rays do not idle behind a warp
-// that is otherwise done.
-__global__ void __launch_bounds__(kTraceThreads)
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Closest-hit kernel (Fig. 3), persistent. A warp takes chunks of kTraceChunk consecutive rays
+// with one atomic and hands them to its lanes; a lane whose ray has finished takes the next ray of
+// the chunk right away, so lanes do not idle until the slowest ray of a batch ends. Lanes run up
+// to kTraceInner traversal steps between refills. Rays and results are streamed with evict-first
+// hints so that the BVH stays resident in L2. Hits whose FP32 t may be inaccurate are appended
+// to a list that k_refine re-evaluates in FP64 with full warps.
+// ctr[0] = next ray, ctr[1] = refine-list length.
+__global__ void __launch_bounds__(kTraceThreads, GSP_TRACE_MIN_BLOCKS)
 k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* __restrict__ tri,
-        float* __restrict__ tout, float2* __restrict__ uv, unsigned long long* __restrict__ next) {
+        float* __restrict__ tout, float2* __restrict__ uv, unsigned long long* __restrict__ ctr,
+        int2* __restrict__ rlist) {
     const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    const int32_t cap = (int32_t)min(4 * S.nnodes + 16, (int64_t)INT32_MAX);  // box tests incl. retests
+    Trav st;
+    st.node = -1;
+    st.slot = -1;
+    int64_t ray = -1, qbase = 0, qend = 0;
+    int32_t pend = -1;  // leaf word of a postponed leaf, -1 = none
+    bool done = false;
     while (true) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(next, 32ull);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= (unsigned long long)n) break;
-        const int64_t i = (int64_t)base + lane;
-        if (i < n) {
-            const float4 a = __ldg(rays + 2 * i), b = __ldg(rays + 2 * i + 1);
-            const Hit h = traverse(S, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z), a.w, b.w);
-            tri[i] = h.id;
-            tout[i] = h.id >= 0 ? h.t : __int_as_float(0x7f800000);
-            if (uv) uv[i] = make_float2(h.u, h.v);
+        bool need = ray < 0 && !done;
+        uint32_t m = __ballot_sync(0xffffffffu, need);
+        while (m) {
+            if (qbase >= qend) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(ctr, (unsigned long long)kTraceChunk);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                qbase = (int64_t)b;
+                qend = min(qbase + kTraceChunk, n);
+                if (qbase >= n) {
+                    done = true;
+                    break;
+                }
+            }
+            const int take = min(__popc(m), (int)(qend - qbase));
+            const int rank = __popc(m & lt);
+            if (need && rank < take) {
+                ray = qbase + rank;
+                const float4 a = __ldcs(rays + 2 * ray), b = __ldcs(rays + 2 * ray + 1);
+                trav_init(S, f3(a), f3(b), a.w, b.w, st);
+                need = false;
+            }
+            qbase += take;
+            m = __ballot_sync(0xffffffffu, need);
+        }
+        if (__ballot_sync(0xffffffffu, ray >= 0) == 0) break;
+        // Node steps; a lane that reaches a leaf keeps it pending and goes on along the miss link
+        // with its current best t (which can only make it visit more nodes, never skip the
+        // winner). When a lane meets a second leaf it waits. The warp tests all pending leaves
+        // together when enough lanes hold one, when a lane waits, or when a lane's walk ended.
+#pragma unroll 1
+        for (int it = 0; it < kTraceInner; ++it) {
+            bool waiting = false;
+            if (ray >= 0 && st.node >= 0) {
+                // one fetch brings the node and the next node in preorder (its first child when it
+                // is internal, usually in the same cache line); both boxes can be tested
+                const float4* np = st.nodes + 2 * st.node;
+                const float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2), D = __ldg(np + 3);
+                st.steps += 1;
+                int32_t word, miss;
+                if (st.steps > cap) {
+                    report(S.status, -4);
+                    st.node = -1;
+                } else if (!box_hit(st, A, B, word, miss)) {
+                    st.node = miss;
+                } else if (word >= 0) {
+                    if (pend < 0) {
+                        pend = word;
+                        st.node = miss;
+                    } else {
+                        waiting = true;
+                    }
+                } else {
+                    st.steps += 1;
+                    int32_t w2, m2;
+                    if (!box_hit(st, C, D, w2, m2)) {
+                        st.node = m2;
+                    } else if (w2 >= 0) {
+                        if (pend < 0) {
+                            pend = w2;
+                            st.node = m2;
+                        } else {
+                            waiting = true;
+                            st.node = st.node + 1;
+                        }
+                    } else {
+                        st.node = st.node + 2;
+                    }
+                }
+            }
+            const uint32_t pm = __ballot_sync(0xffffffffu, pend >= 0);
+            const uint32_t urgent = __ballot_sync(0xffffffffu, waiting || (pend >= 0 && st.node < 0));
+            if (urgent || __popc(pm) >= kTraceLeafBatch) {
+                if (pend >= 0) {
+                    trav_leaf(S, st, pend >> 3, pend & 7);
+                    pend = -1;
+                }
+            }
+            if (__ballot_sync(0xffffffffu, ray >= 0 && (st.node >= 0 || pend >= 0)) == 0) break;
+        }
+        const bool fin = ray >= 0 && st.node < 0 && pend < 0;
+        bool flag = false;
+        if (fin) {
+            float u = 0.0f, v = 0.0f;
+            if (st.slot >= 0)
+                flag = hit_error_factor(S.tris + 3 * st.slot, st.o, st.d, st.tbest, u, v) > GSP_REFINE_FACTOR;
+            __stcs(tri + ray, st.best);
+            __stcs(tout + ray, st.best >= 0 ? st.tbest : __int_as_float(0x7f800000));
+            if (uv) __stcs(uv + ray, make_float2(u, v));
+        }
+        const uint32_t fm = __ballot_sync(0xffffffffu, flag);
+        if (fm) {
+            const int leader = __ffs(fm) - 1;
+            unsigned long long b = 0;
+            if (lane == leader) b = atomicAdd(ctr + 1, (unsigned long long)__popc(fm));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (flag) rlist[b + __popc(fm & lt)] = make_int2((int)ray, st.slot);
+        }
+        if (fin) ray = -1;
+    }
+}
+
+// FP64 re-evaluation of the listed hits (their rays are rare; full warps keep the FP64 pipe busy).
+__global__ void __launch_bounds__(256)
+k_refine(DevScene S, const float4* __restrict__ rays, const int2* __restrict__ rlist,
+         const unsigned long long* __restrict__ ctr, float* __restrict__ tout, float2* __restrict__ uv) {
+    const int64_t cnt = (int64_t)ctr[1];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int2 e = rlist[i];
+        const float4 a = __ldg(rays + 2 * (int64_t)e.x), b = __ldg(rays + 2 * (int64_t)e.x + 1);
+        Hit h;
+        h.t = tout[e.x];
+        h.u = h.v = 0.0f;
+        h.id = 0;
+        if (refine_hit(S.tris + 3 * (int64_t)e.y, f3(a), f3(b), h)) {
+            tout[e.x] = h.t;
+            if (uv) uv[e.x] = make_float2(h.u, h.v);
         }
     }
+}
+
+__global__ void k_zero_u64x2(unsigned long long* p) {
+    p[0] = 0ull;
+    p[1] = 0ull;
 }
 
 __global__ void k_zero_u64(unsigned long long* p) { *p = 0ull; }
@@ -71,6 +201,7 @@ gspd::DevScene gsp_dev_scene(const gsp_scene* s) {
     d.shade = s->d_shade;
     d.mats = s->d_mats;
     d.nnodes = s->bvh.nnodes;
+    d.stride = s->bvh.stride;
     d.link_sets = s->bvh.link_sets;
     d.status = s->ctx->d_status;
     return d;
@@ -151,6 +282,7 @@ void gsp_scene_destroy(gsp_scene* s) {
         cudaFree(s->d_shade);
         cudaFree(s->d_mats);
         cudaFree(s->d_counter);
+        cudaFree(s->d_rlist);
     }
     delete s;
 }
@@ -229,7 +361,7 @@ gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, co
     }
     cudaError_t e = cudaMalloc(&s->d_shade, nt * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_mats, 2 * nmat * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(s->d_shade, shade.data(), nt * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_mats, mt.data(), 2 * nmat * sizeof(float4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -284,15 +416,26 @@ gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, i
     if (!s->ctx) return GSP_ERR_INVALID_ARG;  // host-only scene
     if (!s->built) return GSP_ERR_NOT_BUILT;
     if (n == 0) return GSP_OK;
-    if (!d_rays || !d_tri || !d_t) return GSP_ERR_INVALID_ARG;
+    if (!d_rays || !d_tri || !d_t || n > INT32_MAX) return GSP_ERR_INVALID_ARG;
     if (((uintptr_t)d_rays & 15) || ((uintptr_t)d_uv & 7)) return GSP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
     (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
-    unsigned long long* counter = s->d_counter;
-    gspd::k_zero_u64<<<1, 1, 0, st>>>(counter);
-    gspd::k_trace<<<gsp_trace_grid(s->ctx->device), kTraceThreads, 0, st>>>(
-        gsp_dev_scene(s), (const float4*)d_rays, n, d_tri, d_t, (float2*)d_uv, counter);
+    if (n > s->rlist_cap) {  // refine list sized for the largest batch seen (worst case: every ray)
+        GSP_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(s->d_rlist);
+        s->d_rlist = nullptr;
+        s->rlist_cap = 0;
+        GSP_CUDA_TRY(cudaMalloc(&s->d_rlist, (size_t)n * sizeof(int2)));
+        s->rlist_cap = n;
+    }
+    const gspd::DevScene S = gsp_dev_scene(s);
+    gspd::k_zero_u64x2<<<1, 1, 0, st>>>(s->d_counter);
+    const int grid = gsp_trace_grid(s->ctx->device);
+    gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, (const float4*)d_rays, n, d_tri, d_t, (float2*)d_uv,
+                                                  s->d_counter, s->d_rlist);
+    gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, (const float4*)d_rays, s->d_rlist, s->d_counter, d_t,
+                                                          (float2*)d_uv);
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
 }
@@ -323,7 +466,7 @@ gsp_status gsp_bvh_export(gsp_scene* s, int32_t set, float* h_nodes, float* h_tr
     if (set < 0 || set >= s->bvh.link_sets) return GSP_ERR_INVALID_ARG;
     if (nodes_out) *nodes_out = s->bvh.nnodes;
     if (h_nodes)
-        std::memcpy(h_nodes, s->bvh.nodes.data() + (size_t)set * s->bvh.nnodes * 2,
+        std::memcpy(h_nodes, s->bvh.nodes.data() + (size_t)set * s->bvh.stride * 2,
                     s->bvh.nnodes * 2 * sizeof(float4));
     if (h_tris) std::memcpy(h_tris, s->bvh.tris.data(), s->bvh.tris.size() * sizeof(float4));
     return GSP_OK;

@@ -94,6 +94,7 @@ struct DevScene {
     const float4* __restrict__ shade;  // per triangle (upload order): normal xyz, material bits
     const float4* __restrict__ mats;   // 2 per material
     int64_t nnodes;
+    int64_t stride;  // nodes per link set in memory (nnodes + 1 padding node)
     int32_t link_sets;
     int32_t* status;
 };
@@ -120,11 +121,11 @@ __device__ __forceinline__ float safe_inv(float d) {
 // FP32 slab test conservative (Ize 2013).
 #define GSP_ROBUST_FAR 1.0000003576278687f
 
-// The triangle is chosen in FP32; its distance and barycentrics are then re-evaluated in FP64
-// from the exact vertices. FP32 Moller-Trumbore loses relative accuracy in t when the ray origin
-// is far from the vertex compared with t (cancellation in o - v0); one FP64 evaluation per ray
-// removes that without slowing the traversal loop.
-__device__ __forceinline__ void refine_hit(const float4* __restrict__ tri, float3 of, float3 df, Hit& h) {
+// The triangle is chosen in FP32. Its t can lose relative accuracy when the ray origin is far
+// from the triangle compared with t, or the ray is grazing (cancellation in o - v0 and in det);
+// hit_error_factor() estimates that amplification and refine_hit() re-evaluates t, u, v in FP64
+// from the exact vertices for the hits that need it.
+__device__ __forceinline__ bool refine_hit(const float4* __restrict__ tri, float3 of, float3 df, Hit& h) {
     const float4 A = __ldg(tri), B = __ldg(tri + 1), C = __ldg(tri + 2);
     const double ax = A.x, ay = A.y, az = A.z;
     const double e1x = (double)B.x - ax, e1y = (double)B.y - ay, e1z = (double)B.z - az;
@@ -132,81 +133,155 @@ __device__ __forceinline__ void refine_hit(const float4* __restrict__ tri, float
     const double dx = df.x, dy = df.y, dz = df.z;
     const double px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
     const double det = e1x * px + e1y * py + e1z * pz;
-    if (det == 0.0) return;
+    if (det == 0.0) return false;
     const double f = __drcp_rn(det);
     const double sx = (double)of.x - ax, sy = (double)of.y - ay, sz = (double)of.z - az;
     const double qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
     h.u = (float)(f * (sx * px + sy * py + sz * pz));
     h.v = (float)(f * (dx * qx + dy * qy + dz * qz));
     h.t = (float)(f * (e2x * qx + e2y * qy + e2z * qz));
+    return true;
 }
 
-// Closest hit by the stackless traversal of Fig. 3: follow the hit link (index + 1) when the
-// node's box is hit, the miss link otherwise; leaves run Moller-Trumbore on their triangles.
-// The lexicographic (t, triangle index) minimum over tmin < t < tmax is kept.
-__device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, float tmin, float tmax) {
-    Hit h;
-    h.id = -1;
-    h.t = tmax;
-    h.u = h.v = 0.0f;
-    const float3 inv = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+// Relative-error amplification of the FP32 t of a hit, (|s| / (t |d|) + 1) |e1| |e2| |d| / |det|
+// in L1 norms; FP32 Moller-Trumbore errs by about 1e-7 times this. Also returns FP32 (u, v).
+__device__ __forceinline__ float hit_error_factor(const float4* __restrict__ tri, float3 o, float3 d, float t,
+                                                  float& u, float& v) {
+    const float4 A = __ldg(tri), B = __ldg(tri + 1), C = __ldg(tri + 2);
+    const float3 v0 = f3(A);
+    const float3 e1 = f3(B) - v0, e2 = f3(C) - v0;
+    const float3 p = cross3(d, e2);
+    const float det = dot3(e1, p);
+    const float3 s = o - v0;
+    const float f = 1.0f / det;
+    u = f * dot3(s, p);
+    v = f * dot3(d, cross3(s, e1));
+    const float l1d = fabsf(d.x) + fabsf(d.y) + fabsf(d.z);
+    const float l1s = fabsf(s.x) + fabsf(s.y) + fabsf(s.z);
+    const float l1e = (fabsf(e1.x) + fabsf(e1.y) + fabsf(e1.z)) * (fabsf(e2.x) + fabsf(e2.y) + fabsf(e2.z));
+    return (l1s / (t * l1d) + 1.0f) * l1e * l1d / fabsf(det);
+}
+
+// Hits whose estimated amplification exceeds this are re-evaluated in FP64 (expected FP32
+// relative error below about 64 * 6e-8 ~ 4e-6 for the rest).
+#define GSP_REFINE_FACTOR 64.0f
+
+// Traversal state of one ray (Fig. 3): current node in the ray's link set, best hit so far.
+struct Trav {
+    float3 o, d, inv;
+    float tmin, tbest;
+    int32_t best, slot, node, steps;
+    const float4* __restrict__ nodes;
+};
+
+__device__ __forceinline__ void trav_init(const DevScene& S, float3 o, float3 d, float tmin, float tmax, Trav& st) {
+    st.o = o;
+    st.d = d;
+    st.inv = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    st.tmin = tmin;
+    st.tbest = tmax;
+    st.best = -1;
+    st.slot = -1;
+    st.node = 0;
+    st.steps = 0;
     const int c = S.link_sets == 6 ? ray_class(d) : 0;
-    const float4* __restrict__ nodes = S.nodes + (size_t)c * (size_t)S.nnodes * 2;
+    st.nodes = S.nodes + (size_t)c * (size_t)S.stride * 2;
+}
+
+// Moller-Trumbore on the triangles [first, first + cnt) of the leaf-ordered triangle array,
+// keeping the lexicographic (t, triangle index) minimum over tmin < t < best t.
+__device__ __forceinline__ void trav_leaf(const DevScene& S, Trav& st, int32_t first, int32_t cnt) {
+    const float3 o = st.o, d = st.d;
+    for (int32_t k = 0; k < cnt; ++k) {
+        const float4 P = __ldg(S.tris + 3 * (first + k));
+        const float4 V1 = __ldg(S.tris + 3 * (first + k) + 1);
+        const float4 V2 = __ldg(S.tris + 3 * (first + k) + 2);
+        const float3 v0 = f3(P);
+        const float3 e1 = f3(V1) - v0, e2 = f3(V2) - v0;
+        const float3 p = cross3(d, e2);
+        const float det = dot3(e1, p);
+        if (det == 0.0f) continue;
+        const float f = 1.0f / det;
+        const float3 s = o - v0;
+        const float u = f * dot3(s, p);
+        const float3 q = cross3(s, e1);
+        const float v = f * dot3(d, q);
+        const float t = f * dot3(e2, q);
+        const int32_t id = __float_as_int(P.w);
+        if (u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t > st.tmin &&
+            (t < st.tbest || (t == st.tbest && st.best >= 0 && id < st.best))) {
+            st.tbest = t;
+            st.best = id;
+            st.slot = first + k;
+        }
+    }
+}
+
+// Box test of a node {A, B} = {min.xyz, miss | max.xyz, leaf word} against [tmin, best t]
+// (conservative FP32 slab test). Returns true on a hit; `word` and `miss` receive the links.
+__device__ __forceinline__ bool box_hit(const Trav& st, const float4& A, const float4& B, int32_t& word, int32_t& miss) {
+    const float3 o = st.o, inv = st.inv;
+    const float t0x = __fmul_rn(A.x - o.x, inv.x), t1x = __fmul_rn(B.x - o.x, inv.x);
+    const float t0y = __fmul_rn(A.y - o.y, inv.y), t1y = __fmul_rn(B.y - o.y, inv.y);
+    const float t0z = __fmul_rn(A.z - o.z, inv.z), t1z = __fmul_rn(B.z - o.z, inv.z);
+    const float tn = fmaxf(st.tmin, fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z)));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
+    tf = fminf(st.tbest, tf * GSP_ROBUST_FAR);
+    miss = __float_as_int(A.w);
+    word = __float_as_int(B.w);
+    return tn <= tf;
+}
+
+// One step of the stackless traversal (Fig. 3): on a box hit follow the hit link (index + 1),
+// running Moller-Trumbore on a leaf's triangles first (a leaf's hit link is its miss link);
+// otherwise follow the miss link. The node after the current one in preorder (the first child
+// of an internal node) comes with the same fetch, so a descent tests two boxes per step.
+__device__ __forceinline__ void trav_step(const DevScene& S, Trav& st) {
+    const float4* np = st.nodes + 2 * st.node;
+    const float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2), D = __ldg(np + 3);
+    int32_t word, miss;
+    if (!box_hit(st, A, B, word, miss)) {
+        st.node = miss;
+    } else if (word >= 0) {
+        trav_leaf(S, st, word >> 3, word & 7);
+        st.node = miss;
+    } else {
+        int32_t w2, m2;
+        if (!box_hit(st, C, D, w2, m2)) {
+            st.node = m2;
+        } else if (w2 >= 0) {
+            trav_leaf(S, st, w2 >> 3, w2 & 7);
+            st.node = m2;
+        } else {
+            st.node = st.node + 2;
+        }
+    }
+}
+
+// Closest hit of one ray (used by the eye and photon passes): traversal to the end, then the
+// winner's t, u, v re-evaluated in FP64 (always, or only when the FP32 value may be
+// inaccurate). SPPM hit points always take the FP64 value: photons near the gather radius then
+// fall on the same side of it as in an exact evaluation far more often.
+template <bool ALWAYS_REFINE>
+__device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, float tmin, float tmax) {
+    Trav st;
+    trav_init(S, o, d, tmin, tmax, st);
     const int64_t cap = 2 * S.nnodes + 8;
-    int32_t node = 0, hit_slot = -1;
-    int64_t steps = 0;
-    while (node >= 0) {
-        if (++steps > cap) {
+    while (st.node >= 0) {
+        if (++st.steps > cap) {
             report(S.status, -4);
             break;
         }
-        const float4 A = __ldg(nodes + 2 * node);
-        const float4 B = __ldg(nodes + 2 * node + 1);
-        float t0x = __fmul_rn(A.x - o.x, inv.x), t1x = __fmul_rn(B.x - o.x, inv.x);
-        float t0y = __fmul_rn(A.y - o.y, inv.y), t1y = __fmul_rn(B.y - o.y, inv.y);
-        float t0z = __fmul_rn(A.z - o.z, inv.z), t1z = __fmul_rn(B.z - o.z, inv.z);
-        float tn = fmaxf(tmin, fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z)));
-        float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
-        tf = fminf(h.t, tf * GSP_ROBUST_FAR);
-        const int32_t miss = __float_as_int(A.w);
-        const int32_t word = __float_as_int(B.w);
-        if (tn <= tf) {
-            if (word >= 0) {
-                const int32_t first = word >> 3, cnt = word & 7;
-                for (int32_t k = 0; k < cnt; ++k) {
-                    const float4 P = __ldg(S.tris + 3 * (first + k));
-                    const float4 V1 = __ldg(S.tris + 3 * (first + k) + 1);
-                    const float4 V2 = __ldg(S.tris + 3 * (first + k) + 2);
-                    const float3 v0 = f3(P);
-                    const float3 e1 = f3(V1) - v0, e2 = f3(V2) - v0;
-                    const float3 p = cross3(d, e2);
-                    const float det = dot3(e1, p);
-                    if (det == 0.0f) continue;
-                    const float f = 1.0f / det;
-                    const float3 s = o - v0;
-                    const float u = f * dot3(s, p);
-                    const float3 q = cross3(s, e1);
-                    const float v = f * dot3(d, q);
-                    const float t = f * dot3(e2, q);
-                    const int32_t id = __float_as_int(P.w);
-                    if (u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t > tmin &&
-                        (t < h.t || (t == h.t && h.id >= 0 && id < h.id))) {
-                        h.t = t;
-                        h.id = id;
-                        h.u = u;
-                        h.v = v;
-                        hit_slot = first + k;
-                    }
-                }
-                node = miss;
-            } else {
-                node = node + 1;
-            }
-        } else {
-            node = miss;
-        }
+        trav_step(S, st);
     }
-    if (hit_slot >= 0) refine_hit(S.tris + 3 * hit_slot, o, d, h);
+    Hit h;
+    h.id = st.best;
+    h.t = st.tbest;
+    h.u = h.v = 0.0f;
+    if (st.slot >= 0) {
+        const float4* tri = S.tris + 3 * st.slot;
+        if (ALWAYS_REFINE || hit_error_factor(tri, o, d, h.t, h.u, h.v) > GSP_REFINE_FACTOR) refine_hit(tri, o, d, h);
+    }
     return h;
 }
 

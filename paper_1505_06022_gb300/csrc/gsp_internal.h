@@ -14,10 +14,11 @@
 // {v0.xyz, triangle index}, {v1.xyz, 0}, {v2.xyz, 0}.
 struct HostBVH {
     int64_t nnodes = 0;
+    int64_t stride = 0;  // nodes per link set in memory: nnodes + 1 (one padding node)
     int64_t nleaves = 0;
     int32_t depth = 0;
     int32_t link_sets = 0;
-    std::vector<float4> nodes;  // link_sets * nnodes * 2
+    std::vector<float4> nodes;  // link_sets * stride * 2
     std::vector<float4> tris;   // nt * 3, leaf order
     double build_ms = 0, thread_ms = 0;
 };
@@ -53,7 +54,9 @@ struct gsp_scene {
     float4* d_mats = nullptr;   // per material: {albedo.rgb, type bits}, {emission.rgb, ior}
     float4* d_nodes = nullptr;
     float4* d_tris = nullptr;
-    unsigned long long* d_counter = nullptr;  // work counter of the persistent trace kernel
+    unsigned long long* d_counter = nullptr;  // trace kernel: next ray, refine-list length
+    int2* d_rlist = nullptr;                  // trace kernel: hits re-evaluated in FP64
+    int64_t rlist_cap = 0;
     bool built = false;
     HostBVH bvh;
     int64_t device_bytes = 0;

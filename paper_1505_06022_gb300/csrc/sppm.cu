@@ -176,7 +176,7 @@ k_eye(DevScene S, CamDev C, PassDev P, float4* __restrict__ hx, float4* __restri
     float4 rx = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), rn = make_float4(0, 0, 0, 0),
            rf = make_float4(0, 0, 0, 0);
     for (int depth = 0; depth <= P.max_eye; ++depth) {
-        const Hit h = traverse(S, o, d, tmin, __int_as_float(0x7f800000));
+        const Hit h = traverse<true>(S, o, d, tmin, __int_as_float(0x7f800000));
         if (h.id < 0) break;
         const float4 sh = __ldg(S.shade + h.id);
         const float3 n = f3(sh);
@@ -290,7 +290,7 @@ k_photon_full(DevScene S, EmitDev E, PassDev P, DepositDev D) {
     emit_photon(E, rng, o, d, phi);
     uint32_t ndep = 0;
     for (int depth = 0; depth < P.max_photon; ++depth) {
-        const Hit h = traverse(S, o, d, P.eps, __int_as_float(0x7f800000));
+        const Hit h = traverse<true>(S, o, d, P.eps, __int_as_float(0x7f800000));
         if (h.id < 0) break;
         const uint32_t id = (uint32_t)k * kSlotsPerPath + depth;
         const uint32_t slot = (uint32_t)k * kSlotsPerPath + ndep;
@@ -323,7 +323,7 @@ k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R) {
             start = true;
         }
         uint32_t ndep = 0;
-        const Hit h = traverse(S, o, d, P.eps, __int_as_float(0x7f800000));
+        const Hit h = traverse<true>(S, o, d, P.eps, __int_as_float(0x7f800000));
         if (h.id < 0) {
             alive = false;
         } else if (!photon_bounce(S, P, D, rng, h, o, d, phi, (uint32_t)j, (uint32_t)j, ndep)) {
