@@ -215,6 +215,16 @@ void gsp_sppm_destroy(gsp_sppm* r);
  * update N' = N + alpha M, R' = R sqrt((N + alpha M) / (N + M)), tau' = (tau + Phi) R'^2/R^2. */
 gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
 
+/* Execution tuning of the passes (results do not depend on the first two; the third trades
+ * accuracy of hit distances for time). eye_steps / photon_steps: wavefront steps (closest hit of
+ * a compacted ray queue, then shading that pushes continuing paths to the next queue) before the
+ * remaining paths finish one per thread; default 1 and 1 (the first rays of all paths go through
+ * the closest-hit kernel together; later wavefront steps each wait for their slowest ray, which in
+ * scenes with long rays costs more than it saves).
+ * refine_factor: wavefront hits whose estimated FP32 error amplification exceeds it take the FP64
+ * distance; 0 (default) = every hit. Paths traced one per thread always take the FP64 value. */
+gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, float refine_factor);
+
 /* Writes the current estimate L = direct / P + tau / (pi R^2 N_e) to d_rgb [h][w][3] float. */
 gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream);
 

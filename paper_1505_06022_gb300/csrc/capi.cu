@@ -31,16 +31,24 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // to a list that k_refine re-evaluates in FP64 with full warps.
 // ctr[0] = next ray, ctr[1] = refine-list length.
 __global__ void __launch_bounds__(kTraceThreads, GSP_TRACE_MIN_BLOCKS)
-k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* __restrict__ tri,
-        float* __restrict__ tout, float2* __restrict__ uv, unsigned long long* __restrict__ ctr,
-        int2* __restrict__ rlist) {
+k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* __restrict__ d_n,
+        int32_t* __restrict__ tri, float* __restrict__ tout, float2* __restrict__ uv,
+        unsigned long long* __restrict__ ctr, int2* __restrict__ rlist, float refine_factor, int32_t out_slot) {
+    if (d_n) n = min(n, (int64_t)*d_n);  // wavefront queues: the length lives on the device
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     const int32_t cap = (int32_t)min(4 * S.nnodes + 16, (int64_t)INT32_MAX);  // box tests incl. retests
     Trav st;
     st.node = -1;
     st.slot = -1;
-    int64_t ray = -1, qbase = 0, qend = 0;
+    // first chunk of each warp is static (no atomic: an empty or short batch costs no
+    // contention); later chunks come from the counter, which starts after all static chunks
+    // ray indices fit in 31 bits (the entry point rejects larger batches)
+    const int32_t n32 = (int32_t)n;
+    const int32_t static_end = (int32_t)min((int64_t)gridDim.x * (blockDim.x >> 5) * kTraceChunk, n);
+    int32_t ray = -1;
+    int32_t qbase = (int32_t)min(((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTraceChunk, n);
+    int32_t qend = min(qbase + kTraceChunk, n32);
     int32_t pend = -1;  // leaf word of a postponed leaf, -1 = none
     bool done = false;
     while (true) {
@@ -49,20 +57,20 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* __restr
         while (m) {
             if (qbase >= qend) {
                 unsigned long long b = 0;
-                if (lane == 0) b = atomicAdd(ctr, (unsigned long long)kTraceChunk);
+                if (static_end < n32 && lane == 0) b = atomicAdd(ctr, (unsigned long long)kTraceChunk);
                 b = __shfl_sync(0xffffffffu, b, 0);
-                qbase = (int64_t)b;
-                qend = min(qbase + kTraceChunk, n);
-                if (qbase >= n) {
+                qbase = (int32_t)min((int64_t)static_end + (int64_t)b, n);
+                qend = min(qbase + kTraceChunk, n32);
+                if (qbase >= n32) {
                     done = true;
                     break;
                 }
             }
-            const int take = min(__popc(m), (int)(qend - qbase));
+            const int take = min(__popc(m), qend - qbase);
             const int rank = __popc(m & lt);
             if (need && rank < take) {
                 ray = qbase + rank;
-                const float4 a = __ldcs(rays + 2 * ray), b = __ldcs(rays + 2 * ray + 1);
+                const float4 a = __ldcs(rays + 2 * (int64_t)ray), b = __ldcs(rays + 2 * (int64_t)ray + 1);
                 trav_init(S, f3(a), f3(b), a.w, b.w, st);
                 need = false;
             }
@@ -129,8 +137,8 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* __restr
         if (fin) {
             float u = 0.0f, v = 0.0f;
             if (st.slot >= 0)
-                flag = hit_error_factor(S.tris + 3 * st.slot, st.o, st.d, st.tbest, u, v) > GSP_REFINE_FACTOR;
-            __stcs(tri + ray, st.best);
+                flag = hit_error_factor(S.tris + 3 * st.slot, st.o, st.d, st.tbest, u, v) > refine_factor;
+            __stcs(tri + ray, out_slot ? st.slot : st.best);
             __stcs(tout + ray, st.best >= 0 ? st.tbest : __int_as_float(0x7f800000));
             if (uv) __stcs(uv + ray, make_float2(u, v));
         }
@@ -192,6 +200,30 @@ int gsp_trace_grid(int device) {
     int g = std::max(1, sms) * std::max(1, per_sm);
     if (device >= 0 && device < 64) cached[device] = g;
     return g;
+}
+
+cudaError_t gsp_trace_queue(const gsp_scene* s, const float4* rays, int64_t max_n, const uint32_t* d_n, int32_t* tri,
+                            float* t, float refine_factor, bool zero_counters, bool out_slot, cudaStream_t st) {
+    const gspd::DevScene S = gsp_dev_scene(s);
+    const int grid = gsp_trace_grid(s->ctx->device);
+    const bool list = refine_factor < INFINITY;
+    if (list || zero_counters) gspd::k_zero_u64x2<<<1, 1, 0, st>>>(s->d_counter);
+    gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, rays, max_n, d_n, tri, t, nullptr, s->d_counter, s->d_rlist,
+                                                  refine_factor, out_slot ? 1 : 0);
+    if (list) gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, rays, s->d_rlist, s->d_counter, t, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t gsp_scene_reserve_rays(gsp_scene* s, int64_t n) {
+    if (n <= s->rlist_cap) return cudaSuccess;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    cudaFree(s->d_rlist);
+    s->d_rlist = nullptr;
+    s->rlist_cap = 0;
+    e = cudaMalloc(&s->d_rlist, (size_t)n * sizeof(int2));
+    if (e == cudaSuccess) s->rlist_cap = n;
+    return e;
 }
 
 gspd::DevScene gsp_dev_scene(const gsp_scene* s) {
@@ -432,8 +464,8 @@ gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, i
     const gspd::DevScene S = gsp_dev_scene(s);
     gspd::k_zero_u64x2<<<1, 1, 0, st>>>(s->d_counter);
     const int grid = gsp_trace_grid(s->ctx->device);
-    gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, (const float4*)d_rays, n, d_tri, d_t, (float2*)d_uv,
-                                                  s->d_counter, s->d_rlist);
+    gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, (const float4*)d_rays, n, nullptr, d_tri, d_t,
+                                                  (float2*)d_uv, s->d_counter, s->d_rlist, GSP_REFINE_FACTOR, 0);
     gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, (const float4*)d_rays, s->d_rlist, s->d_counter, d_t,
                                                           (float2*)d_uv);
     GSP_CUDA_TRY(cudaGetLastError());

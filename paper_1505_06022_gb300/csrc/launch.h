@@ -15,7 +15,7 @@ constexpr int kTraceThreads = 128;
 #define GSP_TRACE_LEAF_BATCH 12
 #endif
 #ifndef GSP_TRACE_MIN_BLOCKS
-#define GSP_TRACE_MIN_BLOCKS 10
+#define GSP_TRACE_MIN_BLOCKS 9
 #endif
 constexpr int kTraceChunk = GSP_TRACE_CHUNK;           // rays a warp takes from the global counter at once
 constexpr int kTraceInner = GSP_TRACE_INNER;           // traversal steps between refills
@@ -24,3 +24,13 @@ constexpr int kTraceLeafBatch = GSP_TRACE_LEAF_BATCH;  // pending leaves that tr
 // Persistent grid size of the closest-hit kernel: SMs x resident blocks per SM.
 int gsp_trace_grid(int device);
 gspd::DevScene gsp_dev_scene(const gsp_scene* s);
+
+// Closest hit of rays already on the device (a wavefront queue) whose count is read from d_n.
+// With a finite refine_factor, hits whose error factor exceeds it get the FP64 distance (and the
+// scene's trace counters are reset first); with refine_factor = INFINITY nothing is re-evaluated
+// and the counters are reset only if zero_counters is set (else the caller has reset them).
+// out_slot: tri receives the hit's leaf-ordered triangle slot instead of its upload-order index.
+cudaError_t gsp_trace_queue(const gsp_scene* s, const float4* rays, int64_t max_n, const uint32_t* d_n, int32_t* tri,
+                            float* t, float refine_factor, bool zero_counters, bool out_slot, cudaStream_t st);
+// Grows the scene's FP64 re-evaluation list to hold n rays (synchronises the device first).
+cudaError_t gsp_scene_reserve_rays(gsp_scene* s, int64_t n);

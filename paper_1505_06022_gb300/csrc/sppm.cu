@@ -42,6 +42,7 @@ struct EmitDev {
 };
 
 struct PassDev {
+    int32_t tri_is_id;  // wavefront hits: 1 = upload-order triangle index, 0 = leaf-ordered slot
     uint64_t seed;
     uint32_t scene_id, pass;
     float alpha, rr, eps, inv_h;
@@ -152,13 +153,112 @@ __device__ __forceinline__ uint32_t bucket_of(float3 x, float inv_h, uint32_t ma
 }
 
 // ------------------------------------------------------------------------------------------
+// wavefront queues: a ray per entry plus the path state that continues after its hit
+// ------------------------------------------------------------------------------------------
+struct PathQ {
+    float4* ray;   // 2 per entry: {o, tmin}, {d, tmax} (the closest-hit input layout)
+    float4* w;     // eye: {throughput, pixel bits}; photon: {flux, path bits}
+    int4* rng;     // PRNG state after the draws so far
+    int32_t* meta; // depth | deposits << 8
+    int32_t* tri;  // closest-hit output
+    float* t;
+};
+
+// A wavefront hit given as a leaf-ordered triangle slot: FP64 distance from the slot's exact
+// vertices (every lane of the shade kernel does this, so the FP64 work runs in full warps);
+// returns the triangle's upload-order index.
+__device__ __forceinline__ int32_t slot_refine(const DevScene& S, float3 o, float3 d, Hit& h) {
+    const float4* tri = S.tris + 3 * (int64_t)h.id;
+    refine_hit(tri, o, d, h);
+    return __float_as_int(__ldg(tri).w);
+}
+
+// Appends the lanes with `keep` set to queue Q (warp-aggregated: one atomic per warp).
+__device__ __forceinline__ void queue_push(const PathQ& Q, uint32_t* count, bool keep, float3 o, float tmin, float3 d,
+                                           float3 w, int32_t tag, const Rng& rng, int32_t meta) {
+    const uint32_t m = __ballot_sync(0xffffffffu, keep);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!keep) return;
+    const uint32_t j = base + __popc(m & ((1u << lane) - 1u));
+    Q.ray[2 * (size_t)j] = make_float4(o.x, o.y, o.z, tmin);
+    Q.ray[2 * (size_t)j + 1] = make_float4(d.x, d.y, d.z, __int_as_float(0x7f800000));
+    Q.w[j] = make_float4(w.x, w.y, w.z, __int_as_float(tag));
+    Q.rng[j] = make_int4(rng.s[0], rng.s[1], rng.s[2], rng.s[3]);
+    Q.meta[j] = meta;
+}
+
+__device__ __forceinline__ Rng rng_from(int4 v) {
+    Rng r;
+    r.s[0] = v.x;
+    r.s[1] = v.y;
+    r.s[2] = v.z;
+    r.s[3] = v.w;
+    return r;
+}
+
+// ------------------------------------------------------------------------------------------
 // eye pass: jittered pinhole ray, specular chain, first non-specular hit (Sec. 2)
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
-k_eye(DevScene S, CamDev C, PassDev P, float4* __restrict__ hx, float4* __restrict__ hn,
-      float4* __restrict__ hf, float4* __restrict__ st1) {
+struct EyeOut {
+    float4* __restrict__ hx;
+    float4* __restrict__ hn;
+    float4* __restrict__ hf;
+    float4* __restrict__ st1;
+};
+
+// One eye-path interaction at a hit. Emission seen from the front is added to the pixel;
+// a diffuse hit records the hit point and ends the path; a mirror or dielectric bends the ray
+// (returns true: the path continues from x along the new d).
+__device__ __forceinline__ bool eye_interact(const DevScene& S, const PassDev& P, const EyeOut& O, int64_t p,
+                                             const Hit& h, float3& o, float3& d, float3& w, Rng& rng) {
+    const float4 sh = __ldg(S.shade + h.id);
+    const float3 n = f3(sh);
+    const int32_t mid = __float_as_int(sh.w);
+    const Material m = load_mat(S, mid);
+    const bool front = dot3(d, n) < 0.0f;
+    if (front && emits(m)) {
+        float4 s1 = O.st1[p];
+        s1.x += w.x * m.emission.x;
+        s1.y += w.y * m.emission.y;
+        s1.z += w.z * m.emission.z;
+        O.st1[p] = s1;
+    }
+    if (m.type == GSP_EMITTER) return false;
+    const float3 x = o + d * h.t;
+    if (m.type == GSP_DIFFUSE) {
+        const float3 ns = front ? n : n * -1.0f;
+        const float3 f = mul3(w, m.albedo) * (1.0f / kPi);
+        O.hx[p] = make_float4(x.x, x.y, x.z, __int_as_float(mid));
+        O.hn[p] = make_float4(ns.x, ns.y, ns.z, 0.0f);
+        O.hf[p] = make_float4(f.x, f.y, f.z, 0.0f);
+        return false;
+    }
+    if (m.type == GSP_MIRROR) {
+        w = mul3(w, m.albedo);
+        d = reflect3(d, n);
+    } else {
+        d = dielectric(d, n, m.ior, rng_next(rng));
+    }
+    o = x;
+    return true;
+}
+
+// Primary rays: one per pixel, jittered inside the pixel; the queue starts in pixel order.
+__global__ void __launch_bounds__(256)
+k_eye_emit(CamDev C, PassDev P, PathQ Q, EyeOut O, uint32_t* __restrict__ qn, unsigned long long* __restrict__ trace_ctr) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= (int64_t)C.w * C.h) return;
+    const int64_t npix = (int64_t)C.w * C.h;
+    if (p == 0) {
+        trace_ctr[0] = 0ull;
+        qn[0] = (uint32_t)npix;
+        qn[1] = 0;
+        qn[2] = 0;
+    }
+    if (p >= npix) return;
     const int px = (int)(p % C.w), py = (int)(p / C.w);
     Rng rng = rng_seed(P.seed, P.scene_id, 0u, P.pass, (uint64_t)p);
     const float u0 = rng_next(rng), u1 = rng_next(rng);
@@ -168,49 +268,65 @@ k_eye(DevScene S, CamDev C, PassDev P, float4* __restrict__ hx, float4* __restri
     const double dx = C.fwd.x + C.right.x * sx + C.up.x * sy, dy = C.fwd.y + C.right.y * sx + C.up.y * sy,
                  dz = C.fwd.z + C.right.z * sx + C.up.z * sy;
     const double il = rsqrt(dx * dx + dy * dy + dz * dz);
-    float3 d = make_float3((float)(dx * il), (float)(dy * il), (float)(dz * il));
-    float3 o = C.eye;
-    float3 w = make_float3(1.0f, 1.0f, 1.0f);
-    float3 direct = make_float3(0.0f, 0.0f, 0.0f);
-    float tmin = 0.0f;
-    float4 rx = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1)), rn = make_float4(0, 0, 0, 0),
-           rf = make_float4(0, 0, 0, 0);
-    for (int depth = 0; depth <= P.max_eye; ++depth) {
-        const Hit h = traverse<true>(S, o, d, tmin, __int_as_float(0x7f800000));
-        if (h.id < 0) break;
-        const float4 sh = __ldg(S.shade + h.id);
-        const float3 n = f3(sh);
-        const int32_t mid = __float_as_int(sh.w);
-        const Material m = load_mat(S, mid);
-        const bool front = dot3(d, n) < 0.0f;
-        if (front && emits(m)) direct = direct + mul3(w, m.emission);
-        if (m.type == GSP_EMITTER) break;
-        const float3 x = o + d * h.t;
-        if (m.type == GSP_DIFFUSE) {
-            const float3 ns = front ? n : n * -1.0f;
-            rx = make_float4(x.x, x.y, x.z, __int_as_float(mid));
-            rn = make_float4(ns.x, ns.y, ns.z, 0.0f);
-            const float3 f = mul3(w, m.albedo) * (1.0f / kPi);
-            rf = make_float4(f.x, f.y, f.z, 0.0f);
-            break;
-        }
-        if (m.type == GSP_MIRROR) {
-            w = mul3(w, m.albedo);
-            d = reflect3(d, n);
-        } else {
-            d = dielectric(d, n, m.ior, rng_next(rng));
-        }
-        o = x;
-        tmin = P.eps;
+    Q.ray[2 * p] = make_float4(C.eye.x, C.eye.y, C.eye.z, 0.0f);
+    Q.ray[2 * p + 1] = make_float4((float)(dx * il), (float)(dy * il), (float)(dz * il), __int_as_float(0x7f800000));
+    Q.w[p] = make_float4(1.0f, 1.0f, 1.0f, __int_as_float((int32_t)p));
+    Q.rng[p] = make_int4(rng.s[0], rng.s[1], rng.s[2], rng.s[3]);
+    Q.meta[p] = 0;
+    O.hx[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
+}
+
+// Wavefront step b of the eye pass: shade the traced queue qn[b % 3], push continuing paths.
+__global__ void __launch_bounds__(256)
+k_eye_shade(DevScene S, PassDev P, PathQ cur, PathQ nxt, EyeOut O, uint32_t* __restrict__ qn, int b,
+            unsigned long long* __restrict__ trace_ctr) {
+    const uint32_t n = qn[b % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        qn[(b + 2) % 3] = 0;
+        trace_ctr[0] = 0ull;  // for the next step's closest-hit launch
     }
-    hx[p] = rx;
-    hn[p] = rn;
-    hf[p] = rf;
-    float4 s1 = st1[p];
-    s1.x += direct.x;
-    s1.y += direct.y;
-    s1.z += direct.z;
-    st1[p] = s1;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        bool keep = false;
+        float3 o, d, w;
+        Rng rng;
+        int32_t p = 0, depth = 0;
+        if (i < n) {
+            const float4 a = cur.ray[2 * (size_t)i], c = cur.ray[2 * (size_t)i + 1], ww = cur.w[i];
+            o = f3(a);
+            d = f3(c);
+            w = f3(ww);
+            p = __float_as_int(ww.w);
+            depth = cur.meta[i];
+            rng = rng_from(cur.rng[i]);
+            Hit h;
+            h.id = cur.tri[i];
+            h.t = cur.t[i];
+            if (h.id >= 0 && !P.tri_is_id) h.id = slot_refine(S, o, d, h);
+            if (h.id >= 0) {
+                keep = eye_interact(S, P, O, p, h, o, d, w, rng) && depth + 1 <= P.max_eye;
+            }
+        }
+        queue_push(nxt, qn + (b + 1) % 3, keep, o, P.eps, d, w, p, rng, depth + 1);
+    }
+}
+
+// The eye paths still in queue qn[b % 3] after the wavefront steps, finished one per thread.
+__global__ void __launch_bounds__(128)
+k_eye_tail(DevScene S, PassDev P, PathQ cur, EyeOut O, const uint32_t* __restrict__ qn, int b) {
+    const uint32_t n = qn[b % 3];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = cur.ray[2 * (size_t)i], c = cur.ray[2 * (size_t)i + 1], ww = cur.w[i];
+        float3 o = f3(a), d = f3(c), w = f3(ww);
+        float tmin = a.w;
+        const int32_t p = __float_as_int(ww.w);
+        Rng rng = rng_from(cur.rng[i]);
+        for (int depth = cur.meta[i]; depth <= P.max_eye; ++depth) {
+            const Hit h = traverse<true>(S, o, d, tmin, __int_as_float(0x7f800000));
+            if (h.id < 0 || !eye_interact(S, P, O, p, h, o, d, w, rng)) break;
+            tmin = P.eps;
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -281,22 +397,92 @@ __device__ __forceinline__ bool photon_bounce(const DevScene& S, const PassDev& 
     return true;
 }
 
-__global__ void __launch_bounds__(128)
-k_photon_full(DevScene S, EmitDev E, PassDev P, DepositDev D) {
+// Photon paths: emission into the queue in path order (whole paths per pass).
+__global__ void __launch_bounds__(256)
+k_photon_emit(EmitDev E, PassDev P, PathQ Q, uint32_t* __restrict__ pcount, uint32_t* __restrict__ qn,
+              unsigned long long* __restrict__ trace_ctr) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) {
+        trace_ctr[0] = 0ull;
+        qn[0] = (uint32_t)P.np;
+        qn[1] = 0;
+        qn[2] = 0;
+    }
     if (k >= P.np) return;
     Rng rng = rng_seed(P.seed, P.scene_id, 1u, P.pass, (uint64_t)k);
     float3 o, d, phi;
     emit_photon(E, rng, o, d, phi);
-    uint32_t ndep = 0;
-    for (int depth = 0; depth < P.max_photon; ++depth) {
-        const Hit h = traverse<true>(S, o, d, P.eps, __int_as_float(0x7f800000));
-        if (h.id < 0) break;
-        const uint32_t id = (uint32_t)k * kSlotsPerPath + depth;
-        const uint32_t slot = (uint32_t)k * kSlotsPerPath + ndep;
-        if (!photon_bounce(S, P, D, rng, h, o, d, phi, id, slot, ndep)) break;
+    Q.ray[2 * k] = make_float4(o.x, o.y, o.z, P.eps);
+    Q.ray[2 * k + 1] = make_float4(d.x, d.y, d.z, __int_as_float(0x7f800000));
+    Q.w[k] = make_float4(phi.x, phi.y, phi.z, __int_as_float((int32_t)k));
+    Q.rng[k] = make_int4(rng.s[0], rng.s[1], rng.s[2], rng.s[3]);
+    Q.meta[k] = 0;
+    pcount[k] = 0;
+}
+
+// Wavefront step b of the photon pass: shade the traced queue qn[b % 3] (deposit, Russian
+// roulette, new direction) and push the paths that go on.
+__global__ void __launch_bounds__(256)
+k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32_t* __restrict__ qn, int b,
+               unsigned long long* __restrict__ trace_ctr) {
+    const uint32_t n = qn[b % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        qn[(b + 2) % 3] = 0;
+        trace_ctr[0] = 0ull;  // for the next step's closest-hit launch
     }
-    D.pcount[k] = ndep;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        bool keep = false;
+        float3 o, d, phi;
+        Rng rng;
+        int32_t k = 0, depth = 0;
+        uint32_t ndep = 0;
+        if (i < n) {
+            const float4 a = cur.ray[2 * (size_t)i], c = cur.ray[2 * (size_t)i + 1], ww = cur.w[i];
+            o = f3(a);
+            d = f3(c);
+            phi = f3(ww);
+            k = __float_as_int(ww.w);
+            const int32_t meta = cur.meta[i];
+            depth = meta & 0xff;
+            ndep = (uint32_t)(meta >> 8);
+            rng = rng_from(cur.rng[i]);
+            Hit h;
+            h.id = cur.tri[i];
+            h.t = cur.t[i];
+            if (h.id >= 0 && !P.tri_is_id) h.id = slot_refine(S, o, d, h);
+            if (h.id >= 0) {
+                const uint32_t id = (uint32_t)k * kSlotsPerPath + depth;
+                const uint32_t slot = (uint32_t)k * kSlotsPerPath + ndep;
+                const uint32_t before = ndep;
+                keep = photon_bounce(S, P, D, rng, h, o, d, phi, id, slot, ndep) && depth + 1 < P.max_photon;
+                if (ndep != before) D.pcount[k] = ndep;
+            }
+        }
+        queue_push(nxt, qn + (b + 1) % 3, keep, o, P.eps, d, phi, k, rng, (depth + 1) | (int32_t)(ndep << 8));
+    }
+}
+
+// The photon paths still in queue qn[b % 3] after the wavefront steps, finished one per thread.
+__global__ void __launch_bounds__(128)
+k_photon_tail(DevScene S, PassDev P, DepositDev D, PathQ cur, const uint32_t* __restrict__ qn, int b) {
+    const uint32_t n = qn[b % 3];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = cur.ray[2 * (size_t)i], c = cur.ray[2 * (size_t)i + 1], ww = cur.w[i];
+        float3 o = f3(a), d = f3(c), phi = f3(ww);
+        const int32_t k = __float_as_int(ww.w);
+        const int32_t meta = cur.meta[i];
+        uint32_t ndep = (uint32_t)(meta >> 8);
+        Rng rng = rng_from(cur.rng[i]);
+        for (int depth = meta & 0xff; depth < P.max_photon; ++depth) {
+            const Hit h = traverse<true>(S, o, d, P.eps, __int_as_float(0x7f800000));
+            if (h.id < 0) break;
+            const uint32_t id = (uint32_t)k * kSlotsPerPath + depth;
+            const uint32_t slot = (uint32_t)k * kSlotsPerPath + ndep;
+            if (!photon_bounce(S, P, D, rng, h, o, d, phi, id, slot, ndep)) break;
+        }
+        D.pcount[k] = ndep;
+    }
 }
 
 struct RegenDev {
@@ -553,6 +739,12 @@ struct gsp_sppm {
     float4 *ro = nullptr, *rd = nullptr, *rphi = nullptr;
     unsigned long long* started = nullptr;
     uint32_t* last_order = nullptr;  // sorted slot order of the last exact pass
+    // wavefront queues (ping-pong) and their tuning
+    PathQ q[2]{};
+    int64_t qcap = 0;
+    int32_t eye_steps = 1;      // eye wavefront steps before the per-thread paths
+    int32_t photon_steps = 1;   // photon wavefront steps before the per-thread paths
+    float refine_factor = 0.0f; // SPPM hits: always take the FP64 distance
     int64_t passes = 0;
     std::vector<void*> allocs;
 };
@@ -715,6 +907,19 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         A(&r->entry, r->T);
         A(&r->ecount, r->T);
     }
+    r->qcap = std::max(r->npix, P.photon_mode == GSP_FULL_PATH ? r->np : (int64_t)0);
+    r->eye_steps = 1;     // one wavefront step (all primary / first photon rays through the
+    r->photon_steps = 1;  // closest-hit kernel), then per-thread paths: in scenes with long rays
+                          // every further step waits for its slowest ray and costs more than it saves
+    for (int b = 0; b < 2; ++b) {
+        A(&r->q[b].ray, 2 * r->qcap);
+        A(&r->q[b].w, r->qcap);
+        A(&r->q[b].rng, r->qcap);
+        A(&r->q[b].meta, r->qcap);
+        A(&r->q[b].tri, r->qcap);
+        A(&r->q[b].t, r->qcap);
+    }
+    if (e == cudaSuccess) e = gsp_scene_reserve_rays(s, r->qcap);
     if (P.photon_mode == GSP_REGEN) {
         A(&r->ro, r->np);
         A(&r->rd, r->np);
@@ -766,17 +971,41 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
     P.max_photon = r->P.max_photon_depth;
     P.tmask = (uint32_t)(r->T - 1);
     P.np = r->np;
+    P.tri_is_id = r->refine_factor > 0.0f ? 1 : 0;
     EmitDev E{r->d_emit, r->d_cdf, r->nemit};
     const bool stoch = r->P.hash_mode == GSP_STOCHASTIC;
     DepositDev D{r->slots, r->pcount, r->entry, r->ecount, stoch ? 1 : 0};
 
-    k_eye<<<blocks(r->npix, 128), 128, 0, st>>>(S, r->cam, P, r->hx, r->hn, r->hf, r->st1);
+    uint32_t* qn = r->counters + 4;  // wavefront queue lengths (three, used in rotation)
+    const unsigned sblocks = (unsigned)std::min<int64_t>(blocks(r->qcap, 256), 4 * 152);
+    // ---- eye pass: wavefront steps, then the few remaining specular chains per thread ----
+    const EyeOut O{r->hx, r->hn, r->hf, r->st1};
+    unsigned long long* tctr = s->d_counter;
+    const bool list = r->refine_factor > 0.0f;  // 0: every hit takes the FP64 distance in the shade kernel
+    const float rf = list ? r->refine_factor : INFINITY;
+    k_eye_emit<<<blocks(r->npix, 256), 256, 0, st>>>(r->cam, P, r->q[0], O, qn, tctr);
+    int b = 0;
+    for (; b < r->eye_steps; ++b) {
+        const PathQ& cur = r->q[b & 1];
+        GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->npix, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
+        k_eye_shade<<<sblocks, 256, 0, st>>>(S, P, cur, r->q[(b + 1) & 1], O, qn, b, tctr);
+    }
+    // one thread per remaining path (the queue length is only known on the device)
+    if (b <= r->P.max_eye_depth) k_eye_tail<<<blocks(r->npix, 128), 128, 0, st>>>(S, P, r->q[b & 1], O, qn, b);
+    // ---- photon pass ----
     if (stoch) {
         k_fill_u64<<<1024, 256, 0, st>>>(r->entry, r->T, ~0ull);
         GSP_CUDA_TRY(cudaMemsetAsync(r->ecount, 0, r->T * sizeof(uint32_t), st));
     }
     if (r->P.photon_mode == GSP_FULL_PATH) {
-        k_photon_full<<<blocks(r->np, 128), 128, 0, st>>>(S, E, P, D);
+        k_photon_emit<<<blocks(r->np, 256), 256, 0, st>>>(E, P, r->q[0], r->pcount, qn, tctr);
+        for (b = 0; b < r->photon_steps; ++b) {
+            const PathQ& cur = r->q[b & 1];
+            GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->np, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
+            k_photon_shade<<<sblocks, 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
+        }
+        if (b < r->P.max_photon_depth)
+            k_photon_tail<<<blocks(r->np, 128), 128, 0, st>>>(S, P, D, r->q[b & 1], qn, b);
     } else {
         RegenDev R{r->ro, r->rd, r->rphi, r->started};
         k_photon_regen<<<blocks(r->np, 128), 128, 0, st>>>(S, E, P, D, R);
@@ -814,6 +1043,16 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
     }
     GSP_CUDA_TRY(cudaGetLastError());
     r->passes += 1;
+    return GSP_OK;
+}
+
+gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, float refine_factor) {
+    if (!r || eye_steps < 0 || eye_steps > 64 || photon_steps < 0 || photon_steps > kSlotsPerPath ||
+        !(refine_factor >= 0.0f))
+        return GSP_ERR_INVALID_ARG;
+    r->eye_steps = eye_steps;
+    r->photon_steps = photon_steps;
+    r->refine_factor = refine_factor;
     return GSP_OK;
 }
 

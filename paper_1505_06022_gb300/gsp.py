@@ -35,7 +35,7 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_trace_closest_hit", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
-       "gsp_hash_grid_build_static"]
+       "gsp_hash_grid_build_static", "gsp_sppm_tune"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -109,6 +109,7 @@ def lib():
             L.gsp_sppm_sync.argtypes = [P]
             L.gsp_hash_grid_build.argtypes = [P, P, I64, C.c_float, I64, P, P, P]
             L.gsp_hash_grid_build_static.argtypes = [P, I64, C.c_float, I64, P, P, P]
+            L.gsp_sppm_tune.argtypes = [P, I32, I32, C.c_float]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
             _lib = L
     return _lib
@@ -257,6 +258,10 @@ def gsp_sppm_create(scene, params: dict):
     return h
 
 
+def gsp_sppm_tune(r, eye_steps=4, photon_steps=10, refine_factor=0.0):
+    _check("gsp_sppm_tune", lib().gsp_sppm_tune(r, eye_steps, photon_steps, refine_factor))
+
+
 def gsp_sppm_destroy(r):
     lib().gsp_sppm_destroy(r)
 
@@ -359,6 +364,9 @@ class Renderer:
 
     def run(self, npasses=1, stream=None):
         gsp_sppm_pass(self.h, npasses, stream)
+
+    def tune(self, eye_steps=4, photon_steps=10, refine_factor=0.0):
+        gsp_sppm_tune(self.h, eye_steps, photon_steps, refine_factor)
 
     def image(self, stream=None):
         import torch
