@@ -98,6 +98,10 @@ def lib():
         L.orc_mlcg_step_many.argtypes = [I32, P, I64, P]
         L.orc_sppm_update.argtypes = [I64, C.c_double, P, P, P, P, P]
         L.orc_hash_grid.argtypes = [P, I64, C.c_double, I64, P, P, P, P]
+        L.orc_sppm_enable_grad.restype = I32
+        L.orc_sppm_enable_grad.argtypes = [P]
+        L.orc_sppm_grad.restype = I32
+        L.orc_sppm_grad.argtypes = [P, P, P, P]
         _lib = L
     return _lib
 
@@ -254,6 +258,20 @@ class Sppm:
         rc = lib().orc_sppm_run(self.handle, npasses, nthreads or nthreads_default())
         if rc != 0:
             raise RuntimeError("oracle: scene has no emitter")
+
+    def enable_grad(self):
+        """Carry forward-mode derivatives (every material's albedo, the emitter's emission)."""
+        if lib().orc_sppm_enable_grad(self.handle) != 0:
+            raise RuntimeError("oracle: gradients need full paths, one emitting material, no pass run yet")
+
+    def grad(self, g):
+        """Gradient of sum(g * image) w.r.t. (albedo [nmat, 3], emission [3])."""
+        g = np.ascontiguousarray(g, np.float64).reshape(-1, 3)
+        ga = np.zeros((len(self.mats), 3))
+        gl = np.zeros(3)
+        if lib().orc_sppm_grad(self.handle, _p(g), _p(ga), _p(gl)) != 0:
+            raise RuntimeError("oracle: enable_grad() and run() first")
+        return ga, gl
 
     def state(self):
         n = self.w * self.h

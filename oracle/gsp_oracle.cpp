@@ -464,16 +464,23 @@ namespace {
 const double kPi = 3.14159265358979323846;
 enum { DIFFUSE = 0, MIRROR = 1, DIELECTRIC = 2, EMITTER = 3 };
 
+// Derivative vectors (forward mode, for the gradient check): entry [c * NG + j] is the
+// derivative of channel c with respect to parameter j; parameters 0..nmat-1 are the materials'
+// albedos (same channel), parameter nmat is the emission of the single emitting material.
+typedef std::vector<double> Deriv;
+
 struct Photon {
     V3 x, din, phi;
     uint32_t id;
     float z;  // random depth (stochastic hashing)
+    Deriv dphi;
 };
 
 struct HitPoint {
     bool valid;
     V3 x, n, w;
     int mat;
+    Deriv dw;
 };
 
 struct Sppm {
@@ -494,6 +501,10 @@ struct Sppm {
     std::vector<V3> ro, rd, rphi;
     std::vector<int> rdepth;
     std::vector<char> ralive;
+    // forward-mode derivatives (grad mode only)
+    bool grad = false;
+    int NG = 0, emit_mat = -1;
+    std::vector<double> dtau, ddirect;  // [npix][3 * NG]
     // last pass diagnostics
     std::vector<Photon> last_photons;
     std::vector<HitPoint> last_hits;
@@ -551,8 +562,10 @@ Hit trace(const Sppm& S, const V3& o, const V3& d, double tmin) {
 }
 
 // Eye pass for one pixel: jittered pinhole ray, specular chain, first non-specular hit.
-HitPoint eye_path(const Sppm& S, int64_t pix, V3& direct_add) {
-    HitPoint hp{false, {}, {}, {}, 0};
+HitPoint eye_path(const Sppm& S, int64_t pix, V3& direct_add, double* ddirect_add) {
+    HitPoint hp{false, {}, {}, {}, 0, {}};
+    const int NG = S.NG;
+    Deriv dw(S.grad ? 3 * NG : 0, 0.0);
     int W = S.cam.width, H = S.cam.height;
     int px = (int)(pix % W), py = (int)(pix / W);
     Rng rng = rng_seed(S.P.seed, S.P.scene_id, 0, (uint32_t)S.passes, (uint64_t)pix);
@@ -569,14 +582,30 @@ HitPoint eye_path(const Sppm& S, int64_t pix, V3& direct_add) {
         const Tri& T = S.mesh->tris[h.id];
         const orc_material& m = S.mats[T.mat];
         bool front = dot(d, T.n) < 0;
-        if (emits(m) && front) direct_add = direct_add + mul(w, emission(m));
+        if (emits(m) && front) {
+            direct_add = direct_add + mul(w, emission(m));
+            if (S.grad) {
+                const double le[3] = {m.emission[0], m.emission[1], m.emission[2]}, wc[3] = {w.x, w.y, w.z};
+                for (int c = 0; c < 3; ++c) {
+                    for (int j = 0; j < NG; ++j) ddirect_add[c * NG + j] += dw[c * NG + j] * le[c];
+                    if (T.mat == S.emit_mat) ddirect_add[c * NG + NG - 1] += wc[c];
+                }
+            }
+        }
         if (m.type == EMITTER) break;
         V3 x = o + d * h.t;
         if (m.type == DIFFUSE) {
-            hp = {true, x, front ? T.n : T.n * -1.0, w, T.mat};
+            hp = {true, x, front ? T.n : T.n * -1.0, w, T.mat, dw};
             break;
         }
         if (m.type == MIRROR) {
+            if (S.grad) {  // w' = w * a_m
+                const double a[3] = {m.albedo[0], m.albedo[1], m.albedo[2]}, wc[3] = {w.x, w.y, w.z};
+                for (int c = 0; c < 3; ++c) {
+                    for (int j = 0; j < NG; ++j) dw[c * NG + j] *= a[c];
+                    dw[c * NG + T.mat] += wc[c];
+                }
+            }
             w = mul(w, albedo(m));
             d = reflect(d, T.n);
         } else {  // dielectric
@@ -591,7 +620,7 @@ HitPoint eye_path(const Sppm& S, int64_t pix, V3& direct_add) {
 
 // Photon emission: pick an emitting triangle with probability proportional to
 // area * mean(Le), a uniform point on it, a cosine-distributed direction about its normal.
-void emit(const Sppm& S, Rng& rng, V3& o, V3& d, V3& phi) {
+void emit(const Sppm& S, Rng& rng, V3& o, V3& d, V3& phi, Deriv* dphi) {
     float u0 = rng_next(rng);
     size_t j = std::upper_bound(S.cdf.begin(), S.cdf.end(), (double)u0) - S.cdf.begin();
     if (j >= S.emitters.size()) j = S.emitters.size() - 1;
@@ -605,28 +634,48 @@ void emit(const Sppm& S, Rng& rng, V3& o, V3& d, V3& phi) {
     V3 le = emission(m);
     double mean = (le.x + le.y + le.z) / 3.0;
     phi = le * (kPi * S.emit_total / mean);
+    if (dphi) {  // one emitting material: phi_c = pi * A * Le_c, linear in Le_c
+        dphi->assign(3 * S.NG, 0.0);
+        const double pc[3] = {phi.x, phi.y, phi.z}, lc[3] = {le.x, le.y, le.z};
+        for (int c = 0; c < 3; ++c) (*dphi)[c * S.NG + S.NG - 1] = lc[c] > 0 ? pc[c] / lc[c] : kPi * S.emit_total / mean;
+    }
 }
 
 enum Step { CONTINUE, STOP };
 
 // One photon bounce at a hit (shared by both photon modes). Appends a deposit at diffuse hits.
 Step photon_bounce(const Sppm& S, Rng& rng, const Hit& h, V3& o, V3& d, V3& phi, uint32_t id,
-                   std::vector<Photon>& out) {
+                   std::vector<Photon>& out, Deriv* dphi) {
     const Tri& T = S.mesh->tris[h.id];
     const orc_material& m = S.mats[T.mat];
     if (m.type == EMITTER) return STOP;
     V3 x = o + d * h.t;
     if (m.type == DIFFUSE) {
-        Photon p{x, d, phi, id, 0.0f};
+        Photon p{x, d, phi, id, 0.0f, dphi ? *dphi : Deriv()};
         if (S.P.hash_mode == 1) p.z = rng_next(rng);
         out.push_back(p);
         float urr = rng_next(rng);
         if (!((double)urr < (double)S.P.rr_continue)) return STOP;
+        if (dphi) {  // phi' = phi * rho_m / p_c
+            const double rr = (double)S.P.rr_continue, a[3] = {m.albedo[0], m.albedo[1], m.albedo[2]},
+                         pc[3] = {phi.x, phi.y, phi.z};
+            for (int c = 0; c < 3; ++c) {
+                for (int j = 0; j < S.NG; ++j) (*dphi)[c * S.NG + j] *= a[c] / rr;
+                (*dphi)[c * S.NG + T.mat] += pc[c] / rr;
+            }
+        }
         phi = mul(phi, albedo(m)) * (1.0 / (double)S.P.rr_continue);
         V3 ns = dot(d, T.n) < 0 ? T.n : T.n * -1.0;
         float ua = rng_next(rng), ub = rng_next(rng);
         d = cosine_dir(ns, ua, ub);
     } else if (m.type == MIRROR) {
+        if (dphi) {  // phi' = phi * a_m
+            const double a[3] = {m.albedo[0], m.albedo[1], m.albedo[2]}, pc[3] = {phi.x, phi.y, phi.z};
+            for (int c = 0; c < 3; ++c) {
+                for (int j = 0; j < S.NG; ++j) (*dphi)[c * S.NG + j] *= a[c];
+                (*dphi)[c * S.NG + T.mat] += pc[c];
+            }
+        }
         phi = mul(phi, albedo(m));
         d = reflect(d, T.n);
     } else {
@@ -641,11 +690,13 @@ Step photon_bounce(const Sppm& S, Rng& rng, const Hit& h, V3& o, V3& d, V3& phi,
 void photons_full(Sppm& S, int64_t k, std::vector<Photon>& out) {
     Rng rng = rng_seed(S.P.seed, S.P.scene_id, 1, (uint32_t)S.passes, (uint64_t)k);
     V3 o, d, phi;
-    emit(S, rng, o, d, phi);
+    Deriv dphi;
+    emit(S, rng, o, d, phi, S.grad ? &dphi : nullptr);
     for (int depth = 0; depth < S.P.max_photon_depth; ++depth) {
         Hit h = trace(S, o, d, S.P.eps);
         if (h.id < 0) return;
-        if (photon_bounce(S, rng, h, o, d, phi, (uint32_t)(k * 32 + depth), out) == STOP) return;
+        if (photon_bounce(S, rng, h, o, d, phi, (uint32_t)(k * 32 + depth), out, S.grad ? &dphi : nullptr) == STOP)
+            return;
     }
 }
 
@@ -655,7 +706,7 @@ int photons_regen(Sppm& S, int64_t j, std::vector<Photon>& out) {
     Rng rng = rng_seed(S.P.seed, S.P.scene_id, 1, (uint32_t)S.passes, (uint64_t)j);
     int started = 0;
     if (!S.ralive[j]) {
-        emit(S, rng, S.ro[j], S.rd[j], S.rphi[j]);
+        emit(S, rng, S.ro[j], S.rd[j], S.rphi[j], nullptr);
         S.rdepth[j] = 0;
         S.ralive[j] = 1;
         started = 1;
@@ -665,7 +716,7 @@ int photons_regen(Sppm& S, int64_t j, std::vector<Photon>& out) {
         S.ralive[j] = 0;
         return started;
     }
-    if (photon_bounce(S, rng, h, S.ro[j], S.rd[j], S.rphi[j], (uint32_t)j, out) == STOP) {
+    if (photon_bounce(S, rng, h, S.ro[j], S.rd[j], S.rphi[j], (uint32_t)j, out, nullptr) == STOP) {
         S.ralive[j] = 0;
         return started;
     }
@@ -701,8 +752,10 @@ void sppm_pass(Sppm& S, int nthreads) {
     // ---- eye tracing stage ----
     std::vector<HitPoint> hits(npix);
     std::vector<V3> dadd(npix, V3{0, 0, 0});
+    const int NG = S.NG, G3 = 3 * S.NG;
     parallel_for(npix, nthreads, [&](int64_t a, int64_t b, int) {
-        for (int64_t p = a; p < b; ++p) hits[p] = eye_path(S, p, dadd[p]);
+        for (int64_t p = a; p < b; ++p)
+            hits[p] = eye_path(S, p, dadd[p], S.grad ? &S.ddirect[(size_t)p * G3] : nullptr);
     });
     for (int64_t p = 0; p < npix; ++p) {
         S.direct[3 * p] += dadd[p].x;
@@ -729,6 +782,19 @@ void sppm_pass(Sppm& S, int nthreads) {
         for (auto s : started) S.Ne += (double)s;
     // ---- range query + progressive density estimation ----
     std::vector<double> Mv(npix, 0.0), Phiv(3 * npix, 0.0);
+    std::vector<double> dPhiv(S.grad ? (size_t)npix * G3 : 0, 0.0);
+    // d(f * phi_k) for f = w * rho_{m_p} / pi (the hit point's weight), scaled by `scale`
+    auto add_dflux = [&](const HitPoint& hp, const Photon& q, double scale, double* out) {
+        const orc_material& m = S.mats[hp.mat];
+        const double a[3] = {m.albedo[0], m.albedo[1], m.albedo[2]}, wc[3] = {hp.w.x, hp.w.y, hp.w.z},
+                     pc[3] = {q.phi.x, q.phi.y, q.phi.z};
+        for (int c = 0; c < 3; ++c) {
+            const double f = wc[c] * a[c] / kPi;
+            for (int j = 0; j < NG; ++j)
+                out[c * NG + j] += scale * (hp.dw[c * NG + j] * a[c] / kPi * pc[c] + f * q.dphi[c * NG + j]);
+            out[c * NG + hp.mat] += scale * wc[c] / kPi * pc[c];
+        }
+    };
     const double h = S.P.cell_h;
     if (S.P.hash_mode == 0) {
         // exact: every photon within R (cells are only an index, keyed exactly, no hashing)
@@ -761,6 +827,8 @@ void sppm_pass(Sppm& S, int nthreads) {
                 V3 f = mul(hp.w, albedo(S.mats[hp.mat])) * (1.0 / kPi);
                 V3 sum{0, 0, 0};
                 for (int i : acc) sum = sum + mul(f, ph[i].phi);
+                if (S.grad)
+                    for (int i : acc) add_dflux(hp, ph[i], 1.0, &dPhiv[(size_t)p * G3]);
                 Mv[p] = (double)acc.size();
                 Phiv[3 * p] = sum.x;
                 Phiv[3 * p + 1] = sum.y;
@@ -810,6 +878,7 @@ void sppm_pass(Sppm& S, int nthreads) {
                             if (!(dot(dx, dx) < R * R && dot(q.din, hp.n) < 0)) continue;
                             M += (double)cnt[bb];
                             sum = sum + mul(f, q.phi) * (double)cnt[bb];
+                            if (S.grad) add_dflux(hp, q, (double)cnt[bb], &dPhiv[(size_t)p * G3]);
                         }
                 Mv[p] = M;
                 Phiv[3 * p] = sum.x;
@@ -827,6 +896,9 @@ void sppm_pass(Sppm& S, int nthreads) {
         double ratio = Nn / (S.N[p] + M);
         S.R[p] = S.R[p] * std::sqrt(ratio);
         for (int c = 0; c < 3; ++c) S.tau[3 * p + c] = (S.tau[3 * p + c] + Phiv[3 * p + c]) * ratio;
+        if (S.grad)
+            for (int g = 0; g < G3; ++g)
+                S.dtau[(size_t)p * G3 + g] = (S.dtau[(size_t)p * G3 + g] + dPhiv[(size_t)p * G3 + g]) * ratio;
         S.N[p] = Nn;
     }
     S.passes += 1;
@@ -990,6 +1062,50 @@ void orc_hash_grid(const float* xyz, int64_t n, double h, int64_t T, uint32_t* b
         while (j < n && key[j].first < b) ++j;
         bstart[b] = (uint32_t)j;
     }
+}
+
+// Forward-mode derivatives for the gradient check (whole paths per pass only). Must be called
+// before the first pass. Returns -1 unless exactly one material emits.
+int32_t orc_sppm_enable_grad(void* s) {
+    Sppm* S = (Sppm*)s;
+    if (S->passes != 0 || S->P.photon_mode != 0) return -1;
+    int em = -1;
+    for (int m = 0; m < (int)S->mats.size(); ++m)
+        if (emits(S->mats[m])) {
+            if (em >= 0) return -1;
+            em = m;
+        }
+    if (em < 0) return -1;
+    S->grad = true;
+    S->emit_mat = em;
+    S->NG = (int)S->mats.size() + 1;
+    int64_t npix = (int64_t)S->cam.width * S->cam.height;
+    S->dtau.assign((size_t)npix * 3 * S->NG, 0.0);
+    S->ddirect.assign((size_t)npix * 3 * S->NG, 0.0);
+    return 0;
+}
+
+// Gradient of sum_p sum_c g[p][c] * L[p][c] (for L2 loss, g = L - target) with respect to every
+// material's albedo (grad_albedo [nmat][3]) and the emitting material's emission (grad_le [3]):
+// dL/dtheta = d(direct)/dtheta / P + d(tau)/dtheta / (pi R^2 N_e).
+int32_t orc_sppm_grad(void* s, const double* g, double* grad_albedo, double* grad_le) {
+    Sppm* S = (Sppm*)s;
+    if (!S->grad || S->passes == 0) return -1;
+    const int NG = S->NG, nm = NG - 1;
+    const int64_t npix = (int64_t)S->cam.width * S->cam.height;
+    std::vector<double> acc(3 * NG, 0.0);
+    for (int64_t p = 0; p < npix; ++p) {
+        const double kd = 1.0 / (double)S->passes, kt = 1.0 / (kPi * S->R[p] * S->R[p] * S->Ne);
+        for (int c = 0; c < 3; ++c)
+            for (int j = 0; j < NG; ++j) {
+                const size_t i = (size_t)p * 3 * NG + c * NG + j;
+                acc[c * NG + j] += g[3 * p + c] * (S->ddirect[i] * kd + S->dtau[i] * kt);
+            }
+    }
+    for (int m = 0; m < nm; ++m)
+        for (int c = 0; c < 3; ++c) grad_albedo[3 * m + c] = acc[c * NG + m];
+    for (int c = 0; c < 3; ++c) grad_le[c] = acc[c * NG + nm];
+    return 0;
 }
 
 // The progressive update alone, for recurrence tests: applies one pass with counts M and
