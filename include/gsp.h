@@ -11,7 +11,8 @@
  *  - Every function returns gsp_status: 0 on success, a negative code otherwise. Nothing
  *    throws across the ABI. gsp_status_string() gives a static description.
  *  - Handles (gsp_context, gsp_scene, gsp_sppm) are opaque, owned by the library, and freed by
- *    the matching *_destroy call. A handle is not thread-safe; use one per host thread.
+ *    the matching *_destroy call: renderers before their scene, scenes before their context (a
+ *    handle keeps a pointer to its parent). A handle is not thread-safe; use one per host thread.
  *  - Host arrays ("h_" or documented as host) are read during the call and not retained.
  *  - Device arrays ("d_") are borrowed, caller-owned, contiguous, 16-byte aligned device
  *    memory on the context's device. They must stay valid until the stream work that uses
@@ -169,6 +170,10 @@ gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, co
                             int32_t nmat, const gsp_camera* cam, gsp_scene** out);
 void gsp_scene_destroy(gsp_scene* scene);
 
+/* Replaces the scene's material table (same count, same validation as gsp_scene_upload).
+ * Renderers created earlier keep the emitter table they were created with. */
+gsp_status gsp_scene_set_materials(gsp_scene* scene, const gsp_material* mats, int32_t nmat);
+
 /* Builds the SAH BVH and its hit/miss links on the host (Sec. 3.1), packs them, and uploads
  * them to the device (replacing any previous BVH). params NULL = defaults. stats may be NULL. */
 gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh_stats* stats);
@@ -241,6 +246,29 @@ int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity);
 
 /* Waits for the renderer's stream work and returns the first recorded device error. */
 gsp_status gsp_sppm_sync(gsp_sppm* r);
+
+/* ---- gradient of an image loss (path-replay adjoint) ------------------------------------- */
+
+/* Prepares gradients: every pass from now on records the radius each pixel gathered with
+ * (4 bytes per pixel per pass, for at most max_passes passes; more passes then fail with
+ * GSP_ERR_OVERFLOW) and the replay buffers are allocated. Call after gsp_sppm_create, before
+ * the first pass. Needs photon_mode GSP_FULL_PATH, hash_mode GSP_EXACT, at most 64 materials and
+ * exactly one emitting material (GSP_ERR_INVALID_ARG otherwise). */
+gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes);
+
+/* Gradient of a loss of the current image: d_dloss_dimg [h][w][3] float device is the loss's
+ * gradient with respect to the image (L - target for 1/2 |L - target|^2). Outputs (float
+ * device): d_grad_albedo [nmat][3], the derivative with respect to every material's albedo, and
+ * d_grad_emission [3], with respect to the emitting material's emission. Russian roulette at a
+ * constant probability makes the sampled paths, the gathered photon sets and the radii
+ * independent of the albedos, so at fixed seeds the image is a polynomial in them; this is its
+ * exact derivative. Each pass is replayed from its PRNG counters (no path is stored): its hit
+ * points gather their weight into the photons they accepted (same test, recorded radius), and a
+ * reverse walk along each photon path hands it to the albedos met before each deposit. Diffuse
+ * albedos and the emission are differentiated; mirror and dielectric albedos are held constant
+ * (their entries are 0), as are channels whose albedo is 0. The forward state is not changed. */
+gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad_albedo,
+                           float* d_grad_emission, void* stream);
 
 /* ---- hash grid (the exact deposit of the SPPM pass as a standalone operation) ------------- */
 

@@ -405,6 +405,29 @@ gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, co
     return GSP_OK;
 }
 
+gsp_status gsp_scene_set_materials(gsp_scene* s, const gsp_material* mats, int32_t nmat) {
+    if (!s || !mats || nmat != s->nmat) return GSP_ERR_INVALID_ARG;
+    for (int32_t m = 0; m < nmat; ++m) {
+        if (mats[m].type < GSP_DIFFUSE || mats[m].type > GSP_EMITTER) return GSP_ERR_INVALID_ARG;
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(mats[m].albedo[k]) || !std::isfinite(mats[m].emission[k]) || mats[m].emission[k] < 0.0f)
+                return GSP_ERR_INVALID_ARG;
+        if (mats[m].type == GSP_DIELECTRIC && !(mats[m].ior > 0.0f)) return GSP_ERR_INVALID_ARG;
+    }
+    s->mats.assign(mats, mats + nmat);
+    if (!s->ctx) return GSP_OK;
+    std::vector<float4> mt(2 * nmat);
+    for (int32_t m = 0; m < nmat; ++m) {
+        float tf;
+        std::memcpy(&tf, &mats[m].type, 4);
+        mt[2 * m] = float4{mats[m].albedo[0], mats[m].albedo[1], mats[m].albedo[2], tf};
+        mt[2 * m + 1] = float4{mats[m].emission[0], mats[m].emission[1], mats[m].emission[2], mats[m].ior};
+    }
+    GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    GSP_CUDA_TRY(cudaMemcpy(s->d_mats, mt.data(), mt.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    return GSP_OK;
+}
+
 gsp_status gsp_build_bvh(gsp_scene* s, const gsp_bvh_params* params, gsp_bvh_stats* stats) {
     if (!s) return GSP_ERR_INVALID_ARG;
     gsp_bvh_params p{16, 4, 7, 6};

@@ -208,6 +208,7 @@ struct EyeOut {
     float4* __restrict__ hn;
     float4* __restrict__ hf;
     float4* __restrict__ st1;
+    float4* __restrict__ hw;  // optional: eye throughput w of each hit point (gradient replay)
 };
 
 // One eye-path interaction at a hit. Emission seen from the front is added to the pixel;
@@ -235,6 +236,7 @@ __device__ __forceinline__ bool eye_interact(const DevScene& S, const PassDev& P
         O.hx[p] = make_float4(x.x, x.y, x.z, __int_as_float(mid));
         O.hn[p] = make_float4(ns.x, ns.y, ns.z, 0.0f);
         O.hf[p] = make_float4(f.x, f.y, f.z, 0.0f);
+        if (O.hw) O.hw[p] = make_float4(w.x, w.y, w.z, 0.0f);
         return false;
     }
     if (m.type == GSP_MIRROR) {
@@ -358,6 +360,7 @@ struct DepositDev {
     unsigned long long* __restrict__ entry;  // stochastic: min key per bucket
     uint32_t* __restrict__ ecount;       // stochastic: photons per bucket
     int32_t stochastic;
+    int32_t* __restrict__ smat;          // optional: material of each deposit's surface (gradient replay)
 };
 
 // One photon interaction at a hit. Returns false when the path ends.
@@ -370,6 +373,7 @@ __device__ __forceinline__ bool photon_bounce(const DevScene& S, const PassDev& 
     if (m.type == GSP_EMITTER) return false;
     const float3 x = o + d * h.t;
     if (m.type == GSP_DIFFUSE) {
+        if (D.smat) D.smat[slot] = __float_as_int(sh.w);
         float4* rec = D.slots + 2 * (size_t)slot;
         rec[0] = make_float4(x.x, x.y, x.z, __uint_as_float(id));
         rec[1] = make_float4(phi.x, phi.y, phi.z, __uint_as_float(oct_encode(d)));
@@ -576,6 +580,7 @@ struct GatherDev {
     const unsigned long long* __restrict__ entry;
     const uint32_t* __restrict__ ecount;
     int64_t npix;
+    float* __restrict__ rhist;  // optional: the radius each pixel gathered with (gradient)
 };
 
 // Distinct buckets of the cells that overlap the ball of radius R about x. A photon within R
@@ -603,6 +608,16 @@ __device__ __forceinline__ int query_buckets(float3 x, float R, float inv_h, uin
     return nb;
 }
 
+// The photon acceptance test of the range query, with explicit rounding so that the adjoint
+// replay decides exactly as the forward gather did: |x_k - x_p|^2 < R^2 and w_in . n_p < 0.
+__device__ __forceinline__ bool photon_accept(float3 xk, float3 xp, float R, uint32_t dir, float3 n) {
+    const float dx = __fsub_rn(xk.x, xp.x), dy = __fsub_rn(xk.y, xp.y), dz = __fsub_rn(xk.z, xp.z);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    if (!(d2 < __fmul_rn(R, R))) return false;
+    const float3 w = oct_decode(dir);
+    return __fmaf_rn(w.z, n.z, __fmaf_rn(w.y, n.y, __fmul_rn(w.x, n.x))) < 0.0f;
+}
+
 __device__ __forceinline__ void progressive_update(float4& s0, float4& s1, float M, float3 Phi, float alpha) {
     if (!(M > 0.0f)) return;
     const float N = s0.w;
@@ -626,6 +641,7 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
     const float3 f = f3(G.hf[p]);
     float4 s0 = G.st0[p], s1 = G.st1[p];
     const float R = s1.w, R2 = R * R;
+    if (G.rhist) G.rhist[p] = R;
     uint32_t buckets[27];
     const int nb = query_buckets(x, R, P.inv_h, P.tmask, buckets);
     float M = 0.0f;
@@ -637,10 +653,8 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
             if (cnt == 0) continue;
             const uint32_t slot = (uint32_t)(G.entry[b] & 0xffffffffull);
             const float4 a = __ldg(G.slots + 2 * (size_t)slot);
-            const float3 dx = f3(a) - x;
-            if (!(dot3(dx, dx) < R2)) continue;
             const float4 c = __ldg(G.slots + 2 * (size_t)slot + 1);
-            if (!(dot3(oct_decode(__float_as_uint(c.w)), n) < 0.0f)) continue;
+            if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
             const float w = (float)cnt;
             M += w;
             acc = acc + f3(c) * w;
@@ -649,9 +663,9 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
             for (uint32_t i = G.bstart[b]; i < e; ++i) {
                 const float4 a = __ldg(G.spos + i);
                 const float3 dx = f3(a) - x;
-                if (!(dot3(dx, dx) < R2)) continue;
+                if (!(dot3(dx, dx) < R2 * 1.0001f)) continue;  // cheap pre-test, then the exact one
                 const float4 c = __ldg(G.spay + i);
-                if (!(dot3(oct_decode(__float_as_uint(c.w)), n) < 0.0f)) continue;
+                if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
                 M += 1.0f;
                 acc = acc + f3(c);
             }
@@ -660,6 +674,135 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
     progressive_update(s0, s1, M, mul3(f, acc), P.alpha);
     G.st0[p] = s0;
     G.st1[p] = s1;
+}
+
+// ------------------------------------------------------------------------------------------
+// adjoint (gradient of an image loss w.r.t. diffuse albedos and emission) by pass replay
+// ------------------------------------------------------------------------------------------
+constexpr int kMaxGradMats = 64;
+
+struct AdjDev {
+    const float4* __restrict__ hx;      // replayed hit points: x, material bits (< 0: none)
+    const float4* __restrict__ hn;
+    const float4* __restrict__ hf;      // w * albedo / pi
+    const float4* __restrict__ hw;      // w (eye throughput)
+    const float* __restrict__ rhist;    // radius each pixel gathered with in this pass
+    const float* __restrict__ g;        // dLoss/dL [npix][3]
+    const uint32_t* __restrict__ hp_order;   // hit-point grid: pixel at each sorted position
+    const uint32_t* __restrict__ hp_bstart;
+    uint32_t hp_mask;
+    float inv_hp;                       // 1 / hit-point cell size
+    float rmax;                         // largest gather radius (r0)
+    const float4* __restrict__ spos;    // deposits of the pass, bucket-sorted
+    const float4* __restrict__ spay;
+    const uint32_t* __restrict__ order; // sorted deposit -> photon slot
+    const uint32_t* __restrict__ d_total;
+    float4* __restrict__ badj;          // per slot: B_k, the weight of Phi_k in the loss
+    double* __restrict__ acc;           // [nmat][3] albedo accumulators (before 1 / (pi N_e))
+    int32_t nmat;
+};
+
+// Photon-centric adjoint gather. For deposit k the hit points that gathered it in the forward
+// pass (same acceptance test, same radii) give B_k = sum_p g_p (w rho / pi)_p / R_p^2, and their
+// own albedo terms g_p (w_p / pi) Phi_k / R_p^2 add to acc[m_p].
+__global__ void __launch_bounds__(128) k_adj_photons(AdjDev A) {
+    __shared__ double s_acc[kMaxGradMats * 3];
+    for (int i = threadIdx.x; i < A.nmat * 3; i += blockDim.x) s_acc[i] = 0.0;
+    __syncthreads();
+    const int64_t nd = (int64_t)*A.d_total;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = A.spos[i], c = A.spay[i];
+        const float3 xk = f3(a), phik = f3(c);
+        const uint32_t dir = __float_as_uint(c.w);
+        uint32_t buckets[27];
+        const int nb = query_buckets(xk, A.rmax, A.inv_hp, A.hp_mask, buckets);
+        float3 B = make_float3(0.0f, 0.0f, 0.0f);
+        for (int q = 0; q < nb; ++q) {
+            const uint32_t b = buckets[q], e = A.hp_bstart[b + 1];
+            for (uint32_t j = A.hp_bstart[b]; j < e; ++j) {
+                const uint32_t p = A.hp_order[j];
+                const float4 hxp = __ldg(A.hx + p);
+                const int32_t m = __float_as_int(hxp.w);
+                if (m < 0) continue;
+                const float R = __ldg(A.rhist + p);
+                if (!photon_accept(xk, f3(hxp), R, dir, f3(__ldg(A.hn + p)))) continue;
+                const float inv = 1.0f / (R * R);
+                const float3 gp = make_float3(__ldg(A.g + 3 * p), __ldg(A.g + 3 * p + 1), __ldg(A.g + 3 * p + 2));
+                B = B + mul3(gp, f3(__ldg(A.hf + p))) * inv;
+                const float3 t1 = mul3(mul3(gp, f3(__ldg(A.hw + p))), phik) * (inv * (1.0f / kPi));
+                atomicAdd(&s_acc[3 * m], (double)t1.x);
+                atomicAdd(&s_acc[3 * m + 1], (double)t1.y);
+                atomicAdd(&s_acc[3 * m + 2], (double)t1.z);
+            }
+        }
+        A.badj[A.order[i]] = make_float4(B.x, B.y, B.z, 0.0f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.nmat * 3; i += blockDim.x)
+        if (s_acc[i] != 0.0) atomicAdd(&A.acc[i], s_acc[i]);
+}
+
+// Path terms: Phi_j of deposit j carries rho_m / p_c for every diffuse bounce on material m before
+// it, so dLoss/drho_m gains sum over those bounces b of (sum_{j > b} B_j Phi_j) / rho_m (per
+// channel; channels with rho = 0 are skipped). A reverse walk over each path's deposits keeps
+// that suffix sum.
+__global__ void __launch_bounds__(128)
+k_adj_paths(const float4* __restrict__ slots, const uint32_t* __restrict__ pcount, const int32_t* __restrict__ smat,
+            const float4* __restrict__ badj, const float4* __restrict__ mats, int64_t np, double* __restrict__ acc,
+            int32_t nmat) {
+    __shared__ double s_acc[kMaxGradMats * 3];
+    for (int i = threadIdx.x; i < nmat * 3; i += blockDim.x) s_acc[i] = 0.0;
+    __syncthreads();
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t n = (int32_t)pcount[k];
+        float3 suffix = make_float3(0.0f, 0.0f, 0.0f);
+        for (int32_t j = n - 1; j >= 0; --j) {
+            const size_t slot = (size_t)k * kSlotsPerPath + j;
+            const int32_t m = smat[slot];
+            if (j < n - 1) {
+                const float3 al = f3(__ldg(mats + 2 * m));
+                if (al.x > 0.0f) atomicAdd(&s_acc[3 * m], (double)(suffix.x / al.x));
+                if (al.y > 0.0f) atomicAdd(&s_acc[3 * m + 1], (double)(suffix.y / al.y));
+                if (al.z > 0.0f) atomicAdd(&s_acc[3 * m + 2], (double)(suffix.z / al.z));
+            }
+            suffix = suffix + mul3(f3(badj[slot]), f3(slots[2 * slot + 1]));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nmat * 3; i += blockDim.x)
+        if (s_acc[i] != 0.0) atomicAdd(&acc[i], s_acc[i]);
+}
+
+// Emission: with one emitting material the image is linear in its Le, so dLoss/dLe_c is
+// sum_p g_pc L_pc / Le_c; this kernel sums g * L.
+__global__ void __launch_bounds__(256)
+k_adj_emission(const float4* __restrict__ st0, const float4* __restrict__ st1, const float* __restrict__ g,
+               int64_t npix, float inv_passes, double ne, double* __restrict__ acc_le) {
+    __shared__ double s[3];
+    if (threadIdx.x < 3) s[threadIdx.x] = 0.0;
+    __syncthreads();
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const float4 t = st0[p], d = st1[p];
+        const double k = 1.0 / ((double)kPi * (double)d.w * (double)d.w * ne);
+        a0 += (double)g[3 * p] * ((double)d.x * inv_passes + (double)t.x * k);
+        a1 += (double)g[3 * p + 1] * ((double)d.y * inv_passes + (double)t.y * k);
+        a2 += (double)g[3 * p + 2] * ((double)d.z * inv_passes + (double)t.z * k);
+    }
+    atomicAdd(&s[0], a0);
+    atomicAdd(&s[1], a1);
+    atomicAdd(&s[2], a2);
+    __syncthreads();
+    if (threadIdx.x < 3) atomicAdd(&acc_le[threadIdx.x], s[threadIdx.x]);
+}
+
+__global__ void k_adj_finalize(const double* __restrict__ acc, int32_t nmat, double scale, float4 le,
+                               float* __restrict__ out_albedo, float* __restrict__ out_le) {
+    for (int i = threadIdx.x; i < nmat * 3; i += blockDim.x) out_albedo[i] = (float)(acc[i] * scale);
+    if (threadIdx.x < 3) {
+        const double l = threadIdx.x == 0 ? le.x : (threadIdx.x == 1 ? le.y : le.z);
+        out_le[threadIdx.x] = l > 0.0 ? (float)(acc[nmat * 3 + threadIdx.x] / l) : 0.0f;
+    }
 }
 
 __global__ void k_image(const float4* __restrict__ st0, const float4* __restrict__ st1, int64_t npix,
@@ -717,6 +860,10 @@ __global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long 
 // ============================================================================================
 using namespace gspd;
 
+int64_t gsp_grid_scratch_words(int64_t n, int64_t T);
+gsp_status gsp_grid_build_with(const float4* pos, int64_t n, float cell_h, int64_t T, uint32_t* order,
+                               uint32_t* bstart, uint32_t* scratch, cudaStream_t st);
+
 struct gsp_sppm {
     gsp_scene* scene = nullptr;
     gsp_sppm_params P{};
@@ -745,6 +892,15 @@ struct gsp_sppm {
     int32_t eye_steps = 1;      // eye wavefront steps before the per-thread paths
     int32_t photon_steps = 1;   // photon wavefront steps before the per-thread paths
     float refine_factor = 0.0f; // SPPM hits: always take the FP64 distance
+    // gradient (pass replay) buffers, allocated by gsp_sppm_enable_grad
+    bool grad = false;
+    int32_t grad_max_passes = 0, emit_mat = -1;
+    float* rhist = nullptr;            // [max passes][npix] gather radius
+    float4 *st1_scratch = nullptr, *hw = nullptr, *badj = nullptr;
+    int32_t* smat = nullptr;
+    double* gacc = nullptr;            // [nmat * 3 + 3]
+    uint32_t *hp_order = nullptr, *hp_bstart = nullptr, *hp_scratch = nullptr;
+    int64_t hp_T = 0;
     int64_t passes = 0;
     std::vector<void*> allocs;
 };
@@ -956,13 +1112,11 @@ void gsp_sppm_destroy(gsp_sppm* r) {
     delete r;
 }
 
-static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
-    gsp_scene* s = r->scene;
-    const DevScene S = gsp_dev_scene(s);
+static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
     PassDev P;
     P.seed = r->P.seed;
     P.scene_id = r->P.scene_id;
-    P.pass = (uint32_t)r->passes;
+    P.pass = (uint32_t)pass;
     P.alpha = r->P.alpha;
     P.rr = r->P.rr_continue;
     P.eps = r->P.eps;
@@ -972,14 +1126,16 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
     P.tmask = (uint32_t)(r->T - 1);
     P.np = r->np;
     P.tri_is_id = r->refine_factor > 0.0f ? 1 : 0;
-    EmitDev E{r->d_emit, r->d_cdf, r->nemit};
-    const bool stoch = r->P.hash_mode == GSP_STOCHASTIC;
-    DepositDev D{r->slots, r->pcount, r->entry, r->ecount, stoch ? 1 : 0};
+    return P;
+}
 
+static unsigned shade_blocks(const gsp_sppm* r) { return (unsigned)std::min<int64_t>(blocks(r->qcap, 256), 4 * 152); }
+
+// Eye pass: wavefront steps, then the remaining specular chains one per thread.
+static gsp_status stage_eye(gsp_sppm* r, const PassDev& P, const EyeOut& O, cudaStream_t st) {
+    gsp_scene* s = r->scene;
+    const DevScene S = gsp_dev_scene(s);
     uint32_t* qn = r->counters + 4;  // wavefront queue lengths (three, used in rotation)
-    const unsigned sblocks = (unsigned)std::min<int64_t>(blocks(r->qcap, 256), 4 * 152);
-    // ---- eye pass: wavefront steps, then the few remaining specular chains per thread ----
-    const EyeOut O{r->hx, r->hn, r->hf, r->st1};
     unsigned long long* tctr = s->d_counter;
     const bool list = r->refine_factor > 0.0f;  // 0: every hit takes the FP64 distance in the shade kernel
     const float rf = list ? r->refine_factor : INFINITY;
@@ -988,21 +1144,34 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
     for (; b < r->eye_steps; ++b) {
         const PathQ& cur = r->q[b & 1];
         GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->npix, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
-        k_eye_shade<<<sblocks, 256, 0, st>>>(S, P, cur, r->q[(b + 1) & 1], O, qn, b, tctr);
+        k_eye_shade<<<shade_blocks(r), 256, 0, st>>>(S, P, cur, r->q[(b + 1) & 1], O, qn, b, tctr);
     }
     // one thread per remaining path (the queue length is only known on the device)
     if (b <= r->P.max_eye_depth) k_eye_tail<<<blocks(r->npix, 128), 128, 0, st>>>(S, P, r->q[b & 1], O, qn, b);
-    // ---- photon pass ----
-    if (stoch) {
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+// Photon pass: whole paths (wavefront steps + per-thread paths) or one bounce per thread.
+static gsp_status stage_photons(gsp_sppm* r, const PassDev& P, const DepositDev& D, cudaStream_t st) {
+    gsp_scene* s = r->scene;
+    const DevScene S = gsp_dev_scene(s);
+    uint32_t* qn = r->counters + 4;
+    unsigned long long* tctr = s->d_counter;
+    const bool list = r->refine_factor > 0.0f;
+    const float rf = list ? r->refine_factor : INFINITY;
+    const EmitDev E{r->d_emit, r->d_cdf, r->nemit};
+    if (D.stochastic) {
         k_fill_u64<<<1024, 256, 0, st>>>(r->entry, r->T, ~0ull);
         GSP_CUDA_TRY(cudaMemsetAsync(r->ecount, 0, r->T * sizeof(uint32_t), st));
     }
     if (r->P.photon_mode == GSP_FULL_PATH) {
         k_photon_emit<<<blocks(r->np, 256), 256, 0, st>>>(E, P, r->q[0], r->pcount, qn, tctr);
-        for (b = 0; b < r->photon_steps; ++b) {
+        int b = 0;
+        for (; b < r->photon_steps; ++b) {
             const PathQ& cur = r->q[b & 1];
             GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->np, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
-            k_photon_shade<<<sblocks, 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
+            k_photon_shade<<<shade_blocks(r), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
         }
         if (b < r->P.max_photon_depth)
             k_photon_tail<<<blocks(r->np, 128), 128, 0, st>>>(S, P, D, r->q[b & 1], qn, b);
@@ -1010,6 +1179,40 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
         RegenDev R{r->ro, r->rd, r->rphi, r->started};
         k_photon_regen<<<blocks(r->np, 128), 128, 0, st>>>(S, E, P, D, R);
     }
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+// Exact hash grid of the pass's deposits: compaction in id order, stable sort by bucket,
+// bucket starts, sorted SoA copies.
+static gsp_status stage_deposit(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
+    uint32_t* d_total = r->counters;  // deposits this pass
+    GSP_CUDA_TRY(gsp_scan_u32(r->pcount, r->poff, r->np, d_total, r->scan_tmp, st));
+    GSP_CUDA_TRY(cudaMemsetAsync(r->bcount, 0, r->T * sizeof(uint32_t), st));
+    k_compact<<<blocks(r->np, 256), 256, 0, st>>>(r->slots, r->pcount, r->poff, r->np, r->slots_per_path, r->inv_h,
+                                                  P.tmask, r->keys[0], r->vals[0], r->bcount);
+    GSP_CUDA_TRY(gsp_scan_u32(r->bcount, r->bstart, r->T, r->bstart + r->T, r->scan_tmp, st));
+    uint32_t *ko = nullptr, *vo = nullptr;
+    GSP_CUDA_TRY(gsp_radix_sort_u32(r->keys[0], r->vals[0], r->keys[1], r->vals[1], d_total, r->tbits, r->hist,
+                                    r->scan_tmp, st, &ko, &vo));
+    r->last_order = vo;
+    k_permute<<<1024, 256, 0, st>>>(r->slots, vo, d_total, r->spos, r->spay);
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
+    const PassDev P = pass_params(r, r->passes);
+    const bool stoch = r->P.hash_mode == GSP_STOCHASTIC;
+    const EyeOut O{r->hx, r->hn, r->hf, r->st1, nullptr};
+    DepositDev D{r->slots, r->pcount, r->entry, r->ecount, stoch ? 1 : 0, nullptr};
+    if (r->grad && r->passes >= r->grad_max_passes) {
+        gsp_set_last_error("gsp_sppm_pass: more passes than gsp_sppm_enable_grad reserved radius history for");
+        return GSP_ERR_OVERFLOW;
+    }
+    gsp_status e = stage_eye(r, P, O, st);
+    if (e == GSP_OK) e = stage_photons(r, P, D, st);
+    if (e != GSP_OK) return e;
     GatherDev G{};
     G.hx = r->hx;
     G.hn = r->hn;
@@ -1017,6 +1220,7 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
     G.st0 = r->st0;
     G.st1 = r->st1;
     G.npix = r->npix;
+    G.rhist = r->grad ? r->rhist + (size_t)r->passes * r->npix : nullptr;
     if (stoch) {
         G.slots = r->slots;
         G.entry = r->entry;
@@ -1025,17 +1229,8 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
         GSP_CUDA_TRY(gsp_scan_u32(r->pcount, r->poff, r->np, r->counters, r->scan_tmp, st));
         k_gather<true><<<blocks(r->npix, 128), 128, 0, st>>>(G, P);
     } else {
-        uint32_t* d_total = r->counters;  // deposits this pass
-        GSP_CUDA_TRY(gsp_scan_u32(r->pcount, r->poff, r->np, d_total, r->scan_tmp, st));
-        GSP_CUDA_TRY(cudaMemsetAsync(r->bcount, 0, r->T * sizeof(uint32_t), st));
-        k_compact<<<blocks(r->np, 256), 256, 0, st>>>(r->slots, r->pcount, r->poff, r->np, r->slots_per_path,
-                                                      r->inv_h, P.tmask, r->keys[0], r->vals[0], r->bcount);
-        GSP_CUDA_TRY(gsp_scan_u32(r->bcount, r->bstart, r->T, r->bstart + r->T, r->scan_tmp, st));
-        uint32_t *ko = nullptr, *vo = nullptr;
-        GSP_CUDA_TRY(gsp_radix_sort_u32(r->keys[0], r->vals[0], r->keys[1], r->vals[1], d_total, r->tbits,
-                                        r->hist, r->scan_tmp, st, &ko, &vo));
-        r->last_order = vo;
-        k_permute<<<1024, 256, 0, st>>>(r->slots, vo, d_total, r->spos, r->spay);
+        e = stage_deposit(r, P, st);
+        if (e != GSP_OK) return e;
         G.spos = r->spos;
         G.spay = r->spay;
         G.bstart = r->bstart;
@@ -1064,6 +1259,105 @@ gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream) {
         gsp_status s = sppm_one_pass(r, (cudaStream_t)stream);
         if (s != GSP_OK) return s;
     }
+    return GSP_OK;
+}
+
+gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
+    if (!r || max_passes < 1) return GSP_ERR_INVALID_ARG;
+    if (r->passes != 0 || r->grad) return GSP_ERR_BAD_STATE;
+    if (r->P.photon_mode != GSP_FULL_PATH || r->P.hash_mode != GSP_EXACT || r->scene->nmat > kMaxGradMats) {
+        gsp_set_last_error("gsp_sppm_enable_grad: needs whole photon paths, the exact hash grid and at most 64 materials");
+        return GSP_ERR_INVALID_ARG;
+    }
+    int em = -1;
+    for (int32_t m = 0; m < r->scene->nmat; ++m) {
+        const gsp_material& mt = r->scene->mats[m];
+        if ((mt.type == GSP_DIFFUSE || mt.type == GSP_EMITTER) &&
+            std::max({mt.emission[0], mt.emission[1], mt.emission[2]}) > 0.0f) {
+            if (em >= 0) {
+                gsp_set_last_error("gsp_sppm_enable_grad: needs exactly one emitting material");
+                return GSP_ERR_INVALID_ARG;
+            }
+            em = m;
+        }
+    }
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    r->hp_T = 1;
+    while (r->hp_T < 2 * r->npix) r->hp_T *= 2;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, int64_t n) { if (e == cudaSuccess) e = alloc(r, p, n); };
+    A(&r->rhist, (int64_t)max_passes * r->npix);
+    A(&r->st1_scratch, r->npix);
+    A(&r->hw, r->npix);
+    A(&r->badj, r->slot_cap);
+    A(&r->smat, r->slot_cap);
+    A(&r->gacc, (int64_t)kMaxGradMats * 3 + 3);
+    A(&r->hp_order, r->npix);
+    A(&r->hp_bstart, r->hp_T + 1);
+    A(&r->hp_scratch, gsp_grid_scratch_words(r->npix, r->hp_T));
+    if (e != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+    }
+    r->grad = true;
+    r->grad_max_passes = max_passes;
+    r->emit_mat = em;
+    return GSP_OK;
+}
+
+gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad_albedo, float* d_grad_emission,
+                           void* stream) {
+    if (!r || !d_dloss_dimg || !d_grad_albedo || !d_grad_emission) return GSP_ERR_INVALID_ARG;
+    if (!r->grad || r->passes < 1) return GSP_ERR_BAD_STATE;
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    (void)cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t nmat = r->scene->nmat;
+    GSP_CUDA_TRY(cudaMemsetAsync(r->gacc, 0, ((size_t)kMaxGradMats * 3 + 3) * sizeof(double), st));
+    const EyeOut O{r->hx, r->hn, r->hf, r->st1_scratch, r->hw};
+    const DepositDev D{r->slots, r->pcount, nullptr, nullptr, 0, r->smat};
+    const float hp_cell = 2.0f * r->P.r0;
+    const int grid = 4 * 152;
+    for (int64_t i = 0; i < r->passes; ++i) {
+        // replay pass i from its PRNG counters: the same hit points, photons and radii
+        const PassDev P = pass_params(r, i);
+        gsp_status e = stage_eye(r, P, O, st);
+        if (e == GSP_OK) e = stage_photons(r, P, D, st);
+        if (e == GSP_OK) e = stage_deposit(r, P, st);
+        if (e != GSP_OK) return e;
+        e = gsp_grid_build_with(r->hx, r->npix, hp_cell, r->hp_T, r->hp_order, r->hp_bstart, r->hp_scratch, st);
+        if (e != GSP_OK) return e;
+        AdjDev A;
+        A.hx = r->hx;
+        A.hn = r->hn;
+        A.hf = r->hf;
+        A.hw = r->hw;
+        A.rhist = r->rhist + (size_t)i * r->npix;
+        A.g = d_dloss_dimg;
+        A.hp_order = r->hp_order;
+        A.hp_bstart = r->hp_bstart;
+        A.hp_mask = (uint32_t)(r->hp_T - 1);
+        A.inv_hp = 1.0f / hp_cell;
+        A.rmax = r->P.r0;
+        A.spos = r->spos;
+        A.spay = r->spay;
+        A.order = r->last_order;
+        A.d_total = r->counters;
+        A.badj = r->badj;
+        A.acc = r->gacc;
+        A.nmat = nmat;
+        k_adj_photons<<<grid * 2, 128, 0, st>>>(A);
+        k_adj_paths<<<grid, 128, 0, st>>>(r->slots, r->pcount, r->smat, r->badj, r->scene->d_mats, r->np, r->gacc,
+                                          nmat);
+    }
+    const double ne = (double)r->passes * (double)r->np;
+    k_adj_emission<<<256, 256, 0, st>>>(r->st0, r->st1, d_dloss_dimg, r->npix, 1.0f / (float)r->passes, ne,
+                                        r->gacc + (size_t)nmat * 3);
+    const gsp_material& em = r->scene->mats[r->emit_mat];
+    k_adj_finalize<<<1, 256, 0, st>>>(r->gacc, nmat, 1.0 / (M_PI * ne),
+                                      make_float4(em.emission[0], em.emission[1], em.emission[2], 0.0f), d_grad_albedo,
+                                      d_grad_emission);
+    GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
 }
 

@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -35,7 +36,8 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_trace_closest_hit", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
-       "gsp_hash_grid_build_static", "gsp_sppm_tune"]
+       "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
+       "gsp_scene_set_materials"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -110,6 +112,9 @@ def lib():
             L.gsp_hash_grid_build.argtypes = [P, P, I64, C.c_float, I64, P, P, P]
             L.gsp_hash_grid_build_static.argtypes = [P, I64, C.c_float, I64, P, P, P]
             L.gsp_sppm_tune.argtypes = [P, I32, I32, C.c_float]
+            L.gsp_sppm_enable_grad.argtypes = [P, I32]
+            L.gsp_render_grad.argtypes = [P, P, P, P, P]
+            L.gsp_scene_set_materials.argtypes = [P, P, I32]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
             _lib = L
     return _lib
@@ -262,6 +267,20 @@ def gsp_sppm_tune(r, eye_steps=4, photon_steps=10, refine_factor=0.0):
     _check("gsp_sppm_tune", lib().gsp_sppm_tune(r, eye_steps, photon_steps, refine_factor))
 
 
+def gsp_sppm_enable_grad(r, max_passes):
+    _check("gsp_sppm_enable_grad", lib().gsp_sppm_enable_grad(r, max_passes))
+
+
+def gsp_render_grad(r, dloss_dimg, grad_albedo, grad_emission, stream=None):
+    rc = lib().gsp_render_grad(r, _dev(dloss_dimg), _dev(grad_albedo), _dev(grad_emission), _stream(stream))
+    _check("gsp_render_grad", rc)
+
+
+def gsp_scene_set_materials(scene, mats):
+    m = np.ascontiguousarray(mats, dtype=_inputs.MATERIAL_DTYPE)
+    _check("gsp_scene_set_materials", lib().gsp_scene_set_materials(scene, m.ctypes.data_as(C.c_void_p), len(m)))
+
+
 def gsp_sppm_destroy(r):
     lib().gsp_sppm_destroy(r)
 
@@ -299,14 +318,20 @@ def gsp_sppm_sync(r):
 
 # ------------------------------------------------------------------------- convenience owners
 class Context:
+    """Owns a gsp_context. Closing it first closes every scene (and renderer) made from it, so no
+    handle outlives the context it points to."""
+
     def __init__(self, device: int = 0):
         self.h = gsp_context_create(device)
         self.device = device
+        self._children = weakref.WeakSet()
 
     def sync(self):
         gsp_context_sync(self.h)
 
     def close(self):
+        for ch in list(self._children):
+            ch.close()
         if self.h:
             gsp_context_destroy(self.h)
             self.h = None
@@ -324,9 +349,12 @@ class Scene:
     def __init__(self, ctx, scene: "_inputs.Scene", **bvh):
         self.ctx = ctx
         self.src = scene
+        self._children = weakref.WeakSet()
         self.h = gsp_scene_upload(None if ctx is None else ctx.h, scene.verts, scene.tris, scene.tri_mat,
                                   scene.mats, scene.camera)
-        self.stats = gsp_build_bvh(self.h, **bvh) if bvh is not None else None
+        if ctx is not None:
+            ctx._children.add(self)
+        self.stats = gsp_build_bvh(self.h, **bvh)
 
     def trace(self, rays, stream=None, with_uv=False):
         import torch
@@ -341,6 +369,8 @@ class Scene:
         return gsp_bvh_host_walk(self.h, rays)
 
     def close(self):
+        for ch in list(self._children):
+            ch.close()
         if self.h:
             gsp_scene_destroy(self.h)
             self.h = None
@@ -359,6 +389,7 @@ class Renderer:
         self.scene = scene
         self.params = dict(params)
         self.h = gsp_sppm_create(scene.h, self.params)
+        scene._children.add(self)
         cam = scene.src.camera[0]
         self.w, self.h_px = int(cam["width"]), int(cam["height"])
 
@@ -389,6 +420,19 @@ class Renderer:
 
     def last_deposits(self):
         return gsp_sppm_last_deposits(self.h)
+
+    def enable_grad(self, max_passes):
+        gsp_sppm_enable_grad(self.h, max_passes)
+
+    def grad(self, dloss_dimg, stream=None):
+        """(d loss / d albedo [nmat, 3], d loss / d emission [3]) for the given image gradient."""
+        import torch
+        dev = dloss_dimg.device
+        nmat = len(self.scene.src.mats)
+        ga = torch.empty((nmat, 3), dtype=torch.float32, device=dev)
+        gl = torch.empty(3, dtype=torch.float32, device=dev)
+        gsp_render_grad(self.h, dloss_dimg.contiguous(), ga, gl, stream)
+        return ga, gl
 
     def sync(self):
         gsp_sppm_sync(self.h)
@@ -421,3 +465,51 @@ def sppm_params(scene, photons_per_pass, seed=1, alpha=0.7, r0=None, r0_frac=0.0
                 cell_h=cell_h, eps=float(np.float32(eps_frac * ext)), photon_mode=int(photon_mode),
                 hash_mode=int(hash_mode), max_eye_depth=int(max_eye_depth),
                 max_photon_depth=int(max_photon_depth), scene_id=int(scene_id))
+
+
+def emitting_material(mats) -> int:
+    """Index of the single emitting material (the one whose emission the gradient covers)."""
+    em = [i for i, m in enumerate(mats) if m["type"] in (_inputs.DIFFUSE, _inputs.EMITTER) and max(m["emission"]) > 0]
+    if len(em) != 1:
+        raise ValueError("gradients need exactly one emitting material")
+    return em[0]
+
+
+def _make_render_function():
+    import torch
+
+    class SPPMRender(torch.autograd.Function):
+        """image = SPPM render of `scene` with the given material albedos [nmat, 3] and emission [3]
+        of the emitting material; backward = gsp_render_grad (path-replay adjoint)."""
+
+        @staticmethod
+        def forward(ctx, albedo, emission, scene, params, passes):
+            mats = scene.src.mats.copy()
+            mats["albedo"] = albedo.detach().cpu().numpy()
+            em = emitting_material(mats)
+            mats["emission"][em] = emission.detach().cpu().numpy()
+            gsp_scene_set_materials(scene.h, mats)
+            r = Renderer(scene, params)
+            r.enable_grad(passes)
+            r.run(passes)
+            img = r.image()
+            ctx.renderer = r
+            return img
+
+        @staticmethod
+        def backward(ctx, grad_img):
+            ga, gl = ctx.renderer.grad(grad_img.float())
+            return ga, gl, None, None, None
+
+    return SPPMRender
+
+
+_render_fn = None
+
+
+def render(albedo, emission, scene, params, passes):
+    """Differentiable SPPM render (torch autograd): see SPPMRender."""
+    global _render_fn
+    if _render_fn is None:
+        _render_fn = _make_render_function()
+    return _render_fn.apply(albedo, emission, scene, params, passes)

@@ -1,0 +1,119 @@
+"""GPU path-replay adjoint (gsp_render_grad) against the oracle's FP64 forward-mode gradient,
+central finite differences of the GPU forward, and the torch autograd wrapper."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1505_06022_gb300 import gsp, inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KW = dict(photons_per_pass=20000, seed=4, r0_frac=0.02)
+PASSES = 3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gsp.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def case():
+    sc = I.grad_scene(width=64, height=64, plane_quads=48, sphere_n=8)
+    orc = O.Sppm(sc, O.default_params(sc, **KW))
+    orc.enable_grad()
+    orc.run(PASSES)
+    L = orc.image()
+    g = L - 0.9 * L.mean() - 0.05 * np.random.default_rng(7).standard_normal(L.shape)
+    ga, gl = orc.grad(g)
+    return sc, g, ga, gl
+
+
+def gpu_grad(ctx, sc, g):
+    s = gsp.Scene(ctx, sc)
+    r = gsp.Renderer(s, gsp.sppm_params(sc, **KW))
+    r.enable_grad(PASSES)
+    r.run(PASSES)
+    before = r.image().clone()
+    ga, gl = r.grad(torch.from_numpy(g.astype(np.float32)).cuda())
+    after = r.image()
+    torch.cuda.synchronize()
+    r.sync()
+    assert torch.equal(before, after)  # the replay leaves the forward state alone
+    return ga.cpu().numpy(), gl.cpu().numpy(), r, s
+
+
+def test_adjoint_matches_oracle_gradient(ctx, case):
+    sc, g, ga_o, gl_o = case
+    ga, gl, _, _ = gpu_grad(ctx, sc, g)
+    diffuse = sc.mats["type"] == I.DIFFUSE
+    scale = np.abs(ga_o[diffuse]).max()
+    assert scale > 0
+    err = np.abs(ga[diffuse] - ga_o[diffuse]).max()
+    assert err <= 1e-3 * scale, f"albedo gradient error {err:.3g} vs scale {scale:.3g}"
+    np.testing.assert_allclose(gl, gl_o, rtol=1e-3, atol=1e-3 * np.abs(gl_o).max())
+    assert np.all(ga[~diffuse] == 0)
+
+
+def test_adjoint_matches_gpu_central_differences(ctx, case):
+    sc, g, _, _ = case
+    ga, gl, r, s = gpu_grad(ctx, sc, g)
+
+    def objective(mats):
+        gsp.gsp_scene_set_materials(s.h, mats)
+        rr = gsp.Renderer(s, gsp.sppm_params(sc, **KW))
+        rr.run(PASSES)
+        img = rr.image().cpu().numpy().astype(np.float64)
+        return float(np.sum(g * img))
+
+    scale = np.abs(ga).max()
+    for m, c in [(1, 0), (6, 2), (13, 1)]:
+        mp, mm = sc.mats.copy(), sc.mats.copy()
+        mp["albedo"][m, c] += 1e-2
+        mm["albedo"][m, c] -= 1e-2
+        dh = float(mp["albedo"][m, c]) - float(mm["albedo"][m, c])
+        fd = (objective(mp) - objective(mm)) / dh
+        assert abs(fd - ga[m, c]) <= 2e-3 * scale, (m, c, fd, ga[m, c])
+    gsp.gsp_scene_set_materials(s.h, sc.mats)
+
+
+def test_autograd_function(ctx):
+    sc = I.grad_scene(width=32, height=32, plane_quads=24, sphere_n=4)
+    s = gsp.Scene(ctx, sc)
+    params = gsp.sppm_params(sc, photons_per_pass=8000, seed=9, r0_frac=0.03)
+    em = gsp.emitting_material(sc.mats)
+    albedo = torch.tensor(sc.mats["albedo"], device="cuda", requires_grad=True)
+    emission = torch.tensor(sc.mats["emission"][em], device="cuda", requires_grad=True)
+    target = torch.zeros((32, 32, 3), device="cuda")
+    img = gsp.render(albedo, emission, s, params, 2)
+    loss = 0.5 * ((img - target) ** 2).sum()
+    loss.backward()
+    r = gsp.Renderer(s, params)
+    r.enable_grad(2)
+    r.run(2)
+    ga, gl = r.grad((r.image() - target).contiguous())
+    torch.testing.assert_close(albedo.grad, ga, rtol=1e-4, atol=1e-6)
+    torch.testing.assert_close(emission.grad, gl, rtol=1e-4, atol=1e-6)
+
+
+def test_call_order_is_checked(ctx):
+    sc = I.grad_scene(width=16, height=16, plane_quads=16, sphere_n=3)
+    s = gsp.Scene(ctx, sc)
+    params = gsp.sppm_params(sc, photons_per_pass=1000, seed=1)
+    r = gsp.Renderer(s, params)
+    g = torch.zeros((16, 16, 3), device="cuda")
+    with pytest.raises(gsp.GspError) as e:
+        r.grad(g)  # no enable_grad
+    assert e.value.code == -7
+    r.run(1)
+    with pytest.raises(gsp.GspError):
+        r.enable_grad(4)  # after a pass
+    r2 = gsp.Renderer(s, params)
+    r2.enable_grad(1)
+    r2.run(1)
+    with pytest.raises(gsp.GspError) as e:
+        r2.run(1)  # radius history full
+    assert e.value.code == -9
