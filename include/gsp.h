@@ -105,7 +105,7 @@ typedef struct {
  *  alpha             radius reduction parameter in (0, 1]
  *  r0                initial gather radius (world units, > 0)
  *  rr_continue       Russian-roulette continue probability at diffuse hits, in (0, 1]
- *  cell_h            hash cell edge; 0 = 2 * r0. Must be >= 2 * r0 in STOCHASTIC mode.
+ *  cell_h            hash cell edge; 0 = 2 * r0. Must be >= r0 (>= 2 * r0 in STOCHASTIC mode).
  *  eps               ray offset (tmin) of every secondary ray, world units
  *  photon_mode       GSP_FULL_PATH: whole photon paths each pass; GSP_REGEN: one bounce per
  *                    pass per thread, a thread starts a new path when its path ends (Sec. 3.3)
@@ -246,6 +246,35 @@ int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity);
 
 /* Waits for the renderer's stream work and returns the first recorded device error. */
 gsp_status gsp_sppm_sync(gsp_sppm* r);
+
+/* ---- many scenes per launch, CUDA graphs, autotuning ------------------------------------ */
+
+typedef struct gsp_batch gsp_batch;
+
+/* Groups renderers (of distinct scenes on one device; each renderer in at most one batch) so
+ * that a pass of all of them runs as one CUDA graph: a branch per renderer, so the kernels of
+ * small and large scenes overlap on the GPU. The graph is captured at the first gsp_batch_pass
+ * and replayed for every pass; each branch reads its pass index from the device. Results are
+ * those of gsp_sppm_pass on each renderer. Tuning changes (gsp_sppm_tune/autotune) made after the
+ * first gsp_batch_pass do not reach the captured graph. The renderers must outlive the batch. */
+gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** out);
+void gsp_batch_destroy(gsp_batch* b);
+/* Runs npasses passes of every renderer of the batch on `stream`. */
+gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream);
+
+typedef struct {
+    int32_t eye_steps, photon_steps; /* chosen wavefront steps */
+    float cell_h;                    /* chosen hash cell edge (exact mode) */
+    float ms_per_pass;               /* its measured time per pass */
+    float first_ms_per_pass;         /* time of the first candidate (1/0/2 r0 settings order) */
+    int32_t candidates;
+} gsp_tune_result;
+
+/* Times candidate execution settings that leave the estimate unchanged -- eye and photon
+ * wavefront steps, and in exact mode the hash cell edge (2, 1.5 or 1 times r0; the gather then
+ * scans fewer photons) -- for trial_passes passes each on a temporary renderer over the same
+ * scene (the renderer's own state is not touched), and applies the fastest. out may be NULL. */
+gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out);
 
 /* ---- gradient of an image loss (path-replay adjoint) ------------------------------------- */
 

@@ -424,6 +424,7 @@ gsp_status gsp_scene_set_materials(gsp_scene* s, const gsp_material* mats, int32
         mt[2 * m + 1] = float4{mats[m].emission[0], mats[m].emission[1], mats[m].emission[2], mats[m].ior};
     }
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    (void)cudaGetLastError();
     GSP_CUDA_TRY(cudaMemcpy(s->d_mats, mt.data(), mt.size() * sizeof(float4), cudaMemcpyHostToDevice));
     return GSP_OK;
 }

@@ -43,6 +43,7 @@ struct EmitDev {
 
 struct PassDev {
     int32_t tri_is_id;  // wavefront hits: 1 = upload-order triangle index, 0 = leaf-ordered slot
+    const uint32_t* pass_dev;  // if set, the pass index is read here (replayed CUDA graphs)
     uint64_t seed;
     uint32_t scene_id, pass;
     float alpha, rr, eps, inv_h;
@@ -50,6 +51,8 @@ struct PassDev {
     uint32_t tmask;
     int64_t np;
 };
+
+__device__ __forceinline__ uint32_t pass_index(const PassDev& P) { return P.pass_dev ? *P.pass_dev : P.pass; }
 
 struct Material {
     float3 albedo, emission;
@@ -262,7 +265,7 @@ k_eye_emit(CamDev C, PassDev P, PathQ Q, EyeOut O, uint32_t* __restrict__ qn, un
     }
     if (p >= npix) return;
     const int px = (int)(p % C.w), py = (int)(p / C.w);
-    Rng rng = rng_seed(P.seed, P.scene_id, 0u, P.pass, (uint64_t)p);
+    Rng rng = rng_seed(P.seed, P.scene_id, 0u, pass_index(P), (uint64_t)p);
     const float u0 = rng_next(rng), u1 = rng_next(rng);
     // primary ray in FP64 (once per pixel), rounded once
     const double sx = (((double)px + u0) / (double)C.w * 2.0 - 1.0) * C.th * C.aspect;
@@ -413,7 +416,7 @@ k_photon_emit(EmitDev E, PassDev P, PathQ Q, uint32_t* __restrict__ pcount, uint
         qn[2] = 0;
     }
     if (k >= P.np) return;
-    Rng rng = rng_seed(P.seed, P.scene_id, 1u, P.pass, (uint64_t)k);
+    Rng rng = rng_seed(P.seed, P.scene_id, 1u, pass_index(P), (uint64_t)k);
     float3 o, d, phi;
     emit_photon(E, rng, o, d, phi);
     Q.ray[2 * k] = make_float4(o.x, o.y, o.z, P.eps);
@@ -501,7 +504,7 @@ k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool start = false;
     if (j < P.np) {
-        Rng rng = rng_seed(P.seed, P.scene_id, 1u, P.pass, (uint64_t)j);
+        Rng rng = rng_seed(P.seed, P.scene_id, 1u, pass_index(P), (uint64_t)j);
         float4 a = R.ro[j], b = R.rd[j], c = R.rphi[j];
         float3 o = f3(a), d = f3(b), phi = f3(c);
         int32_t depth = __float_as_int(a.w);
@@ -580,7 +583,7 @@ struct GatherDev {
     const unsigned long long* __restrict__ entry;
     const uint32_t* __restrict__ ecount;
     int64_t npix;
-    float* __restrict__ rhist;  // optional: the radius each pixel gathered with (gradient)
+    float* __restrict__ rhist;  // optional: [pass][npix] radius each pixel gathered with (gradient)
 };
 
 // Distinct buckets of the cells that overlap the ball of radius R about x. A photon within R
@@ -641,7 +644,7 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
     const float3 f = f3(G.hf[p]);
     float4 s0 = G.st0[p], s1 = G.st1[p];
     const float R = s1.w, R2 = R * R;
-    if (G.rhist) G.rhist[p] = R;
+    if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
     uint32_t buckets[27];
     const int nb = query_buckets(x, R, P.inv_h, P.tmask, buckets);
     float M = 0.0f;
@@ -849,6 +852,8 @@ __global__ void k_grid_keys(const float4* __restrict__ pos, int64_t n, float inv
 
 __global__ void k_store_u32(uint32_t* p, uint32_t v) { *p = v; }
 
+__global__ void k_add_u32(uint32_t* p, uint32_t v) { *p += v; }
+
 __global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -932,6 +937,7 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     *out = nullptr;
     if (!s->ctx || !s->has_cam) return GSP_ERR_INVALID_ARG;
     if (!s->built) return GSP_ERR_NOT_BUILT;
+    (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
     gsp_sppm_params P = *params;
     if (P.photons_per_pass <= 0 || P.photons_per_pass > (int64_t(1) << 27)) return GSP_ERR_INVALID_ARG;
     if (!(P.alpha > 0.0f && P.alpha <= 1.0f) || !(P.r0 > 0.0f) || !(P.rr_continue > 0.0f && P.rr_continue <= 1.0f) ||
@@ -940,7 +946,9 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         (P.hash_mode != GSP_EXACT && P.hash_mode != GSP_STOCHASTIC))
         return GSP_ERR_INVALID_ARG;
     if (P.cell_h == 0.0f) P.cell_h = 2.0f * P.r0;
-    if (!(P.cell_h > 0.0f) || (P.hash_mode == GSP_STOCHASTIC && P.cell_h < 2.0f * P.r0)) return GSP_ERR_INVALID_ARG;
+    // the range query visits at most three cells per axis: exact mode needs h >= R (R <= r0);
+    // stochastic hashing's estimator is defined with h >= 2 r0
+    if (!(P.cell_h >= P.r0) || (P.hash_mode == GSP_STOCHASTIC && P.cell_h < 2.0f * P.r0)) return GSP_ERR_INVALID_ARG;
     if (P.table_size == 0) {
         P.table_size = 1;
         while (P.table_size < 2 * P.photons_per_pass) P.table_size *= 2;
@@ -1117,6 +1125,7 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
     P.seed = r->P.seed;
     P.scene_id = r->P.scene_id;
     P.pass = (uint32_t)pass;
+    P.pass_dev = nullptr;
     P.alpha = r->P.alpha;
     P.rr = r->P.rr_continue;
     P.eps = r->P.eps;
@@ -1201,8 +1210,12 @@ static gsp_status stage_deposit(gsp_sppm* r, const PassDev& P, cudaStream_t st) 
     return GSP_OK;
 }
 
-static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
-    const PassDev P = pass_params(r, r->passes);
+// One pass on stream st. In graph mode (a pass captured once and replayed) the pass index is read
+// from the device counter counters[7], which the pass advances itself, and the host count is left
+// to the caller.
+static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false) {
+    PassDev P = pass_params(r, r->passes);
+    if (graph) P.pass_dev = r->counters + 7;
     const bool stoch = r->P.hash_mode == GSP_STOCHASTIC;
     const EyeOut O{r->hx, r->hn, r->hf, r->st1, nullptr};
     DepositDev D{r->slots, r->pcount, r->entry, r->ecount, stoch ? 1 : 0, nullptr};
@@ -1220,7 +1233,7 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
     G.st0 = r->st0;
     G.st1 = r->st1;
     G.npix = r->npix;
-    G.rhist = r->grad ? r->rhist + (size_t)r->passes * r->npix : nullptr;
+    G.rhist = r->grad ? r->rhist : nullptr;
     if (stoch) {
         G.slots = r->slots;
         G.entry = r->entry;
@@ -1236,8 +1249,9 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st) {
         G.bstart = r->bstart;
         k_gather<false><<<blocks(r->npix, 128), 128, 0, st>>>(G, P);
     }
+    if (graph) k_add_u32<<<1, 1, 0, st>>>(r->counters + 7, 1u);
     GSP_CUDA_TRY(cudaGetLastError());
-    r->passes += 1;
+    if (!graph) r->passes += 1;
     return GSP_OK;
 }
 
@@ -1308,6 +1322,7 @@ gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
 gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad_albedo, float* d_grad_emission,
                            void* stream) {
     if (!r || !d_dloss_dimg || !d_grad_albedo || !d_grad_emission) return GSP_ERR_INVALID_ARG;
+    (void)cudaGetLastError();
     if (!r->grad || r->passes < 1) return GSP_ERR_BAD_STATE;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
     (void)cudaGetLastError();
@@ -1358,6 +1373,183 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
                                       make_float4(em.emission[0], em.emission[1], em.emission[2], 0.0f), d_grad_albedo,
                                       d_grad_emission);
     GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+}  // extern "C"
+
+struct gsp_batch {
+    std::vector<gsp_sppm*> rs;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;  // private stream the graph is captured on (never the legacy stream)
+    cudaGraphExec_t exec = nullptr;
+    int32_t device = 0;
+};
+
+static void batch_free(gsp_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    for (auto e : b->joins) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+// One pass of every renderer captured as a single CUDA graph: a branch per renderer, forked
+// from and joined to the capturing stream, so the scenes' kernels overlap on the GPU.
+static gsp_status batch_capture(gsp_batch* b, cudaStream_t st) {
+    GSP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    gsp_status e = GSP_OK;
+    cudaError_t ce = cudaEventRecord(b->fork, st);
+    for (size_t i = 0; i < b->rs.size() && ce == cudaSuccess && e == GSP_OK; ++i) {
+        ce = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        if (ce == cudaSuccess) e = sppm_one_pass(b->rs[i], b->streams[i], true);
+        if (ce == cudaSuccess && e == GSP_OK) ce = cudaEventRecord(b->joins[i], b->streams[i]);
+        if (ce == cudaSuccess && e == GSP_OK) ce = cudaStreamWaitEvent(st, b->joins[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(st, &g);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess && e == GSP_OK) ce = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != GSP_OK) return e;
+    if (ce != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(ce));
+        return GSP_ERR_CUDA;
+    }
+    return GSP_OK;
+}
+
+extern "C" {
+
+gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** out) {
+    if (!renderers || n < 1 || !out) return GSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int32_t dev = renderers[0] ? renderers[0]->scene->ctx->device : -1;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!renderers[i] || renderers[i]->scene->ctx->device != dev) return GSP_ERR_INVALID_ARG;
+        for (int32_t j = 0; j < i; ++j)
+            if (renderers[j]->scene == renderers[i]->scene) {  // a scene's trace scratch is shared
+                gsp_set_last_error("gsp_batch_create: renderers of one batch need distinct scenes");
+                return GSP_ERR_INVALID_ARG;
+            }
+    }
+    GSP_CUDA_TRY(cudaSetDevice(dev));
+    gsp_batch* b = new (std::nothrow) gsp_batch;
+    if (!b) return GSP_ERR_OOM;
+    b->device = dev;
+    b->rs.assign(renderers, renderers + n);
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t j = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->streams.push_back(s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->joins.push_back(j);
+    }
+    (void)gsp_trace_grid(dev);  // fill the launch-size cache outside any capture
+    if (e != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(e));
+        batch_free(b);
+        return GSP_ERR_CUDA;
+    }
+    *out = b;
+    return GSP_OK;
+}
+
+void gsp_batch_destroy(gsp_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    batch_free(b);
+}
+
+gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
+    if (!b || npasses < 0) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(b->device));
+    (void)cudaGetLastError();
+    cudaStream_t st = (cudaStream_t)stream;
+    for (gsp_sppm* r : b->rs)
+        if (r->grad && r->passes + npasses > r->grad_max_passes) return GSP_ERR_OVERFLOW;
+    if (npasses == 0) return GSP_OK;
+    if (!b->exec) {
+        gsp_status e = batch_capture(b, b->cap);  // capture runs nothing; the graph launches on st
+        if (e != GSP_OK) return e;
+    }
+    for (gsp_sppm* r : b->rs) k_store_u32<<<1, 1, 0, st>>>(r->counters + 7, (uint32_t)r->passes);
+    for (int32_t k = 0; k < npasses; ++k) GSP_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    for (gsp_sppm* r : b->rs) r->passes += npasses;
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out) {
+    if (!r || trial_passes < 1) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    (void)cudaGetLastError();
+    gsp_sppm* t = nullptr;
+    gsp_sppm_params P = r->P;
+    gsp_status e = gsp_sppm_create(r->scene, &P, &t);
+    if (e != GSP_OK) return e;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, z = nullptr;
+    cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&a);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&z);
+    struct Cand { int32_t es, ps; float cell; };
+    std::vector<Cand> cands;
+    const bool full = r->P.photon_mode == GSP_FULL_PATH;
+    const std::vector<float> cells = r->P.hash_mode == GSP_EXACT ? std::vector<float>{2.0f, 1.5f, 1.0f}
+                                                                 : std::vector<float>{r->P.cell_h / r->P.r0};
+    for (float c : cells)
+        for (int32_t es : {0, 1, 2})
+            for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2, 4} : std::vector<int32_t>{0})
+                cands.push_back({es, ps, c * r->P.r0});
+    float best = INFINITY, first = INFINITY;
+    Cand pick = cands[0];
+    for (size_t i = 0; i < cands.size() && ce == cudaSuccess && e == GSP_OK; ++i) {
+        t->eye_steps = cands[i].es;
+        t->photon_steps = cands[i].ps;
+        t->inv_h = 1.0f / cands[i].cell;
+        e = sppm_one_pass(t, st);  // warm-up
+        if (e != GSP_OK) break;
+        ce = cudaEventRecord(a, st);
+        for (int32_t k = 0; k < trial_passes && e == GSP_OK; ++k) e = sppm_one_pass(t, st);
+        if (ce == cudaSuccess) ce = cudaEventRecord(z, st);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(z);
+        float ms = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, z);
+        ms /= (float)trial_passes;
+        if (i == 0) first = ms;
+        if (ms < best) {
+            best = ms;
+            pick = cands[i];
+        }
+    }
+    if (st) cudaStreamDestroy(st);
+    if (a) cudaEventDestroy(a);
+    if (z) cudaEventDestroy(z);
+    gsp_sppm_destroy(t);
+    if (e != GSP_OK) return e;
+    if (ce != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(ce));
+        return GSP_ERR_CUDA;
+    }
+    r->eye_steps = pick.es;
+    r->photon_steps = pick.ps;
+    r->inv_h = 1.0f / pick.cell;
+    r->P.cell_h = pick.cell;
+    if (out) {
+        out->eye_steps = pick.es;
+        out->photon_steps = pick.ps;
+        out->cell_h = pick.cell;
+        out->ms_per_pass = best;
+        out->first_ms_per_pass = first;
+        out->candidates = (int32_t)cands.size();
+    }
     return GSP_OK;
 }
 

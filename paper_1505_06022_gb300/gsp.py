@@ -37,7 +37,8 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
-       "gsp_scene_set_materials"]
+       "gsp_scene_set_materials", "gsp_batch_create", "gsp_batch_destroy", "gsp_batch_pass",
+       "gsp_sppm_autotune"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -61,6 +62,14 @@ class BvhStats(C.Structure):
     _fields_ = [("nodes", C.c_int64), ("leaves", C.c_int64), ("depth", C.c_int32),
                 ("link_sets", C.c_int32), ("build_ms", C.c_double), ("thread_ms", C.c_double),
                 ("device_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("eye_steps", C.c_int32), ("photon_steps", C.c_int32), ("cell_h", C.c_float),
+                ("ms_per_pass", C.c_float), ("first_ms_per_pass", C.c_float), ("candidates", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +124,11 @@ def lib():
             L.gsp_sppm_enable_grad.argtypes = [P, I32]
             L.gsp_render_grad.argtypes = [P, P, P, P, P]
             L.gsp_scene_set_materials.argtypes = [P, P, I32]
+            L.gsp_batch_create.argtypes = [P, I32, C.POINTER(P)]
+            L.gsp_batch_destroy.argtypes = [P]
+            L.gsp_batch_destroy.restype = None
+            L.gsp_batch_pass.argtypes = [P, I32, P]
+            L.gsp_sppm_autotune.argtypes = [P, I32, P]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
             _lib = L
     return _lib
@@ -281,6 +295,27 @@ def gsp_scene_set_materials(scene, mats):
     _check("gsp_scene_set_materials", lib().gsp_scene_set_materials(scene, m.ctypes.data_as(C.c_void_p), len(m)))
 
 
+def gsp_sppm_autotune(r, trial_passes=2) -> dict:
+    out = TuneResult()
+    _check("gsp_sppm_autotune", lib().gsp_sppm_autotune(r, trial_passes, C.byref(out)))
+    return out.as_dict()
+
+
+def gsp_batch_create(renderer_handles):
+    arr = (C.c_void_p * len(renderer_handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in renderer_handles])
+    h = C.c_void_p()
+    _check("gsp_batch_create", lib().gsp_batch_create(arr, len(renderer_handles), C.byref(h)))
+    return h
+
+
+def gsp_batch_destroy(b):
+    lib().gsp_batch_destroy(b)
+
+
+def gsp_batch_pass(b, npasses=1, stream=None):
+    _check("gsp_batch_pass", lib().gsp_batch_pass(b, npasses, _stream(stream)))
+
+
 def gsp_sppm_destroy(r):
     lib().gsp_sppm_destroy(r)
 
@@ -396,8 +431,11 @@ class Renderer:
     def run(self, npasses=1, stream=None):
         gsp_sppm_pass(self.h, npasses, stream)
 
-    def tune(self, eye_steps=4, photon_steps=10, refine_factor=0.0):
+    def tune(self, eye_steps=1, photon_steps=1, refine_factor=0.0):
         gsp_sppm_tune(self.h, eye_steps, photon_steps, refine_factor)
+
+    def autotune(self, trial_passes=2) -> dict:
+        return gsp_sppm_autotune(self.h, trial_passes)
 
     def image(self, stream=None):
         import torch
@@ -440,6 +478,31 @@ class Renderer:
     def close(self):
         if self.h:
             gsp_sppm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Renderers whose passes run together as one CUDA graph (gsp_batch_*). Closing a renderer's
+    scene or context first closes the batch."""
+
+    def __init__(self, renderers):
+        self.renderers = list(renderers)
+        self.h = gsp_batch_create([r.h for r in self.renderers])
+        for r in self.renderers:
+            r.scene._children.add(self)
+
+    def run(self, npasses=1, stream=None):
+        gsp_batch_pass(self.h, npasses, stream)
+
+    def close(self):
+        if self.h:
+            gsp_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

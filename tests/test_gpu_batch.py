@@ -1,0 +1,73 @@
+"""Batched passes (one CUDA graph over many renderers) and the autotuner, against the plain
+per-renderer passes."""
+import numpy as np
+import pytest
+
+from paper_1505_06022_gb300 import gsp, inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gsp.Context(0)
+    yield c
+    c.close()
+
+
+def scenes():
+    out = [I.cornell_box(width=48, height=40),
+           I.full_scene(seed=7, width=64, height=64, plane_quads=32, sphere_n=6),
+           I.grad_scene(seed=8, width=40, height=56, plane_quads=24, sphere_n=5),
+           I.cornell_box(seed=3, width=16, height=16)]
+    kws = [dict(photons_per_pass=9000, seed=1), dict(photons_per_pass=15000, seed=2, r0_frac=0.01),
+           dict(photons_per_pass=6000, seed=3, r0_frac=0.02), dict(photons_per_pass=4000, seed=4, photon_mode=1,
+                                                                    hash_mode=1)]
+    return out, kws
+
+
+def test_batch_graph_matches_individual_passes(ctx):
+    scs, kws = scenes()
+    solo = []
+    for sc, kw in zip(scs, kws):
+        r = gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw))
+        r.run(3)
+        solo.append(r.image().cpu().numpy())
+    rs = [gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw)) for sc, kw in zip(scs, kws)]
+    rs[0].run(1)  # a renderer that already ran a pass joins the batch at its own pass index
+    b = gsp.Batch(rs)
+    b.run(2)      # one captured graph, replayed twice: renderer 0 at 3 passes, the others at 2
+    for r in rs[1:]:
+        r.run(1)  # plain passes continue from where the graph left off
+    torch.cuda.synchronize()
+    for r, want in zip(rs, solo):
+        r.sync()
+        assert np.array_equal(r.image().cpu().numpy(), want)
+    b.close()
+
+
+def test_batch_rejects_shared_scene(ctx):
+    sc = I.cornell_box(width=8, height=8)
+    s = gsp.Scene(ctx, sc)
+    r1 = gsp.Renderer(s, gsp.sppm_params(sc, 100))
+    r2 = gsp.Renderer(s, gsp.sppm_params(sc, 100))
+    with pytest.raises(gsp.GspError):
+        gsp.Batch([r1, r2])
+
+
+def test_autotune_keeps_the_estimate(ctx):
+    sc = I.full_scene(seed=9, width=96, height=96, plane_quads=48, sphere_n=8)
+    kw = dict(photons_per_pass=40000, seed=5, r0_frac=0.01)
+    s = gsp.Scene(ctx, sc)
+    ref = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
+    ref.run(3)
+    a = ref.image().cpu().numpy()
+    r = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
+    res = r.autotune(trial_passes=1)
+    assert res["candidates"] == 36 and res["ms_per_pass"] <= res["first_ms_per_pass"]
+    assert res["cell_h"] >= np.float32(kw["r0_frac"] * sc.extent()) * 0.999
+    r.run(3)
+    b = r.image().cpu().numpy()
+    # the same photons are gathered; only the summation order can differ with the cell size
+    np.testing.assert_allclose(b, a, rtol=2e-5, atol=1e-7 * a.max())
