@@ -269,10 +269,10 @@ def run_ours(args, world, rank, local):
         except Exception:
             pass
 
-    # ---- SPPM pass at 512x512 ----
-    sppm = None
-    if not args.skip_sppm:
-        sppm = bench_sppm(args, ctx, dev, stream, pg)
+    # ---- SPPM pass at 512x512, the gradient workload, the 64-scene batch ----
+    sppm = bench_sppm(args, ctx, dev, stream, pg) if not args.skip_sppm else None
+    grad = bench_grad(args, ctx, dev, stream) if not args.skip_grad else None
+    batch = bench_batch(args, ctx, dev, stream) if not args.skip_batch else None
 
     # ---- CPU baseline: the oracle on the same workload ----
     cpu = None
@@ -302,6 +302,8 @@ def run_ours(args, world, rank, local):
             "wall_s_timed": round(wall, 4),
             "check": {"host_walk_agreement": round(agree, 5)},
             "sppm_512": sppm,
+            "grad_256": grad,
+            "batch_64": batch,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -315,6 +317,17 @@ def gsp_kernel_digest():
     return build._digest()[:16]
 
 
+def timed_passes(r, k, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r.run(k, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r.sync()
+    return e0.elapsed_time(e1) / k
+
+
 def bench_sppm(args, ctx, dev, stream, pg):
     import torch
     from paper_1505_06022_gb300 import gsp, inputs as I
@@ -325,25 +338,122 @@ def bench_sppm(args, ctx, dev, stream, pg):
     r.run(2, stream)
     torch.cuda.synchronize()
     k = args.sppm_passes
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    r.run(k, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    r.sync()
-    ms = e0.elapsed_time(e1) / k
+    ms = timed_passes(r, k, stream)
     if pg:
         tm = torch.tensor([ms], device=dev)
         pg.all_reduce(tm, op=pg.ReduceOp.MAX)
         ms = float(tm.item())
     img = r.image(stream)
     torch.cuda.synchronize()
+    tuned = gsp.Renderer(s, params)
+    t0 = time.perf_counter()
+    choice = tuned.autotune(trial_passes=2)
+    tune_s = time.perf_counter() - t0
+    tuned.run(2, stream)
+    ms_tuned = timed_passes(tuned, k, stream)
     out = {"passes_per_s": round(1000.0 / ms, 2), "ms_per_pass": round(ms, 3), "passes_timed": k,
+           "autotuned": {"passes_per_s": round(1000.0 / ms_tuned, 2), "ms_per_pass": round(ms_tuned, 3),
+                         "choice": {kk: (round(v, 5) if isinstance(v, float) else v) for kk, v in choice.items()},
+                         "tuning_s": round(tune_s, 2)},
            "config": "512x512, 247,234 triangles (displaced plane, glass/mirror/diffuse icospheres, area light), "
                      "1,048,576 photon paths/pass, alpha 0.7, r0 = 0.004 * diagonal, full paths + exact hash grid",
            "image_mean": round(float(img.mean()), 5)}
+    tuned.close()
     r.close()
     s.close()
+    return out
+
+
+def bench_grad(args, ctx, dev, stream):
+    """Backward/forward time of the path-replay adjoint: 256x256, 50,770 triangles, 16 diffuse
+    materials, 262,144 photon paths/pass, 8 passes, L2 loss against a render at perturbed albedos."""
+    import torch
+    from paper_1505_06022_gb300 import gsp, inputs as I
+    sc = I.grad_scene(seed=4)
+    s = gsp.Scene(ctx, sc)
+    params = gsp.sppm_params(sc, 1 << 18, seed=4, r0_frac=0.004)
+    passes = 8
+    tgt = sc.mats.copy()
+    tgt["albedo"] = np.clip(tgt["albedo"] * np.random.default_rng(40).uniform(0.8, 1.2, tgt["albedo"].shape), 0.05, 0.95)
+    gsp.gsp_scene_set_materials(s.h, tgt)
+    rt = gsp.Renderer(s, params)
+    rt.run(passes, stream)
+    target = rt.image(stream)
+    gsp.gsp_scene_set_materials(s.h, sc.mats)
+    fwd, bwd = [], []
+    for rep in range(3):
+        r = gsp.Renderer(s, params)
+        r.enable_grad(passes)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        r.run(passes, stream)
+        img = r.image(stream)
+        e[1].record(stream)
+        g = (img - target).contiguous()
+        ga, gl = r.grad(g, stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        r.sync()
+        if rep > 0:  # the first repetition warms up
+            fwd.append(e[0].elapsed_time(e[1]))
+            bwd.append(e[1].elapsed_time(e[2]))
+        r.close()
+    f, b = statistics.median(fwd), statistics.median(bwd)
+    return {"forward_ms": round(f, 3), "backward_ms": round(b, 3), "backward_over_forward": round(b / f, 3),
+            "grad_norm": round(float(ga.norm()), 6),
+            "config": "256x256, 50,770 triangles (displaced plane in 12 material regions + 4 icospheres), "
+                      "16 diffuse materials + light, 262,144 photon paths/pass, 8 passes, L2 loss vs a render "
+                      "at perturbed albedos; gradient w.r.t. 16 RGB albedos and the light's emission"}
+
+
+def bench_batch(args, ctx, dev, stream):
+    """64 scenes (1k-200k triangles log-uniform, 64^2-512^2): scene-passes per second as one CUDA
+    graph per pass vs the same renderers run one after another (bit-identical results)."""
+    import torch
+    from paper_1505_06022_gb300 import gsp, inputs as I
+    scs = I.batch_scenes(args.batch_scenes, seed=5)
+    scenes = [gsp.Scene(ctx, sc) for sc in scs]
+    mk = lambda: [gsp.Renderer(s, gsp.sppm_params(sc, 1 << 18, seed=5 + i, r0_frac=0.004, scene_id=i))
+                  for i, (s, sc) in enumerate(zip(scenes, scs))]
+    k = args.batch_passes
+    seq = mk()
+    for r in seq:
+        r.run(1, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        for r in seq:
+            r.run(1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / k
+    for r in seq:
+        r.close()
+    bat = mk()
+    b = gsp.Batch(bat)
+    b.run(1, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.run(k, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bat_ms = e0.elapsed_time(e1) / k
+    for r in bat:
+        r.sync()
+    n = len(scs)
+    out = {"scenes": n, "triangles": [int(min(sc.ntris for sc in scs)), int(max(sc.ntris for sc in scs))],
+           "sequential_scene_passes_per_s": round(1000.0 * n / seq_ms, 1),
+           "graph_scene_passes_per_s": round(1000.0 * n / bat_ms, 1),
+           "speedup": round(seq_ms / bat_ms, 3), "ms_per_batch_pass": round(bat_ms, 3), "passes_timed": k,
+           "config": f"{n} scenes, 1e3-2e5 triangles log-uniform, image side in {{64,128,256,512}}, "
+                     "262,144 photon paths/pass each, full paths + exact hash grid"}
+    b.close()
+    for r in bat:
+        r.close()
+    for s in scenes:
+        s.close()
     return out
 
 
@@ -355,6 +465,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sppm-passes", type=int, default=16)
     ap.add_argument("--skip-sppm", action="store_true")
+    ap.add_argument("--skip-grad", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--batch-scenes", type=int, default=64)
+    ap.add_argument("--batch-passes", type=int, default=4)
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)

@@ -278,9 +278,9 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
 
 /* ---- gradient of an image loss (path-replay adjoint) ------------------------------------- */
 
-/* Prepares gradients: every pass from now on records the radius each pixel gathered with
- * (4 bytes per pixel per pass, for at most max_passes passes; more passes then fail with
- * GSP_ERR_OVERFLOW) and the replay buffers are allocated. Call after gsp_sppm_create, before
+/* Prepares gradients: every pass from now on records the radius each pixel gathered with and
+ * the flux sum it gathered (20 bytes per pixel per pass, for at most max_passes passes; more
+ * passes then fail with GSP_ERR_OVERFLOW) and the replay buffers are allocated. Call after gsp_sppm_create, before
  * the first pass. Needs photon_mode GSP_FULL_PATH, hash_mode GSP_EXACT, at most 64 materials and
  * exactly one emitting material (GSP_ERR_INVALID_ARG otherwise). */
 gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes);

@@ -16,7 +16,7 @@
 // Shared with gsp_hash_grid_build (sppm.cu).
 int64_t gsp_grid_scratch_words(int64_t n, int64_t T);
 gsp_status gsp_grid_build_with(const float4* pos, int64_t n, float cell_h, int64_t T, uint32_t* order,
-                               uint32_t* bstart, uint32_t* scratch, cudaStream_t st);
+                               uint32_t* bstart, uint32_t* scratch, cudaStream_t st, bool skip_invalid);
 
 namespace {
 
@@ -64,5 +64,5 @@ extern "C" gsp_status gsp_hash_grid_build_static(const float* d_pos, int64_t n, 
     }
     (void)cudaGetLastError();
     return gsp_grid_build_with((const float4*)d_pos, n, cell_h, table_size, d_order, d_bstart, scratch,
-                               (cudaStream_t)stream);
+                               (cudaStream_t)stream, false);
 }

@@ -584,6 +584,7 @@ struct GatherDev {
     const uint32_t* __restrict__ ecount;
     int64_t npix;
     float* __restrict__ rhist;  // optional: [pass][npix] radius each pixel gathered with (gradient)
+    float4* __restrict__ shist; // optional: [pass][npix] sum of the gathered photons' flux (gradient)
 };
 
 // Distinct buckets of the cells that overlap the ball of radius R about x. A photon within R
@@ -674,6 +675,7 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
             }
         }
     }
+    if (G.shist) G.shist[(size_t)pass_index(P) * G.npix + p] = make_float4(acc.x, acc.y, acc.z, 0.0f);
     progressive_update(s0, s1, M, mul3(f, acc), P.alpha);
     G.st0[p] = s0;
     G.st1[p] = s1;
@@ -701,21 +703,16 @@ struct AdjDev {
     const uint32_t* __restrict__ order; // sorted deposit -> photon slot
     const uint32_t* __restrict__ d_total;
     float4* __restrict__ badj;          // per slot: B_k, the weight of Phi_k in the loss
-    double* __restrict__ acc;           // [nmat][3] albedo accumulators (before 1 / (pi N_e))
-    int32_t nmat;
 };
 
 // Photon-centric adjoint gather. For deposit k the hit points that gathered it in the forward
-// pass (same acceptance test, same radii) give B_k = sum_p g_p (w rho / pi)_p / R_p^2, and their
-// own albedo terms g_p (w_p / pi) Phi_k / R_p^2 add to acc[m_p].
+// pass (same acceptance test, same radii) give B_k = sum_p g_p (w rho / pi)_p / R_p^2, the weight
+// of Phi_k in the loss. Each deposit is one thread; nothing is shared, nothing is atomic.
 __global__ void __launch_bounds__(128) k_adj_photons(AdjDev A) {
-    __shared__ double s_acc[kMaxGradMats * 3];
-    for (int i = threadIdx.x; i < A.nmat * 3; i += blockDim.x) s_acc[i] = 0.0;
-    __syncthreads();
     const int64_t nd = (int64_t)*A.d_total;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (int64_t)gridDim.x * blockDim.x) {
         const float4 a = A.spos[i], c = A.spay[i];
-        const float3 xk = f3(a), phik = f3(c);
+        const float3 xk = f3(a);
         const uint32_t dir = __float_as_uint(c.w);
         uint32_t buckets[27];
         const int nb = query_buckets(xk, A.rmax, A.inv_hp, A.hp_mask, buckets);
@@ -725,24 +722,39 @@ __global__ void __launch_bounds__(128) k_adj_photons(AdjDev A) {
             for (uint32_t j = A.hp_bstart[b]; j < e; ++j) {
                 const uint32_t p = A.hp_order[j];
                 const float4 hxp = __ldg(A.hx + p);
-                const int32_t m = __float_as_int(hxp.w);
-                if (m < 0) continue;
+                if (__float_as_int(hxp.w) < 0) continue;
                 const float R = __ldg(A.rhist + p);
                 if (!photon_accept(xk, f3(hxp), R, dir, f3(__ldg(A.hn + p)))) continue;
-                const float inv = 1.0f / (R * R);
                 const float3 gp = make_float3(__ldg(A.g + 3 * p), __ldg(A.g + 3 * p + 1), __ldg(A.g + 3 * p + 2));
-                B = B + mul3(gp, f3(__ldg(A.hf + p))) * inv;
-                const float3 t1 = mul3(mul3(gp, f3(__ldg(A.hw + p))), phik) * (inv * (1.0f / kPi));
-                atomicAdd(&s_acc[3 * m], (double)t1.x);
-                atomicAdd(&s_acc[3 * m + 1], (double)t1.y);
-                atomicAdd(&s_acc[3 * m + 2], (double)t1.z);
+                B = B + mul3(gp, f3(__ldg(A.hf + p))) * (1.0f / (R * R));
             }
         }
         A.badj[A.order[i]] = make_float4(B.x, B.y, B.z, 0.0f);
     }
+}
+
+// Hit-point albedo terms: through the factor rho_{m_p} of its weight, pixel p gives
+// dLoss/drho_{m_p} += g_p (w_p / pi) S_p / R_p^2, with S_p the flux sum its forward gather saw.
+__global__ void __launch_bounds__(256)
+k_adj_pixels(const float4* __restrict__ hx, const float4* __restrict__ hw, const float* __restrict__ rhist,
+             const float4* __restrict__ shist, const float* __restrict__ g, int64_t npix, double* __restrict__ acc,
+             int32_t nmat) {
+    __shared__ float s_acc[kMaxGradMats * 3];
+    for (int i = threadIdx.x; i < nmat * 3; i += blockDim.x) s_acc[i] = 0.0f;
     __syncthreads();
-    for (int i = threadIdx.x; i < A.nmat * 3; i += blockDim.x)
-        if (s_acc[i] != 0.0) atomicAdd(&A.acc[i], s_acc[i]);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t m = __float_as_int(hx[p].w);
+        if (m < 0) continue;
+        const float R = rhist[p];
+        const float3 t = mul3(mul3(make_float3(g[3 * p], g[3 * p + 1], g[3 * p + 2]), f3(hw[p])), f3(shist[p])) *
+                         (1.0f / (kPi * R * R));
+        atomicAdd(&s_acc[3 * m], t.x);
+        atomicAdd(&s_acc[3 * m + 1], t.y);
+        atomicAdd(&s_acc[3 * m + 2], t.z);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nmat * 3; i += blockDim.x)
+        if (s_acc[i] != 0.0f) atomicAdd(&acc[i], (double)s_acc[i]);
 }
 
 // Path terms: Phi_j of deposit j carries rho_m / p_c for every diffuse bounce on material m before
@@ -753,8 +765,8 @@ __global__ void __launch_bounds__(128)
 k_adj_paths(const float4* __restrict__ slots, const uint32_t* __restrict__ pcount, const int32_t* __restrict__ smat,
             const float4* __restrict__ badj, const float4* __restrict__ mats, int64_t np, double* __restrict__ acc,
             int32_t nmat) {
-    __shared__ double s_acc[kMaxGradMats * 3];
-    for (int i = threadIdx.x; i < nmat * 3; i += blockDim.x) s_acc[i] = 0.0;
+    __shared__ float s_acc[kMaxGradMats * 3];
+    for (int i = threadIdx.x; i < nmat * 3; i += blockDim.x) s_acc[i] = 0.0f;
     __syncthreads();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t n = (int32_t)pcount[k];
@@ -764,16 +776,16 @@ k_adj_paths(const float4* __restrict__ slots, const uint32_t* __restrict__ pcoun
             const int32_t m = smat[slot];
             if (j < n - 1) {
                 const float3 al = f3(__ldg(mats + 2 * m));
-                if (al.x > 0.0f) atomicAdd(&s_acc[3 * m], (double)(suffix.x / al.x));
-                if (al.y > 0.0f) atomicAdd(&s_acc[3 * m + 1], (double)(suffix.y / al.y));
-                if (al.z > 0.0f) atomicAdd(&s_acc[3 * m + 2], (double)(suffix.z / al.z));
+                if (al.x > 0.0f) atomicAdd(&s_acc[3 * m], suffix.x / al.x);
+                if (al.y > 0.0f) atomicAdd(&s_acc[3 * m + 1], suffix.y / al.y);
+                if (al.z > 0.0f) atomicAdd(&s_acc[3 * m + 2], suffix.z / al.z);
             }
             suffix = suffix + mul3(f3(badj[slot]), f3(slots[2 * slot + 1]));
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nmat * 3; i += blockDim.x)
-        if (s_acc[i] != 0.0) atomicAdd(&acc[i], s_acc[i]);
+        if (s_acc[i] != 0.0f) atomicAdd(&acc[i], (double)s_acc[i]);
 }
 
 // Emission: with one emitting material the image is linear in its Le, so dLoss/dLe_c is
@@ -839,13 +851,21 @@ __global__ void k_init_state(float4* st0, float4* st1, int64_t npix, float r0) {
     st1[p] = make_float4(0.0f, 0.0f, 0.0f, r0);
 }
 
-// Bucket key of each point of a standalone hash-grid build; counts per bucket.
+// Bucket key of each point of a hash-grid build; counts per bucket. With skip_invalid, points
+// whose w holds a negative integer (hit points of pixels that saw no diffuse surface) get the key
+// T = mask + 1: they sort after every bucket and are in none.
 __global__ void k_grid_keys(const float4* __restrict__ pos, int64_t n, float inv_h, uint32_t mask,
-                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ bcount) {
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ bcount,
+                            int32_t skip_invalid) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t b = bucket_of(f3(pos[i]), inv_h, mask);
-        keys[i] = b;
+        const float4 q = pos[i];
         vals[i] = (uint32_t)i;
+        if (skip_invalid && __float_as_int(q.w) < 0) {
+            keys[i] = mask + 1u;
+            continue;
+        }
+        const uint32_t b = bucket_of(f3(q), inv_h, mask);
+        keys[i] = b;
         atomicAdd(bcount + b, 1u);
     }
 }
@@ -867,7 +887,7 @@ using namespace gspd;
 
 int64_t gsp_grid_scratch_words(int64_t n, int64_t T);
 gsp_status gsp_grid_build_with(const float4* pos, int64_t n, float cell_h, int64_t T, uint32_t* order,
-                               uint32_t* bstart, uint32_t* scratch, cudaStream_t st);
+                               uint32_t* bstart, uint32_t* scratch, cudaStream_t st, bool skip_invalid);
 
 struct gsp_sppm {
     gsp_scene* scene = nullptr;
@@ -901,6 +921,7 @@ struct gsp_sppm {
     bool grad = false;
     int32_t grad_max_passes = 0, emit_mat = -1;
     float* rhist = nullptr;            // [max passes][npix] gather radius
+    float4* shist = nullptr;           // [max passes][npix] gathered flux sum
     float4 *st1_scratch = nullptr, *hw = nullptr, *badj = nullptr;
     int32_t* smat = nullptr;
     double* gacc = nullptr;            // [nmat * 3 + 3]
@@ -1234,6 +1255,7 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
     G.st1 = r->st1;
     G.npix = r->npix;
     G.rhist = r->grad ? r->rhist : nullptr;
+    G.shist = r->grad ? r->shist : nullptr;
     if (stoch) {
         G.slots = r->slots;
         G.entry = r->entry;
@@ -1301,6 +1323,7 @@ gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
     cudaError_t e = cudaSuccess;
     auto A = [&](auto** p, int64_t n) { if (e == cudaSuccess) e = alloc(r, p, n); };
     A(&r->rhist, (int64_t)max_passes * r->npix);
+    A(&r->shist, (int64_t)max_passes * r->npix);
     A(&r->st1_scratch, r->npix);
     A(&r->hw, r->npix);
     A(&r->badj, r->slot_cap);
@@ -1340,7 +1363,7 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
         if (e == GSP_OK) e = stage_photons(r, P, D, st);
         if (e == GSP_OK) e = stage_deposit(r, P, st);
         if (e != GSP_OK) return e;
-        e = gsp_grid_build_with(r->hx, r->npix, hp_cell, r->hp_T, r->hp_order, r->hp_bstart, r->hp_scratch, st);
+        e = gsp_grid_build_with(r->hx, r->npix, hp_cell, r->hp_T, r->hp_order, r->hp_bstart, r->hp_scratch, st, true);
         if (e != GSP_OK) return e;
         AdjDev A;
         A.hx = r->hx;
@@ -1359,9 +1382,9 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
         A.order = r->last_order;
         A.d_total = r->counters;
         A.badj = r->badj;
-        A.acc = r->gacc;
-        A.nmat = nmat;
         k_adj_photons<<<grid * 2, 128, 0, st>>>(A);
+        k_adj_pixels<<<grid, 256, 0, st>>>(r->hx, r->hw, A.rhist, r->shist + (size_t)i * r->npix, d_dloss_dimg,
+                                           r->npix, r->gacc, nmat);
         k_adj_paths<<<grid, 128, 0, st>>>(r->slots, r->pcount, r->smat, r->badj, r->scene->d_mats, r->np, r->gacc,
                                           nmat);
     }
@@ -1627,9 +1650,10 @@ int64_t gsp_grid_scratch_words(int64_t n, int64_t T) {
 
 // Exact hash grid of n points: keys -> counts -> in-place bucket scan -> stable radix sort.
 gsp_status gsp_grid_build_with(const float4* pos, int64_t n, float cell_h, int64_t T, uint32_t* order,
-                               uint32_t* bstart, uint32_t* scratch, cudaStream_t st) {
+                               uint32_t* bstart, uint32_t* scratch, cudaStream_t st, bool skip_invalid) {
     int tbits = 0;
     while ((int64_t(1) << tbits) < T) ++tbits;
+    if (skip_invalid) ++tbits;  // the key T of skipped points needs one more bit
     uint32_t* ka = scratch;
     uint32_t* va = ka + n;
     uint32_t* kb = va + n;
@@ -1641,7 +1665,7 @@ gsp_status gsp_grid_build_with(const float4* pos, int64_t n, float cell_h, int64
     k_store_u32<<<1, 1, 0, st>>>(nbuf, (uint32_t)n);
     if (n > 0)
         k_grid_keys<<<(unsigned)std::min<int64_t>(blocks(n, 256), 4096), 256, 0, st>>>(
-            pos, n, 1.0f / cell_h, (uint32_t)(T - 1), ka, va, bstart);
+            pos, n, 1.0f / cell_h, (uint32_t)(T - 1), ka, va, bstart, skip_invalid ? 1 : 0);
     GSP_CUDA_TRY(gsp_scan_u32(bstart, bstart, T, bstart + T, tmp, st));
     uint32_t *ko = nullptr, *vo = nullptr;
     GSP_CUDA_TRY(gsp_radix_sort_u32(ka, va, kb, vb, nbuf, tbits, hist, tmp, st, &ko, &vo));
@@ -1677,7 +1701,7 @@ gsp_status gsp_hash_grid_build(gsp_context* ctx, const float* d_pos, int64_t n, 
         ctx->grid_words = words;
     }
     return gsp_grid_build_with((const float4*)d_pos, n, cell_h, table_size, d_order, d_bstart, ctx->grid_scratch,
-                               (cudaStream_t)stream);
+                               (cudaStream_t)stream, false);
 }
 
 gsp_status gsp_sppm_sync(gsp_sppm* r) {

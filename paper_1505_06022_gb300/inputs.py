@@ -370,8 +370,8 @@ def batch_scenes(count: int = 64, seed: int = 5):
     for i in range(count):
         target = float(np.exp(rng.uniform(np.log(1e3), np.log(2e5))))
         side = int(rng.choice([64, 128, 256, 512]))
-        g = max(8, int(np.sqrt(target * 0.6 / 2)))
-        sn = max(2, int(np.sqrt(target * 0.4 / 60)))
+        g = max(8, int(np.ceil(np.sqrt(target * 0.6 / 2))))
+        sn = max(2, int(np.ceil(np.sqrt(target * 0.4 / 60))))
         sc = full_scene(seed=1000 + i, width=side, height=side, plane_quads=g, sphere_n=sn)
         sc.name = f"batch{i}"
         out.append(sc)
