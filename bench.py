@@ -107,6 +107,33 @@ def dist_setup(args):
     return world, rank, local
 
 
+def init_ranks(world, dev):
+    """One process per GPU: NCCL between GPUs, gloo for host-only ranks. None when world == 1."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if dev.type == "cuda":
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist.init_process_group("gloo")
+    return dist
+
+
+def max_over_ranks(x, pg, dev):
+    """The largest x over all ranks: the slowest replica sets the job's time."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mrays(world, rays_per_rank, ms_per_step):
+    """Whole-job throughput: every replica traces its own batch each step."""
+    return world * rays_per_rank / (ms_per_step / 1000.0) / 1e6
+
+
 def traversal_workload():
     from paper_1505_06022_gb300 import inputs as I
     sc = I.traversal_sphere(n=224, seed=2)
@@ -121,28 +148,32 @@ def stratified(n, k, seed=11):
                                    half + rng.choice(n - half, k - k // 2, replace=False)]))
 
 
-def cpu_oracle_rays(sc, rays, sample_rays, steps=1, warmup=0):
-    """Times the FP64 oracle's closest-hit query on `sample_rays` rays per step, all cores."""
+def cpu_oracle_rays(sc, rays, sample_rays, steps=1, warmup=0, min_seconds=0.0):
+    """Times the FP64 oracle's closest-hit query on `sample_rays` rays per step, all cores;
+    with min_seconds, repeats the step until that much time has passed. Returns (Mrays/s,
+    cores, seconds, steps run)."""
     import oracle as O
     mesh = O.Mesh(sc.verts, sc.tris)
-    idx = stratified(len(rays), sample_rays)
+    idx = stratified(len(rays), sample_rays) if sample_rays < len(rays) else np.arange(len(rays))
     sub = np.ascontiguousarray(rays[idx])
     cores = O.nthreads_default()
     for _ in range(warmup):
         mesh.closest_hit(sub, classify=False, nthreads=cores)
     t0 = time.perf_counter()
-    for _ in range(steps):
+    done = 0
+    while done < steps or time.perf_counter() - t0 < min_seconds:
         mesh.closest_hit(sub, classify=False, nthreads=cores)
+        done += 1
     dt = time.perf_counter() - t0
-    return sample_rays * steps / dt / 1e6, cores, dt
+    return len(sub) * done / dt / 1e6, cores, dt, done
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
     sc, rays = traversal_workload()
-    sample = 1 << 19
-    mrays, cores, dt = cpu_oracle_rays(sc, rays, sample, steps=args.steps, warmup=args.warmup)
+    sample = args.ref_rays
+    mrays, cores, dt, _ = cpu_oracle_rays(sc, rays, sample, steps=args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": "closest-hit Mrays/s", "value": round(mrays, 4), "unit": "Mrays/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -165,11 +196,7 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-        pg = dist
+    pg = init_ranks(world, dev)
     gsp.lib()
     ctx = gsp.Context(local)
     sc, rays_h = traversal_workload()
@@ -201,14 +228,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    ms_total = ev[0].elapsed_time(ev[1])
-    if pg:
-        tm = torch.tensor([ms_total], device=dev)
-        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
-        ms_total = float(tm.item())
+    ms_total = max_over_ranks(ev[0].elapsed_time(ev[1]), pg, dev)
     ctx.sync()
     ms_step = ms_total / args.steps
-    mrays = world * n / (ms_step / 1000.0) / 1e6
+    mrays = job_mrays(world, n, ms_step)
 
     # ---- end to end through the C ABI with host buffers ----
     rays_pin = torch.from_numpy(rays_h).pin_memory()
@@ -231,11 +254,7 @@ def run_ours(args, world, rank, local):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if pg:
-        tm = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
-        e2e_ms = float(tm.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, pg, dev)
     # correctness of the timed results on a few rays (host walk of the same BVH)
     chk = stratified(n, 4096, seed=5)
     htri, _, vis, tests = scene.host_walk(rays_h[chk])
@@ -277,11 +296,10 @@ def run_ours(args, world, rank, local):
     # ---- CPU baseline: the oracle on the same workload ----
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        sample = 1 << 20
-        mr, cores, dt = cpu_oracle_rays(sc, rays_h, sample)
+        mr, cores, dt, reps = cpu_oracle_rays(sc, rays_h, n, warmup=1, min_seconds=10.0)
         cpu = {"value": round(mr, 4), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-               "sample": f"{sample} stratified rays (half coherent, half random) of the 4,194,304-ray batch, "
-                         f"FP64 oracle BVH, {dt:.1f} s"}
+               "sample": f"the whole 4,194,304-ray batch (half coherent, half random) traced {reps} times by "
+                         f"the FP64 oracle BVH, {dt:.1f} s"}
     if rank == 0:
         line = {
             "metric": "closest-hit Mrays/s", "value": round(mrays, 2), "unit": "Mrays/s", "n_gpus": world,
@@ -295,9 +313,9 @@ def run_ours(args, world, rank, local):
                        "bvh": scene.stats},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": round(world * n / (e2e_ms / 1000.0) / 1e6, 2), "unit": "Mrays/s",
+            "e2e": {"value": round(job_mrays(world, n, e2e_ms), 2), "unit": "Mrays/s",
                     "h2d_bytes_per_step": int(rays_h.nbytes), "d2h_bytes_per_step": int(n * 8)},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "clocks": clk,
             "wall_s_timed": round(wall, 4),
             "check": {"host_walk_agreement": round(agree, 5)},
@@ -314,7 +332,7 @@ def run_ours(args, world, rank, local):
 
 def gsp_kernel_digest():
     from paper_1505_06022_gb300 import build
-    return build._digest()[:16]
+    return build.trace_digest()
 
 
 def timed_passes(r, k, stream):
@@ -334,30 +352,31 @@ def bench_sppm(args, ctx, dev, stream, pg):
     sc = I.full_scene(seed=3)
     s = gsp.Scene(ctx, sc)
     params = gsp.sppm_params(sc, 1 << 20, seed=3, r0_frac=0.004)
-    r = gsp.Renderer(s, params)
-    r.run(2, stream)
+    warm = gsp.Renderer(s, params)
+    warm.run(3, stream)
     torch.cuda.synchronize()
+    warm.close()
+    # a render of k passes from its first pass (the radii shrink as it goes)
     k = args.sppm_passes
-    ms = timed_passes(r, k, stream)
-    if pg:
-        tm = torch.tensor([ms], device=dev)
-        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
-        ms = float(tm.item())
+    r = gsp.Renderer(s, params)
+    ms = max_over_ranks(timed_passes(r, k, stream), pg, dev)
     img = r.image(stream)
     torch.cuda.synchronize()
+    # autotune times its candidates on a temporary renderer: `tuned` itself is still at pass 0
     tuned = gsp.Renderer(s, params)
     t0 = time.perf_counter()
     choice = tuned.autotune(trial_passes=2)
     tune_s = time.perf_counter() - t0
-    tuned.run(2, stream)
     ms_tuned = timed_passes(tuned, k, stream)
+    img_tuned = tuned.image(stream)
+    same = bool(torch.equal(img, img_tuned))
     out = {"passes_per_s": round(1000.0 / ms, 2), "ms_per_pass": round(ms, 3), "passes_timed": k,
            "autotuned": {"passes_per_s": round(1000.0 / ms_tuned, 2), "ms_per_pass": round(ms_tuned, 3),
                          "choice": {kk: (round(v, 5) if isinstance(v, float) else v) for kk, v in choice.items()},
                          "tuning_s": round(tune_s, 2)},
            "config": "512x512, 247,234 triangles (displaced plane, glass/mirror/diffuse icospheres, area light), "
                      "1,048,576 photon paths/pass, alpha 0.7, r0 = 0.004 * diagonal, full paths + exact hash grid",
-           "image_mean": round(float(img.mean()), 5)}
+           "image_mean": round(float(img.mean()), 5), "autotuned_image_identical": same}
     tuned.close()
     r.close()
     s.close()
@@ -463,13 +482,15 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--sppm-passes", type=int, default=16)
+    ap.add_argument("--sppm-passes", type=int, default=64)
     ap.add_argument("--skip-sppm", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--batch-scenes", type=int, default=64)
     ap.add_argument("--batch-passes", type=int, default=4)
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ref-rays", type=int, default=1 << 19,
+                    help="rays per step of the CPU reference arm (a stratified sample of the batch)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

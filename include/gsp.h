@@ -247,6 +247,17 @@ int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity);
 /* Waits for the renderer's stream work and returns the first recorded device error. */
 gsp_status gsp_sppm_sync(gsp_sppm* r);
 
+/* Checkpoint: writes the renderer's progressive state (per-pixel N, R, tau, direct; the pass
+ * count; in REGEN mode the per-thread photon paths; with gradients enabled the recorded radii
+ * and flux sums) to a file. Synchronises the device. */
+gsp_status gsp_sppm_save(gsp_sppm* r, const char* path);
+/* Restores a checkpoint into a renderer created with the same scene and parameters (and, if the
+ * checkpoint has gradient records, with gradients enabled for at least as many passes). The PRNG
+ * is keyed by the pass index, so passes after a load give bit for bit the result of an
+ * uninterrupted run. GSP_ERR_BAD_STATE if the parameters differ, GSP_ERR_IO if the file is
+ * unreadable or short. */
+gsp_status gsp_sppm_load(gsp_sppm* r, const char* path);
+
 /* ---- many scenes per launch, CUDA graphs, autotuning ------------------------------------ */
 
 typedef struct gsp_batch gsp_batch;

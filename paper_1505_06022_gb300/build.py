@@ -43,6 +43,20 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+# Everything the closest-hit kernel (k_trace, k_refine) is compiled from: a change elsewhere in the
+# library leaves its profile counters valid.
+TRACE_SOURCES = ["capi.cu", "devcommon.cuh", "launch.h", "gsp_internal.h"]
+
+
+def trace_digest() -> str:
+    h = hashlib.sha256()
+    for name in TRACE_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(CSRC, name), "rb").read())
+    h.update(" ".join(_flags()).encode())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     stamp = os.path.join(BUILD, "libgsp.sha256")

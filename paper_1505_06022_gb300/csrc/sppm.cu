@@ -14,6 +14,7 @@
 //   stochastic    entry[T] = min(random depth bits << 32 | slot), ecount[T]
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -1574,6 +1575,86 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         out->candidates = (int32_t)cands.size();
     }
     return GSP_OK;
+}
+
+// ---- checkpoint -------------------------------------------------------------------------------
+// File: "GSPPMCK1", then a header of int64 fields {version, npix, np, passes, photon_mode,
+// hash_mode, grad passes recorded}, the creation parameters (raw gsp_sppm_params), then the
+// arrays: pixel state st0, st1 (npix float4 each); in REGEN mode the per-thread path state
+// ro, rd, rphi (np float4 each) and the started-path count; with gradients the recorded radii
+// and flux sums of the passes so far.
+static const char kCkMagic[8] = {'G', 'S', 'P', 'P', 'M', 'C', 'K', '1'};
+
+static bool ck_write(FILE* f, const void* d_src, size_t bytes, std::vector<char>& buf) {
+    buf.resize(bytes);
+    if (bytes && cudaMemcpy(buf.data(), d_src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    return fwrite(buf.data(), 1, bytes, f) == bytes;
+}
+
+static bool ck_read(FILE* f, void* d_dst, size_t bytes, std::vector<char>& buf) {
+    buf.resize(bytes);
+    if (fread(buf.data(), 1, bytes, f) != bytes) return false;
+    return !bytes || cudaMemcpy(d_dst, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+gsp_status gsp_sppm_save(gsp_sppm* r, const char* path) {
+    if (!r || !path) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    GSP_CUDA_TRY(cudaDeviceSynchronize());
+    FILE* f = fopen(path, "wb");
+    if (!f) return GSP_ERR_IO;
+    const int64_t hdr[7] = {1, r->npix, r->np, r->passes, r->P.photon_mode, r->P.hash_mode,
+                            r->grad ? r->passes : 0};
+    std::vector<char> buf;
+    bool ok = fwrite(kCkMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof hdr, 1, f) == 1 &&
+              fwrite(&r->P, sizeof r->P, 1, f) == 1 && ck_write(f, r->st0, r->npix * sizeof(float4), buf) &&
+              ck_write(f, r->st1, r->npix * sizeof(float4), buf);
+    if (ok && r->P.photon_mode == GSP_REGEN)
+        ok = ck_write(f, r->ro, r->np * sizeof(float4), buf) && ck_write(f, r->rd, r->np * sizeof(float4), buf) &&
+             ck_write(f, r->rphi, r->np * sizeof(float4), buf) && ck_write(f, r->started, sizeof(unsigned long long), buf);
+    if (ok && r->grad && r->passes > 0)
+        ok = ck_write(f, r->rhist, (size_t)r->passes * r->npix * sizeof(float), buf) &&
+             ck_write(f, r->shist, (size_t)r->passes * r->npix * sizeof(float4), buf);
+    ok = (fclose(f) == 0) && ok;
+    return ok ? GSP_OK : GSP_ERR_IO;
+}
+
+gsp_status gsp_sppm_load(gsp_sppm* r, const char* path) {
+    if (!r || !path) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    GSP_CUDA_TRY(cudaDeviceSynchronize());
+    FILE* f = fopen(path, "rb");
+    if (!f) return GSP_ERR_IO;
+    char magic[8];
+    int64_t hdr[7];
+    gsp_sppm_params P, mine = r->P;
+    std::vector<char> buf;
+    gsp_status st = GSP_OK;
+    const bool read_ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkMagic, 8) == 0 &&
+                         fread(hdr, sizeof hdr, 1, f) == 1 && fread(&P, sizeof P, 1, f) == 1;
+    // In exact mode the cell edge is an execution setting (the autotuner changes it): ignore it.
+    if (read_ok && P.hash_mode == GSP_EXACT) P.cell_h = mine.cell_h;
+    if (!read_ok) {
+        st = GSP_ERR_IO;
+    } else if (hdr[0] != 1 || hdr[1] != r->npix || hdr[2] != r->np || hdr[4] != r->P.photon_mode ||
+               hdr[5] != r->P.hash_mode || std::memcmp(&P, &mine, sizeof P) != 0 || hdr[3] < 0 ||
+               (hdr[6] > 0 && (!r->grad || hdr[6] > r->grad_max_passes)) || (r->grad && hdr[6] != hdr[3])) {
+        gsp_set_last_error("gsp_sppm_load: the checkpoint was written by a renderer with other parameters");
+        st = GSP_ERR_BAD_STATE;
+    } else {
+        bool ok = ck_read(f, r->st0, r->npix * sizeof(float4), buf) && ck_read(f, r->st1, r->npix * sizeof(float4), buf);
+        if (ok && r->P.photon_mode == GSP_REGEN)
+            ok = ck_read(f, r->ro, r->np * sizeof(float4), buf) && ck_read(f, r->rd, r->np * sizeof(float4), buf) &&
+                 ck_read(f, r->rphi, r->np * sizeof(float4), buf) &&
+                 ck_read(f, r->started, sizeof(unsigned long long), buf);
+        if (ok && hdr[6] > 0)
+            ok = ck_read(f, r->rhist, (size_t)hdr[6] * r->npix * sizeof(float), buf) &&
+                 ck_read(f, r->shist, (size_t)hdr[6] * r->npix * sizeof(float4), buf);
+        if (ok) r->passes = hdr[3];
+        st = ok ? GSP_OK : GSP_ERR_IO;
+    }
+    fclose(f);
+    return st;
 }
 
 gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream) {

@@ -38,7 +38,7 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
        "gsp_scene_set_materials", "gsp_batch_create", "gsp_batch_destroy", "gsp_batch_pass",
-       "gsp_sppm_autotune"]
+       "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -129,6 +129,8 @@ def lib():
             L.gsp_batch_destroy.restype = None
             L.gsp_batch_pass.argtypes = [P, I32, P]
             L.gsp_sppm_autotune.argtypes = [P, I32, P]
+            L.gsp_sppm_save.argtypes = [P, C.c_char_p]
+            L.gsp_sppm_load.argtypes = [P, C.c_char_p]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
             _lib = L
     return _lib
@@ -316,6 +318,14 @@ def gsp_batch_pass(b, npasses=1, stream=None):
     _check("gsp_batch_pass", lib().gsp_batch_pass(b, npasses, _stream(stream)))
 
 
+def gsp_sppm_save(r, path):
+    _check("gsp_sppm_save", lib().gsp_sppm_save(r, os.fsencode(path)))
+
+
+def gsp_sppm_load(r, path):
+    _check("gsp_sppm_load", lib().gsp_sppm_load(r, os.fsencode(path)))
+
+
 def gsp_sppm_destroy(r):
     lib().gsp_sppm_destroy(r)
 
@@ -458,6 +468,12 @@ class Renderer:
 
     def last_deposits(self):
         return gsp_sppm_last_deposits(self.h)
+
+    def save(self, path):
+        gsp_sppm_save(self.h, path)
+
+    def load(self, path):
+        gsp_sppm_load(self.h, path)
 
     def enable_grad(self, max_passes):
         gsp_sppm_enable_grad(self.h, max_passes)
