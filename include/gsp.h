@@ -105,7 +105,7 @@ typedef struct {
  *  alpha             radius reduction parameter in (0, 1]
  *  r0                initial gather radius (world units, > 0)
  *  rr_continue       Russian-roulette continue probability at diffuse hits, in (0, 1]
- *  cell_h            hash cell edge; 0 = 2 * r0. Must be >= r0 (>= 2 * r0 in STOCHASTIC mode).
+ *  cell_h            hash cell edge; 0 = 2 * r0. Must be >= r0 / 4 (>= 2 * r0 in STOCHASTIC mode).
  *  eps               ray offset (tmin) of every secondary ray, world units
  *  photon_mode       GSP_FULL_PATH: whole photon paths each pass; GSP_REGEN: one bounce per
  *                    pass per thread, a thread starts a new path when its path ends (Sec. 3.3)
@@ -277,14 +277,16 @@ typedef struct {
     int32_t eye_steps, photon_steps; /* chosen wavefront steps */
     float cell_h;                    /* chosen hash cell edge (exact mode) */
     float ms_per_pass;               /* its measured time per pass */
-    float first_ms_per_pass;         /* time of the first candidate (1/0/2 r0 settings order) */
+    float first_ms_per_pass;         /* time of the renderer's settings before tuning */
     int32_t candidates;
 } gsp_tune_result;
 
-/* Times candidate execution settings that leave the estimate unchanged -- eye and photon
- * wavefront steps, and in exact mode the hash cell edge (2, 1.5 or 1 times r0; the gather then
- * scans fewer photons) -- for trial_passes passes each on a temporary renderer over the same
- * scene (the renderer's own state is not touched), and applies the fastest. out may be NULL. */
+/* Times candidate execution settings that leave the estimate unchanged, each from a fresh state
+ * for trial_passes passes (after one untimed pass) on a temporary renderer over the same scene
+ * (the renderer's own state is not touched), and applies the fastest: first the eye and photon
+ * wavefront steps (0-2 and 0, 1, 2, 4), then in exact mode the hash cell edge (2, 1.5, 1, 0.75
+ * or 0.5 times r0; smaller cells scan fewer photons but more buckets). The cell edge changes only
+ * the order in which a pixel sums its photons. out may be NULL. */
 gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out);
 
 /* ---- gradient of an image loss (path-replay adjoint) ------------------------------------- */

@@ -45,7 +45,7 @@ def _digest() -> str:
 
 # Everything the closest-hit kernel (k_trace, k_refine) is compiled from: a change elsewhere in the
 # library leaves its profile counters valid.
-TRACE_SOURCES = ["capi.cu", "devcommon.cuh", "launch.h", "gsp_internal.h"]
+TRACE_SOURCES = ["capi.cu", "devcommon.cuh", "launch.h", "persist.cuh", "gsp_internal.h"]
 
 
 def trace_digest() -> str:

@@ -8,6 +8,7 @@
 #include "devcommon.cuh"
 #include "gsp_internal.h"
 #include "launch.h"
+#include "persist.cuh"
 
 namespace {
 thread_local std::string g_last_error;
@@ -17,14 +18,8 @@ void gsp_set_last_error(const std::string& msg) { g_last_error = msg; }
 
 namespace gspd {
 
-__device__ __forceinline__ uint32_t lanemask_lt() {
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
 // Closest-hit kernel (Fig. 3), persistent. A warp takes chunks of kTraceChunk consecutive rays
-// with one atomic and hands them to its lanes; a lane whose ray has finished takes the next ray of
+// and hands them to its lanes (WarpQueue); a lane whose ray has finished takes the next ray of
 // the chunk right away, so lanes do not idle until the slowest ray of a batch ends. Lanes run up
 // to kTraceInner traversal steps between refills. Rays and results are streamed with evict-first
 // hints so that the BVH stays resident in L2. Hits whose FP32 t may be inaccurate are appended
@@ -37,101 +32,23 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* 
     if (d_n) n = min(n, (int64_t)*d_n);  // wavefront queues: the length lives on the device
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    const int32_t cap = (int32_t)min(4 * S.nnodes + 16, (int64_t)INT32_MAX);  // box tests incl. retests
+    const int32_t cap = trav_cap(S);
     Trav st;
     st.node = -1;
     st.slot = -1;
-    // first chunk of each warp is static (no atomic: an empty or short batch costs no
-    // contention); later chunks come from the counter, which starts after all static chunks
-    // ray indices fit in 31 bits (the entry point rejects larger batches)
-    const int32_t n32 = (int32_t)n;
-    const int32_t static_end = (int32_t)min((int64_t)gridDim.x * (blockDim.x >> 5) * kTraceChunk, n);
+    WarpQueue wq;
+    wq.init((int32_t)n);  // ray indices fit in 31 bits (the entry point rejects larger batches)
     int32_t ray = -1;
-    int32_t qbase = (int32_t)min(((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTraceChunk, n);
-    int32_t qend = min(qbase + kTraceChunk, n32);
     int32_t pend = -1;  // leaf word of a postponed leaf, -1 = none
-    bool done = false;
     while (true) {
-        bool need = ray < 0 && !done;
-        uint32_t m = __ballot_sync(0xffffffffu, need);
-        while (m) {
-            if (qbase >= qend) {
-                unsigned long long b = 0;
-                if (static_end < n32 && lane == 0) b = atomicAdd(ctr, (unsigned long long)kTraceChunk);
-                b = __shfl_sync(0xffffffffu, b, 0);
-                qbase = (int32_t)min((int64_t)static_end + (int64_t)b, n);
-                qend = min(qbase + kTraceChunk, n32);
-                if (qbase >= n32) {
-                    done = true;
-                    break;
-                }
-            }
-            const int take = min(__popc(m), qend - qbase);
-            const int rank = __popc(m & lt);
-            if (need && rank < take) {
-                ray = qbase + rank;
-                const float4 a = __ldcs(rays + 2 * (int64_t)ray), b = __ldcs(rays + 2 * (int64_t)ray + 1);
-                trav_init(S, f3(a), f3(b), a.w, b.w, st);
-                need = false;
-            }
-            qbase += take;
-            m = __ballot_sync(0xffffffffu, need);
+        const int32_t got = wq.take(ray < 0, ctr);
+        if (got >= 0) {
+            ray = got;
+            const float4 a = __ldcs(rays + 2 * (int64_t)ray), b = __ldcs(rays + 2 * (int64_t)ray + 1);
+            trav_init(S, f3(a), f3(b), a.w, b.w, st);
         }
         if (__ballot_sync(0xffffffffu, ray >= 0) == 0) break;
-        // Node steps; a lane that reaches a leaf keeps it pending and goes on along the miss link
-        // with its current best t (which can only make it visit more nodes, never skip the
-        // winner). When a lane meets a second leaf it waits. The warp tests all pending leaves
-        // together when enough lanes hold one, when a lane waits, or when a lane's walk ended.
-#pragma unroll 1
-        for (int it = 0; it < kTraceInner; ++it) {
-            bool waiting = false;
-            if (ray >= 0 && st.node >= 0) {
-                // one fetch brings the node and the next node in preorder (its first child when it
-                // is internal, usually in the same cache line); both boxes can be tested
-                const float4* np = st.nodes + 2 * st.node;
-                const float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2), D = __ldg(np + 3);
-                st.steps += 1;
-                int32_t word, miss;
-                if (st.steps > cap) {
-                    report(S.status, -4);
-                    st.node = -1;
-                } else if (!box_hit(st, A, B, word, miss)) {
-                    st.node = miss;
-                } else if (word >= 0) {
-                    if (pend < 0) {
-                        pend = word;
-                        st.node = miss;
-                    } else {
-                        waiting = true;
-                    }
-                } else {
-                    st.steps += 1;
-                    int32_t w2, m2;
-                    if (!box_hit(st, C, D, w2, m2)) {
-                        st.node = m2;
-                    } else if (w2 >= 0) {
-                        if (pend < 0) {
-                            pend = w2;
-                            st.node = m2;
-                        } else {
-                            waiting = true;
-                            st.node = st.node + 1;
-                        }
-                    } else {
-                        st.node = st.node + 2;
-                    }
-                }
-            }
-            const uint32_t pm = __ballot_sync(0xffffffffu, pend >= 0);
-            const uint32_t urgent = __ballot_sync(0xffffffffu, waiting || (pend >= 0 && st.node < 0));
-            if (urgent || __popc(pm) >= kTraceLeafBatch) {
-                if (pend >= 0) {
-                    trav_leaf(S, st, pend >> 3, pend & 7);
-                    pend = -1;
-                }
-            }
-            if (__ballot_sync(0xffffffffu, ray >= 0 && (st.node >= 0 || pend >= 0)) == 0) break;
-        }
+        trav_steps(S, st, pend, ray >= 0, cap);
         const bool fin = ray >= 0 && st.node < 0 && pend < 0;
         bool flag = false;
         if (fin) {
@@ -231,6 +148,7 @@ gspd::DevScene gsp_dev_scene(const gsp_scene* s) {
     d.nodes = s->d_nodes;
     d.tris = s->d_tris;
     d.shade = s->d_shade;
+    d.nlo = s->d_nlo;
     d.mats = s->d_mats;
     d.nnodes = s->bvh.nnodes;
     d.stride = s->bvh.stride;
@@ -312,6 +230,7 @@ void gsp_scene_destroy(gsp_scene* s) {
         cudaSetDevice(s->ctx->device);
         scene_free_bvh(s);
         cudaFree(s->d_shade);
+        cudaFree(s->d_nlo);
         cudaFree(s->d_mats);
         cudaFree(s->d_counter);
         cudaFree(s->d_rlist);
@@ -365,7 +284,7 @@ gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, co
     s->extent = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
                           (hi[2] - lo[2]) * (hi[2] - lo[2]));
     // shading record per triangle: unit geometric normal (computed in FP64) + material
-    std::vector<float4> shade(nt);
+    std::vector<float4> shade(nt), nlo(nt);
     for (int64_t i = 0; i < nt; ++i) {
         const float* a = verts + 3 * (int64_t)tris[3 * i];
         const float* b = verts + 3 * (int64_t)tris[3 * i + 1];
@@ -378,7 +297,10 @@ gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, co
         int32_t m = s->tri_mat[i];
         float mf;
         std::memcpy(&mf, &m, 4);
-        shade[i] = float4{(float)(n[0] * il), (float)(n[1] * il), (float)(n[2] * il), mf};
+        const double u[3] = {n[0] * il, n[1] * il, n[2] * il};
+        shade[i] = float4{(float)u[0], (float)u[1], (float)u[2], mf};
+        nlo[i] = float4{(float)(u[0] - (double)shade[i].x), (float)(u[1] - (double)shade[i].y),
+                        (float)(u[2] - (double)shade[i].z), 0.0f};
     }
     std::vector<float4> mt(2 * nmat);
     for (int32_t m = 0; m < nmat; ++m) {
@@ -392,9 +314,11 @@ gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, co
         return GSP_OK;
     }
     cudaError_t e = cudaMalloc(&s->d_shade, nt * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_nlo, nt * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_mats, 2 * nmat * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(s->d_shade, shade.data(), nt * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_nlo, nlo.data(), nt * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_mats, mt.data(), 2 * nmat * sizeof(float4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         gsp_set_last_error(cudaGetErrorString(e));

@@ -92,6 +92,7 @@ struct DevScene {
     const float4* __restrict__ nodes;  // link_sets * nnodes * 2
     const float4* __restrict__ tris;   // 3 per triangle, leaf order
     const float4* __restrict__ shade;  // per triangle (upload order): normal xyz, material bits
+    const float4* __restrict__ nlo;    // per triangle (upload order): FP32 remainder of the normal
     const float4* __restrict__ mats;   // 2 per material
     int64_t nnodes;
     int64_t stride;  // nodes per link set in memory (nnodes + 1 padding node)
@@ -165,6 +166,69 @@ __device__ __forceinline__ float hit_error_factor(const float4* __restrict__ tri
 // Hits whose estimated amplification exceeds this are re-evaluated in FP64 (expected FP32
 // relative error below about 64 * 6e-8 ~ 4e-6 for the rest).
 #define GSP_REFINE_FACTOR 64.0f
+
+// Error-free transformations in FP32: a + b = s + e exactly (Knuth's two-sum) and a * b = p + e
+// exactly (two-product with one FMA). Sums and dot products built from them carry about twice
+// the working precision (Ogita, Rump & Oishi, SIAM J. Sci. Comput. 26(6), 2005).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// (nh + nl) . (vh + vl) as a normalised double-float hi + lo (|lo| <= ulp(hi) / 2): the
+// products nh * vh exactly, the cross terms once rounded, nl * vl dropped. Normalising matters
+// when the dot product cancels: the quotient below corrects only to first order in lo / hi.
+__device__ __forceinline__ void dot2(float3 nh, float3 nl, float3 vh, float3 vl, float& hi, float& lo) {
+    float p0, e0, p1, e1, p2, e2, c;
+    two_prod(nh.x, vh.x, p0, e0);
+    two_prod(nh.y, vh.y, p1, e1);
+    two_prod(nh.z, vh.z, p2, e2);
+    two_sum(p0, p1, hi, lo);
+    two_sum(hi, p2, hi, c);
+    lo = __fadd_rn(lo, c);
+    lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(e0, e1), e2));
+    lo = __fmaf_rn(nh.x, vl.x, __fmaf_rn(nh.y, vl.y, __fmaf_rn(nh.z, vl.z, lo)));
+    lo = __fmaf_rn(nl.x, vh.x, __fmaf_rn(nl.y, vh.y, __fmaf_rn(nl.z, vh.z, lo)));
+    two_sum(hi, lo, hi, lo);
+}
+
+// Distance along the ray to the plane through v0 with unit normal nh + nl (a double-float
+// normal, exact to ~2^-48), t = n.(v0 - o) / n.d, with v0 - o formed exactly and both dot
+// products and the quotient carried in double-float FP32 arithmetic: t comes out within about
+// one FP32 rounding of the exact value, at FP32 instruction cost (GB300's FP64 rate is a small
+// fraction of its FP32 rate). Returns false if the ray is parallel to the plane.
+__device__ __forceinline__ bool plane_t(float3 v0, float3 nh, float3 nl, float3 o, float3 d, float& t) {
+    float3 sh, sl;
+    two_sum(v0.x, -o.x, sh.x, sl.x);
+    two_sum(v0.y, -o.y, sh.y, sl.y);
+    two_sum(v0.z, -o.z, sh.z, sl.z);
+    float num_h, num_l, den_h, den_l;
+    dot2(nh, nl, sh, sl, num_h, num_l);
+    dot2(nh, nl, d, make_float3(0.0f, 0.0f, 0.0f), den_h, den_l);
+    if (den_h == 0.0f) return false;
+    const float q = __fdiv_rn(num_h, den_h);
+    const float r = __fadd_rn(__fmaf_rn(-q, den_h, num_h), __fmaf_rn(-q, den_l, num_l));  // num - q den
+    t = __fadd_rn(q, __fdiv_rn(r, den_h));
+    return true;
+}
+
+// SPPM hits (eye hit points and photon positions, where t decides which side of a gather radius
+// a photon falls): t from the plane of the winning triangle (slot in leaf order, upload-order
+// index id) in double-float arithmetic.
+__device__ __forceinline__ void refine_plane(const float4* __restrict__ tris, const float4* __restrict__ shade,
+                                             const float4* __restrict__ nlo, int32_t slot, int32_t id, float3 o,
+                                             float3 d, float& t) {
+    const float3 v0 = f3(__ldg(tris + 3 * (int64_t)slot));
+    const float3 nh = f3(__ldg(shade + id)), nl = f3(__ldg(nlo + id));
+    float tt;
+    if (plane_t(v0, nh, nl, o, d, tt)) t = tt;
+}
 
 // Traversal state of one ray (Fig. 3): current node in the ray's link set, best hit so far.
 struct Trav {
@@ -258,10 +322,10 @@ __device__ __forceinline__ void trav_step(const DevScene& S, Trav& st) {
     }
 }
 
-// Closest hit of one ray (used by the eye and photon passes): traversal to the end, then the
-// winner's t, u, v re-evaluated in FP64 (always, or only when the FP32 value may be
-// inaccurate). SPPM hit points always take the FP64 value: photons near the gather radius then
-// fall on the same side of it as in an exact evaluation far more often.
+// Closest hit of one ray: traversal to the end, then the winner's t re-evaluated, either always
+// from its plane in double-float arithmetic (SPPM hit points: photons near the gather radius then
+// fall on the same side of it as in an exact evaluation far more often), or with t, u, v in FP64
+// when the FP32 value may be inaccurate.
 template <bool ALWAYS_REFINE>
 __device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, float tmin, float tmax) {
     Trav st;
@@ -280,7 +344,10 @@ __device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, f
     h.u = h.v = 0.0f;
     if (st.slot >= 0) {
         const float4* tri = S.tris + 3 * st.slot;
-        if (ALWAYS_REFINE || hit_error_factor(tri, o, d, h.t, h.u, h.v) > GSP_REFINE_FACTOR) refine_hit(tri, o, d, h);
+        if (ALWAYS_REFINE)
+            refine_plane(S.tris, S.shade, S.nlo, st.slot, h.id, o, d, h.t);
+        else if (hit_error_factor(tri, o, d, h.t, h.u, h.v) > GSP_REFINE_FACTOR)
+            refine_hit(tri, o, d, h);
     }
     return h;
 }

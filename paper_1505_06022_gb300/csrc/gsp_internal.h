@@ -51,6 +51,7 @@ struct gsp_scene {
     double extent = 0;  // diagonal of the vertex bounding box
     // device copies
     float4* d_shade = nullptr;  // per triangle (upload order): unit normal xyz, material (int bits)
+    float4* d_nlo = nullptr;    // per triangle (upload order): unit normal - its FP32 rounding (xyz)
     float4* d_mats = nullptr;   // per material: {albedo.rgb, type bits}, {emission.rgb, ior}
     float4* d_nodes = nullptr;
     float4* d_tris = nullptr;

@@ -1,0 +1,130 @@
+// persist.cuh -- the machinery shared by the persistent traversal kernels (closest hit, eye
+// paths, photon paths): warp-level work distribution with per-lane refill, and the stackless
+// traversal steps of Fig. 3 with postponed leaf tests.
+#pragma once
+
+#include "launch.h"
+
+namespace gspd {
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Work distribution of a persistent kernel over items [0, n). A warp takes kTraceChunk
+// consecutive items at a time and hands them to its lanes as they become free, so a lane whose
+// item has finished starts the next one without waiting for the rest of the warp. Each warp's
+// first chunk is static (an empty or short launch costs no atomics); later chunks come from a
+// counter that the caller has zeroed and that counts past the static chunks. All fields are
+// warp-uniform.
+struct WarpQueue {
+    int32_t n, static_end, qbase, qend;
+    bool done;
+
+    __device__ __forceinline__ void init(int32_t n_) {
+        n = n_;
+        const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+        static_end = (int32_t)min(warps * kTraceChunk, (int64_t)n);
+        qbase = (int32_t)min(((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTraceChunk, (int64_t)n);
+        qend = min(qbase + kTraceChunk, n);
+        done = false;
+    }
+
+    // Lanes with `need` set receive the next item (-1 once the queue is exhausted).
+    template <typename CounterT>
+    __device__ __forceinline__ int32_t take(bool need, CounterT* ctr) {
+        int32_t item = -1;
+        const uint32_t lt = lanemask_lt();
+        need = need && !done;
+        uint32_t m = __ballot_sync(0xffffffffu, need);
+        while (m) {
+            if (qbase >= qend) {
+                CounterT b = 0;
+                if (static_end < n && (threadIdx.x & 31) == 0) b = atomicAdd(ctr, (CounterT)kTraceChunk);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                qbase = (int32_t)min((int64_t)static_end + (int64_t)b, (int64_t)n);
+                qend = min(qbase + kTraceChunk, n);
+                if (qbase >= n) {
+                    done = true;
+                    break;
+                }
+            }
+            const int take = min(__popc(m), qend - qbase);
+            const int rank = __popc(m & lt);
+            if (need && rank < take) {
+                item = qbase + rank;
+                need = false;
+            }
+            qbase += take;
+            m = __ballot_sync(0xffffffffu, need);
+        }
+        return item;
+    }
+};
+
+// Up to kTraceInner traversal steps of the warp's active lanes. A lane that reaches a leaf keeps
+// it pending and goes on along the miss link with its current best t (which can only make it
+// visit more nodes, never skip the winner); when it meets a second leaf it waits. The warp tests
+// all pending leaves together when kTraceLeafBatch lanes hold one, when a lane waits, or when a
+// lane's walk has ended. A walk is over when st.node < 0 and pend < 0. `cap` bounds the box
+// tests of one walk (corrupt links end the walk with GSP_ERR_TRAVERSAL_LIMIT).
+__device__ __forceinline__ void trav_steps(const DevScene& S, Trav& st, int32_t& pend, bool active, int32_t cap) {
+#pragma unroll 1
+    for (int it = 0; it < kTraceInner; ++it) {
+        bool waiting = false;
+        if (active && st.node >= 0) {
+            // one fetch brings the node and the next node in preorder (its first child when it
+            // is internal, usually in the same cache line); both boxes can be tested
+            const float4* np = st.nodes + 2 * st.node;
+            const float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2), D = __ldg(np + 3);
+            st.steps += 1;
+            int32_t word, miss;
+            if (st.steps > cap) {
+                report(S.status, -4);
+                st.node = -1;
+            } else if (!box_hit(st, A, B, word, miss)) {
+                st.node = miss;
+            } else if (word >= 0) {
+                if (pend < 0) {
+                    pend = word;
+                    st.node = miss;
+                } else {
+                    waiting = true;
+                }
+            } else {
+                st.steps += 1;
+                int32_t w2, m2;
+                if (!box_hit(st, C, D, w2, m2)) {
+                    st.node = m2;
+                } else if (w2 >= 0) {
+                    if (pend < 0) {
+                        pend = w2;
+                        st.node = m2;
+                    } else {
+                        waiting = true;
+                        st.node = st.node + 1;
+                    }
+                } else {
+                    st.node = st.node + 2;
+                }
+            }
+        }
+        const uint32_t pm = __ballot_sync(0xffffffffu, pend >= 0);
+        const uint32_t urgent = __ballot_sync(0xffffffffu, waiting || (pend >= 0 && st.node < 0));
+        if (urgent || __popc(pm) >= kTraceLeafBatch) {
+            if (pend >= 0) {
+                trav_leaf(S, st, pend >> 3, pend & 7);
+                pend = -1;
+            }
+        }
+        if (__ballot_sync(0xffffffffu, active && (st.node >= 0 || pend >= 0)) == 0) break;
+    }
+}
+
+__device__ __forceinline__ int32_t trav_cap(const DevScene& S) {
+    return (int32_t)min(4 * S.nnodes + 16, (int64_t)INT32_MAX);  // box tests incl. retests
+}
+
+}  // namespace gspd

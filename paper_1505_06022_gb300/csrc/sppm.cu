@@ -22,6 +22,7 @@
 #include "devcommon.cuh"
 #include "gsp_internal.h"
 #include "launch.h"
+#include "persist.cuh"
 #include "scan_sort.h"
 
 namespace gspd {
@@ -168,13 +169,22 @@ struct PathQ {
     float* t;
 };
 
-// A wavefront hit given as a leaf-ordered triangle slot: FP64 distance from the slot's exact
-// vertices (every lane of the shade kernel does this, so the FP64 work runs in full warps);
-// returns the triangle's upload-order index.
+// A wavefront hit given as a leaf-ordered triangle slot: t from the triangle's plane in
+// double-float arithmetic (as for per-thread paths); returns the upload-order index.
 __device__ __forceinline__ int32_t slot_refine(const DevScene& S, float3 o, float3 d, Hit& h) {
-    const float4* tri = S.tris + 3 * (int64_t)h.id;
-    refine_hit(tri, o, d, h);
-    return __float_as_int(__ldg(tri).w);
+    const int32_t id = __float_as_int(__ldg(S.tris + 3 * (int64_t)h.id).w);
+    refine_plane(S.tris, S.shade, S.nlo, h.id, id, o, d, h.t);
+    return id;
+}
+
+// Closest hit of a finished walk (trav_steps), t refined as above.
+__device__ __forceinline__ Hit walk_hit(const DevScene& S, const Trav& st) {
+    Hit h;
+    h.id = st.best;
+    h.t = st.tbest;
+    h.u = h.v = 0.0f;
+    if (st.slot >= 0) refine_plane(S.tris, S.shade, S.nlo, st.slot, h.id, st.o, st.d, h.t);
+    return h;
 }
 
 // Appends the lanes with `keep` set to queue Q (warp-aggregated: one atomic per warp).
@@ -255,7 +265,8 @@ __device__ __forceinline__ bool eye_interact(const DevScene& S, const PassDev& P
 
 // Primary rays: one per pixel, jittered inside the pixel; the queue starts in pixel order.
 __global__ void __launch_bounds__(256)
-k_eye_emit(CamDev C, PassDev P, PathQ Q, EyeOut O, uint32_t* __restrict__ qn, unsigned long long* __restrict__ trace_ctr) {
+k_eye_emit(CamDev C, PassDev P, PathQ Q, EyeOut O, uint32_t* __restrict__ qn, unsigned long long* __restrict__ trace_ctr,
+           uint32_t* __restrict__ tail_ctr) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t npix = (int64_t)C.w * C.h;
     if (p == 0) {
@@ -263,6 +274,7 @@ k_eye_emit(CamDev C, PassDev P, PathQ Q, EyeOut O, uint32_t* __restrict__ qn, un
         qn[0] = (uint32_t)npix;
         qn[1] = 0;
         qn[2] = 0;
+        *tail_ctr = 0;  // work counter of k_paths
     }
     if (p >= npix) return;
     const int px = (int)(p % C.w), py = (int)(p / C.w);
@@ -314,24 +326,6 @@ k_eye_shade(DevScene S, PassDev P, PathQ cur, PathQ nxt, EyeOut O, uint32_t* __r
             }
         }
         queue_push(nxt, qn + (b + 1) % 3, keep, o, P.eps, d, w, p, rng, depth + 1);
-    }
-}
-
-// The eye paths still in queue qn[b % 3] after the wavefront steps, finished one per thread.
-__global__ void __launch_bounds__(128)
-k_eye_tail(DevScene S, PassDev P, PathQ cur, EyeOut O, const uint32_t* __restrict__ qn, int b) {
-    const uint32_t n = qn[b % 3];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float4 a = cur.ray[2 * (size_t)i], c = cur.ray[2 * (size_t)i + 1], ww = cur.w[i];
-        float3 o = f3(a), d = f3(c), w = f3(ww);
-        float tmin = a.w;
-        const int32_t p = __float_as_int(ww.w);
-        Rng rng = rng_from(cur.rng[i]);
-        for (int depth = cur.meta[i]; depth <= P.max_eye; ++depth) {
-            const Hit h = traverse<true>(S, o, d, tmin, __int_as_float(0x7f800000));
-            if (h.id < 0 || !eye_interact(S, P, O, p, h, o, d, w, rng)) break;
-            tmin = P.eps;
-        }
     }
 }
 
@@ -408,13 +402,14 @@ __device__ __forceinline__ bool photon_bounce(const DevScene& S, const PassDev& 
 // Photon paths: emission into the queue in path order (whole paths per pass).
 __global__ void __launch_bounds__(256)
 k_photon_emit(EmitDev E, PassDev P, PathQ Q, uint32_t* __restrict__ pcount, uint32_t* __restrict__ qn,
-              unsigned long long* __restrict__ trace_ctr) {
+              unsigned long long* __restrict__ trace_ctr, uint32_t* __restrict__ tail_ctr) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) {
         trace_ctr[0] = 0ull;
         qn[0] = (uint32_t)P.np;
         qn[1] = 0;
         qn[2] = 0;
+        *tail_ctr = 0;  // work counter of k_paths
     }
     if (k >= P.np) return;
     Rng rng = rng_seed(P.seed, P.scene_id, 1u, pass_index(P), (uint64_t)k);
@@ -471,25 +466,65 @@ k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32
     }
 }
 
-// The photon paths still in queue qn[b % 3] after the wavefront steps, finished one per thread.
-__global__ void __launch_bounds__(128)
-k_photon_tail(DevScene S, PassDev P, DepositDev D, PathQ cur, const uint32_t* __restrict__ qn, int b) {
-    const uint32_t n = qn[b % 3];
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float4 a = cur.ray[2 * (size_t)i], c = cur.ray[2 * (size_t)i + 1], ww = cur.w[i];
-        float3 o = f3(a), d = f3(c), phi = f3(ww);
-        const int32_t k = __float_as_int(ww.w);
-        const int32_t meta = cur.meta[i];
-        uint32_t ndep = (uint32_t)(meta >> 8);
-        Rng rng = rng_from(cur.rng[i]);
-        for (int depth = meta & 0xff; depth < P.max_photon; ++depth) {
-            const Hit h = traverse<true>(S, o, d, P.eps, __int_as_float(0x7f800000));
-            if (h.id < 0) break;
-            const uint32_t id = (uint32_t)k * kSlotsPerPath + depth;
-            const uint32_t slot = (uint32_t)k * kSlotsPerPath + ndep;
-            if (!photon_bounce(S, P, D, rng, h, o, d, phi, id, slot, ndep)) break;
+// The eye and photon paths left in their queues after the wavefront steps (all of them when
+// there are none), finished by one persistent kernel: items [0, ne) are eye-queue entries,
+// [ne, ne + nph) photon-queue entries. Each lane follows one path bounce by bounce and takes the
+// next item as soon as its path ends (WarpQueue, counter *ctr), so the long specular eye paths,
+// which start first, run beside the bulk of the photon work instead of after it. Eye entries
+// have depth <= max_eye, photon entries depth < max_photon (the host launches accordingly).
+__global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
+k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ ne_ptr, PathQ qp, DepositDev D,
+        const uint32_t* __restrict__ np_ptr, uint32_t* __restrict__ ctr) {
+    const int32_t cap = trav_cap(S);
+    const int32_t ne = ne_ptr ? (int32_t)*ne_ptr : 0;
+    const int32_t nph = np_ptr ? (int32_t)*np_ptr : 0;
+    WarpQueue wq;
+    wq.init(ne + nph);
+    Trav st;
+    st.node = -1;
+    st.slot = -1;
+    int32_t i = -1, pend = -1, id = 0, depth = 0;
+    uint32_t ndep = 0;
+    bool eye = false;
+    float3 w = make_float3(0.0f, 0.0f, 0.0f);  // eye: throughput; photon: flux
+    Rng rng;
+    while (true) {
+        const int32_t got = wq.take(i < 0, ctr);
+        if (got >= 0) {
+            i = got;
+            eye = got < ne;
+            const PathQ Q = eye ? qe : qp;
+            const size_t j = (size_t)(eye ? got : got - ne);
+            const float4 a = Q.ray[2 * j], c = Q.ray[2 * j + 1], ww = Q.w[j];
+            const int32_t meta = Q.meta[j];
+            w = f3(ww);
+            id = __float_as_int(ww.w);
+            rng = rng_from(Q.rng[j]);
+            depth = eye ? meta : (meta & 0xff);
+            ndep = eye ? 0u : (uint32_t)(meta >> 8);
+            trav_init(S, f3(a), f3(c), eye ? a.w : P.eps, __int_as_float(0x7f800000), st);
         }
-        D.pcount[k] = ndep;
+        if (__ballot_sync(0xffffffffu, i >= 0) == 0) break;
+        trav_steps(S, st, pend, i >= 0, cap);
+        if (i >= 0 && st.node < 0 && pend < 0) {
+            const Hit h = walk_hit(S, st);
+            float3 o = st.o, d = st.d;
+            bool more = false;
+            if (eye) {
+                more = h.id >= 0 && eye_interact(S, P, O, id, h, o, d, w, rng) && ++depth <= P.max_eye;
+            } else {
+                if (h.id >= 0) {
+                    const uint32_t pid = (uint32_t)id * kSlotsPerPath + depth;
+                    const uint32_t slot = (uint32_t)id * kSlotsPerPath + ndep;
+                    more = photon_bounce(S, P, D, rng, h, o, d, w, pid, slot, ndep) && ++depth < P.max_photon;
+                }
+                if (!more) D.pcount[id] = ndep;
+            }
+            if (more)
+                trav_init(S, o, d, P.eps, __int_as_float(0x7f800000), st);
+            else
+                i = -1;
+        }
     }
 }
 
@@ -635,6 +670,20 @@ __device__ __forceinline__ void progressive_update(float4& s0, float4& s1, float
     s0.w = Nn;
 }
 
+// Cells overlapping the box x +- R along one axis. The box is widened by a few ulps of |x| so
+// that a photon which the rounded distance test accepts always lies in one of its cells.
+__device__ __forceinline__ void cell_range(float x, float R, float inv_h, int32_t& lo, int32_t& hi) {
+    const float Rq = fmaf(R, 1.0001f, (fabsf(x) + R) * 4.8e-7f);
+    lo = cell_of(x - Rq, inv_h);
+    hi = cell_of(x + Rq, inv_h);
+}
+
+// Range query + progressive update, one hit point per thread.
+// Exact mode: every cell overlapping the box x +- R is visited (any number per axis, so the cell
+// may be smaller than the radius); a photon that passes the distance test is counted only while
+// its own cell is the one being visited, so a photon whose bucket is shared by several visited
+// cells (hash collisions) is counted once. Stochastic mode: each distinct bucket of the at most
+// 3 x 3 x 3 query cells once, weighted by its count (cell >= 2 r0 there).
 template <bool STOCH>
 __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -647,13 +696,13 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
     float4 s0 = G.st0[p], s1 = G.st1[p];
     const float R = s1.w, R2 = R * R;
     if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
-    uint32_t buckets[27];
-    const int nb = query_buckets(x, R, P.inv_h, P.tmask, buckets);
     float M = 0.0f;
     float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-    for (int q = 0; q < nb; ++q) {
-        const uint32_t b = buckets[q];
-        if (STOCH) {
+    if (STOCH) {
+        uint32_t buckets[27];
+        const int nb = query_buckets(x, R, P.inv_h, P.tmask, buckets);
+        for (int q = 0; q < nb; ++q) {
+            const uint32_t b = buckets[q];
             const uint32_t cnt = G.ecount[b];
             if (cnt == 0) continue;
             const uint32_t slot = (uint32_t)(G.entry[b] & 0xffffffffull);
@@ -663,18 +712,30 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
             const float w = (float)cnt;
             M += w;
             acc = acc + f3(c) * w;
-        } else {
-            const uint32_t e = G.bstart[b + 1];
-            for (uint32_t i = G.bstart[b]; i < e; ++i) {
-                const float4 a = __ldg(G.spos + i);
-                const float3 dx = f3(a) - x;
-                if (!(dot3(dx, dx) < R2 * 1.0001f)) continue;  // cheap pre-test, then the exact one
-                const float4 c = __ldg(G.spay + i);
-                if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
-                M += 1.0f;
-                acc = acc + f3(c);
-            }
         }
+    } else {
+        int32_t lx, hx, ly, hy, lz, hz;
+        cell_range(x.x, R, P.inv_h, lx, hx);
+        cell_range(x.y, R, P.inv_h, ly, hy);
+        cell_range(x.z, R, P.inv_h, lz, hz);
+        const float R2p = R2 * 1.0001f;  // cheap pre-test, then the exact one
+        for (int32_t ix = lx; ix <= hx; ++ix)
+            for (int32_t iy = ly; iy <= hy; ++iy)
+                for (int32_t iz = lz; iz <= hz; ++iz) {
+                    const uint32_t b = cell_hash(ix, iy, iz, P.tmask);
+                    const uint32_t e = __ldg(G.bstart + b + 1);
+                    for (uint32_t i = __ldg(G.bstart + b); i < e; ++i) {
+                        const float4 a = __ldg(G.spos + i);
+                        const float3 dx = f3(a) - x;
+                        if (!(dot3(dx, dx) < R2p)) continue;
+                        if (cell_of(a.x, P.inv_h) != ix || cell_of(a.y, P.inv_h) != iy || cell_of(a.z, P.inv_h) != iz)
+                            continue;  // a colliding cell's photon, counted when its own cell is visited
+                        const float4 c = __ldg(G.spay + i);
+                        if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
+                        M += 1.0f;
+                        acc = acc + f3(c);
+                    }
+                }
     }
     if (G.shist) G.shist[(size_t)pass_index(P) * G.npix + p] = make_float4(acc.x, acc.y, acc.z, 0.0f);
     progressive_update(s0, s1, M, mul3(f, acc), P.alpha);
@@ -913,7 +974,8 @@ struct gsp_sppm {
     unsigned long long* started = nullptr;
     uint32_t* last_order = nullptr;  // sorted slot order of the last exact pass
     // wavefront queues (ping-pong) and their tuning
-    PathQ q[2]{};
+    PathQ q[2]{};   // photon wavefront queues (np entries; full paths only)
+    PathQ qe[2]{};  // eye wavefront queues (npix entries)
     int64_t qcap = 0;
     int32_t eye_steps = 1;      // eye wavefront steps before the per-thread paths
     int32_t photon_steps = 1;   // photon wavefront steps before the per-thread paths
@@ -970,7 +1032,9 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     if (P.cell_h == 0.0f) P.cell_h = 2.0f * P.r0;
     // the range query visits at most three cells per axis: exact mode needs h >= R (R <= r0);
     // stochastic hashing's estimator is defined with h >= 2 r0
-    if (!(P.cell_h >= P.r0) || (P.hash_mode == GSP_STOCHASTIC && P.cell_h < 2.0f * P.r0)) return GSP_ERR_INVALID_ARG;
+    if (!(P.cell_h >= 0.25f * P.r0) || !std::isfinite(P.cell_h) ||
+        (P.hash_mode == GSP_STOCHASTIC && P.cell_h < 2.0f * P.r0))
+        return GSP_ERR_INVALID_ARG;
     if (P.table_size == 0) {
         P.table_size = 1;
         while (P.table_size < 2 * P.photons_per_pass) P.table_size *= 2;
@@ -1074,7 +1138,7 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     A(&r->slots, 2 * r->slot_cap);
     A(&r->pcount, r->np);
     A(&r->poff, r->np);
-    A(&r->counters, 8);
+    A(&r->counters, 16);
     A(&r->started, 1);
     const int64_t scan_tmp = std::max({gsp_scan_temp_elems(r->np), gsp_scan_temp_elems(r->T),
                                        gsp_scan_temp_elems(gsp_sort_hist_elems())});
@@ -1095,15 +1159,22 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     }
     r->qcap = std::max(r->npix, P.photon_mode == GSP_FULL_PATH ? r->np : (int64_t)0);
     r->eye_steps = 1;     // one wavefront step (all primary / first photon rays through the
-    r->photon_steps = 1;  // closest-hit kernel), then per-thread paths: in scenes with long rays
-                          // every further step waits for its slowest ray and costs more than it saves
+    r->photon_steps = 1;  // closest-hit kernel), then persistent per-lane paths: in scenes with
+                          // long rays every further step waits for its slowest ray
+    const int64_t nq = P.photon_mode == GSP_FULL_PATH ? r->np : 0;
     for (int b = 0; b < 2; ++b) {
-        A(&r->q[b].ray, 2 * r->qcap);
-        A(&r->q[b].w, r->qcap);
-        A(&r->q[b].rng, r->qcap);
-        A(&r->q[b].meta, r->qcap);
-        A(&r->q[b].tri, r->qcap);
-        A(&r->q[b].t, r->qcap);
+        A(&r->q[b].ray, 2 * nq);
+        A(&r->q[b].w, nq);
+        A(&r->q[b].rng, nq);
+        A(&r->q[b].meta, nq);
+        A(&r->q[b].tri, nq);
+        A(&r->q[b].t, nq);
+        A(&r->qe[b].ray, 2 * r->npix);
+        A(&r->qe[b].w, r->npix);
+        A(&r->qe[b].rng, r->npix);
+        A(&r->qe[b].meta, r->npix);
+        A(&r->qe[b].tri, r->npix);
+        A(&r->qe[b].t, r->npix);
     }
     if (e == cudaSuccess) e = gsp_scene_reserve_rays(s, r->qcap);
     if (P.photon_mode == GSP_REGEN) {
@@ -1118,7 +1189,7 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemset(r->started, 0, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(r->counters, 0, 8 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(r->counters, 0, 16 * sizeof(uint32_t));
     if (e == cudaSuccess && r->ro) {
         e = cudaMemset(r->ro, 0, r->np * sizeof(float4));
         if (e == cudaSuccess) e = cudaMemset(r->rd, 0, r->np * sizeof(float4));
@@ -1160,34 +1231,52 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
     return P;
 }
 
-static unsigned shade_blocks(const gsp_sppm* r) { return (unsigned)std::min<int64_t>(blocks(r->qcap, 256), 4 * 152); }
+// Renderer counters (uint32): [0] deposits of the pass, [4..6] eye queue lengths, [8..10] photon
+// queue lengths (three each, used in rotation), [12] work counter of k_paths, [7] pass index of a
+// replayed graph.
+static unsigned shade_blocks(int64_t n) { return (unsigned)std::min<int64_t>(blocks(n, 256), 4 * 152); }
 
-// Eye pass: wavefront steps, then the remaining specular chains one per thread.
-static gsp_status stage_eye(gsp_sppm* r, const PassDev& P, const EyeOut& O, cudaStream_t st) {
-    gsp_scene* s = r->scene;
-    const DevScene S = gsp_dev_scene(s);
-    uint32_t* qn = r->counters + 4;  // wavefront queue lengths (three, used in rotation)
-    unsigned long long* tctr = s->d_counter;
-    const bool list = r->refine_factor > 0.0f;  // 0: every hit takes the FP64 distance in the shade kernel
-    const float rf = list ? r->refine_factor : INFINITY;
-    k_eye_emit<<<blocks(r->npix, 256), 256, 0, st>>>(r->cam, P, r->q[0], O, qn, tctr);
-    int b = 0;
-    for (; b < r->eye_steps; ++b) {
-        const PathQ& cur = r->q[b & 1];
-        GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->npix, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
-        k_eye_shade<<<shade_blocks(r), 256, 0, st>>>(S, P, cur, r->q[(b + 1) & 1], O, qn, b, tctr);
+// Grid of k_paths: resident blocks on every SM, but no more warps than items.
+static int path_grid(int64_t items, int device) {
+    static int per_sm[64] = {0};
+    static int sms[64] = {0};
+    if (device < 0 || device >= 64) device = 0;
+    if (!per_sm[device]) {
+        int b = 0;
+        cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths, kTraceThreads, 0);
+        per_sm[device] = std::max(1, b);
     }
-    // one thread per remaining path (the queue length is only known on the device)
-    if (b <= r->P.max_eye_depth) k_eye_tail<<<blocks(r->npix, 128), 128, 0, st>>>(S, P, r->q[b & 1], O, qn, b);
-    GSP_CUDA_TRY(cudaGetLastError());
-    return GSP_OK;
+    const int64_t full = (int64_t)std::max(1, sms[device]) * per_sm[device];
+    const int64_t need = (items + kTraceThreads - 1) / kTraceThreads;
+    return (int)std::max<int64_t>(1, std::min(full, need));
 }
 
-// Photon pass: whole paths (wavefront steps + per-thread paths) or one bounce per thread.
-static gsp_status stage_photons(gsp_sppm* r, const PassDev& P, const DepositDev& D, cudaStream_t st) {
+// Eye pass up to the persistent kernel: primary rays, then eye_steps wavefront steps. Returns in
+// b the queue holding the paths still going (none if b > max_eye_depth).
+static gsp_status eye_front(gsp_sppm* r, const PassDev& P, const EyeOut& O, cudaStream_t st, int& b) {
     gsp_scene* s = r->scene;
     const DevScene S = gsp_dev_scene(s);
     uint32_t* qn = r->counters + 4;
+    unsigned long long* tctr = s->d_counter;
+    const bool list = r->refine_factor > 0.0f;  // 0: every hit is refined in the shade kernel
+    const float rf = list ? r->refine_factor : INFINITY;
+    k_eye_emit<<<blocks(r->npix, 256), 256, 0, st>>>(r->cam, P, r->qe[0], O, qn, tctr, r->counters + 12);
+    for (b = 0; b < r->eye_steps && b <= r->P.max_eye_depth; ++b) {
+        const PathQ& cur = r->qe[b & 1];
+        GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->npix, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
+        k_eye_shade<<<shade_blocks(r->npix), 256, 0, st>>>(S, P, cur, r->qe[(b + 1) & 1], O, qn, b, tctr);
+    }
+    return GSP_OK;
+}
+
+// Photon pass up to the persistent kernel: emission and photon_steps wavefront steps of whole
+// paths (b = the queue still going; none if b >= max_photon_depth), or the one-bounce-per-thread
+// pass of Sec. 3.3 (b = -1).
+static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& D, cudaStream_t st, int& b) {
+    gsp_scene* s = r->scene;
+    const DevScene S = gsp_dev_scene(s);
+    uint32_t* qn = r->counters + 8;
     unsigned long long* tctr = s->d_counter;
     const bool list = r->refine_factor > 0.0f;
     const float rf = list ? r->refine_factor : INFINITY;
@@ -1196,19 +1285,36 @@ static gsp_status stage_photons(gsp_sppm* r, const PassDev& P, const DepositDev&
         k_fill_u64<<<1024, 256, 0, st>>>(r->entry, r->T, ~0ull);
         GSP_CUDA_TRY(cudaMemsetAsync(r->ecount, 0, r->T * sizeof(uint32_t), st));
     }
+    b = -1;
     if (r->P.photon_mode == GSP_FULL_PATH) {
-        k_photon_emit<<<blocks(r->np, 256), 256, 0, st>>>(E, P, r->q[0], r->pcount, qn, tctr);
-        int b = 0;
-        for (; b < r->photon_steps; ++b) {
+        k_photon_emit<<<blocks(r->np, 256), 256, 0, st>>>(E, P, r->q[0], r->pcount, qn, tctr, r->counters + 12);
+        for (b = 0; b < r->photon_steps && b < r->P.max_photon_depth; ++b) {
             const PathQ& cur = r->q[b & 1];
             GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->np, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
-            k_photon_shade<<<shade_blocks(r), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
+            k_photon_shade<<<shade_blocks(r->np), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
         }
-        if (b < r->P.max_photon_depth)
-            k_photon_tail<<<blocks(r->np, 128), 128, 0, st>>>(S, P, D, r->q[b & 1], qn, b);
     } else {
         RegenDev R{r->ro, r->rd, r->rphi, r->started};
         k_photon_regen<<<blocks(r->np, 128), 128, 0, st>>>(S, E, P, D, R);
+    }
+    return GSP_OK;
+}
+
+// Eye and photon passes of one pass (Sec. 2): both fronts, then one persistent kernel finishes
+// the eye and photon paths still going.
+static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, const DepositDev& D, cudaStream_t st) {
+    int be = 0, bp = -1;
+    gsp_status e = eye_front(r, P, O, st, be);
+    if (e == GSP_OK) e = photon_front(r, P, D, st, bp);
+    if (e != GSP_OK) return e;
+    const bool eye_left = be <= r->P.max_eye_depth;
+    const bool ph_left = bp >= 0 && bp < r->P.max_photon_depth;
+    if (eye_left || ph_left) {
+        const int64_t items = (eye_left ? r->npix : 0) + (ph_left ? r->np : 0);
+        const DevScene S = gsp_dev_scene(r->scene);
+        k_paths<<<path_grid(items, r->scene->ctx->device), kTraceThreads, 0, st>>>(
+            S, P, r->qe[be & 1], O, eye_left ? r->counters + 4 + be % 3 : nullptr, r->q[ph_left ? bp & 1 : 0], D,
+            ph_left ? r->counters + 8 + bp % 3 : nullptr, r->counters + 12);
     }
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
@@ -1245,8 +1351,7 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
         gsp_set_last_error("gsp_sppm_pass: more passes than gsp_sppm_enable_grad reserved radius history for");
         return GSP_ERR_OVERFLOW;
     }
-    gsp_status e = stage_eye(r, P, O, st);
-    if (e == GSP_OK) e = stage_photons(r, P, D, st);
+    gsp_status e = stage_paths(r, P, O, D, st);
     if (e != GSP_OK) return e;
     GatherDev G{};
     G.hx = r->hx;
@@ -1360,8 +1465,7 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
     for (int64_t i = 0; i < r->passes; ++i) {
         // replay pass i from its PRNG counters: the same hit points, photons and radii
         const PassDev P = pass_params(r, i);
-        gsp_status e = stage_eye(r, P, O, st);
-        if (e == GSP_OK) e = stage_photons(r, P, D, st);
+        gsp_status e = stage_paths(r, P, O, D, st);
         if (e == GSP_OK) e = stage_deposit(r, P, st);
         if (e != GSP_OK) return e;
         e = gsp_grid_build_with(r->hx, r->npix, hp_cell, r->hp_T, r->hp_order, r->hp_bstart, r->hp_scratch, st, true);
@@ -1524,22 +1628,23 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     if (ce == cudaSuccess) ce = cudaEventCreate(&a);
     if (ce == cudaSuccess) ce = cudaEventCreate(&z);
     struct Cand { int32_t es, ps; float cell; };
-    std::vector<Cand> cands;
-    const bool full = r->P.photon_mode == GSP_FULL_PATH;
-    const std::vector<float> cells = r->P.hash_mode == GSP_EXACT ? std::vector<float>{2.0f, 1.5f, 1.0f}
-                                                                 : std::vector<float>{r->P.cell_h / r->P.r0};
-    for (float c : cells)
-        for (int32_t es : {0, 1, 2})
-            for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2, 4} : std::vector<int32_t>{0})
-                cands.push_back({es, ps, c * r->P.r0});
+    int32_t ncand = 0;
     float best = INFINITY, first = INFINITY;
-    Cand pick = cands[0];
-    for (size_t i = 0; i < cands.size() && ce == cudaSuccess && e == GSP_OK; ++i) {
-        t->eye_steps = cands[i].es;
-        t->photon_steps = cands[i].ps;
-        t->inv_h = 1.0f / cands[i].cell;
-        e = sppm_one_pass(t, st);  // warm-up
-        if (e != GSP_OK) break;
+    Cand pick{r->eye_steps, r->photon_steps, r->P.cell_h};
+    // Each candidate starts from a fresh state (radii r0), runs one untimed pass and times
+    // trial_passes more, so every candidate sees the same radii.
+    auto trial = [&](const Cand& c) {
+        if (ce != cudaSuccess || e != GSP_OK) return;
+        t->eye_steps = c.es;
+        t->photon_steps = c.ps;
+        t->inv_h = 1.0f / c.cell;
+        t->passes = 0;
+        k_init_state<<<blocks(t->npix, 256), 256, 0, st>>>(t->st0, t->st1, t->npix, t->P.r0);
+        ce = cudaMemsetAsync(t->started, 0, sizeof(unsigned long long), st);
+        if (ce == cudaSuccess && t->rd) ce = cudaMemsetAsync(t->rd, 0, t->np * sizeof(float4), st);
+        if (ce != cudaSuccess) return;
+        e = sppm_one_pass(t, st);
+        if (e != GSP_OK) return;
         ce = cudaEventRecord(a, st);
         for (int32_t k = 0; k < trial_passes && e == GSP_OK; ++k) e = sppm_one_pass(t, st);
         if (ce == cudaSuccess) ce = cudaEventRecord(z, st);
@@ -1547,11 +1652,22 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         float ms = 0.0f;
         if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, z);
         ms /= (float)trial_passes;
-        if (i == 0) first = ms;
+        if (ncand++ == 0) first = ms;
         if (ms < best) {
             best = ms;
-            pick = cands[i];
+            pick = c;
         }
+    };
+    // stage 1: wavefront steps at the renderer's cell edge; stage 2: the cell edge (exact mode)
+    const bool full = r->P.photon_mode == GSP_FULL_PATH;
+    trial({r->eye_steps, r->photon_steps, r->P.cell_h});  // the current settings first
+    for (int32_t es : {0, 1, 2})
+        for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2, 4} : std::vector<int32_t>{0})
+            if (es != r->eye_steps || ps != r->photon_steps) trial({es, ps, r->P.cell_h});
+    if (r->P.hash_mode == GSP_EXACT) {
+        const Cand steps = pick;
+        for (float c : {2.0f, 1.5f, 1.0f, 0.75f, 0.5f})
+            if (c * r->P.r0 != r->P.cell_h) trial({steps.es, steps.ps, c * r->P.r0});
     }
     if (st) cudaStreamDestroy(st);
     if (a) cudaEventDestroy(a);
@@ -1572,7 +1688,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         out->cell_h = pick.cell;
         out->ms_per_pass = best;
         out->first_ms_per_pass = first;
-        out->candidates = (int32_t)cands.size();
+        out->candidates = ncand;
     }
     return GSP_OK;
 }

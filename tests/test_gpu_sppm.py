@@ -49,6 +49,37 @@ def test_cornell_deposit_ids_match(ctx):
     assert len(diff) <= 2e-4 * len(oid), f"{len(diff)} of {len(oid)} deposit ids differ"
 
 
+@pytest.mark.parametrize("cell_frac", [0.25, 0.6, 1.0, 3.0])
+def test_exact_gather_any_cell_size(ctx, cell_frac):
+    """Exact hashing finds every photon within R whatever the cell edge, also below the radius
+    (many cells per axis) and far above it (many colliding photons per bucket)."""
+    sc = I.cornell_box(seed=1)
+    r0 = float(np.float32(0.05 * sc.extent()))
+    img, orc, r, st = render_both(ctx, sc, 4, photons_per_pass=16384, seed=1,
+                                  cell_h=float(np.float32(cell_frac * r0)), table_size=1 << 12)
+    ref = orc.state()
+    image_parity(img, ref["image"])
+    image_parity(st["N"].cpu().numpy()[..., None], ref["N"][..., None])
+
+
+def test_exact_gather_counts_do_not_depend_on_cell_size(ctx):
+    """The same photons are found whatever the cell edge: photon counts and radii are bitwise
+    equal, flux sums equal up to summation order."""
+    sc = I.full_scene(seed=9, width=80, height=64, plane_quads=40, sphere_n=8)
+    s = gsp.Scene(ctx, sc)
+    r0 = float(np.float32(0.01 * sc.extent()))
+    states = []
+    for frac in (0.25, 0.5, 1.0, 2.0, 3.0):
+        r = gsp.Renderer(s, gsp.sppm_params(sc, 30000, seed=4, r0_frac=0.01,
+                                            cell_h=float(np.float32(frac * r0))))
+        r.run(3)
+        states.append({k: v.cpu().numpy() if hasattr(v, "cpu") else v for k, v in r.state().items()})
+        r.close()
+    for st in states[1:]:
+        assert np.array_equal(st["N"], states[0]["N"]) and np.array_equal(st["R"], states[0]["R"])
+        np.testing.assert_allclose(st["tau"], states[0]["tau"], rtol=1e-5, atol=1e-7 * states[0]["tau"].max())
+
+
 @pytest.mark.parametrize("photon_mode,hash_mode", [(1, 0), (0, 1), (1, 1)])
 def test_cornell_parity_paper_modes(ctx, photon_mode, hash_mode):
     sc = I.cornell_box(seed=1)
