@@ -220,15 +220,18 @@ void gsp_sppm_destroy(gsp_sppm* r);
  * update N' = N + alpha M, R' = R sqrt((N + alpha M) / (N + M)), tau' = (tau + Phi) R'^2/R^2. */
 gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
 
-/* Execution tuning of the passes (results do not depend on the first two; the third trades
- * accuracy of hit distances for time). eye_steps / photon_steps: wavefront steps (closest hit of
- * a compacted ray queue, then shading that pushes continuing paths to the next queue) before the
- * remaining paths finish one per thread; default 1 and 1 (the first rays of all paths go through
- * the closest-hit kernel together; later wavefront steps each wait for their slowest ray, which in
- * scenes with long rays costs more than it saves).
- * refine_factor: wavefront hits whose estimated FP32 error amplification exceeds it take the FP64
- * distance; 0 (default) = every hit. Paths traced one per thread always take the FP64 value. */
-gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, float refine_factor);
+/* Execution tuning of the passes. eye_steps / photon_steps: wavefront steps (closest hit of a
+ * compacted ray queue, then shading that pushes continuing paths to the next queue) before one
+ * persistent kernel finishes the remaining eye and photon paths lane by lane; default 1 and 1.
+ * Results do not depend on them.
+ * refine_factor: 0 (default) = every wavefront hit takes its distance from the triangle's plane
+ * in double-float arithmetic, as the persistent kernel's hits always do; > 0 = only hits whose
+ * estimated FP32 error amplification exceeds it take an FP64 distance (trades hit-distance
+ * accuracy for time).
+ * gather_lanes: lanes that share one hit point's exact range query (1, 4, 8 or 16; default 8;
+ * 0 = keep); changes only the order in which a pixel sums its photons. */
+gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, float refine_factor,
+                         int32_t gather_lanes);
 
 /* Writes the current estimate L = direct / P + tau / (pi R^2 N_e) to d_rgb [h][w][3] float. */
 gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream);
@@ -278,15 +281,17 @@ typedef struct {
     float cell_h;                    /* chosen hash cell edge (exact mode) */
     float ms_per_pass;               /* its measured time per pass */
     float first_ms_per_pass;         /* time of the renderer's settings before tuning */
-    int32_t candidates;
+    int32_t candidates;              /* settings timed */
+    int32_t gather_lanes;            /* chosen lanes per hit point in the exact gather (1, 4, 8, 16) */
 } gsp_tune_result;
 
 /* Times candidate execution settings that leave the estimate unchanged, each from a fresh state
  * for trial_passes passes (after one untimed pass) on a temporary renderer over the same scene
  * (the renderer's own state is not touched), and applies the fastest: first the eye and photon
  * wavefront steps (0-2 and 0, 1, 2, 4), then in exact mode the hash cell edge (2, 1.5, 1, 0.75
- * or 0.5 times r0; smaller cells scan fewer photons but more buckets). The cell edge changes only
- * the order in which a pixel sums its photons. out may be NULL. */
+ * or 0.5 times r0; smaller cells scan fewer photons but more buckets), then the lanes that share
+ * one hit point's range query (1, 4, 8 or 16). Cell edge and lanes change only the order in which
+ * a pixel sums its photons. out may be NULL. */
 gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out);
 
 /* ---- gradient of an image loss (path-replay adjoint) ------------------------------------- */

@@ -28,8 +28,10 @@ def _nvcc() -> str:
 
 
 def _flags():
+    # GSP_NVCC_EXTRA: extra nvcc arguments, e.g. -DGSP_PATH_MIN_BLOCKS=8 to sweep launch shapes
+    extra = os.environ.get("GSP_NVCC_EXTRA", "").split()
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                   "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+                   "-I", os.path.join(ROOT, "include"), "-I", CSRC] + extra
 
 
 def _digest() -> str:

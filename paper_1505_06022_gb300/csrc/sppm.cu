@@ -678,14 +678,10 @@ __device__ __forceinline__ void cell_range(float x, float R, float inv_h, int32_
     hi = cell_of(x + Rq, inv_h);
 }
 
-// Range query + progressive update, one hit point per thread.
-// Exact mode: every cell overlapping the box x +- R is visited (any number per axis, so the cell
-// may be smaller than the radius); a photon that passes the distance test is counted only while
-// its own cell is the one being visited, so a photon whose bucket is shared by several visited
-// cells (hash collisions) is counted once. Stochastic mode: each distinct bucket of the at most
-// 3 x 3 x 3 query cells once, weighted by its count (cell >= 2 r0 there).
-template <bool STOCH>
-__global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
+// Stochastic range query + progressive update, one hit point per thread: each distinct bucket
+// of the at most 3 x 3 x 3 query cells once, its survivor weighted by the bucket's count (the
+// cell edge is >= 2 r0 in this mode).
+__global__ void __launch_bounds__(128) k_gather_stoch(GatherDev G, PassDev P) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= G.npix) return;
     const float4 hxp = G.hx[p];
@@ -694,51 +690,86 @@ __global__ void __launch_bounds__(128) k_gather(GatherDev G, PassDev P) {
     const float3 n = f3(G.hn[p]);
     const float3 f = f3(G.hf[p]);
     float4 s0 = G.st0[p], s1 = G.st1[p];
-    const float R = s1.w, R2 = R * R;
+    const float R = s1.w;
     if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
     float M = 0.0f;
     float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-    if (STOCH) {
-        uint32_t buckets[27];
-        const int nb = query_buckets(x, R, P.inv_h, P.tmask, buckets);
-        for (int q = 0; q < nb; ++q) {
-            const uint32_t b = buckets[q];
-            const uint32_t cnt = G.ecount[b];
-            if (cnt == 0) continue;
-            const uint32_t slot = (uint32_t)(G.entry[b] & 0xffffffffull);
-            const float4 a = __ldg(G.slots + 2 * (size_t)slot);
-            const float4 c = __ldg(G.slots + 2 * (size_t)slot + 1);
-            if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
-            const float w = (float)cnt;
-            M += w;
-            acc = acc + f3(c) * w;
-        }
-    } else {
-        int32_t lx, hx, ly, hy, lz, hz;
-        cell_range(x.x, R, P.inv_h, lx, hx);
-        cell_range(x.y, R, P.inv_h, ly, hy);
-        cell_range(x.z, R, P.inv_h, lz, hz);
-        const float R2p = R2 * 1.0001f;  // cheap pre-test, then the exact one
-        for (int32_t ix = lx; ix <= hx; ++ix)
-            for (int32_t iy = ly; iy <= hy; ++iy)
-                for (int32_t iz = lz; iz <= hz; ++iz) {
-                    const uint32_t b = cell_hash(ix, iy, iz, P.tmask);
-                    const uint32_t e = __ldg(G.bstart + b + 1);
-                    for (uint32_t i = __ldg(G.bstart + b); i < e; ++i) {
-                        const float4 a = __ldg(G.spos + i);
-                        const float3 dx = f3(a) - x;
-                        if (!(dot3(dx, dx) < R2p)) continue;
-                        if (cell_of(a.x, P.inv_h) != ix || cell_of(a.y, P.inv_h) != iy || cell_of(a.z, P.inv_h) != iz)
-                            continue;  // a colliding cell's photon, counted when its own cell is visited
-                        const float4 c = __ldg(G.spay + i);
-                        if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
-                        M += 1.0f;
-                        acc = acc + f3(c);
-                    }
-                }
+    uint32_t buckets[27];
+    const int nb = query_buckets(x, R, P.inv_h, P.tmask, buckets);
+    for (int q = 0; q < nb; ++q) {
+        const uint32_t b = buckets[q];
+        const uint32_t cnt = G.ecount[b];
+        if (cnt == 0) continue;
+        const uint32_t slot = (uint32_t)(G.entry[b] & 0xffffffffull);
+        const float4 a = __ldg(G.slots + 2 * (size_t)slot);
+        const float4 c = __ldg(G.slots + 2 * (size_t)slot + 1);
+        if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
+        const float w = (float)cnt;
+        M += w;
+        acc = acc + f3(c) * w;
     }
     if (G.shist) G.shist[(size_t)pass_index(P) * G.npix + p] = make_float4(acc.x, acc.y, acc.z, 0.0f);
     progressive_update(s0, s1, M, mul3(f, acc), P.alpha);
+    G.st0[p] = s0;
+    G.st1[p] = s1;
+}
+
+// Exact range query + progressive update, a group of L lanes per hit point. The group visits
+// every cell overlapping the box x +- R (any number per axis, so the cell may be smaller than the
+// radius); its lanes split each bucket's photons (consecutive, coalesced), and a photon that passes
+// the distance test counts only while its own cell is the one being visited, so a photon whose
+// bucket several visited cells share (hash collisions) counts once. Lane sums are combined by a
+// fixed butterfly, so the result does not depend on scheduling.
+template <int L>
+__global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
+    static_assert(L >= 1 && L <= 32 && (L & (L - 1)) == 0, "group size");
+    const int gl = threadIdx.x & (L - 1);
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
+    if (p >= G.npix) return;
+    const float4 hxp = G.hx[p];
+    if (__float_as_int(hxp.w) < 0) return;  // the whole group leaves together
+    const float3 x = f3(hxp);
+    const float3 n = f3(G.hn[p]);
+    const float R = G.st1[p].w, R2p = R * R * 1.0001f;  // cheap pre-test, then the exact one
+    int32_t lx, hx, ly, hy, lz, hz;
+    cell_range(x.x, R, P.inv_h, lx, hx);
+    cell_range(x.y, R, P.inv_h, ly, hy);
+    cell_range(x.z, R, P.inv_h, lz, hz);
+    float M = 0.0f;
+    float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+    for (int32_t ix = lx; ix <= hx; ++ix)
+        for (int32_t iy = ly; iy <= hy; ++iy)
+            for (int32_t iz = lz; iz <= hz; ++iz) {
+                const uint32_t b = cell_hash(ix, iy, iz, P.tmask);
+                const uint32_t e = __ldg(G.bstart + b + 1);
+                for (uint32_t i = __ldg(G.bstart + b) + gl; i < e; i += L) {
+                    const float4 a = __ldg(G.spos + i);
+                    const float3 dx = f3(a) - x;
+                    if (!(dot3(dx, dx) < R2p)) continue;
+                    if (cell_of(a.x, P.inv_h) != ix || cell_of(a.y, P.inv_h) != iy || cell_of(a.z, P.inv_h) != iz)
+                        continue;  // a colliding cell's photon, counted when its own cell is visited
+                    const float4 c = __ldg(G.spay + i);
+                    if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
+                    M += 1.0f;
+                    acc = acc + f3(c);
+                }
+            }
+    if (L > 1) {
+        const int lane = threadIdx.x & 31;
+        const uint32_t gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) {
+            M += __shfl_xor_sync(gmask, M, off, L);
+            acc.x += __shfl_xor_sync(gmask, acc.x, off, L);
+            acc.y += __shfl_xor_sync(gmask, acc.y, off, L);
+            acc.z += __shfl_xor_sync(gmask, acc.z, off, L);
+        }
+    }
+    if (gl != 0) return;
+    if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
+    if (G.shist) G.shist[(size_t)pass_index(P) * G.npix + p] = make_float4(acc.x, acc.y, acc.z, 0.0f);
+    float4 s0 = G.st0[p], s1 = G.st1[p];
+    progressive_update(s0, s1, M, mul3(f3(G.hf[p]), acc), P.alpha);
     G.st0[p] = s0;
     G.st1[p] = s1;
 }
@@ -976,6 +1007,7 @@ struct gsp_sppm {
     // wavefront queues (ping-pong) and their tuning
     PathQ q[2]{};   // photon wavefront queues (np entries; full paths only)
     PathQ qe[2]{};  // eye wavefront queues (npix entries)
+    int32_t gather_lanes = 8;  // lanes per hit point in the exact gather
     int64_t qcap = 0;
     int32_t eye_steps = 1;      // eye wavefront steps before the per-thread paths
     int32_t photon_steps = 1;   // photon wavefront steps before the per-thread paths
@@ -1236,6 +1268,16 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
 // replayed graph.
 static unsigned shade_blocks(int64_t n) { return (unsigned)std::min<int64_t>(blocks(n, 256), 4 * 152); }
 
+// Exact gather with `lanes` lanes per hit point (1, 4, 8 or 16).
+static void launch_gather_exact(int lanes, const GatherDev& G, const PassDev& P, int64_t npix, cudaStream_t st) {
+    switch (lanes) {
+        case 1: k_gather_exact<1><<<blocks(npix, 128), 128, 0, st>>>(G, P); break;
+        case 4: k_gather_exact<4><<<blocks(npix * 4, 128), 128, 0, st>>>(G, P); break;
+        case 16: k_gather_exact<16><<<blocks(npix * 16, 128), 128, 0, st>>>(G, P); break;
+        default: k_gather_exact<8><<<blocks(npix * 8, 128), 128, 0, st>>>(G, P); break;
+    }
+}
+
 // Grid of k_paths: resident blocks on every SM, but no more warps than items.
 static int path_grid(int64_t items, int device) {
     static int per_sm[64] = {0};
@@ -1368,14 +1410,14 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
         G.ecount = r->ecount;
         // deposit count for diagnostics
         GSP_CUDA_TRY(gsp_scan_u32(r->pcount, r->poff, r->np, r->counters, r->scan_tmp, st));
-        k_gather<true><<<blocks(r->npix, 128), 128, 0, st>>>(G, P);
+        k_gather_stoch<<<blocks(r->npix, 128), 128, 0, st>>>(G, P);
     } else {
         e = stage_deposit(r, P, st);
         if (e != GSP_OK) return e;
         G.spos = r->spos;
         G.spay = r->spay;
         G.bstart = r->bstart;
-        k_gather<false><<<blocks(r->npix, 128), 128, 0, st>>>(G, P);
+        launch_gather_exact(r->gather_lanes, G, P, r->npix, st);
     }
     if (graph) k_add_u32<<<1, 1, 0, st>>>(r->counters + 7, 1u);
     GSP_CUDA_TRY(cudaGetLastError());
@@ -1383,13 +1425,16 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
     return GSP_OK;
 }
 
-gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, float refine_factor) {
+gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, float refine_factor,
+                         int32_t gather_lanes) {
     if (!r || eye_steps < 0 || eye_steps > 64 || photon_steps < 0 || photon_steps > kSlotsPerPath ||
-        !(refine_factor >= 0.0f))
+        !(refine_factor >= 0.0f) ||
+        (gather_lanes != 0 && gather_lanes != 1 && gather_lanes != 4 && gather_lanes != 8 && gather_lanes != 16))
         return GSP_ERR_INVALID_ARG;
     r->eye_steps = eye_steps;
     r->photon_steps = photon_steps;
     r->refine_factor = refine_factor;
+    if (gather_lanes) r->gather_lanes = gather_lanes;
     return GSP_OK;
 }
 
@@ -1627,10 +1672,10 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreate(&a);
     if (ce == cudaSuccess) ce = cudaEventCreate(&z);
-    struct Cand { int32_t es, ps; float cell; };
+    struct Cand { int32_t es, ps; float cell; int32_t gl; };
     int32_t ncand = 0;
     float best = INFINITY, first = INFINITY;
-    Cand pick{r->eye_steps, r->photon_steps, r->P.cell_h};
+    Cand pick{r->eye_steps, r->photon_steps, r->P.cell_h, r->gather_lanes};
     // Each candidate starts from a fresh state (radii r0), runs one untimed pass and times
     // trial_passes more, so every candidate sees the same radii.
     auto trial = [&](const Cand& c) {
@@ -1638,6 +1683,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         t->eye_steps = c.es;
         t->photon_steps = c.ps;
         t->inv_h = 1.0f / c.cell;
+        t->gather_lanes = c.gl;
         t->passes = 0;
         k_init_state<<<blocks(t->npix, 256), 256, 0, st>>>(t->st0, t->st1, t->npix, t->P.r0);
         ce = cudaMemsetAsync(t->started, 0, sizeof(unsigned long long), st);
@@ -1660,14 +1706,19 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     };
     // stage 1: wavefront steps at the renderer's cell edge; stage 2: the cell edge (exact mode)
     const bool full = r->P.photon_mode == GSP_FULL_PATH;
-    trial({r->eye_steps, r->photon_steps, r->P.cell_h});  // the current settings first
+    const int32_t gl0 = r->gather_lanes;
+    trial({r->eye_steps, r->photon_steps, r->P.cell_h, gl0});  // the current settings first
     for (int32_t es : {0, 1, 2})
         for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2, 4} : std::vector<int32_t>{0})
-            if (es != r->eye_steps || ps != r->photon_steps) trial({es, ps, r->P.cell_h});
+            if (es != r->eye_steps || ps != r->photon_steps) trial({es, ps, r->P.cell_h, gl0});
     if (r->P.hash_mode == GSP_EXACT) {
+        // stage 2: the cell edge; stage 3: lanes per hit point in the gather
         const Cand steps = pick;
         for (float c : {2.0f, 1.5f, 1.0f, 0.75f, 0.5f})
-            if (c * r->P.r0 != r->P.cell_h) trial({steps.es, steps.ps, c * r->P.r0});
+            if (c * r->P.r0 != r->P.cell_h) trial({steps.es, steps.ps, c * r->P.r0, gl0});
+        const Cand cell = pick;
+        for (int32_t gl : {1, 4, 8, 16})
+            if (gl != gl0) trial({cell.es, cell.ps, cell.cell, gl});
     }
     if (st) cudaStreamDestroy(st);
     if (a) cudaEventDestroy(a);
@@ -1680,6 +1731,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     }
     r->eye_steps = pick.es;
     r->photon_steps = pick.ps;
+    r->gather_lanes = pick.gl;
     r->inv_h = 1.0f / pick.cell;
     r->P.cell_h = pick.cell;
     if (out) {
@@ -1689,6 +1741,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         out->ms_per_pass = best;
         out->first_ms_per_pass = first;
         out->candidates = ncand;
+        out->gather_lanes = pick.gl;
     }
     return GSP_OK;
 }

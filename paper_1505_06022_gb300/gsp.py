@@ -69,7 +69,8 @@ class BvhStats(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("eye_steps", C.c_int32), ("photon_steps", C.c_int32), ("cell_h", C.c_float),
-                ("ms_per_pass", C.c_float), ("first_ms_per_pass", C.c_float), ("candidates", C.c_int32)]
+                ("ms_per_pass", C.c_float), ("first_ms_per_pass", C.c_float), ("candidates", C.c_int32),
+                ("gather_lanes", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -120,7 +121,7 @@ def lib():
             L.gsp_sppm_sync.argtypes = [P]
             L.gsp_hash_grid_build.argtypes = [P, P, I64, C.c_float, I64, P, P, P]
             L.gsp_hash_grid_build_static.argtypes = [P, I64, C.c_float, I64, P, P, P]
-            L.gsp_sppm_tune.argtypes = [P, I32, I32, C.c_float]
+            L.gsp_sppm_tune.argtypes = [P, I32, I32, C.c_float, I32]
             L.gsp_sppm_enable_grad.argtypes = [P, I32]
             L.gsp_render_grad.argtypes = [P, P, P, P, P]
             L.gsp_scene_set_materials.argtypes = [P, P, I32]
@@ -279,8 +280,8 @@ def gsp_sppm_create(scene, params: dict):
     return h
 
 
-def gsp_sppm_tune(r, eye_steps=4, photon_steps=10, refine_factor=0.0):
-    _check("gsp_sppm_tune", lib().gsp_sppm_tune(r, eye_steps, photon_steps, refine_factor))
+def gsp_sppm_tune(r, eye_steps=1, photon_steps=1, refine_factor=0.0, gather_lanes=0):
+    _check("gsp_sppm_tune", lib().gsp_sppm_tune(r, eye_steps, photon_steps, refine_factor, gather_lanes))
 
 
 def gsp_sppm_enable_grad(r, max_passes):
@@ -441,8 +442,8 @@ class Renderer:
     def run(self, npasses=1, stream=None):
         gsp_sppm_pass(self.h, npasses, stream)
 
-    def tune(self, eye_steps=1, photon_steps=1, refine_factor=0.0):
-        gsp_sppm_tune(self.h, eye_steps, photon_steps, refine_factor)
+    def tune(self, eye_steps=1, photon_steps=1, refine_factor=0.0, gather_lanes=0):
+        gsp_sppm_tune(self.h, eye_steps, photon_steps, refine_factor, gather_lanes)
 
     def autotune(self, trial_passes=2) -> dict:
         return gsp_sppm_autotune(self.h, trial_passes)

@@ -65,7 +65,8 @@ def test_autotune_keeps_the_estimate(ctx):
     a = ref.image().cpu().numpy()
     r = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
     res = r.autotune(trial_passes=1)
-    assert 12 <= res["candidates"] <= 17 and res["ms_per_pass"] <= res["first_ms_per_pass"]
+    assert 12 <= res["candidates"] <= 20 and res["ms_per_pass"] <= res["first_ms_per_pass"]
+    assert res["gather_lanes"] in (1, 4, 8, 16)
     assert res["cell_h"] >= np.float32(0.5 * kw["r0_frac"] * sc.extent()) * 0.999
     r.run(3)
     b = r.image().cpu().numpy()
