@@ -399,9 +399,15 @@ def bench_grad(args, ctx, dev, stream):
     rt.run(passes, stream)
     target = rt.image(stream)
     gsp.gsp_scene_set_materials(s.h, sc.mats)
+    # execution settings for this scene (they leave the estimate unchanged; the replay uses them too)
+    probe = gsp.Renderer(s, params)
+    choice = probe.autotune(trial_passes=2)
+    probe.close()
+    params = dict(params, cell_h=float(choice["cell_h"]))
     fwd, bwd = [], []
     for rep in range(3):
         r = gsp.Renderer(s, params)
+        r.tune(choice["eye_steps"], choice["photon_steps"], 0.0, choice["gather_lanes"])
         r.enable_grad(passes)
         torch.cuda.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -421,6 +427,8 @@ def bench_grad(args, ctx, dev, stream):
     f, b = statistics.median(fwd), statistics.median(bwd)
     return {"forward_ms": round(f, 3), "backward_ms": round(b, 3), "backward_over_forward": round(b / f, 3),
             "grad_norm": round(float(ga.norm()), 6),
+            "settings": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in choice.items()
+                         if k in ("eye_steps", "photon_steps", "cell_h", "gather_lanes")},
             "config": "256x256, 50,770 triangles (displaced plane in 12 material regions + 4 icospheres), "
                       "16 diffuse materials + light, 262,144 photon paths/pass, 8 passes, L2 loss vs a render "
                       "at perturbed albedos; gradient w.r.t. 16 RGB albedos and the light's emission"}

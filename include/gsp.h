@@ -222,7 +222,7 @@ gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
 
 /* Execution tuning of the passes. eye_steps / photon_steps: wavefront steps (closest hit of a
  * compacted ray queue, then shading that pushes continuing paths to the next queue) before one
- * persistent kernel finishes the remaining eye and photon paths lane by lane; default 1 and 1.
+ * persistent kernel finishes the remaining eye and photon paths lane by lane; default 0 and 0.
  * Results do not depend on them.
  * refine_factor: 0 (default) = every wavefront hit takes its distance from the triangle's plane
  * in double-float arithmetic, as the persistent kernel's hits always do; > 0 = only hits whose

@@ -221,11 +221,12 @@ struct EyeOut {
     float4* __restrict__ hx;
     float4* __restrict__ hn;
     float4* __restrict__ hf;
-    float4* __restrict__ st1;
+    float4* __restrict__ hd;  // this pass's directly seen emission per pixel (added by the gather)
     float4* __restrict__ hw;  // optional: eye throughput w of each hit point (gradient replay)
 };
 
-// One eye-path interaction at a hit. Emission seen from the front is added to the pixel;
+// One eye-path interaction at a hit. Emission seen from the front is added to the pixel's
+// direct term of this pass (one path per pixel, so no atomics);
 // a diffuse hit records the hit point and ends the path; a mirror or dielectric bends the ray
 // (returns true: the path continues from x along the new d).
 __device__ __forceinline__ bool eye_interact(const DevScene& S, const PassDev& P, const EyeOut& O, int64_t p,
@@ -236,11 +237,11 @@ __device__ __forceinline__ bool eye_interact(const DevScene& S, const PassDev& P
     const Material m = load_mat(S, mid);
     const bool front = dot3(d, n) < 0.0f;
     if (front && emits(m)) {
-        float4 s1 = O.st1[p];
-        s1.x += w.x * m.emission.x;
-        s1.y += w.y * m.emission.y;
-        s1.z += w.z * m.emission.z;
-        O.st1[p] = s1;
+        float4 v = O.hd[p];
+        v.x += w.x * m.emission.x;
+        v.y += w.y * m.emission.y;
+        v.z += w.z * m.emission.z;
+        O.hd[p] = v;
     }
     if (m.type == GSP_EMITTER) return false;
     const float3 x = o + d * h.t;
@@ -292,6 +293,7 @@ k_eye_emit(CamDev C, PassDev P, PathQ Q, EyeOut O, uint32_t* __restrict__ qn, un
     Q.rng[p] = make_int4(rng.s[0], rng.s[1], rng.s[2], rng.s[3]);
     Q.meta[p] = 0;
     O.hx[p] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
+    O.hd[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 // Wavefront step b of the eye pass: shade the traced queue qn[b % 3], push continuing paths.
@@ -608,6 +610,7 @@ struct GatherDev {
     const float4* __restrict__ hx;
     const float4* __restrict__ hn;
     const float4* __restrict__ hf;
+    const float4* __restrict__ hd;  // direct emission of this pass, folded into st1.xyz
     float4* __restrict__ st0;
     float4* __restrict__ st1;
     // exact
@@ -658,6 +661,12 @@ __device__ __forceinline__ bool photon_accept(float3 xk, float3 xp, float R, uin
     return __fmaf_rn(w.z, n.z, __fmaf_rn(w.y, n.y, __fmul_rn(w.x, n.x))) < 0.0f;
 }
 
+__device__ __forceinline__ void add_direct(float4& s1, float4 d) {
+    s1.x += d.x;
+    s1.y += d.y;
+    s1.z += d.z;
+}
+
 __device__ __forceinline__ void progressive_update(float4& s0, float4& s1, float M, float3 Phi, float alpha) {
     if (!(M > 0.0f)) return;
     const float N = s0.w;
@@ -685,11 +694,16 @@ __global__ void __launch_bounds__(128) k_gather_stoch(GatherDev G, PassDev P) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= G.npix) return;
     const float4 hxp = G.hx[p];
-    if (__float_as_int(hxp.w) < 0) return;
+    float4 s1 = G.st1[p];
+    add_direct(s1, G.hd[p]);
+    if (__float_as_int(hxp.w) < 0) {
+        G.st1[p] = s1;
+        return;
+    }
     const float3 x = f3(hxp);
     const float3 n = f3(G.hn[p]);
     const float3 f = f3(G.hf[p]);
-    float4 s0 = G.st0[p], s1 = G.st1[p];
+    float4 s0 = G.st0[p];
     const float R = s1.w;
     if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
     float M = 0.0f;
@@ -727,7 +741,14 @@ __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L;
     if (p >= G.npix) return;
     const float4 hxp = G.hx[p];
-    if (__float_as_int(hxp.w) < 0) return;  // the whole group leaves together
+    if (__float_as_int(hxp.w) < 0) {  // the whole group leaves together
+        if (gl == 0) {
+            float4 s1 = G.st1[p];
+            add_direct(s1, G.hd[p]);
+            G.st1[p] = s1;
+        }
+        return;
+    }
     const float3 x = f3(hxp);
     const float3 n = f3(G.hn[p]);
     const float R = G.st1[p].w, R2p = R * R * 1.0001f;  // cheap pre-test, then the exact one
@@ -769,6 +790,7 @@ __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
     if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
     if (G.shist) G.shist[(size_t)pass_index(P) * G.npix + p] = make_float4(acc.x, acc.y, acc.z, 0.0f);
     float4 s0 = G.st0[p], s1 = G.st1[p];
+    add_direct(s1, G.hd[p]);
     progressive_update(s0, s1, M, mul3(f3(G.hf[p]), acc), P.alpha);
     G.st0[p] = s0;
     G.st1[p] = s1;
@@ -800,29 +822,51 @@ struct AdjDev {
 
 // Photon-centric adjoint gather. For deposit k the hit points that gathered it in the forward
 // pass (same acceptance test, same radii) give B_k = sum_p g_p (w rho / pi)_p / R_p^2, the weight
-// of Phi_k in the loss. Each deposit is one thread; nothing is shared, nothing is atomic.
+// of Phi_k in the loss. A group of L lanes serves one deposit: it visits the hit-point grid's cells
+// overlapping xk +- r0 (no radius exceeds r0), its lanes split each bucket's hit points, and a hit
+// point counts only in its own cell. Group sums combine by a fixed butterfly; nothing is atomic.
+template <int L>
 __global__ void __launch_bounds__(128) k_adj_photons(AdjDev A) {
-    const int64_t nd = (int64_t)*A.d_total;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += (int64_t)gridDim.x * blockDim.x) {
+    const int nd = (int)*A.d_total;
+    const int gl = threadIdx.x & (L - 1);
+    const int lane = threadIdx.x & 31;
+    const uint32_t gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
+    const int groups = (int)(((int64_t)gridDim.x * blockDim.x) / L);
+    for (int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / L); i < nd; i += groups) {
         const float4 a = A.spos[i], c = A.spay[i];
         const float3 xk = f3(a);
         const uint32_t dir = __float_as_uint(c.w);
-        uint32_t buckets[27];
-        const int nb = query_buckets(xk, A.rmax, A.inv_hp, A.hp_mask, buckets);
+        int32_t lx, hx, ly, hy, lz, hz;
+        cell_range(xk.x, A.rmax, A.inv_hp, lx, hx);
+        cell_range(xk.y, A.rmax, A.inv_hp, ly, hy);
+        cell_range(xk.z, A.rmax, A.inv_hp, lz, hz);
         float3 B = make_float3(0.0f, 0.0f, 0.0f);
-        for (int q = 0; q < nb; ++q) {
-            const uint32_t b = buckets[q], e = A.hp_bstart[b + 1];
-            for (uint32_t j = A.hp_bstart[b]; j < e; ++j) {
-                const uint32_t p = A.hp_order[j];
-                const float4 hxp = __ldg(A.hx + p);
-                if (__float_as_int(hxp.w) < 0) continue;
-                const float R = __ldg(A.rhist + p);
-                if (!photon_accept(xk, f3(hxp), R, dir, f3(__ldg(A.hn + p)))) continue;
-                const float3 gp = make_float3(__ldg(A.g + 3 * p), __ldg(A.g + 3 * p + 1), __ldg(A.g + 3 * p + 2));
-                B = B + mul3(gp, f3(__ldg(A.hf + p))) * (1.0f / (R * R));
-            }
+        for (int32_t ix = lx; ix <= hx; ++ix)
+            for (int32_t iy = ly; iy <= hy; ++iy)
+                for (int32_t iz = lz; iz <= hz; ++iz) {
+                    const uint32_t b = cell_hash(ix, iy, iz, A.hp_mask);
+                    const uint32_t e = __ldg(A.hp_bstart + b + 1);
+                    for (uint32_t j = __ldg(A.hp_bstart + b) + gl; j < e; j += L) {
+                        const uint32_t p = __ldg(A.hp_order + j);
+                        const float4 hxp = __ldg(A.hx + p);
+                        if (__float_as_int(hxp.w) < 0) continue;
+                        if (cell_of(hxp.x, A.inv_hp) != ix || cell_of(hxp.y, A.inv_hp) != iy ||
+                            cell_of(hxp.z, A.inv_hp) != iz)
+                            continue;
+                        const float R = __ldg(A.rhist + p);
+                        if (!photon_accept(xk, f3(hxp), R, dir, f3(__ldg(A.hn + p)))) continue;
+                        const float3 gp =
+                            make_float3(__ldg(A.g + 3 * p), __ldg(A.g + 3 * p + 1), __ldg(A.g + 3 * p + 2));
+                        B = B + mul3(gp, f3(__ldg(A.hf + p))) * (1.0f / (R * R));
+                    }
+                }
+#pragma unroll
+        for (int off = L / 2; off > 0; off >>= 1) {
+            B.x += __shfl_xor_sync(gmask, B.x, off, L);
+            B.y += __shfl_xor_sync(gmask, B.y, off, L);
+            B.z += __shfl_xor_sync(gmask, B.z, off, L);
         }
-        A.badj[A.order[i]] = make_float4(B.x, B.y, B.z, 0.0f);
+        if (gl == 0) A.badj[A.order[i]] = make_float4(B.x, B.y, B.z, 0.0f);
     }
 }
 
@@ -993,9 +1037,20 @@ struct gsp_sppm {
     int32_t nemit = 0;
     float4* d_emit = nullptr;
     float* d_cdf = nullptr;
-    float4 *st0 = nullptr, *st1 = nullptr, *hx = nullptr, *hn = nullptr, *hf = nullptr;
+    float4 *st0 = nullptr, *st1 = nullptr;
+    // The outputs of a pass's eye and photon tracing, read by its deposit and gather. Two sets, so
+    // that the tracing of pass i + 1 can run while pass i is gathered (gsp_sppm_pass with
+    // several passes); the second set is allocated on first use. hx .. pcount alias the set in use.
+    struct TraceBuf {
+        float4 *hx = nullptr, *hn = nullptr, *hf = nullptr, *hd = nullptr, *slots = nullptr;
+        uint32_t* pcount = nullptr;
+    } tb[2];
+    float4 *hx = nullptr, *hn = nullptr, *hf = nullptr, *hd = nullptr;
     float4* slots = nullptr;
-    uint32_t *pcount = nullptr, *poff = nullptr, *counters = nullptr;
+    uint32_t* pcount = nullptr;
+    cudaStream_t tstream = nullptr;  // tracing stream of overlapped passes
+    cudaEvent_t ev_start = nullptr, ev_traced[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    uint32_t *poff = nullptr, *counters = nullptr;
     uint32_t *keys[2] = {nullptr, nullptr}, *vals[2] = {nullptr, nullptr};
     uint32_t *hist = nullptr, *scan_tmp = nullptr, *bcount = nullptr, *bstart = nullptr;
     float4 *spos = nullptr, *spay = nullptr;
@@ -1009,15 +1064,15 @@ struct gsp_sppm {
     PathQ qe[2]{};  // eye wavefront queues (npix entries)
     int32_t gather_lanes = 8;  // lanes per hit point in the exact gather
     int64_t qcap = 0;
-    int32_t eye_steps = 1;      // eye wavefront steps before the per-thread paths
-    int32_t photon_steps = 1;   // photon wavefront steps before the per-thread paths
-    float refine_factor = 0.0f; // SPPM hits: always take the FP64 distance
+    int32_t eye_steps = 0;      // eye wavefront steps before the persistent path kernel
+    int32_t photon_steps = 0;   // photon wavefront steps before the persistent path kernel
+    float refine_factor = 0.0f; // 0: every SPPM hit takes the refined (plane) distance
     // gradient (pass replay) buffers, allocated by gsp_sppm_enable_grad
     bool grad = false;
     int32_t grad_max_passes = 0, emit_mat = -1;
     float* rhist = nullptr;            // [max passes][npix] gather radius
     float4* shist = nullptr;           // [max passes][npix] gathered flux sum
-    float4 *st1_scratch = nullptr, *hw = nullptr, *badj = nullptr;
+    float4 *hw = nullptr, *badj = nullptr;
     int32_t* smat = nullptr;
     double* gacc = nullptr;            // [nmat * 3 + 3]
     uint32_t *hp_order = nullptr, *hp_bstart = nullptr, *hp_scratch = nullptr;
@@ -1040,6 +1095,15 @@ cudaError_t alloc(gsp_sppm* r, T** p, int64_t count) {
 void free_all(gsp_sppm* r) {
     for (void* p : r->allocs) cudaFree(p);
     r->allocs.clear();
+}
+
+void use_buf(gsp_sppm* r, int j) {
+    r->hx = r->tb[j].hx;
+    r->hn = r->tb[j].hn;
+    r->hf = r->tb[j].hf;
+    r->hd = r->tb[j].hd;
+    r->slots = r->tb[j].slots;
+    r->pcount = r->tb[j].pcount;
 }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -1164,11 +1228,13 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     A(&r->d_cdf, ne);
     A(&r->st0, r->npix);
     A(&r->st1, r->npix);
-    A(&r->hx, r->npix);
-    A(&r->hn, r->npix);
-    A(&r->hf, r->npix);
-    A(&r->slots, 2 * r->slot_cap);
-    A(&r->pcount, r->np);
+    A(&r->tb[0].hx, r->npix);
+    A(&r->tb[0].hn, r->npix);
+    A(&r->tb[0].hf, r->npix);
+    A(&r->tb[0].hd, r->npix);
+    A(&r->tb[0].slots, 2 * r->slot_cap);
+    A(&r->tb[0].pcount, r->np);
+    use_buf(r, 0);
     A(&r->poff, r->np);
     A(&r->counters, 16);
     A(&r->started, 1);
@@ -1190,9 +1256,9 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         A(&r->ecount, r->T);
     }
     r->qcap = std::max(r->npix, P.photon_mode == GSP_FULL_PATH ? r->np : (int64_t)0);
-    r->eye_steps = 1;     // one wavefront step (all primary / first photon rays through the
-    r->photon_steps = 1;  // closest-hit kernel), then persistent per-lane paths: in scenes with
-                          // long rays every further step waits for its slowest ray
+    r->eye_steps = 0;     // no wavefront steps: the persistent path kernel (per-lane refill)
+    r->photon_steps = 0;  // traces every bounce; a step costs a closest-hit launch over the whole
+                          // queue plus a shade launch, and waits for its slowest ray
     const int64_t nq = P.photon_mode == GSP_FULL_PATH ? r->np : 0;
     for (int b = 0; b < 2; ++b) {
         A(&r->q[b].ray, 2 * nq);
@@ -1241,6 +1307,9 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
 void gsp_sppm_destroy(gsp_sppm* r) {
     if (!r) return;
     cudaSetDevice(r->scene->ctx->device);
+    if (r->tstream) cudaStreamDestroy(r->tstream);
+    for (cudaEvent_t ev : {r->ev_start, r->ev_traced[0], r->ev_traced[1], r->ev_free[0], r->ev_free[1]})
+        if (ev) cudaEventDestroy(ev);
     free_all(r);
     delete r;
 }
@@ -1383,28 +1452,26 @@ static gsp_status stage_deposit(gsp_sppm* r, const PassDev& P, cudaStream_t st) 
 // One pass on stream st. In graph mode (a pass captured once and replayed) the pass index is read
 // from the device counter counters[7], which the pass advances itself, and the host count is left
 // to the caller.
-static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false) {
-    PassDev P = pass_params(r, r->passes);
-    if (graph) P.pass_dev = r->counters + 7;
-    const bool stoch = r->P.hash_mode == GSP_STOCHASTIC;
-    const EyeOut O{r->hx, r->hn, r->hf, r->st1, nullptr};
-    DepositDev D{r->slots, r->pcount, r->entry, r->ecount, stoch ? 1 : 0, nullptr};
-    if (r->grad && r->passes >= r->grad_max_passes) {
-        gsp_set_last_error("gsp_sppm_pass: more passes than gsp_sppm_enable_grad reserved radius history for");
-        return GSP_ERR_OVERFLOW;
-    }
-    gsp_status e = stage_paths(r, P, O, D, st);
-    if (e != GSP_OK) return e;
+// Tracing half of a pass: eye and photon passes into the trace buffers in use.
+static gsp_status trace_half(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
+    const EyeOut O{r->hx, r->hn, r->hf, r->hd, nullptr};
+    const DepositDev D{r->slots, r->pcount, r->entry, r->ecount, r->P.hash_mode == GSP_STOCHASTIC ? 1 : 0, nullptr};
+    return stage_paths(r, P, O, D, st);
+}
+
+// Gather half of a pass: deposit (exact mode) and the fused range query + progressive update.
+static gsp_status gather_half(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
     GatherDev G{};
     G.hx = r->hx;
     G.hn = r->hn;
     G.hf = r->hf;
+    G.hd = r->hd;
     G.st0 = r->st0;
     G.st1 = r->st1;
     G.npix = r->npix;
     G.rhist = r->grad ? r->rhist : nullptr;
     G.shist = r->grad ? r->shist : nullptr;
-    if (stoch) {
+    if (r->P.hash_mode == GSP_STOCHASTIC) {
         G.slots = r->slots;
         G.entry = r->entry;
         G.ecount = r->ecount;
@@ -1412,16 +1479,81 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
         GSP_CUDA_TRY(gsp_scan_u32(r->pcount, r->poff, r->np, r->counters, r->scan_tmp, st));
         k_gather_stoch<<<blocks(r->npix, 128), 128, 0, st>>>(G, P);
     } else {
-        e = stage_deposit(r, P, st);
+        gsp_status e = stage_deposit(r, P, st);
         if (e != GSP_OK) return e;
         G.spos = r->spos;
         G.spay = r->spay;
         G.bstart = r->bstart;
         launch_gather_exact(r->gather_lanes, G, P, r->npix, st);
     }
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+static gsp_status check_grad_room(gsp_sppm* r, int64_t npasses) {
+    if (r->grad && r->passes + npasses > r->grad_max_passes) {
+        gsp_set_last_error("gsp_sppm_pass: more passes than gsp_sppm_enable_grad reserved radius history for");
+        return GSP_ERR_OVERFLOW;
+    }
+    return GSP_OK;
+}
+
+static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false) {
+    PassDev P = pass_params(r, r->passes);
+    if (graph) P.pass_dev = r->counters + 7;
+    gsp_status e = check_grad_room(r, graph ? 0 : 1);
+    if (e == GSP_OK) e = trace_half(r, P, st);
+    if (e == GSP_OK) e = gather_half(r, P, st);
+    if (e != GSP_OK) return e;
     if (graph) k_add_u32<<<1, 1, 0, st>>>(r->counters + 7, 1u);
     GSP_CUDA_TRY(cudaGetLastError());
     if (!graph) r->passes += 1;
+    return GSP_OK;
+}
+
+// Several passes with the tracing of pass i + 1 (on the renderer's tracing stream, into the other
+// trace buffers) running while pass i is deposited and gathered on the caller's stream: the long
+// tail of the path kernel, when only the longest paths are still running, overlaps the previous
+// pass's sort and gather. Events order each buffer's reuse; results are those of one pass after
+// the other. Exact hashing only (stochastic hashing shares its table between the two halves).
+static gsp_status passes_overlapped(gsp_sppm* r, int32_t npasses, cudaStream_t st) {
+    if (!r->tb[1].hx) {
+        cudaError_t e = cudaSuccess;
+        auto A = [&](auto** p, int64_t n) {
+            if (e == cudaSuccess) e = alloc(r, p, n);
+        };
+        A(&r->tb[1].hx, r->npix);
+        A(&r->tb[1].hn, r->npix);
+        A(&r->tb[1].hf, r->npix);
+        A(&r->tb[1].hd, r->npix);
+        A(&r->tb[1].slots, 2 * r->slot_cap);
+        A(&r->tb[1].pcount, r->np);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->tstream, cudaStreamNonBlocking);
+        for (cudaEvent_t* ev : {&r->ev_start, &r->ev_traced[0], &r->ev_traced[1], &r->ev_free[0], &r->ev_free[1]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            gsp_set_last_error(cudaGetErrorString(e));
+            r->tb[1] = gsp_sppm::TraceBuf{};
+            return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+        }
+    }
+    // the tracing stream starts after everything the caller queued before
+    GSP_CUDA_TRY(cudaEventRecord(r->ev_start, st));
+    GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_start, 0));
+    for (int32_t i = 0; i < npasses; ++i) {
+        const int j = i & 1;
+        use_buf(r, j);
+        const PassDev P = pass_params(r, r->passes);
+        if (i >= 2) GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_free[j], 0));  // pass i - 2 gathered
+        gsp_status e = trace_half(r, P, r->tstream);
+        if (e != GSP_OK) return e;
+        GSP_CUDA_TRY(cudaEventRecord(r->ev_traced[j], r->tstream));
+        GSP_CUDA_TRY(cudaStreamWaitEvent(st, r->ev_traced[j], 0));
+        e = gather_half(r, P, st);
+        if (e != GSP_OK) return e;
+        GSP_CUDA_TRY(cudaEventRecord(r->ev_free[j], st));
+        r->passes += 1;
+    }
     return GSP_OK;
 }
 
@@ -1442,8 +1574,11 @@ gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream) {
     if (!r || npasses < 0) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
     (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
+    gsp_status s = check_grad_room(r, npasses);
+    if (s != GSP_OK) return s;
+    if (npasses >= 2 && r->P.hash_mode == GSP_EXACT) return passes_overlapped(r, npasses, (cudaStream_t)stream);
     for (int32_t i = 0; i < npasses; ++i) {
-        gsp_status s = sppm_one_pass(r, (cudaStream_t)stream);
+        s = sppm_one_pass(r, (cudaStream_t)stream);
         if (s != GSP_OK) return s;
     }
     return GSP_OK;
@@ -1475,7 +1610,6 @@ gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
     auto A = [&](auto** p, int64_t n) { if (e == cudaSuccess) e = alloc(r, p, n); };
     A(&r->rhist, (int64_t)max_passes * r->npix);
     A(&r->shist, (int64_t)max_passes * r->npix);
-    A(&r->st1_scratch, r->npix);
     A(&r->hw, r->npix);
     A(&r->badj, r->slot_cap);
     A(&r->smat, r->slot_cap);
@@ -1503,7 +1637,7 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t nmat = r->scene->nmat;
     GSP_CUDA_TRY(cudaMemsetAsync(r->gacc, 0, ((size_t)kMaxGradMats * 3 + 3) * sizeof(double), st));
-    const EyeOut O{r->hx, r->hn, r->hf, r->st1_scratch, r->hw};
+    const EyeOut O{r->hx, r->hn, r->hf, r->hd, r->hw};
     const DepositDev D{r->slots, r->pcount, nullptr, nullptr, 0, r->smat};
     const float hp_cell = 2.0f * r->P.r0;
     const int grid = 4 * 152;
@@ -1532,7 +1666,7 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
         A.order = r->last_order;
         A.d_total = r->counters;
         A.badj = r->badj;
-        k_adj_photons<<<grid * 2, 128, 0, st>>>(A);
+        k_adj_photons<8><<<grid * 8, 128, 0, st>>>(A);
         k_adj_pixels<<<grid, 256, 0, st>>>(r->hx, r->hw, A.rhist, r->shist + (size_t)i * r->npix, d_dloss_dimg,
                                            r->npix, r->gacc, nmat);
         k_adj_paths<<<grid, 128, 0, st>>>(r->slots, r->pcount, r->smat, r->badj, r->scene->d_mats, r->np, r->gacc,

@@ -280,7 +280,7 @@ def gsp_sppm_create(scene, params: dict):
     return h
 
 
-def gsp_sppm_tune(r, eye_steps=1, photon_steps=1, refine_factor=0.0, gather_lanes=0):
+def gsp_sppm_tune(r, eye_steps=0, photon_steps=0, refine_factor=0.0, gather_lanes=0):
     _check("gsp_sppm_tune", lib().gsp_sppm_tune(r, eye_steps, photon_steps, refine_factor, gather_lanes))
 
 
@@ -442,7 +442,7 @@ class Renderer:
     def run(self, npasses=1, stream=None):
         gsp_sppm_pass(self.h, npasses, stream)
 
-    def tune(self, eye_steps=1, photon_steps=1, refine_factor=0.0, gather_lanes=0):
+    def tune(self, eye_steps=0, photon_steps=0, refine_factor=0.0, gather_lanes=0):
         gsp_sppm_tune(self.h, eye_steps, photon_steps, refine_factor, gather_lanes)
 
     def autotune(self, trial_passes=2) -> dict:
