@@ -1044,7 +1044,10 @@ struct gsp_sppm {
     struct TraceBuf {
         float4 *hx = nullptr, *hn = nullptr, *hf = nullptr, *hd = nullptr, *slots = nullptr;
         uint32_t* pcount = nullptr;
+        float4* hw = nullptr;     // gradient replay: eye throughput per hit point
+        int32_t* smat = nullptr;  // gradient replay: material under each deposit
     } tb[2];
+    int cur = 0;
     float4 *hx = nullptr, *hn = nullptr, *hf = nullptr, *hd = nullptr;
     float4* slots = nullptr;
     uint32_t* pcount = nullptr;
@@ -1072,8 +1075,8 @@ struct gsp_sppm {
     int32_t grad_max_passes = 0, emit_mat = -1;
     float* rhist = nullptr;            // [max passes][npix] gather radius
     float4* shist = nullptr;           // [max passes][npix] gathered flux sum
-    float4 *hw = nullptr, *badj = nullptr;
-    int32_t* smat = nullptr;
+    float4 *hw = nullptr, *badj = nullptr;  // hw aliases the trace buffers in use
+    int32_t* smat = nullptr;                 // alias as hw
     double* gacc = nullptr;            // [nmat * 3 + 3]
     uint32_t *hp_order = nullptr, *hp_bstart = nullptr, *hp_scratch = nullptr;
     int64_t hp_T = 0;
@@ -1098,6 +1101,9 @@ void free_all(gsp_sppm* r) {
 }
 
 void use_buf(gsp_sppm* r, int j) {
+    r->cur = j;
+    r->hw = r->tb[j].hw;
+    r->smat = r->tb[j].smat;
     r->hx = r->tb[j].hx;
     r->hn = r->tb[j].hn;
     r->hf = r->tb[j].hf;
@@ -1511,32 +1517,42 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
     return GSP_OK;
 }
 
+// The second set of trace buffers, the tracing stream and its events, made on first use.
+static gsp_status ensure_second_buffer(gsp_sppm* r) {
+    if (r->tb[1].hx && (!r->grad || r->tb[1].hw)) return GSP_OK;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, int64_t n) {
+        if (e == cudaSuccess && !*p) e = alloc(r, p, n);
+    };
+    A(&r->tb[1].hx, r->npix);
+    A(&r->tb[1].hn, r->npix);
+    A(&r->tb[1].hf, r->npix);
+    A(&r->tb[1].hd, r->npix);
+    A(&r->tb[1].slots, 2 * r->slot_cap);
+    A(&r->tb[1].pcount, r->np);
+    if (r->grad) {
+        A(&r->tb[1].hw, r->npix);
+        A(&r->tb[1].smat, r->slot_cap);
+    }
+    if (e == cudaSuccess && !r->tstream) e = cudaStreamCreateWithFlags(&r->tstream, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&r->ev_start, &r->ev_traced[0], &r->ev_traced[1], &r->ev_free[0], &r->ev_free[1]})
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+    }
+    use_buf(r, r->cur);
+    return GSP_OK;
+}
+
 // Several passes with the tracing of pass i + 1 (on the renderer's tracing stream, into the other
 // trace buffers) running while pass i is deposited and gathered on the caller's stream: the long
 // tail of the path kernel, when only the longest paths are still running, overlaps the previous
 // pass's sort and gather. Events order each buffer's reuse; results are those of one pass after
 // the other. Exact hashing only (stochastic hashing shares its table between the two halves).
 static gsp_status passes_overlapped(gsp_sppm* r, int32_t npasses, cudaStream_t st) {
-    if (!r->tb[1].hx) {
-        cudaError_t e = cudaSuccess;
-        auto A = [&](auto** p, int64_t n) {
-            if (e == cudaSuccess) e = alloc(r, p, n);
-        };
-        A(&r->tb[1].hx, r->npix);
-        A(&r->tb[1].hn, r->npix);
-        A(&r->tb[1].hf, r->npix);
-        A(&r->tb[1].hd, r->npix);
-        A(&r->tb[1].slots, 2 * r->slot_cap);
-        A(&r->tb[1].pcount, r->np);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->tstream, cudaStreamNonBlocking);
-        for (cudaEvent_t* ev : {&r->ev_start, &r->ev_traced[0], &r->ev_traced[1], &r->ev_free[0], &r->ev_free[1]})
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            gsp_set_last_error(cudaGetErrorString(e));
-            r->tb[1] = gsp_sppm::TraceBuf{};
-            return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
-        }
-    }
+    gsp_status se = ensure_second_buffer(r);
+    if (se != GSP_OK) return se;
     // the tracing stream starts after everything the caller queued before
     GSP_CUDA_TRY(cudaEventRecord(r->ev_start, st));
     GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_start, 0));
@@ -1610,9 +1626,12 @@ gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
     auto A = [&](auto** p, int64_t n) { if (e == cudaSuccess) e = alloc(r, p, n); };
     A(&r->rhist, (int64_t)max_passes * r->npix);
     A(&r->shist, (int64_t)max_passes * r->npix);
-    A(&r->hw, r->npix);
+    for (int j = 0; j < 2; ++j)
+        if (r->tb[j].hx) {
+            A(&r->tb[j].hw, r->npix);
+            A(&r->tb[j].smat, r->slot_cap);
+        }
     A(&r->badj, r->slot_cap);
-    A(&r->smat, r->slot_cap);
     A(&r->gacc, (int64_t)kMaxGradMats * 3 + 3);
     A(&r->hp_order, r->npix);
     A(&r->hp_bstart, r->hp_T + 1);
@@ -1624,6 +1643,7 @@ gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
     r->grad = true;
     r->grad_max_passes = max_passes;
     r->emit_mat = em;
+    use_buf(r, r->cur);
     return GSP_OK;
 }
 
@@ -1637,15 +1657,27 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t nmat = r->scene->nmat;
     GSP_CUDA_TRY(cudaMemsetAsync(r->gacc, 0, ((size_t)kMaxGradMats * 3 + 3) * sizeof(double), st));
-    const EyeOut O{r->hx, r->hn, r->hf, r->hd, r->hw};
-    const DepositDev D{r->slots, r->pcount, nullptr, nullptr, 0, r->smat};
     const float hp_cell = 2.0f * r->P.r0;
     const int grid = 4 * 152;
+    // Pass i + 1 is replayed on the tracing stream into the other trace buffers while the adjoint
+    // kernels of pass i run on the caller's stream (the same double buffering as gsp_sppm_pass).
+    gsp_status e = ensure_second_buffer(r);
+    if (e != GSP_OK) return e;
+    GSP_CUDA_TRY(cudaEventRecord(r->ev_start, st));
+    GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_start, 0));
     for (int64_t i = 0; i < r->passes; ++i) {
+        const int j = (int)(i & 1);
+        use_buf(r, j);
         // replay pass i from its PRNG counters: the same hit points, photons and radii
         const PassDev P = pass_params(r, i);
-        gsp_status e = stage_paths(r, P, O, D, st);
-        if (e == GSP_OK) e = stage_deposit(r, P, st);
+        const EyeOut O{r->hx, r->hn, r->hf, r->hd, r->hw};
+        const DepositDev D{r->slots, r->pcount, nullptr, nullptr, 0, r->smat};
+        if (i >= 2) GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_free[j], 0));
+        e = stage_paths(r, P, O, D, r->tstream);
+        if (e != GSP_OK) return e;
+        GSP_CUDA_TRY(cudaEventRecord(r->ev_traced[j], r->tstream));
+        GSP_CUDA_TRY(cudaStreamWaitEvent(st, r->ev_traced[j], 0));
+        e = stage_deposit(r, P, st);
         if (e != GSP_OK) return e;
         e = gsp_grid_build_with(r->hx, r->npix, hp_cell, r->hp_T, r->hp_order, r->hp_bstart, r->hp_scratch, st, true);
         if (e != GSP_OK) return e;
@@ -1671,6 +1703,7 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
                                            r->npix, r->gacc, nmat);
         k_adj_paths<<<grid, 128, 0, st>>>(r->slots, r->pcount, r->smat, r->badj, r->scene->d_mats, r->np, r->gacc,
                                           nmat);
+        GSP_CUDA_TRY(cudaEventRecord(r->ev_free[j], st));
     }
     const double ne = (double)r->passes * (double)r->np;
     k_adj_emission<<<256, 256, 0, st>>>(r->st0, r->st1, d_dloss_dimg, r->npix, 1.0f / (float)r->passes, ne,
