@@ -294,6 +294,15 @@ typedef struct {
  * a pixel sums its photons. out may be NULL. */
 gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out);
 
+/* Autotuning of a whole batch, before its first pass: times batch passes (one CUDA graph each)
+ * under candidate settings applied to every renderer -- wavefront steps (eye 0-1, photon 0-2),
+ * then lanes per hit point in the exact gather (4, 8, 16) -- and keeps the fastest. Each
+ * candidate runs one untimed and trial_passes timed passes, after which every renderer is back
+ * to its initial state, so the renders that follow are those of untuned renderers (bit for bit
+ * for the steps; the lanes change only a pixel's summation order). GSP_ERR_BAD_STATE if a
+ * renderer has run a pass or has gradients enabled. out may be NULL (cell_h reports renderer 0's). */
+gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_result* out);
+
 /* ---- gradient of an image loss (path-replay adjoint) ------------------------------------- */
 
 /* Prepares gradients: every pass from now on records the radius each pixel gathered with and

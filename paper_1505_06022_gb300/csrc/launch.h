@@ -18,7 +18,7 @@ constexpr int kTraceThreads = 128;
 #define GSP_TRACE_MIN_BLOCKS 9
 #endif
 #ifndef GSP_PATH_MIN_BLOCKS
-#define GSP_PATH_MIN_BLOCKS 6
+#define GSP_PATH_MIN_BLOCKS 8
 #endif
 constexpr int kTraceChunk = GSP_TRACE_CHUNK;           // rays a warp takes from the global counter at once
 constexpr int kTraceInner = GSP_TRACE_INNER;           // traversal steps between refills

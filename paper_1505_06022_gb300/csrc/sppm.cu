@@ -1739,6 +1739,16 @@ static void batch_free(gsp_batch* b) {
 
 // One pass of every renderer captured as a single CUDA graph: a branch per renderer, forked
 // from and joined to the capturing stream, so the scenes' kernels overlap on the GPU.
+// Back to the state of a new renderer (radii r0, nothing gathered, no pass run).
+static cudaError_t reset_state(gsp_sppm* t, cudaStream_t st) {
+    t->passes = 0;
+    k_init_state<<<blocks(t->npix, 256), 256, 0, st>>>(t->st0, t->st1, t->npix, t->P.r0);
+    cudaError_t e = cudaMemsetAsync(t->started, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && t->rd) e = cudaMemsetAsync(t->rd, 0, t->np * sizeof(float4), st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
+
 static gsp_status batch_capture(gsp_batch* b, cudaStream_t st) {
     GSP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     gsp_status e = GSP_OK;
@@ -1826,6 +1836,84 @@ gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
     return GSP_OK;
 }
 
+gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_result* out) {
+    if (!b || trial_passes < 1) return GSP_ERR_INVALID_ARG;
+    for (gsp_sppm* r : b->rs)
+        if (r->passes != 0 || r->grad) return GSP_ERR_BAD_STATE;
+    GSP_CUDA_TRY(cudaSetDevice(b->device));
+    (void)cudaGetLastError();
+    cudaStream_t st = b->cap;
+    cudaEvent_t a = nullptr, z = nullptr;
+    cudaError_t ce = cudaEventCreate(&a);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&z);
+    gsp_status e = GSP_OK;
+    struct Cand { int32_t es, ps, gl; };
+    const Cand start{b->rs[0]->eye_steps, b->rs[0]->photon_steps, b->rs[0]->gather_lanes};
+    Cand pick = start;
+    float best = INFINITY, first = INFINITY;
+    int32_t ncand = 0;
+    auto apply = [&](const Cand& c) {
+        for (gsp_sppm* r : b->rs) {
+            r->eye_steps = c.es;
+            r->photon_steps = c.ps;
+            r->gather_lanes = c.gl;
+        }
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    };
+    // Each candidate: capture its graph, one untimed batch pass, trial_passes timed ones, then
+    // every renderer back to its initial state.
+    auto trial = [&](const Cand& c) {
+        if (ce != cudaSuccess || e != GSP_OK) return;
+        apply(c);
+        e = batch_capture(b, st);
+        for (int32_t k = 0; k <= trial_passes && e == GSP_OK && ce == cudaSuccess; ++k) {
+            if (k == 1) ce = cudaEventRecord(a, st);
+            for (gsp_sppm* r : b->rs) k_store_u32<<<1, 1, 0, st>>>(r->counters + 7, (uint32_t)k);
+            if (ce == cudaSuccess) ce = cudaGraphLaunch(b->exec, st);
+        }
+        if (ce == cudaSuccess && e == GSP_OK) ce = cudaEventRecord(z, st);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(z);
+        float ms = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, z);
+        for (gsp_sppm* r : b->rs)
+            if (ce == cudaSuccess) ce = reset_state(r, st);
+        ms /= (float)trial_passes;
+        if (ncand++ == 0) first = ms;
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    };
+    trial(start);
+    const bool full = b->rs[0]->P.photon_mode == GSP_FULL_PATH;
+    for (int32_t es : {0, 1})
+        for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2} : std::vector<int32_t>{0})
+            if (es != start.es || ps != start.ps) trial({es, ps, start.gl});
+    const Cand steps = pick;
+    for (int32_t gl : {4, 8, 16})
+        if (gl != start.gl) trial({steps.es, steps.ps, gl});
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (a) cudaEventDestroy(a);
+    if (z) cudaEventDestroy(z);
+    apply(pick);  // captured again at the next gsp_batch_pass
+    if (e != GSP_OK) return e;
+    if (ce != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(ce));
+        return GSP_ERR_CUDA;
+    }
+    if (out) {
+        out->eye_steps = pick.es;
+        out->photon_steps = pick.ps;
+        out->cell_h = b->rs[0]->P.cell_h;
+        out->ms_per_pass = best;
+        out->first_ms_per_pass = first;
+        out->candidates = ncand;
+        out->gather_lanes = pick.gl;
+    }
+    return GSP_OK;
+}
+
 gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out) {
     if (!r || trial_passes < 1) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
@@ -1851,10 +1939,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         t->photon_steps = c.ps;
         t->inv_h = 1.0f / c.cell;
         t->gather_lanes = c.gl;
-        t->passes = 0;
-        k_init_state<<<blocks(t->npix, 256), 256, 0, st>>>(t->st0, t->st1, t->npix, t->P.r0);
-        ce = cudaMemsetAsync(t->started, 0, sizeof(unsigned long long), st);
-        if (ce == cudaSuccess && t->rd) ce = cudaMemsetAsync(t->rd, 0, t->np * sizeof(float4), st);
+        ce = reset_state(t, st);
         if (ce != cudaSuccess) return;
         e = sppm_one_pass(t, st);
         if (e != GSP_OK) return;

@@ -38,7 +38,7 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
        "gsp_scene_set_materials", "gsp_batch_create", "gsp_batch_destroy", "gsp_batch_pass",
-       "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load"]
+       "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load", "gsp_batch_autotune"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -130,6 +130,7 @@ def lib():
             L.gsp_batch_destroy.restype = None
             L.gsp_batch_pass.argtypes = [P, I32, P]
             L.gsp_sppm_autotune.argtypes = [P, I32, P]
+            L.gsp_batch_autotune.argtypes = [P, I32, P]
             L.gsp_sppm_save.argtypes = [P, C.c_char_p]
             L.gsp_sppm_load.argtypes = [P, C.c_char_p]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
@@ -301,6 +302,12 @@ def gsp_scene_set_materials(scene, mats):
 def gsp_sppm_autotune(r, trial_passes=2) -> dict:
     out = TuneResult()
     _check("gsp_sppm_autotune", lib().gsp_sppm_autotune(r, trial_passes, C.byref(out)))
+    return out.as_dict()
+
+
+def gsp_batch_autotune(b, trial_passes=2) -> dict:
+    out = TuneResult()
+    _check("gsp_batch_autotune", lib().gsp_batch_autotune(b, trial_passes, C.byref(out)))
     return out.as_dict()
 
 
@@ -516,6 +523,9 @@ class Batch:
 
     def run(self, npasses=1, stream=None):
         gsp_batch_pass(self.h, npasses, stream)
+
+    def autotune(self, trial_passes=2) -> dict:
+        return gsp_batch_autotune(self.h, trial_passes)
 
     def close(self):
         if self.h:

@@ -47,6 +47,31 @@ def test_batch_graph_matches_individual_passes(ctx):
     b.close()
 
 
+def test_batch_autotune_keeps_the_estimate(ctx):
+    scs, kws = scenes()
+    solo = []
+    for sc, kw in zip(scs, kws):
+        r = gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw))
+        r.run(3)
+        solo.append((r.image().cpu().numpy(), r.state()["N"].cpu().numpy()))
+    rs = [gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw)) for sc, kw in zip(scs, kws)]
+    b = gsp.Batch(rs)
+    res = b.autotune(trial_passes=1)
+    assert res["eye_steps"] in (0, 1) and res["photon_steps"] in (0, 1, 2) and res["gather_lanes"] in (4, 8, 16)
+    assert 6 <= res["candidates"] <= 9 and res["ms_per_pass"] <= res["first_ms_per_pass"]
+    b.run(3)
+    torch.cuda.synchronize()
+    for r, (img, n) in zip(rs, solo):
+        r.sync()
+        st = r.state()
+        assert st["passes"] == 3
+        assert np.array_equal(st["N"].cpu().numpy(), n)  # the same photons were gathered
+        np.testing.assert_allclose(r.image().cpu().numpy(), img, rtol=2e-5, atol=1e-7 * img.max())
+    with pytest.raises(gsp.GspError):
+        b.autotune(trial_passes=1)  # only before the first pass
+    b.close()
+
+
 def test_batch_rejects_shared_scene(ctx):
     sc = I.cornell_box(width=8, height=8)
     s = gsp.Scene(ctx, sc)
