@@ -288,7 +288,8 @@ def run_ours(args, world, rank, local):
         except Exception:
             pass
 
-    # ---- SPPM pass at 512x512, the gradient workload, the 64-scene batch ----
+    # ---- Fig. 4's traversal comparison, SPPM pass at 512x512, the gradient workload, the batch ----
+    fig4 = bench_traversals(args, ctx, dev, stream, sc, scene, rays) if not args.skip_fig4 else None
     sppm = bench_sppm(args, ctx, dev, stream, pg) if not args.skip_sppm else None
     grad = bench_grad(args, ctx, dev, stream) if not args.skip_grad else None
     batch = bench_batch(args, ctx, dev, stream) if not args.skip_batch else None
@@ -319,6 +320,7 @@ def run_ours(args, world, rank, local):
             "clocks": clk,
             "wall_s_timed": round(wall, 4),
             "check": {"host_walk_agreement": round(agree, 5)},
+            "traversal_fig4": fig4,
             "sppm_512": sppm,
             "grad_256": grad,
             "batch_64": batch,
@@ -434,6 +436,42 @@ def bench_grad(args, ctx, dev, stream):
                       "at perturbed albedos; gradient w.r.t. 16 RGB albedos and the light's emission"}
 
 
+def bench_traversals(args, ctx, dev, stream, sc, scene, rays):
+    """Fig. 4's comparison on the closest-hit workload: the multiple-threaded BVH (6 link sets),
+    the original threaded BVH (1 link set, one fixed order) and a stack-based near-first
+    traversal of the same SAH tree, each on all rays and on the coherent and random halves."""
+    import torch
+    from paper_1505_06022_gb300 import gsp
+    n = rays.shape[0]
+    tbvh = gsp.Scene(ctx, sc, bins=16, leaf_threshold=4, max_leaf=7, link_sets=1)
+    tri = torch.empty(n, dtype=torch.int32, device=dev)
+    tt = torch.empty(n, dtype=torch.float32, device=dev)
+    parts = {"all": (0, n), "coherent": (0, n // 2), "random": (n // 2, n)}
+    kinds = {"mtbvh": (scene, gsp.gsp_trace_closest_hit), "tbvh": (tbvh, gsp.gsp_trace_closest_hit),
+             "stack": (scene, gsp.gsp_trace_closest_hit_stack)}
+    reps = max(3, min(args.steps, 30))
+    out = {}
+    for kind, (scn, fn) in kinds.items():
+        out[kind] = {}
+        for part, (a, b) in parts.items():
+            r, o1, o2 = rays[a:b], tri[a:b], tt[a:b]
+            for _ in range(2):
+                fn(scn.h, r, o1, o2, None, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn(scn.h, r, o1, o2, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out[kind][part] = round((b - a) / (ms / 1000.0) / 1e6, 1)
+    ctx.sync()
+    tbvh.close()
+    out["mtbvh_over_tbvh"] = {p: round(out["mtbvh"][p] / out["tbvh"][p], 3) for p in parts}
+    out["unit"] = "Mrays/s"
+    return out
+
+
 def bench_batch(args, ctx, dev, stream):
     """64 scenes (1k-200k triangles log-uniform, 64^2-512^2): scene-passes per second as one CUDA
     graph per pass (settings from the batch autotuner) vs the same renderers run one after
@@ -501,6 +539,7 @@ def main():
     ap.add_argument("--skip-sppm", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-fig4", action="store_true")
     ap.add_argument("--batch-scenes", type=int, default=64)
     ap.add_argument("--batch-passes", type=int, default=4)
     ap.add_argument("--skip-cpu", action="store_true")

@@ -192,6 +192,14 @@ gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh
 gsp_status gsp_trace_closest_hit(gsp_scene* scene, const float* d_rays, int64_t n, int32_t* d_tri,
                                  float* d_t, float* d_uv, void* stream);
 
+/* The same closest-hit query (same arguments, results and refinement) answered by a stack-based
+ * near-first traversal of the same SAH tree, stored as child pairs (both children's boxes in one
+ * 64-byte node): the kind of traversal the paper compares its stackless one with (Fig. 4; after
+ * Aila & Laine 2009). For measuring the multiple-threaded BVH against it on this hardware.
+ * GSP_ERR_INVALID_ARG if the tree is 64 or more levels deep (the per-ray stack holds 64). */
+gsp_status gsp_trace_closest_hit_stack(gsp_scene* scene, const float* d_rays, int64_t n, int32_t* d_tri,
+                                       float* d_t, float* d_uv, void* stream);
+
 /* Instrumented host walk of the same threaded BVH (no GPU): per ray, the number of node
  * visits and triangle tests that the device traversal performs, and its closest hit.
  * Used to count the algorithmic bytes of a traversal. Host arrays; any output may be NULL. */

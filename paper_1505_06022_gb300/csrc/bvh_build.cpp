@@ -217,6 +217,37 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
     }
     auto t2 = clk::now();
 
+    // ---- the same tree as child pairs (stack-based traversal), internal nodes in preorder ----
+    {
+        std::vector<int32_t> ref(nn, 0);
+        int32_t ni = 0;
+        st.clear();
+        st.push_back(0);
+        while (!st.empty()) {  // preorder numbering of the internal nodes
+            int32_t n = st.back();
+            st.pop_back();
+            if (nodes[n].left < 0) {
+                ref[n] = ~((nodes[n].first << 3) | nodes[n].count);
+                continue;
+            }
+            ref[n] = ni++;
+            st.push_back(nodes[n].right);
+            st.push_back(nodes[n].left);
+        }
+        out.bin.assign((size_t)ni * 4, float4{0, 0, 0, 0});
+        for (int64_t n = 0; n < nn; ++n) {
+            const BNode& nd = nodes[n];
+            if (nd.left < 0) continue;
+            const BNode &L = nodes[nd.left], &R = nodes[nd.right];
+            float4* q = out.bin.data() + (size_t)ref[n] * 4;
+            q[0] = float4{L.lo[0], L.lo[1], L.lo[2], as_float(ref[nd.left])};
+            q[1] = float4{L.hi[0], L.hi[1], L.hi[2], as_float(ref[nd.right])};
+            q[2] = float4{R.lo[0], R.lo[1], R.lo[2], 0.0f};
+            q[3] = float4{R.hi[0], R.hi[1], R.hi[2], 0.0f};
+        }
+        out.bin_root = ref[0];
+    }
+
     // ---- triangles in leaf order: exact vertices v0, v1, v2 (edges are formed in the kernel) ----
     out.tris.resize((size_t)nt * 3);
     for (int64_t k = 0; k < nt; ++k) {

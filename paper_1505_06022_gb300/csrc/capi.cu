@@ -71,6 +71,102 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* 
     }
 }
 
+// Closest hit by stack-based near-first traversal of the same SAH tree in its child-pair layout:
+// one 64-byte fetch brings both children's boxes, the nearer hit child is visited next and the
+// other pushed with its entry distance, and popped entries farther than the best hit so far are
+// skipped. It is the kind of traversal the paper measures the multiple-threaded BVH against
+// (Fig. 4; the stack-based kernels of Aila & Laine 2009), written here with the same work
+// distribution, leaf test, output and FP64 refinement list as k_trace.
+constexpr int kStackDepth = 64;            // the entry point requires tree depth < kStackDepth
+constexpr int32_t kWalkDone = INT32_MIN;   // never a node or leaf reference
+
+__global__ void __launch_bounds__(kTraceThreads, GSP_TRACE_MIN_BLOCKS)
+k_trace_stack(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* __restrict__ tri,
+              float* __restrict__ tout, float2* __restrict__ uv, unsigned long long* __restrict__ ctr,
+              int2* __restrict__ rlist, float refine_factor) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    WarpQueue wq;
+    wq.init((int32_t)n);
+    Trav st;
+    st.slot = -1;
+    int32_t ray = -1, node = kWalkDone, sp = 0;
+    int32_t stk_node[kStackDepth];
+    float stk_t[kStackDepth];
+    auto pop = [&]() {
+        while (sp > 0) {
+            --sp;
+            if (stk_t[sp] <= st.tbest) return stk_node[sp];  // ties may still hold a smaller index
+        }
+        return kWalkDone;
+    };
+    while (true) {
+        const int32_t got = wq.take(ray < 0, ctr);
+        if (got >= 0) {
+            ray = got;
+            const float4 a = __ldcs(rays + 2 * (int64_t)ray), b = __ldcs(rays + 2 * (int64_t)ray + 1);
+            trav_init(S, f3(a), f3(b), a.w, b.w, st);
+            node = S.bin_root;
+            sp = 0;
+        }
+        if (__ballot_sync(0xffffffffu, ray >= 0) == 0) break;
+#pragma unroll 1
+        for (int it = 0; it < kTraceInner; ++it) {
+            if (ray >= 0 && node != kWalkDone) {
+                if (node >= 0) {
+                    const float4* q = S.bin + 4 * (int64_t)node;
+                    const float4 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2), a3 = __ldg(q + 3);
+                    float tl, tr;
+                    const bool hl = box_entry(st, f3(a0), f3(a1), tl);
+                    const bool hr = box_entry(st, f3(a2), f3(a3), tr);
+                    const int32_t rl = __float_as_int(a0.w), rr = __float_as_int(a1.w);
+                    if (hl && hr) {
+                        const bool lnear = tl <= tr;
+                        if (sp < kStackDepth) {
+                            stk_node[sp] = lnear ? rr : rl;
+                            stk_t[sp] = lnear ? tr : tl;
+                            ++sp;
+                            node = lnear ? rl : rr;
+                        } else {  // deeper than the entry point allows: end the walk, report
+                            report(S.status, -4);
+                            node = kWalkDone;
+                        }
+                    } else if (hl) {
+                        node = rl;
+                    } else if (hr) {
+                        node = rr;
+                    } else {
+                        node = pop();
+                    }
+                } else {
+                    trav_leaf(S, st, (~node) >> 3, (~node) & 7);
+                    node = pop();
+                }
+            }
+            if (__ballot_sync(0xffffffffu, ray >= 0 && node != kWalkDone) == 0) break;
+        }
+        const bool fin = ray >= 0 && node == kWalkDone;
+        bool flag = false;
+        if (fin) {
+            float u = 0.0f, v = 0.0f;
+            if (st.slot >= 0)
+                flag = hit_error_factor(S.tris + 3 * st.slot, st.o, st.d, st.tbest, u, v) > refine_factor;
+            __stcs(tri + ray, st.best);
+            __stcs(tout + ray, st.best >= 0 ? st.tbest : __int_as_float(0x7f800000));
+            if (uv) __stcs(uv + ray, make_float2(u, v));
+        }
+        const uint32_t fm = __ballot_sync(0xffffffffu, flag);
+        if (fm) {
+            const int leader = __ffs(fm) - 1;
+            unsigned long long b = 0;
+            if (lane == leader) b = atomicAdd(ctr + 1, (unsigned long long)__popc(fm));
+            b = __shfl_sync(0xffffffffu, b, leader);
+            if (flag) rlist[b + __popc(fm & lt)] = make_int2((int)ray, st.slot);
+        }
+        if (fin) ray = -1;
+    }
+}
+
 // FP64 re-evaluation of the listed hits (their rays are rare; full warps keep the FP64 pipe busy).
 __global__ void __launch_bounds__(256)
 k_refine(DevScene S, const float4* __restrict__ rays, const int2* __restrict__ rlist,
@@ -147,6 +243,8 @@ gspd::DevScene gsp_dev_scene(const gsp_scene* s) {
     gspd::DevScene d;
     d.nodes = s->d_nodes;
     d.tris = s->d_tris;
+    d.bin = s->d_bin;
+    d.bin_root = s->bvh.bin_root;
     d.shade = s->d_shade;
     d.nlo = s->d_nlo;
     d.mats = s->d_mats;
@@ -219,8 +317,10 @@ gsp_status gsp_context_sync(gsp_context* ctx) {
 static void scene_free_bvh(gsp_scene* s) {
     cudaFree(s->d_nodes);
     cudaFree(s->d_tris);
+    cudaFree(s->d_bin);
     s->d_nodes = nullptr;
     s->d_tris = nullptr;
+    s->d_bin = nullptr;
     s->built = false;
 }
 
@@ -367,6 +467,7 @@ gsp_status gsp_build_bvh(gsp_scene* s, const gsp_bvh_params* params, gsp_bvh_sta
         return GSP_ERR_INVALID_ARG;
     }
     size_t nb = bvh.nodes.size() * sizeof(float4), tb = bvh.tris.size() * sizeof(float4);
+    const size_t bb = std::max<size_t>(1, bvh.bin.size()) * sizeof(float4);
     if (s->ctx) {
         GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
         scene_free_bvh(s);
@@ -374,10 +475,13 @@ gsp_status gsp_build_bvh(gsp_scene* s, const gsp_bvh_params* params, gsp_bvh_sta
         GSP_CUDA_TRY(cudaMalloc(&s->d_tris, tb));
         GSP_CUDA_TRY(cudaMemcpy(s->d_nodes, bvh.nodes.data(), nb, cudaMemcpyHostToDevice));
         GSP_CUDA_TRY(cudaMemcpy(s->d_tris, bvh.tris.data(), tb, cudaMemcpyHostToDevice));
+        GSP_CUDA_TRY(cudaMalloc(&s->d_bin, bb));
+        if (!bvh.bin.empty())
+            GSP_CUDA_TRY(cudaMemcpy(s->d_bin, bvh.bin.data(), bvh.bin.size() * sizeof(float4), cudaMemcpyHostToDevice));
     }
     s->bvh = std::move(bvh);
     s->built = true;
-    s->device_bytes = (int64_t)(nb + tb) + s->nt * (int64_t)sizeof(float4);
+    s->device_bytes = (int64_t)(nb + tb) + s->nt * (int64_t)sizeof(float4);  // MTBVH + triangles + shading
     if (stats) {
         stats->nodes = s->bvh.nnodes;
         stats->leaves = s->bvh.nleaves;
@@ -414,6 +518,40 @@ gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, i
     const int grid = gsp_trace_grid(s->ctx->device);
     gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, (const float4*)d_rays, n, nullptr, d_tri, d_t,
                                                   (float2*)d_uv, s->d_counter, s->d_rlist, GSP_REFINE_FACTOR, 0);
+    gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, (const float4*)d_rays, s->d_rlist, s->d_counter, d_t,
+                                                          (float2*)d_uv);
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+gsp_status gsp_trace_closest_hit_stack(gsp_scene* s, const float* d_rays, int64_t n, int32_t* d_tri,
+                                 float* d_t, float* d_uv, void* stream) {
+    if (!s || n < 0) return GSP_ERR_INVALID_ARG;
+    if (!s->ctx) return GSP_ERR_INVALID_ARG;  // host-only scene
+    if (!s->built) return GSP_ERR_NOT_BUILT;
+    if (s->bvh.depth >= gspd::kStackDepth) {
+        gsp_set_last_error("gsp_trace_closest_hit_stack: the tree is deeper than the traversal stack (64)");
+        return GSP_ERR_INVALID_ARG;
+    }
+    if (n == 0) return GSP_OK;
+    if (!d_rays || !d_tri || !d_t || n > INT32_MAX) return GSP_ERR_INVALID_ARG;
+    if (((uintptr_t)d_rays & 15) || ((uintptr_t)d_uv & 7)) return GSP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
+    if (n > s->rlist_cap) {  // refine list sized for the largest batch seen (worst case: every ray)
+        GSP_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(s->d_rlist);
+        s->d_rlist = nullptr;
+        s->rlist_cap = 0;
+        GSP_CUDA_TRY(cudaMalloc(&s->d_rlist, (size_t)n * sizeof(int2)));
+        s->rlist_cap = n;
+    }
+    const gspd::DevScene S = gsp_dev_scene(s);
+    gspd::k_zero_u64x2<<<1, 1, 0, st>>>(s->d_counter);
+    const int grid = gsp_trace_grid(s->ctx->device);
+    gspd::k_trace_stack<<<grid, kTraceThreads, 0, st>>>(S, (const float4*)d_rays, n, d_tri, d_t, (float2*)d_uv,
+                                                        s->d_counter, s->d_rlist, GSP_REFINE_FACTOR);
     gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, (const float4*)d_rays, s->d_rlist, s->d_counter, d_t,
                                                           (float2*)d_uv);
     GSP_CUDA_TRY(cudaGetLastError());

@@ -94,9 +94,11 @@ struct DevScene {
     const float4* __restrict__ shade;  // per triangle (upload order): normal xyz, material bits
     const float4* __restrict__ nlo;    // per triangle (upload order): FP32 remainder of the normal
     const float4* __restrict__ mats;   // 2 per material
+    const float4* __restrict__ bin;    // child-pair layout of the same tree (stack traversal)
     int64_t nnodes;
     int64_t stride;  // nodes per link set in memory (nnodes + 1 padding node)
     int32_t link_sets;
+    int32_t bin_root;
     int32_t* status;
 };
 
@@ -293,6 +295,19 @@ __device__ __forceinline__ bool box_hit(const Trav& st, const float4& A, const f
     tf = fminf(st.tbest, tf * GSP_ROBUST_FAR);
     miss = __float_as_int(A.w);
     word = __float_as_int(B.w);
+    return tn <= tf;
+}
+
+// Slab test of the box [lo, hi] against [tmin, best t] as box_hit; on a hit tn is the entry
+// distance (stack-based traversal orders children by it).
+__device__ __forceinline__ bool box_entry(const Trav& st, float3 lo, float3 hi, float& tn) {
+    const float3 o = st.o, inv = st.inv;
+    const float t0x = __fmul_rn(lo.x - o.x, inv.x), t1x = __fmul_rn(hi.x - o.x, inv.x);
+    const float t0y = __fmul_rn(lo.y - o.y, inv.y), t1y = __fmul_rn(hi.y - o.y, inv.y);
+    const float t0z = __fmul_rn(lo.z - o.z, inv.z), t1z = __fmul_rn(hi.z - o.z, inv.z);
+    tn = fmaxf(st.tmin, fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z)));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
+    tf = fminf(st.tbest, tf * GSP_ROBUST_FAR);
     return tn <= tf;
 }
 

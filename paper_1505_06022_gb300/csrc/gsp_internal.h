@@ -20,6 +20,11 @@ struct HostBVH {
     int32_t link_sets = 0;
     std::vector<float4> nodes;  // link_sets * stride * 2
     std::vector<float4> tris;   // nt * 3, leaf order
+    // The same tree as child pairs, for stack-based traversal: per internal node (preorder) four
+    // float4 {left.min, left ref}, {left.max, right ref}, {right.min, 0}, {right.max, 0}; a ref
+    // >= 0 is an internal node, < 0 is ~(leaf word). bin_root: ref of the root.
+    std::vector<float4> bin;
+    int32_t bin_root = 0;
     double build_ms = 0, thread_ms = 0;
 };
 
@@ -55,6 +60,7 @@ struct gsp_scene {
     float4* d_mats = nullptr;   // per material: {albedo.rgb, type bits}, {emission.rgb, ior}
     float4* d_nodes = nullptr;
     float4* d_tris = nullptr;
+    float4* d_bin = nullptr;  // child-pair layout (HostBVH::bin)
     unsigned long long* d_counter = nullptr;  // trace kernel: next ray, refine-list length
     int2* d_rlist = nullptr;                  // trace kernel: hits re-evaluated in FP64
     int64_t rlist_cap = 0;

@@ -33,7 +33,7 @@ EXACT, STOCHASTIC = 0, 1
 # exported symbols of include/gsp.h
 ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp_context_destroy",
        "gsp_context_sync", "gsp_scene_upload", "gsp_scene_destroy", "gsp_build_bvh",
-       "gsp_trace_closest_hit", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
+       "gsp_trace_closest_hit", "gsp_trace_closest_hit_stack", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
@@ -108,6 +108,7 @@ def lib():
             L.gsp_scene_destroy.restype = None
             L.gsp_build_bvh.argtypes = [P, P, P]
             L.gsp_trace_closest_hit.argtypes = [P, P, I64, P, P, P, P]
+            L.gsp_trace_closest_hit_stack.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_bvh_host_walk.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_bvh_export.argtypes = [P, I32, P, P, C.POINTER(I64)]
             L.gsp_sppm_create.argtypes = [P, P, C.POINTER(P)]
@@ -247,6 +248,13 @@ def gsp_trace_closest_hit(scene, rays, tri, t, uv=None, stream=None):
     n = rays.shape[0]
     rc = lib().gsp_trace_closest_hit(scene, _dev(rays), n, _dev(tri), _dev(t), _dev(uv), _stream(stream))
     _check("gsp_trace_closest_hit", rc)
+
+
+def gsp_trace_closest_hit_stack(scene, rays, tri, t, uv=None, stream=None):
+    """As gsp_trace_closest_hit, by stack-based near-first traversal of the same tree."""
+    n = rays.shape[0]
+    rc = lib().gsp_trace_closest_hit_stack(scene, _dev(rays), n, _dev(tri), _dev(t), _dev(uv), _stream(stream))
+    _check("gsp_trace_closest_hit_stack", rc)
 
 
 def gsp_bvh_host_walk(scene, rays):
@@ -409,13 +417,15 @@ class Scene:
             ctx._children.add(self)
         self.stats = gsp_build_bvh(self.h, **bvh)
 
-    def trace(self, rays, stream=None, with_uv=False):
+    def trace(self, rays, stream=None, with_uv=False, method="mtbvh"):
+        """Closest hits; method "mtbvh" (stackless, the scene's link sets) or "stack"."""
         import torch
         n = rays.shape[0]
         tri = torch.empty(n, dtype=torch.int32, device=rays.device)
         t = torch.empty(n, dtype=torch.float32, device=rays.device)
         uv = torch.empty((n, 2), dtype=torch.float32, device=rays.device) if with_uv else None
-        gsp_trace_closest_hit(self.h, rays, tri, t, uv, stream)
+        fn = {"mtbvh": gsp_trace_closest_hit, "stack": gsp_trace_closest_hit_stack}[method]
+        fn(self.h, rays, tri, t, uv, stream)
         return (tri, t, uv) if with_uv else (tri, t)
 
     def host_walk(self, rays):

@@ -17,10 +17,10 @@ def ctx():
     c.close()
 
 
-def gpu_trace(ctx, sc, rays, **bvh):
+def gpu_trace(ctx, sc, rays, method="mtbvh", **bvh):
     s = gsp.Scene(ctx, sc, **bvh)
     d = torch.from_numpy(np.ascontiguousarray(rays)).cuda()
-    tri, t, uv = s.trace(d, with_uv=True)
+    tri, t, uv = s.trace(d, with_uv=True, method=method)
     torch.cuda.synchronize()
     ctx.sync()
     return tri.cpu().numpy(), t.cpu().numpy(), uv.cpu().numpy(), s
@@ -37,10 +37,11 @@ def test_rng_streams_are_bit_exact():
     c.close()
 
 
-def test_soup_against_brute_force(ctx):
+@pytest.mark.parametrize("method", ["mtbvh", "stack"])
+def test_soup_against_brute_force(ctx, method):
     sc = I.random_soup(300, seed=31, size=0.15)
     rays = I.random_rays(20011, seed=32)  # ragged count
-    tri, t, uv, _ = gpu_trace(ctx, sc, rays)
+    tri, t, uv, _ = gpu_trace(ctx, sc, rays, method=method)
     ids, tt, uu, vv, nd = O.Mesh(sc.verts, sc.tris).closest_hit(rays, brute=True)
     parity_hits(tri, t, ids, tt, nd)
     hit = nd.astype(bool) & (ids >= 0)
@@ -55,6 +56,17 @@ def test_sphere_both_link_sets(ctx, link_sets):
     tri, t, _, _ = gpu_trace(ctx, sc, rays, link_sets=link_sets)
     ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(rays)
     parity_hits(tri, t, ids, tt, nd)
+
+
+def test_stack_traversal_agrees_with_mtbvh(ctx):
+    """Both traversals return the lexicographic minimum over the same FP32 triangle tests."""
+    sc = I.traversal_sphere(n=40, seed=6)
+    rays = I.traversal_rays(128, 64, n_random=16384, seed=36)
+    a = gpu_trace(ctx, sc, rays, method="stack")
+    b = gpu_trace(ctx, sc, rays)
+    ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(rays)
+    parity_hits(a[0], a[1], ids, tt, nd)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.int32), b[1].view(np.int32))
 
 
 def test_link_sets_agree_bitwise(ctx):
@@ -81,11 +93,12 @@ def test_edge_cases(ctx):
                      [0.5, 0.5, 0.5, 5.0, 0, 0, -1, np.inf],
                      [5, 5, 5, 0, 1, 0, 0, np.inf],
                      [0.3, 0.2, 0.25, 0, 0.3, 0.9, -0.2, np.inf]], np.float32)
-    for batch in (rays[:1], rays, np.concatenate([rays] * 5)[:33]):
-        tri, t, _, _ = gpu_trace(ctx, sc, batch)
-        ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(batch, brute=True)
-        parity_hits(tri, t, ids, tt, nd, max_excluded=1.0)
-    assert gpu_trace(ctx, sc, rays[3:6])[0].tolist() == [-1, -1, -1]
+    for method in ("mtbvh", "stack"):
+        for batch in (rays[:1], rays, np.concatenate([rays] * 5)[:33]):
+            tri, t, _, _ = gpu_trace(ctx, sc, batch, method=method)
+            ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(batch, brute=True)
+            parity_hits(tri, t, ids, tt, nd, max_excluded=1.0)
+        assert gpu_trace(ctx, sc, rays[3:6], method=method)[0].tolist() == [-1, -1, -1]
 
 
 def test_matches_host_walk(ctx):
@@ -105,11 +118,12 @@ def full_size():
     return sc, rays
 
 
-def test_full_size_traversal_sampled(ctx, full_size):
+@pytest.mark.parametrize("method", ["mtbvh", "stack"])
+def test_full_size_traversal_sampled(ctx, full_size, method):
     """The benchmark's workload and launch: all 4M rays in one call; the oracle checks a
     stratified sample of 24,576 rays (both halves) with its FP64 BVH, and 256 by brute force."""
     sc, rays = full_size
-    tri, t, _, _ = gpu_trace(ctx, sc, rays)
+    tri, t, _, _ = gpu_trace(ctx, sc, rays, method=method)
     n = len(rays)
     rng = np.random.default_rng(77)
     sample = np.sort(np.concatenate([rng.choice(n // 2, 12288, replace=False),
