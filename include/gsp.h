@@ -192,6 +192,17 @@ gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh
 gsp_status gsp_trace_closest_hit(gsp_scene* scene, const float* d_rays, int64_t n, int32_t* d_tri,
                                  float* d_t, float* d_uv, void* stream);
 
+/* The same closest-hit query on HOST buffers (h_rays [n][8], h_tri [n], h_t [n], h_uv [n][2] or
+ * NULL), synchronous. Page-locked buffers the device can address (cudaHostAlloc /
+ * cudaHostRegister, e.g. pinned torch tensors; h_rays 16-byte and h_uv 8-byte aligned) are read
+ * and written by the traversal kernel itself, so the transfers overlap the traversal. Other
+ * buffers go in chunks of up to 2^18 rays through page-locked staging buffers on three streams,
+ * the copies of one chunk overlapping the traversal of others. The scene keeps per-stream device
+ * and staging buffers (about 45 MB), allocated after a device synchronisation when first needed.
+ * Results equal those of gsp_trace_closest_hit. */
+gsp_status gsp_trace_closest_hit_host(gsp_scene* scene, const float* h_rays, int64_t n, int32_t* h_tri,
+                                      float* h_t, float* h_uv);
+
 /* The same closest-hit query (same arguments, results and refinement) answered by a stack-based
  * near-first traversal of the same SAH tree, stored as child pairs (both children's boxes in one
  * 64-byte node): the kind of traversal the paper compares its stackless one with (Fig. 4; after

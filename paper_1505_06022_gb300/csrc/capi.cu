@@ -215,6 +215,17 @@ int gsp_trace_grid(int device) {
     return g;
 }
 
+// One closest-hit call on device buffers: counters zeroed, k_trace, FP64 refinement of the
+// flagged hits. ctr (2 u64) and rlist (n entries) belong to this call's stream.
+static void launch_trace(const gsp_scene* s, const float4* rays, int64_t n, int32_t* tri, float* t, float2* uv,
+                         unsigned long long* ctr, int2* rlist, cudaStream_t st) {
+    const gspd::DevScene S = gsp_dev_scene(s);
+    gspd::k_zero_u64x2<<<1, 1, 0, st>>>(ctr);
+    const int grid = gsp_trace_grid(s->ctx->device);
+    gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, rays, n, nullptr, tri, t, uv, ctr, rlist, GSP_REFINE_FACTOR, 0);
+    gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, rays, rlist, ctr, t, uv);
+}
+
 cudaError_t gsp_trace_queue(const gsp_scene* s, const float4* rays, int64_t max_n, const uint32_t* d_n, int32_t* tri,
                             float* t, float refine_factor, bool zero_counters, bool out_slot, cudaStream_t st) {
     const gspd::DevScene S = gsp_dev_scene(s);
@@ -314,6 +325,23 @@ gsp_status gsp_context_sync(gsp_context* ctx) {
     return st;
 }
 
+static void host_lanes_free(gsp_scene* s) {
+    for (auto& L : s->lanes) {
+        if (L.st) cudaStreamDestroy(L.st);
+        if (L.done) cudaEventDestroy(L.done);
+        cudaFree(L.d_rays);
+        cudaFree(L.d_tri);
+        cudaFree(L.d_t);
+        cudaFree(L.d_uv);
+        cudaFree(L.d_ctr);
+        cudaFree(L.d_rlist);
+        cudaFreeHost(L.h_in);
+        cudaFreeHost(L.h_out);
+        L = gsp_scene::HostLane{};
+    }
+    s->lane_cap = 0;
+}
+
 static void scene_free_bvh(gsp_scene* s) {
     cudaFree(s->d_nodes);
     cudaFree(s->d_tris);
@@ -334,6 +362,7 @@ void gsp_scene_destroy(gsp_scene* s) {
         cudaFree(s->d_mats);
         cudaFree(s->d_counter);
         cudaFree(s->d_rlist);
+        host_lanes_free(s);
     }
     delete s;
 }
@@ -513,13 +542,135 @@ gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, i
         GSP_CUDA_TRY(cudaMalloc(&s->d_rlist, (size_t)n * sizeof(int2)));
         s->rlist_cap = n;
     }
-    const gspd::DevScene S = gsp_dev_scene(s);
-    gspd::k_zero_u64x2<<<1, 1, 0, st>>>(s->d_counter);
-    const int grid = gsp_trace_grid(s->ctx->device);
-    gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, (const float4*)d_rays, n, nullptr, d_tri, d_t,
-                                                  (float2*)d_uv, s->d_counter, s->d_rlist, GSP_REFINE_FACTOR, 0);
-    gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, (const float4*)d_rays, s->d_rlist, s->d_counter, d_t,
-                                                          (float2*)d_uv);
+    launch_trace(s, (const float4*)d_rays, n, d_tri, d_t, (float2*)d_uv, s->d_counter, s->d_rlist, st);
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+#ifndef GSP_HOST_ZERO_COPY
+#define GSP_HOST_ZERO_COPY 1  // mapped page-locked host buffers: traverse them in place
+#endif
+#ifndef GSP_HOST_CHUNK
+#define GSP_HOST_CHUNK (1 << 18)
+#endif
+
+// Host buffers: the rays go to the device, are traced and come back chunk by chunk, with the
+// copies of one chunk overlapping the traversal of the others (kHostLanes streams, each with its
+// own device buffers and trace counters). Pinned caller memory is copied directly; pageable
+// memory passes through pinned staging buffers, filled and drained by the host while the
+// device works on other chunks.
+gsp_status gsp_trace_closest_hit_host(gsp_scene* s, const float* h_rays, int64_t n, int32_t* h_tri, float* h_t,
+                                      float* h_uv) {
+    if (!s || n < 0) return GSP_ERR_INVALID_ARG;
+    if (!s->ctx) return GSP_ERR_INVALID_ARG;
+    if (!s->built) return GSP_ERR_NOT_BUILT;
+    if (n == 0) return GSP_OK;
+    if (!h_rays || !h_tri || !h_t || n > INT32_MAX) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    (void)cudaGetLastError();
+    constexpr int64_t kChunk = GSP_HOST_CHUNK;
+    const int64_t chunk = std::min<int64_t>(kChunk, n);
+    if (s->lane_cap < chunk) {
+        GSP_CUDA_TRY(cudaDeviceSynchronize());
+        host_lanes_free(s);
+        for (auto& L : s->lanes) {
+            GSP_CUDA_TRY(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking));
+            GSP_CUDA_TRY(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+            GSP_CUDA_TRY(cudaMalloc(&L.d_rays, (size_t)chunk * 2 * sizeof(float4)));
+            GSP_CUDA_TRY(cudaMalloc(&L.d_tri, (size_t)chunk * sizeof(int32_t)));
+            GSP_CUDA_TRY(cudaMalloc(&L.d_t, (size_t)chunk * sizeof(float)));
+            GSP_CUDA_TRY(cudaMalloc(&L.d_uv, (size_t)chunk * sizeof(float2)));
+            GSP_CUDA_TRY(cudaMalloc(&L.d_ctr, 2 * sizeof(unsigned long long)));
+            GSP_CUDA_TRY(cudaMalloc(&L.d_rlist, (size_t)chunk * sizeof(int2)));
+        }
+        s->lane_cap = chunk;
+    }
+    // page-locked host memory that the device can address directly (NULL if it cannot)
+    auto mapped = [](const void* p) -> void* {
+        cudaPointerAttributes a{};
+        if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+    };
+    void* m_rays = mapped(h_rays);
+    void* m_tri = mapped(h_tri);
+    void* m_t = mapped(h_t);
+    void* m_uv = h_uv ? mapped(h_uv) : nullptr;
+    const bool direct = m_rays && m_tri && m_t && (!h_uv || m_uv);
+    if (GSP_HOST_ZERO_COPY && direct && !((uintptr_t)m_rays & 15) && !((uintptr_t)m_uv & 7)) {
+        // Page-locked and mapped: the traversal reads the rays from host memory and writes the
+        // hits there itself (the NVLink-C2C / PCIe transfers happen inside the kernel, spread
+        // over its run, instead of as separate copies before and after it).
+        if (n > s->rlist_cap) {
+            GSP_CUDA_TRY(cudaDeviceSynchronize());
+            cudaFree(s->d_rlist);
+            s->d_rlist = nullptr;
+            s->rlist_cap = 0;
+            GSP_CUDA_TRY(cudaMalloc(&s->d_rlist, (size_t)n * sizeof(int2)));
+            s->rlist_cap = n;
+        }
+        cudaStream_t st = s->lanes[0].st;
+        launch_trace(s, (const float4*)m_rays, n, (int32_t*)m_tri, (float*)m_t, (float2*)m_uv, s->d_counter, s->d_rlist,
+                     st);
+        GSP_CUDA_TRY(cudaGetLastError());
+        GSP_CUDA_TRY(cudaStreamSynchronize(st));
+        return GSP_OK;
+    }
+    const size_t in_b = (size_t)s->lane_cap * 32, out_b = (size_t)s->lane_cap * 16;
+    if (!direct)
+        for (auto& L : s->lanes) {
+            if (!L.h_in) GSP_CUDA_TRY(cudaMallocHost(&L.h_in, in_b));
+            if (!L.h_out) GSP_CUDA_TRY(cudaMallocHost(&L.h_out, out_b));
+        }
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    std::vector<int64_t> pending(gsp_scene::kHostLanes, -1);  // staged chunk whose outputs wait on the host
+    auto drain = [&](int k) -> cudaError_t {  // copy a staged chunk's results to the caller
+        if (pending[k] < 0) return cudaSuccess;
+        cudaError_t e = cudaEventSynchronize(s->lanes[k].done);
+        if (e != cudaSuccess) return e;
+        const int64_t off = pending[k] * chunk, m = std::min(chunk, n - off);
+        const char* o = (const char*)s->lanes[k].h_out;
+        std::memcpy(h_tri + off, o, (size_t)m * 4);
+        std::memcpy(h_t + off, o + (size_t)s->lane_cap * 4, (size_t)m * 4);
+        if (h_uv) std::memcpy(h_uv + 2 * off, o + (size_t)s->lane_cap * 8, (size_t)m * 8);
+        pending[k] = -1;
+        return cudaSuccess;
+    };
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int k = (int)(c % gsp_scene::kHostLanes);
+        auto& L = s->lanes[k];
+        const int64_t off = c * chunk, m = std::min(chunk, n - off);
+        const float* src = h_rays + off * 8;
+        if (!direct) {
+            GSP_CUDA_TRY(drain(k));  // the lane's staging buffers are free again
+            GSP_CUDA_TRY(cudaEventSynchronize(L.done));
+            std::memcpy(L.h_in, src, (size_t)m * 32);
+            src = (const float*)L.h_in;
+        }
+        GSP_CUDA_TRY(cudaMemcpyAsync(L.d_rays, src, (size_t)m * 32, cudaMemcpyHostToDevice, L.st));
+        launch_trace(s, L.d_rays, m, L.d_tri, L.d_t, h_uv ? L.d_uv : nullptr, L.d_ctr, L.d_rlist, L.st);
+        if (direct) {
+            GSP_CUDA_TRY(cudaMemcpyAsync(h_tri + off, L.d_tri, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
+            GSP_CUDA_TRY(cudaMemcpyAsync(h_t + off, L.d_t, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
+            if (h_uv)
+                GSP_CUDA_TRY(cudaMemcpyAsync(h_uv + 2 * off, L.d_uv, (size_t)m * 8, cudaMemcpyDeviceToHost, L.st));
+        } else {
+            char* o = (char*)L.h_out;
+            GSP_CUDA_TRY(cudaMemcpyAsync(o, L.d_tri, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
+            GSP_CUDA_TRY(cudaMemcpyAsync(o + (size_t)s->lane_cap * 4, L.d_t, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
+            if (h_uv)
+                GSP_CUDA_TRY(cudaMemcpyAsync(o + (size_t)s->lane_cap * 8, L.d_uv, (size_t)m * 8, cudaMemcpyDeviceToHost,
+                                             L.st));
+            pending[k] = c;
+        }
+        GSP_CUDA_TRY(cudaEventRecord(L.done, L.st));
+    }
+    for (int k = 0; k < gsp_scene::kHostLanes; ++k) {
+        GSP_CUDA_TRY(drain(k));
+        GSP_CUDA_TRY(cudaStreamSynchronize(s->lanes[k].st));
+    }
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
 }

@@ -67,6 +67,22 @@ struct gsp_scene {
     bool built = false;
     HostBVH bvh;
     int64_t device_bytes = 0;
+    // host-buffer tracing (gsp_trace_closest_hit_host): a pipeline of chunks over kHostLanes
+    // streams, each with its own device buffers, trace counters, refine list and pinned staging
+    static constexpr int kHostLanes = 3;
+    struct HostLane {
+        cudaStream_t st = nullptr;
+        cudaEvent_t done = nullptr;
+        float4* d_rays = nullptr;
+        int32_t* d_tri = nullptr;
+        float* d_t = nullptr;
+        float2* d_uv = nullptr;
+        unsigned long long* d_ctr = nullptr;
+        int2* d_rlist = nullptr;
+        void* h_in = nullptr;   // pinned staging for pageable caller buffers
+        void* h_out = nullptr;
+    } lanes[kHostLanes];
+    int64_t lane_cap = 0;  // rays per chunk the lanes were allocated for
 };
 
 #define GSP_CUDA_TRY(expr)                                   \

@@ -33,7 +33,7 @@ EXACT, STOCHASTIC = 0, 1
 # exported symbols of include/gsp.h
 ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp_context_destroy",
        "gsp_context_sync", "gsp_scene_upload", "gsp_scene_destroy", "gsp_build_bvh",
-       "gsp_trace_closest_hit", "gsp_trace_closest_hit_stack", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
+       "gsp_trace_closest_hit", "gsp_trace_closest_hit_stack", "gsp_trace_closest_hit_host", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
@@ -109,6 +109,7 @@ def lib():
             L.gsp_build_bvh.argtypes = [P, P, P]
             L.gsp_trace_closest_hit.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_trace_closest_hit_stack.argtypes = [P, P, I64, P, P, P, P]
+            L.gsp_trace_closest_hit_host.argtypes = [P, P, I64, P, P, P]
             L.gsp_bvh_host_walk.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_bvh_export.argtypes = [P, I32, P, P, C.POINTER(I64)]
             L.gsp_sppm_create.argtypes = [P, P, C.POINTER(P)]
@@ -255,6 +256,27 @@ def gsp_trace_closest_hit_stack(scene, rays, tri, t, uv=None, stream=None):
     n = rays.shape[0]
     rc = lib().gsp_trace_closest_hit_stack(scene, _dev(rays), n, _dev(tri), _dev(t), _dev(uv), _stream(stream))
     _check("gsp_trace_closest_hit_stack", rc)
+
+
+def _host_ptr(x):
+    """Address of a host array: a CPU torch tensor (pinned or not) or a C-contiguous numpy array."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda or not x.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        return x.data_ptr()
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous array")
+    return x.ctypes.data
+
+
+def gsp_trace_closest_hit_host(scene, rays, tri, t, uv=None):
+    """Host buffers (numpy arrays or CPU tensors): rays float32 [n, 8] in; tri int32 [n], t float32
+    [n], uv float32 [n, 2] or None out. Synchronous; copies overlap the traversal."""
+    n = rays.shape[0]
+    rc = lib().gsp_trace_closest_hit_host(scene, _host_ptr(rays), n, _host_ptr(tri), _host_ptr(t), _host_ptr(uv))
+    _check("gsp_trace_closest_hit_host", rc)
 
 
 def gsp_bvh_host_walk(scene, rays):

@@ -135,3 +135,33 @@ def test_full_size_traversal_sampled(ctx, full_size, method):
     bids, btt, _, _, bnd = mesh.closest_hit(rays[sub], brute=True)
     parity_hits(tri[sub], t[sub], bids, btt, bnd)
     assert (tri >= 0).mean() > 0.2
+
+
+def test_host_buffer_entry_matches_device_entry(ctx, full_size):
+    """gsp_trace_closest_hit_host: chunked copies over three streams, pinned (direct) and pageable
+    (staged) host buffers, a ragged last chunk; results equal the device-buffer call's."""
+    sc, rays = full_size
+    rays = rays[: len(rays) - 12345]
+    s = gsp.Scene(ctx, sc)
+    d = torch.from_numpy(rays).cuda()
+    tri_d, t_d, uv_d = s.trace(d, with_uv=True)
+    torch.cuda.synchronize()
+    want = (tri_d.cpu().numpy(), t_d.cpu().numpy(), uv_d.cpu().numpy())
+    n = len(rays)
+    # pinned
+    r_pin = torch.from_numpy(rays).pin_memory()
+    tri_p = torch.empty(n, dtype=torch.int32).pin_memory()
+    t_p = torch.empty(n, dtype=torch.float32).pin_memory()
+    uv_p = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+    gsp.gsp_trace_closest_hit_host(s.h, r_pin, tri_p, t_p, uv_p)
+    # pageable, without uv
+    tri_n = np.empty(n, np.int32)
+    t_n = np.empty(n, np.float32)
+    gsp.gsp_trace_closest_hit_host(s.h, np.ascontiguousarray(rays), tri_n, t_n)
+    ctx.sync()
+    assert np.array_equal(tri_p.numpy(), want[0]) and np.array_equal(t_p.numpy().view(np.int32), want[1].view(np.int32))
+    assert np.array_equal(uv_p.numpy().view(np.int32), want[2].view(np.int32))
+    assert np.array_equal(tri_n, want[0]) and np.array_equal(t_n.view(np.int32), want[1].view(np.int32))
+    # a small call after a large one reuses the lanes
+    gsp.gsp_trace_closest_hit_host(s.h, np.ascontiguousarray(rays[:1000]), tri_n[:1000], t_n[:1000])
+    assert np.array_equal(tri_n[:1000], want[0][:1000])
