@@ -194,12 +194,13 @@ gsp_status gsp_trace_closest_hit(gsp_scene* scene, const float* d_rays, int64_t 
 
 /* The same closest-hit query on HOST buffers (h_rays [n][8], h_tri [n], h_t [n], h_uv [n][2] or
  * NULL), synchronous. Page-locked buffers the device can address (cudaHostAlloc /
- * cudaHostRegister, e.g. pinned torch tensors; h_rays 16-byte and h_uv 8-byte aligned) are read
- * and written by the traversal kernel itself, so the transfers overlap the traversal. Other
- * buffers go in chunks of up to 2^18 rays through page-locked staging buffers on three streams,
- * the copies of one chunk overlapping the traversal of others. The scene keeps per-stream device
- * and staging buffers (about 45 MB), allocated after a device synchronisation when first needed.
- * Results equal those of gsp_trace_closest_hit. */
+ * cudaHostRegister, e.g. pinned torch tensors; h_rays 16-byte aligned): the traversal reads the
+ * rays from host memory itself, in two halves on two streams, and each half's results are copied
+ * back while the other half is traced. Other buffers go in chunks of up to 2^20 rays through
+ * page-locked staging buffers on three streams. The scene keeps per-stream device buffers (24
+ * bytes per ray of a half or chunk, plus 32 + 48 bytes per ray of a chunk when staging),
+ * allocated after a device synchronisation when first needed or outgrown. Results equal those
+ * of gsp_trace_closest_hit. */
 gsp_status gsp_trace_closest_hit_host(gsp_scene* scene, const float* h_rays, int64_t n, int32_t* h_tri,
                                       float* h_t, float* h_uv);
 

@@ -547,18 +547,45 @@ gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, i
     return GSP_OK;
 }
 
-#ifndef GSP_HOST_ZERO_COPY
-#define GSP_HOST_ZERO_COPY 1  // mapped page-locked host buffers: traverse them in place
-#endif
 #ifndef GSP_HOST_CHUNK
-#define GSP_HOST_CHUNK (1 << 18)
+#define GSP_HOST_CHUNK (1 << 20)  // rays per chunk of the staged pipeline
 #endif
 
-// Host buffers: the rays go to the device, are traced and come back chunk by chunk, with the
-// copies of one chunk overlapping the traversal of the others (kHostLanes streams, each with its
-// own device buffers and trace counters). Pinned caller memory is copied directly; pageable
-// memory passes through pinned staging buffers, filled and drained by the host while the
-// device works on other chunks.
+// (Re)allocates the host-tracing lanes for `cap` rays each; the ray and staging buffers only when
+// `staged` (the mapped path reads the caller's rays in place).
+static gsp_status host_lanes_reserve(gsp_scene* s, int64_t cap, bool staged) {
+    const bool have_in = s->lanes[0].d_rays != nullptr;
+    if (s->lane_cap >= cap && (!staged || have_in)) return GSP_OK;
+    cap = std::max(cap, s->lane_cap);
+    GSP_CUDA_TRY(cudaDeviceSynchronize());
+    host_lanes_free(s);
+    for (auto& L : s->lanes) {
+        GSP_CUDA_TRY(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking));
+        GSP_CUDA_TRY(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+        if (staged || have_in) {
+            GSP_CUDA_TRY(cudaMalloc(&L.d_rays, (size_t)cap * 2 * sizeof(float4)));
+            GSP_CUDA_TRY(cudaMallocHost(&L.h_in, (size_t)cap * 32));
+            GSP_CUDA_TRY(cudaMallocHost(&L.h_out, (size_t)cap * 16));
+        }
+        GSP_CUDA_TRY(cudaMalloc(&L.d_tri, (size_t)cap * sizeof(int32_t)));
+        GSP_CUDA_TRY(cudaMalloc(&L.d_t, (size_t)cap * sizeof(float)));
+        GSP_CUDA_TRY(cudaMalloc(&L.d_uv, (size_t)cap * sizeof(float2)));
+        GSP_CUDA_TRY(cudaMalloc(&L.d_ctr, 2 * sizeof(unsigned long long)));
+        GSP_CUDA_TRY(cudaMalloc(&L.d_rlist, (size_t)cap * sizeof(int2)));
+    }
+    s->lane_cap = cap;
+    return GSP_OK;
+}
+
+// Closest hits for host buffers. Page-locked buffers that the device can address: the rays are
+// split in two halves on two streams; k_trace reads each half's rays from host memory itself (the
+// transfer spreads over the traversal) and writes the hits to device buffers, which are copied
+// back while the other half is traced. Measured alternatives were slower on GB300 (4,194,304
+// rays): the traversal also writing its 4-byte results to host memory (3,390 Mrays/s against
+// 3,560 for one part), a copy of the rays before the traversal (2,640), and copy-engine
+// pipelines of 2^17-2^20-ray chunks (1,240-2,940). Other buffers: chunks through page-locked
+// staging buffers on three streams, the host filling and draining them while the device works
+// on other chunks.
 gsp_status gsp_trace_closest_hit_host(gsp_scene* s, const float* h_rays, int64_t n, int32_t* h_tri, float* h_t,
                                       float* h_uv) {
     if (!s || n < 0) return GSP_ERR_INVALID_ARG;
@@ -568,25 +595,8 @@ gsp_status gsp_trace_closest_hit_host(gsp_scene* s, const float* h_rays, int64_t
     if (!h_rays || !h_tri || !h_t || n > INT32_MAX) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
     (void)cudaGetLastError();
-    constexpr int64_t kChunk = GSP_HOST_CHUNK;
-    const int64_t chunk = std::min<int64_t>(kChunk, n);
-    if (s->lane_cap < chunk) {
-        GSP_CUDA_TRY(cudaDeviceSynchronize());
-        host_lanes_free(s);
-        for (auto& L : s->lanes) {
-            GSP_CUDA_TRY(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking));
-            GSP_CUDA_TRY(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
-            GSP_CUDA_TRY(cudaMalloc(&L.d_rays, (size_t)chunk * 2 * sizeof(float4)));
-            GSP_CUDA_TRY(cudaMalloc(&L.d_tri, (size_t)chunk * sizeof(int32_t)));
-            GSP_CUDA_TRY(cudaMalloc(&L.d_t, (size_t)chunk * sizeof(float)));
-            GSP_CUDA_TRY(cudaMalloc(&L.d_uv, (size_t)chunk * sizeof(float2)));
-            GSP_CUDA_TRY(cudaMalloc(&L.d_ctr, 2 * sizeof(unsigned long long)));
-            GSP_CUDA_TRY(cudaMalloc(&L.d_rlist, (size_t)chunk * sizeof(int2)));
-        }
-        s->lane_cap = chunk;
-    }
     // page-locked host memory that the device can address directly (NULL if it cannot)
-    auto mapped = [](const void* p) -> void* {
+    auto mapped = [](const void* p) -> const void* {
         cudaPointerAttributes a{};
         if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -594,47 +604,41 @@ gsp_status gsp_trace_closest_hit_host(gsp_scene* s, const float* h_rays, int64_t
         }
         return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
     };
-    void* m_rays = mapped(h_rays);
-    void* m_tri = mapped(h_tri);
-    void* m_t = mapped(h_t);
-    void* m_uv = h_uv ? mapped(h_uv) : nullptr;
-    const bool direct = m_rays && m_tri && m_t && (!h_uv || m_uv);
-    if (GSP_HOST_ZERO_COPY && direct && !((uintptr_t)m_rays & 15) && !((uintptr_t)m_uv & 7)) {
-        // Page-locked and mapped: the traversal reads the rays from host memory and writes the
-        // hits there itself (the NVLink-C2C / PCIe transfers happen inside the kernel, spread
-        // over its run, instead of as separate copies before and after it).
-        if (n > s->rlist_cap) {
-            GSP_CUDA_TRY(cudaDeviceSynchronize());
-            cudaFree(s->d_rlist);
-            s->d_rlist = nullptr;
-            s->rlist_cap = 0;
-            GSP_CUDA_TRY(cudaMalloc(&s->d_rlist, (size_t)n * sizeof(int2)));
-            s->rlist_cap = n;
+    const float4* m_rays = (const float4*)mapped(h_rays);
+    if (m_rays && !((uintptr_t)m_rays & 15) && mapped(h_tri) && mapped(h_t) && (!h_uv || mapped(h_uv))) {
+        constexpr int kParts = 2;
+        const int64_t per = (n + kParts - 1) / kParts;
+        gsp_status e = host_lanes_reserve(s, per, false);
+        if (e != GSP_OK) return e;
+        for (int k = 0; k < kParts; ++k) {
+            const int64_t off = k * per, m = std::min(per, n - off);
+            if (m <= 0) break;
+            auto& L = s->lanes[k];
+            launch_trace(s, m_rays + 2 * off, m, L.d_tri, L.d_t, h_uv ? L.d_uv : nullptr, L.d_ctr, L.d_rlist, L.st);
+            GSP_CUDA_TRY(cudaMemcpyAsync(h_tri + off, L.d_tri, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
+            GSP_CUDA_TRY(cudaMemcpyAsync(h_t + off, L.d_t, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
+            if (h_uv)
+                GSP_CUDA_TRY(cudaMemcpyAsync(h_uv + 2 * off, L.d_uv, (size_t)m * 8, cudaMemcpyDeviceToHost, L.st));
         }
-        cudaStream_t st = s->lanes[0].st;
-        launch_trace(s, (const float4*)m_rays, n, (int32_t*)m_tri, (float*)m_t, (float2*)m_uv, s->d_counter, s->d_rlist,
-                     st);
+        for (int k = 0; k < kParts; ++k) GSP_CUDA_TRY(cudaStreamSynchronize(s->lanes[k].st));
         GSP_CUDA_TRY(cudaGetLastError());
-        GSP_CUDA_TRY(cudaStreamSynchronize(st));
         return GSP_OK;
     }
-    const size_t in_b = (size_t)s->lane_cap * 32, out_b = (size_t)s->lane_cap * 16;
-    if (!direct)
-        for (auto& L : s->lanes) {
-            if (!L.h_in) GSP_CUDA_TRY(cudaMallocHost(&L.h_in, in_b));
-            if (!L.h_out) GSP_CUDA_TRY(cudaMallocHost(&L.h_out, out_b));
-        }
+    const int64_t chunk = std::min<int64_t>(GSP_HOST_CHUNK, n);
+    gsp_status e = host_lanes_reserve(s, chunk, true);
+    if (e != GSP_OK) return e;
+    const int64_t cap = s->lane_cap;
     const int64_t nchunks = (n + chunk - 1) / chunk;
-    std::vector<int64_t> pending(gsp_scene::kHostLanes, -1);  // staged chunk whose outputs wait on the host
-    auto drain = [&](int k) -> cudaError_t {  // copy a staged chunk's results to the caller
+    std::vector<int64_t> pending(gsp_scene::kHostLanes, -1);  // chunk whose results wait in staging
+    auto drain = [&](int k) -> cudaError_t {                    // copy a staged chunk's results out
         if (pending[k] < 0) return cudaSuccess;
-        cudaError_t e = cudaEventSynchronize(s->lanes[k].done);
-        if (e != cudaSuccess) return e;
+        cudaError_t ce = cudaEventSynchronize(s->lanes[k].done);
+        if (ce != cudaSuccess) return ce;
         const int64_t off = pending[k] * chunk, m = std::min(chunk, n - off);
         const char* o = (const char*)s->lanes[k].h_out;
         std::memcpy(h_tri + off, o, (size_t)m * 4);
-        std::memcpy(h_t + off, o + (size_t)s->lane_cap * 4, (size_t)m * 4);
-        if (h_uv) std::memcpy(h_uv + 2 * off, o + (size_t)s->lane_cap * 8, (size_t)m * 8);
+        std::memcpy(h_t + off, o + (size_t)cap * 4, (size_t)m * 4);
+        if (h_uv) std::memcpy(h_uv + 2 * off, o + (size_t)cap * 8, (size_t)m * 8);
         pending[k] = -1;
         return cudaSuccess;
     };
@@ -642,29 +646,16 @@ gsp_status gsp_trace_closest_hit_host(gsp_scene* s, const float* h_rays, int64_t
         const int k = (int)(c % gsp_scene::kHostLanes);
         auto& L = s->lanes[k];
         const int64_t off = c * chunk, m = std::min(chunk, n - off);
-        const float* src = h_rays + off * 8;
-        if (!direct) {
-            GSP_CUDA_TRY(drain(k));  // the lane's staging buffers are free again
-            GSP_CUDA_TRY(cudaEventSynchronize(L.done));
-            std::memcpy(L.h_in, src, (size_t)m * 32);
-            src = (const float*)L.h_in;
-        }
-        GSP_CUDA_TRY(cudaMemcpyAsync(L.d_rays, src, (size_t)m * 32, cudaMemcpyHostToDevice, L.st));
+        GSP_CUDA_TRY(drain(k));  // the lane's staging buffers are free again
+        GSP_CUDA_TRY(cudaEventSynchronize(L.done));
+        std::memcpy(L.h_in, h_rays + off * 8, (size_t)m * 32);
+        GSP_CUDA_TRY(cudaMemcpyAsync(L.d_rays, L.h_in, (size_t)m * 32, cudaMemcpyHostToDevice, L.st));
         launch_trace(s, L.d_rays, m, L.d_tri, L.d_t, h_uv ? L.d_uv : nullptr, L.d_ctr, L.d_rlist, L.st);
-        if (direct) {
-            GSP_CUDA_TRY(cudaMemcpyAsync(h_tri + off, L.d_tri, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
-            GSP_CUDA_TRY(cudaMemcpyAsync(h_t + off, L.d_t, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
-            if (h_uv)
-                GSP_CUDA_TRY(cudaMemcpyAsync(h_uv + 2 * off, L.d_uv, (size_t)m * 8, cudaMemcpyDeviceToHost, L.st));
-        } else {
-            char* o = (char*)L.h_out;
-            GSP_CUDA_TRY(cudaMemcpyAsync(o, L.d_tri, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
-            GSP_CUDA_TRY(cudaMemcpyAsync(o + (size_t)s->lane_cap * 4, L.d_t, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
-            if (h_uv)
-                GSP_CUDA_TRY(cudaMemcpyAsync(o + (size_t)s->lane_cap * 8, L.d_uv, (size_t)m * 8, cudaMemcpyDeviceToHost,
-                                             L.st));
-            pending[k] = c;
-        }
+        char* o = (char*)L.h_out;
+        GSP_CUDA_TRY(cudaMemcpyAsync(o, L.d_tri, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
+        GSP_CUDA_TRY(cudaMemcpyAsync(o + (size_t)cap * 4, L.d_t, (size_t)m * 4, cudaMemcpyDeviceToHost, L.st));
+        if (h_uv) GSP_CUDA_TRY(cudaMemcpyAsync(o + (size_t)cap * 8, L.d_uv, (size_t)m * 8, cudaMemcpyDeviceToHost, L.st));
+        pending[k] = c;
         GSP_CUDA_TRY(cudaEventRecord(L.done, L.st));
     }
     for (int k = 0; k < gsp_scene::kHostLanes; ++k) {
