@@ -291,6 +291,7 @@ def run_ours(args, world, rank, local):
     sppm = bench_sppm(args, ctx, dev, stream, pg) if not args.skip_sppm else None
     grad = bench_grad(args, ctx, dev, stream) if not args.skip_grad else None
     batch = bench_batch(args, ctx, dev, stream) if not args.skip_batch else None
+    modes = bench_modes(args, ctx, dev, stream) if not args.skip_modes else None
 
     # ---- CPU baseline: the oracle on the same workload ----
     cpu = None
@@ -322,6 +323,7 @@ def run_ours(args, world, rank, local):
             "sppm_512": sppm,
             "grad_256": grad,
             "batch_64": batch,
+            "sppm_modes": modes,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -470,6 +472,52 @@ def bench_traversals(args, ctx, dev, stream, sc, scene, rays):
     return out
 
 
+def bench_modes(args, ctx, dev, stream):
+    """The paper's photon-pass and hashing variants at equal image error (512x512 full scene,
+    2^20 photon paths or threads per pass): RMSE against a 256-pass full-path exact-grid render
+    of another seed, after 16, 32 and 64 passes, time per pass, and the time each mode needs to
+    reach the error of 64 full-path exact-grid passes (log-log interpolation in passes)."""
+    import torch
+    from paper_1505_06022_gb300 import gsp, inputs as I
+    sc = I.full_scene(seed=3)
+    s = gsp.Scene(ctx, sc)
+    ref = gsp.Renderer(s, gsp.sppm_params(sc, 1 << 20, seed=99, r0_frac=0.004))
+    ref.run(256, stream)
+    want = ref.image(stream).double()
+    ref.close()
+    norm = float(want.pow(2).mean().sqrt())
+    modes = {"full_path+exact": (gsp.FULL_PATH, gsp.EXACT), "full_path+stochastic": (gsp.FULL_PATH, gsp.STOCHASTIC),
+             "regen+exact": (gsp.REGEN, gsp.EXACT), "regen+stochastic": (gsp.REGEN, gsp.STOCHASTIC)}
+    marks = [16, 32, 64]
+    out = {}
+    for name, (pm, hm) in modes.items():
+        r = gsp.Renderer(s, gsp.sppm_params(sc, 1 << 20, seed=3, r0_frac=0.004, photon_mode=pm, hash_mode=hm))
+        rmse, ms, done = [], 0.0, 0
+        for k in marks:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r.run(k - done, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            done = k
+            img = r.image(stream).double()
+            rmse.append(float((img - want).pow(2).mean().sqrt()) / norm)
+        out[name] = {"ms_per_pass": round(ms / marks[-1], 3), "relative_rmse": dict(zip(map(str, marks),
+                                                                                   [round(v, 5) for v in rmse]))}
+        r.close()
+    target = out["full_path+exact"]["relative_rmse"]["64"]
+    for name, o in out.items():
+        e = [o["relative_rmse"][str(k)] for k in marks]
+        slope = (np.log(e[-1]) - np.log(e[0])) / (np.log(marks[-1]) - np.log(marks[0]))
+        passes = marks[-1] * np.exp((np.log(target) - np.log(e[-1])) / slope) if slope < 0 else float("nan")
+        o["passes_to_reference_error"] = round(float(passes), 1)
+        o["ms_to_reference_error"] = round(float(passes) * o["ms_per_pass"], 1)
+    s.close()
+    return {"modes": out, "reference": "256 passes, full paths + exact grid, seed 99",
+            "error_target": f"relative RMSE {target} (64 passes of full paths + exact grid)"}
+
+
 def bench_batch(args, ctx, dev, stream):
     """64 scenes (1k-200k triangles log-uniform, 64^2-512^2): scene-passes per second as one CUDA
     graph per pass (settings from the batch autotuner) vs the same renderers run one after
@@ -538,6 +586,7 @@ def main():
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-fig4", action="store_true")
+    ap.add_argument("--skip-modes", action="store_true")
     ap.add_argument("--batch-scenes", type=int, default=64)
     ap.add_argument("--batch-passes", type=int, default=4)
     ap.add_argument("--skip-cpu", action="store_true")
