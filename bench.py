@@ -444,11 +444,16 @@ def bench_traversals(args, ctx, dev, stream, sc, scene, rays):
     from paper_1505_06022_gb300 import gsp
     n = rays.shape[0]
     tbvh = gsp.Scene(ctx, sc, bins=16, leaf_threshold=4, max_leaf=7, link_sets=1)
+    t0 = time.perf_counter()
+    lbvh = gsp.Scene(ctx, sc, builder="device", link_sets=6, max_leaf=4)
+    lbvh_wall_ms = 1000.0 * (time.perf_counter() - t0)
     tri = torch.empty(n, dtype=torch.int32, device=dev)
     tt = torch.empty(n, dtype=torch.float32, device=dev)
     parts = {"all": (0, n), "coherent": (0, n // 2), "random": (n // 2, n)}
     kinds = {"mtbvh": (scene, gsp.gsp_trace_closest_hit), "tbvh": (tbvh, gsp.gsp_trace_closest_hit),
-             "stack": (scene, gsp.gsp_trace_closest_hit_stack)}
+             "stack": (scene, gsp.gsp_trace_closest_hit_stack),
+             "mtbvh_on_device_lbvh": (lbvh, gsp.gsp_trace_closest_hit),
+             "stack_on_device_lbvh": (lbvh, gsp.gsp_trace_closest_hit_stack)}
     reps = max(3, min(args.steps, 30))
     out = {}
     for kind, (scn, fn) in kinds.items():
@@ -469,6 +474,12 @@ def bench_traversals(args, ctx, dev, stream, sc, scene, rays):
     tbvh.close()
     out["mtbvh_over_tbvh"] = {p: round(out["mtbvh"][p] / out["tbvh"][p], 3) for p in parts}
     out["unit"] = "Mrays/s"
+    out["bvh_build"] = {
+        "host_sah_ms": round(scene.stats["build_ms"], 1), "host_threading_ms": round(scene.stats["thread_ms"], 1),
+        "device_lbvh_ms": round(lbvh.stats["build_ms"], 2), "device_threading_ms": round(lbvh.stats["thread_ms"], 2),
+        "device_lbvh_call_ms": round(lbvh_wall_ms, 1),
+        "nodes": {"host_sah": scene.stats["nodes"], "device_lbvh": lbvh.stats["nodes"]}}
+    lbvh.close()
     return out
 
 

@@ -178,6 +178,18 @@ gsp_status gsp_scene_set_materials(gsp_scene* scene, const gsp_material* mats, i
  * them to the device (replacing any previous BVH). params NULL = defaults. stats may be NULL. */
 gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh_stats* stats);
 
+/* Builds the BVH on the device instead (the paper's future work; Karras 2012): 30-bit Morton
+ * codes of the triangle centroids, a stable radix sort, the radix tree's internal nodes found
+ * independently, boxes bottom up, subtrees of at most max_leaf (1..7) triangles collapsed into
+ * leaves, then the hit/miss links of link_sets (1 or 6) direction classes threaded in parallel
+ * into the same packed layout gsp_build_bvh makes (and the child-pair layout of the stack
+ * traversal). Every traversal entry point accepts the result; closest hits are the same, only
+ * the work per ray differs (a Morton tree is not an SAH tree). stats.build_ms / thread_ms are
+ * device times (codes to sizes; threading and layouts), excluding the upload of the vertex and
+ * index arrays. Host copies are kept for gsp_bvh_host_walk / gsp_bvh_export. Device scenes only;
+ * at most 2^28 triangles. */
+gsp_status gsp_build_bvh_device(gsp_scene* scene, int32_t link_sets, int32_t max_leaf, gsp_bvh_stats* stats);
+
 /* Closest-hit ray casting (Fig. 3): for each ray i, the triangle with the lexicographically
  * smallest (t, triangle index) among tmin < t < tmax, Moller-Trumbore in FP32; when the FP32
  * t of the winner may be inaccurate (origin far from the triangle compared with t, grazing

@@ -352,6 +352,7 @@ static void scene_free_bvh(gsp_scene* s) {
     s->built = false;
 }
 
+
 void gsp_scene_destroy(gsp_scene* s) {
     if (!s) return;
     if (s->ctx) {
@@ -733,3 +734,13 @@ gsp_status gsp_bvh_export(gsp_scene* s, int32_t set, float* h_nodes, float* h_tr
 }
 
 }  // extern "C"
+
+void gsp_scene_adopt_bvh(gsp_scene* s, HostBVH&& bvh, float4* d_nodes, float4* d_tris, float4* d_bin) {
+    scene_free_bvh(s);
+    s->d_nodes = d_nodes;
+    s->d_tris = d_tris;
+    s->d_bin = d_bin;
+    s->device_bytes = (int64_t)((bvh.nodes.size() + bvh.tris.size()) * sizeof(float4)) + s->nt * (int64_t)sizeof(float4);
+    s->bvh = std::move(bvh);
+    s->built = true;
+}

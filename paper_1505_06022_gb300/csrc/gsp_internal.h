@@ -85,6 +85,10 @@ struct gsp_scene {
     int64_t lane_cap = 0;  // rays per chunk the lanes were allocated for
 };
 
+// Installs a BVH built elsewhere (host copies + device arrays the scene takes ownership of),
+// replacing the scene's current one.
+void gsp_scene_adopt_bvh(gsp_scene* s, HostBVH&& bvh, float4* d_nodes, float4* d_tris, float4* d_bin);
+
 #define GSP_CUDA_TRY(expr)                                   \
     do {                                                     \
         cudaError_t e_ = (expr);                             \

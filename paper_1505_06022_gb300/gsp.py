@@ -33,7 +33,7 @@ EXACT, STOCHASTIC = 0, 1
 # exported symbols of include/gsp.h
 ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp_context_destroy",
        "gsp_context_sync", "gsp_scene_upload", "gsp_scene_destroy", "gsp_build_bvh",
-       "gsp_trace_closest_hit", "gsp_trace_closest_hit_stack", "gsp_trace_closest_hit_host", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
+       "gsp_build_bvh_device", "gsp_trace_closest_hit", "gsp_trace_closest_hit_stack", "gsp_trace_closest_hit_host", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
@@ -107,6 +107,7 @@ def lib():
             L.gsp_scene_destroy.argtypes = [P]
             L.gsp_scene_destroy.restype = None
             L.gsp_build_bvh.argtypes = [P, P, P]
+            L.gsp_build_bvh_device.argtypes = [P, I32, I32, P]
             L.gsp_trace_closest_hit.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_trace_closest_hit_stack.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_trace_closest_hit_host.argtypes = [P, P, I64, P, P, P]
@@ -241,6 +242,12 @@ def gsp_build_bvh(scene, bins=16, leaf_threshold=4, max_leaf=7, link_sets=6) -> 
     p = BvhParams(bins, leaf_threshold, max_leaf, link_sets)
     st = BvhStats()
     _check("gsp_build_bvh", lib().gsp_build_bvh(scene, C.byref(p), C.byref(st)))
+    return st.as_dict()
+
+
+def gsp_build_bvh_device(scene, link_sets=6, max_leaf=4) -> dict:
+    st = BvhStats()
+    _check("gsp_build_bvh_device", lib().gsp_build_bvh_device(scene, link_sets, max_leaf, C.byref(st)))
     return st.as_dict()
 
 
@@ -429,7 +436,9 @@ class Context:
 class Scene:
     """Uploaded scene + BVH. `ctx` None makes a host-only scene."""
 
-    def __init__(self, ctx, scene: "_inputs.Scene", **bvh):
+    def __init__(self, ctx, scene: "_inputs.Scene", builder="host", **bvh):
+        """builder "host": binned SAH on the host (bins, leaf_threshold, max_leaf, link_sets);
+        "device": Morton-order LBVH built on the GPU (link_sets, max_leaf)."""
         self.ctx = ctx
         self.src = scene
         self._children = weakref.WeakSet()
@@ -437,7 +446,10 @@ class Scene:
                                   scene.mats, scene.camera)
         if ctx is not None:
             ctx._children.add(self)
-        self.stats = gsp_build_bvh(self.h, **bvh)
+        if builder == "device":
+            self.stats = gsp_build_bvh_device(self.h, bvh.get("link_sets", 6), bvh.get("max_leaf", 4))
+        else:
+            self.stats = gsp_build_bvh(self.h, **bvh)
 
     def trace(self, rays, stream=None, with_uv=False, method="mtbvh"):
         """Closest hits; method "mtbvh" (stackless, the scene's link sets) or "stack"."""
