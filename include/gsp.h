@@ -174,6 +174,14 @@ void gsp_scene_destroy(gsp_scene* scene);
  * Renderers created earlier keep the emitter table they were created with. */
 gsp_status gsp_scene_set_materials(gsp_scene* scene, const gsp_material* mats, int32_t nmat);
 
+/* Bounds the box tests of one ray's traversal (0 = the default, a few times the node count,
+ * which only corrupt links can reach). A ray that reaches the bound ends early and the first
+ * such event sets GSP_ERR_TRAVERSAL_LIMIT in the context's status word, which the next
+ * gsp_context_sync / gsp_sppm_sync returns (and clears); nothing traps and the context stays
+ * usable. Applies to launches made after the call (renderers read it per pass). For bounding
+ * worst-case work, and for testing the failure path without corrupting a BVH. */
+gsp_status gsp_scene_set_step_limit(gsp_scene* scene, int32_t max_box_tests);
+
 /* Builds the SAH BVH and its hit/miss links on the host (Sec. 3.1), packs them, and uploads
  * them to the device (replacing any previous BVH). params NULL = defaults. stats may be NULL. */
 gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh_stats* stats);

@@ -90,6 +90,7 @@ k_trace_stack(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* _
     wq.init((int32_t)n);
     Trav st;
     st.slot = -1;
+    const int32_t cap = trav_cap(S);
     int32_t ray = -1, node = kWalkDone, sp = 0;
     int32_t stk_node[kStackDepth];
     float stk_t[kStackDepth];
@@ -112,7 +113,10 @@ k_trace_stack(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* _
         if (__ballot_sync(0xffffffffu, ray >= 0) == 0) break;
 #pragma unroll 1
         for (int it = 0; it < kTraceInner; ++it) {
-            if (ray >= 0 && node != kWalkDone) {
+            if (ray >= 0 && node != kWalkDone && ++st.steps > cap) {  // corrupt data, or a test's limit
+                report(S.status, -4);
+                node = kWalkDone;
+            } else if (ray >= 0 && node != kWalkDone) {
                 if (node >= 0) {
                     const float4* q = S.bin + 4 * (int64_t)node;
                     const float4 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2), a3 = __ldg(q + 3);
@@ -256,6 +260,7 @@ gspd::DevScene gsp_dev_scene(const gsp_scene* s) {
     d.tris = s->d_tris;
     d.bin = s->d_bin;
     d.bin_root = s->bvh.bin_root;
+    d.step_limit = s->step_limit;
     d.shade = s->d_shade;
     d.nlo = s->d_nlo;
     d.mats = s->d_mats;
@@ -480,6 +485,12 @@ gsp_status gsp_scene_set_materials(gsp_scene* s, const gsp_material* mats, int32
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
     (void)cudaGetLastError();
     GSP_CUDA_TRY(cudaMemcpy(s->d_mats, mt.data(), mt.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    return GSP_OK;
+}
+
+gsp_status gsp_scene_set_step_limit(gsp_scene* s, int32_t max_box_tests) {
+    if (!s || max_box_tests < 0) return GSP_ERR_INVALID_ARG;
+    s->step_limit = max_box_tests;
     return GSP_OK;
 }
 

@@ -99,6 +99,7 @@ struct DevScene {
     int64_t stride;  // nodes per link set in memory (nnodes + 1 padding node)
     int32_t link_sets;
     int32_t bin_root;
+    int32_t step_limit;  // > 0: box tests one walk may make before it ends with an error
     int32_t* status;
 };
 
@@ -345,7 +346,7 @@ template <bool ALWAYS_REFINE>
 __device__ __forceinline__ Hit traverse(const DevScene& S, float3 o, float3 d, float tmin, float tmax) {
     Trav st;
     trav_init(S, o, d, tmin, tmax, st);
-    const int64_t cap = 2 * S.nnodes + 8;
+    const int64_t cap = S.step_limit > 0 ? S.step_limit : 2 * S.nnodes + 8;
     while (st.node >= 0) {
         if (++st.steps > cap) {
             report(S.status, -4);

@@ -65,6 +65,7 @@ struct gsp_scene {
     int2* d_rlist = nullptr;                  // trace kernel: hits re-evaluated in FP64
     int64_t rlist_cap = 0;
     bool built = false;
+    int32_t step_limit = 0;  // gsp_scene_set_step_limit (0 = the default cap)
     HostBVH bvh;
     int64_t device_bytes = 0;
     // host-buffer tracing (gsp_trace_closest_hit_host): a pipeline of chunks over kHostLanes

@@ -124,6 +124,7 @@ __device__ __forceinline__ void trav_steps(const DevScene& S, Trav& st, int32_t&
 }
 
 __device__ __forceinline__ int32_t trav_cap(const DevScene& S) {
+    if (S.step_limit > 0) return S.step_limit;
     return (int32_t)min(4 * S.nnodes + 16, (int64_t)INT32_MAX);  // box tests incl. retests
 }
 

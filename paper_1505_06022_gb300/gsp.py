@@ -33,7 +33,7 @@ EXACT, STOCHASTIC = 0, 1
 # exported symbols of include/gsp.h
 ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp_context_destroy",
        "gsp_context_sync", "gsp_scene_upload", "gsp_scene_destroy", "gsp_build_bvh",
-       "gsp_build_bvh_device", "gsp_trace_closest_hit", "gsp_trace_closest_hit_stack", "gsp_trace_closest_hit_host", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
+       "gsp_build_bvh_device", "gsp_scene_set_step_limit", "gsp_trace_closest_hit", "gsp_trace_closest_hit_stack", "gsp_trace_closest_hit_host", "gsp_bvh_host_walk", "gsp_bvh_export", "gsp_sppm_create",
        "gsp_sppm_destroy", "gsp_sppm_pass", "gsp_sppm_image", "gsp_sppm_state",
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
@@ -108,6 +108,7 @@ def lib():
             L.gsp_scene_destroy.restype = None
             L.gsp_build_bvh.argtypes = [P, P, P]
             L.gsp_build_bvh_device.argtypes = [P, I32, I32, P]
+            L.gsp_scene_set_step_limit.argtypes = [P, I32]
             L.gsp_trace_closest_hit.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_trace_closest_hit_stack.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_trace_closest_hit_host.argtypes = [P, P, I64, P, P, P]
@@ -243,6 +244,10 @@ def gsp_build_bvh(scene, bins=16, leaf_threshold=4, max_leaf=7, link_sets=6) -> 
     st = BvhStats()
     _check("gsp_build_bvh", lib().gsp_build_bvh(scene, C.byref(p), C.byref(st)))
     return st.as_dict()
+
+
+def gsp_scene_set_step_limit(scene, max_box_tests):
+    _check("gsp_scene_set_step_limit", lib().gsp_scene_set_step_limit(scene, max_box_tests))
 
 
 def gsp_build_bvh_device(scene, link_sets=6, max_leaf=4) -> dict:
