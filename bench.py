@@ -409,7 +409,7 @@ def bench_grad(args, ctx, dev, stream):
     fwd, bwd = [], []
     for rep in range(3):
         r = gsp.Renderer(s, params)
-        r.tune(choice["eye_steps"], choice["photon_steps"], 0.0, choice["gather_lanes"])
+        r.tune(choice["eye_steps"], choice["photon_steps"], 0.0, choice["gather_lanes"], choice["traversal"])
         r.enable_grad(passes)
         torch.cuda.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -430,7 +430,7 @@ def bench_grad(args, ctx, dev, stream):
     return {"forward_ms": round(f, 3), "backward_ms": round(b, 3), "backward_over_forward": round(b / f, 3),
             "grad_norm": round(float(ga.norm()), 6),
             "settings": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in choice.items()
-                         if k in ("eye_steps", "photon_steps", "cell_h", "gather_lanes")},
+                         if k in ("eye_steps", "photon_steps", "cell_h", "gather_lanes", "traversal")},
             "config": "256x256, 50,770 triangles (displaced plane in 12 material regions + 4 icospheres), "
                       "16 diffuse materials + light, 262,144 photon paths/pass, 8 passes, L2 loss vs a render "
                       "at perturbed albedos; gradient w.r.t. 16 RGB albedos and the light's emission"}
@@ -574,7 +574,7 @@ def bench_batch(args, ctx, dev, stream):
            "graph_scene_passes_per_s": round(1000.0 * n / bat_ms, 1),
            "speedup": round(seq_ms / bat_ms, 3), "ms_per_batch_pass": round(bat_ms, 3), "passes_timed": k,
            "batch_autotune": {"choice": {kk: v for kk, v in choice.items()
-                                         if kk in ("eye_steps", "photon_steps", "gather_lanes")},
+                                         if kk in ("eye_steps", "photon_steps", "gather_lanes", "traversal")},
                               "tuning_s": round(tune_s, 2)},
            "config": f"{n} scenes, 1e3-2e5 triangles log-uniform, image side in {{64,128,256,512}}, "
                      "262,144 photon paths/pass each, full paths + exact hash grid"}

@@ -269,9 +269,14 @@ gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
  * estimated FP32 error amplification exceeds it take an FP64 distance (trades hit-distance
  * accuracy for time).
  * gather_lanes: lanes that share one hit point's exact range query (1, 4, 8 or 16; default 8;
- * 0 = keep); changes only the order in which a pixel sums its photons. */
+ * 0 = keep); changes only the order in which a pixel sums its photons.
+ * traversal: GSP_TRAVERSAL_MTBVH (default) or GSP_TRAVERSAL_STACK for the persistent path kernel
+ * (0 = keep); the closest hits, hence the results, are the same. The stack needs a tree less
+ * than 64 levels deep (GSP_ERR_INVALID_ARG otherwise). */
+#define GSP_TRAVERSAL_MTBVH 1 /* the path kernel follows the hit/miss links (the paper's traversal) */
+#define GSP_TRAVERSAL_STACK 2 /* the path kernel walks the child-pair layout with a stack */
 gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, float refine_factor,
-                         int32_t gather_lanes);
+                         int32_t gather_lanes, int32_t traversal);
 
 /* Writes the current estimate L = direct / P + tau / (pi R^2 N_e) to d_rgb [h][w][3] float. */
 gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream);
@@ -323,6 +328,7 @@ typedef struct {
     float first_ms_per_pass;         /* time of the renderer's settings before tuning */
     int32_t candidates;              /* settings timed */
     int32_t gather_lanes;            /* chosen lanes per hit point in the exact gather (1, 4, 8, 16) */
+    int32_t traversal;               /* chosen path-kernel traversal (GSP_TRAVERSAL_*) */
 } gsp_tune_result;
 
 /* Times candidate execution settings that leave the estimate unchanged, each from a fresh state
@@ -330,13 +336,15 @@ typedef struct {
  * (the renderer's own state is not touched), and applies the fastest: first the eye and photon
  * wavefront steps (0-2 and 0, 1, 2, 4), then in exact mode the hash cell edge (2, 1.5, 1, 0.75
  * or 0.5 times r0; smaller cells scan fewer photons but more buckets), then the lanes that share
- * one hit point's range query (1, 4, 8 or 16). Cell edge and lanes change only the order in which
- * a pixel sums its photons. out may be NULL. */
+ * one hit point's range query (1, 4, 8 or 16), then the path kernel's traversal (hit/miss links
+ * or stack). Cell edge and lanes change only the order in which a pixel sums its photons. out
+ * may be NULL. */
 gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out);
 
 /* Autotuning of a whole batch, before its first pass: times batch passes (one CUDA graph each)
  * under candidate settings applied to every renderer -- wavefront steps (eye 0-1, photon 0-2),
- * then lanes per hit point in the exact gather (4, 8, 16) -- and keeps the fastest. Each
+ * then lanes per hit point in the exact gather (4, 8, 16), then the path kernel's traversal --
+ * and keeps the fastest. Each
  * candidate runs one untimed and trial_passes timed passes, after which every renderer is back
  * to its initial state, so the renders that follow are those of untuned renderers (bit for bit
  * for the steps; the lanes change only a pixel's summation order). GSP_ERR_BAD_STATE if a

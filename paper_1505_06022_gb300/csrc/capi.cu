@@ -71,15 +71,10 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* 
     }
 }
 
-// Closest hit by stack-based near-first traversal of the same SAH tree in its child-pair layout:
-// one 64-byte fetch brings both children's boxes, the nearer hit child is visited next and the
-// other pushed with its entry distance, and popped entries farther than the best hit so far are
-// skipped. It is the kind of traversal the paper measures the multiple-threaded BVH against
-// (Fig. 4; the stack-based kernels of Aila & Laine 2009), written here with the same work
-// distribution, leaf test, output and FP64 refinement list as k_trace.
-constexpr int kStackDepth = 64;            // the entry point requires tree depth < kStackDepth
-constexpr int32_t kWalkDone = INT32_MIN;   // never a node or leaf reference
-
+// Closest hit by stack-based near-first traversal of the same tree in its child-pair layout
+// (StackWalk), the kind of traversal the paper measures the multiple-threaded BVH against
+// (Fig. 4; the stack-based kernels of Aila & Laine 2009), with the same work distribution, leaf
+// test, output and FP64 refinement list as k_trace.
 __global__ void __launch_bounds__(kTraceThreads, GSP_TRACE_MIN_BLOCKS)
 k_trace_stack(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* __restrict__ tri,
               float* __restrict__ tout, float2* __restrict__ uv, unsigned long long* __restrict__ ctr,
@@ -91,65 +86,21 @@ k_trace_stack(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* _
     Trav st;
     st.slot = -1;
     const int32_t cap = trav_cap(S);
-    int32_t ray = -1, node = kWalkDone, sp = 0;
-    int32_t stk_node[kStackDepth];
-    float stk_t[kStackDepth];
-    auto pop = [&]() {
-        while (sp > 0) {
-            --sp;
-            if (stk_t[sp] <= st.tbest) return stk_node[sp];  // ties may still hold a smaller index
-        }
-        return kWalkDone;
-    };
+    int32_t ray = -1;
+    StackWalk w;
+    w.node = kWalkDone;
+    w.sp = 0;
     while (true) {
         const int32_t got = wq.take(ray < 0, ctr);
         if (got >= 0) {
             ray = got;
             const float4 a = __ldcs(rays + 2 * (int64_t)ray), b = __ldcs(rays + 2 * (int64_t)ray + 1);
             trav_init(S, f3(a), f3(b), a.w, b.w, st);
-            node = S.bin_root;
-            sp = 0;
+            stack_init(S, w);
         }
         if (__ballot_sync(0xffffffffu, ray >= 0) == 0) break;
-#pragma unroll 1
-        for (int it = 0; it < kTraceInner; ++it) {
-            if (ray >= 0 && node != kWalkDone && ++st.steps > cap) {  // corrupt data, or a test's limit
-                report(S.status, -4);
-                node = kWalkDone;
-            } else if (ray >= 0 && node != kWalkDone) {
-                if (node >= 0) {
-                    const float4* q = S.bin + 4 * (int64_t)node;
-                    const float4 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2), a3 = __ldg(q + 3);
-                    float tl, tr;
-                    const bool hl = box_entry(st, f3(a0), f3(a1), tl);
-                    const bool hr = box_entry(st, f3(a2), f3(a3), tr);
-                    const int32_t rl = __float_as_int(a0.w), rr = __float_as_int(a1.w);
-                    if (hl && hr) {
-                        const bool lnear = tl <= tr;
-                        if (sp < kStackDepth) {
-                            stk_node[sp] = lnear ? rr : rl;
-                            stk_t[sp] = lnear ? tr : tl;
-                            ++sp;
-                            node = lnear ? rl : rr;
-                        } else {  // deeper than the entry point allows: end the walk, report
-                            report(S.status, -4);
-                            node = kWalkDone;
-                        }
-                    } else if (hl) {
-                        node = rl;
-                    } else if (hr) {
-                        node = rr;
-                    } else {
-                        node = pop();
-                    }
-                } else {
-                    trav_leaf(S, st, (~node) >> 3, (~node) & 7);
-                    node = pop();
-                }
-            }
-            if (__ballot_sync(0xffffffffu, ray >= 0 && node != kWalkDone) == 0) break;
-        }
-        const bool fin = ray >= 0 && node == kWalkDone;
+        stack_steps(S, st, w, ray >= 0, cap);
+        const bool fin = ray >= 0 && w.node == kWalkDone;
         bool flag = false;
         if (fin) {
             float u = 0.0f, v = 0.0f;

@@ -123,6 +123,74 @@ __device__ __forceinline__ void trav_steps(const DevScene& S, Trav& st, int32_t&
     }
 }
 
+// Stack-based near-first walk of the child-pair layout (the comparison traversal of Fig. 4):
+// one 64-byte fetch brings both children's boxes, the nearer hit child is visited next and the
+// other pushed with its entry distance, and popped entries farther than the best hit so far are
+// skipped. node: internal index >= 0, ~(leaf word) < 0, or kWalkDone when the walk is over.
+constexpr int kStackDepth = 64;           // callers require tree depth < kStackDepth
+constexpr int32_t kWalkDone = INT32_MIN;  // never a node or leaf reference
+
+struct StackWalk {
+    int32_t node, sp;
+    int32_t stk_node[kStackDepth];
+    float stk_t[kStackDepth];
+};
+
+__device__ __forceinline__ void stack_init(const DevScene& S, StackWalk& w) {
+    w.node = S.bin_root;
+    w.sp = 0;
+}
+
+__device__ __forceinline__ int32_t stack_pop(const Trav& st, StackWalk& w) {
+    while (w.sp > 0) {
+        --w.sp;
+        if (w.stk_t[w.sp] <= st.tbest) return w.stk_node[w.sp];  // ties may still hold a smaller index
+    }
+    return kWalkDone;
+}
+
+// Up to kTraceInner steps of the active lanes' stack walks (leaves are tested when reached).
+__device__ __forceinline__ void stack_steps(const DevScene& S, Trav& st, StackWalk& w, bool active, int32_t cap) {
+#pragma unroll 1
+    for (int it = 0; it < kTraceInner; ++it) {
+        if (active && w.node != kWalkDone && ++st.steps > cap) {  // corrupt data, or a test's limit
+            report(S.status, -4);
+            w.node = kWalkDone;
+        } else if (active && w.node != kWalkDone) {
+            if (w.node >= 0) {
+                const float4* q = S.bin + 4 * (int64_t)w.node;
+                const float4 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2), a3 = __ldg(q + 3);
+                float tl, tr;
+                const bool hl = box_entry(st, f3(a0), f3(a1), tl);
+                const bool hr = box_entry(st, f3(a2), f3(a3), tr);
+                const int32_t rl = __float_as_int(a0.w), rr = __float_as_int(a1.w);
+                if (hl && hr) {
+                    const bool lnear = tl <= tr;
+                    if (w.sp < kStackDepth) {
+                        w.stk_node[w.sp] = lnear ? rr : rl;
+                        w.stk_t[w.sp] = lnear ? tr : tl;
+                        ++w.sp;
+                        w.node = lnear ? rl : rr;
+                    } else {  // deeper than callers allow: end the walk, report
+                        report(S.status, -4);
+                        w.node = kWalkDone;
+                    }
+                } else if (hl) {
+                    w.node = rl;
+                } else if (hr) {
+                    w.node = rr;
+                } else {
+                    w.node = stack_pop(st, w);
+                }
+            } else {
+                trav_leaf(S, st, (~w.node) >> 3, (~w.node) & 7);
+                w.node = stack_pop(st, w);
+            }
+        }
+        if (__ballot_sync(0xffffffffu, active && w.node != kWalkDone) == 0) break;
+    }
+}
+
 __device__ __forceinline__ int32_t trav_cap(const DevScene& S) {
     if (S.step_limit > 0) return S.step_limit;
     return (int32_t)min(4 * S.nnodes + 16, (int64_t)INT32_MAX);  // box tests incl. retests

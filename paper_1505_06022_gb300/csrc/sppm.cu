@@ -474,6 +474,8 @@ k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32
 // next item as soon as its path ends (WarpQueue, counter *ctr), so the long specular eye paths,
 // which start first, run beside the bulk of the photon work instead of after it. Eye entries
 // have depth <= max_eye, photon entries depth < max_photon (the host launches accordingly).
+// STACK: walk the child-pair layout with a stack (StackWalk) instead of the hit/miss links.
+template <bool STACK>
 __global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
 k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ ne_ptr, PathQ qp, DepositDev D,
         const uint32_t* __restrict__ np_ptr, uint32_t* __restrict__ ctr) {
@@ -488,6 +490,9 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
     int32_t i = -1, pend = -1, id = 0, depth = 0;
     uint32_t ndep = 0;
     bool eye = false;
+    StackWalk sw;
+    sw.node = kWalkDone;
+    sw.sp = 0;
     float3 w = make_float3(0.0f, 0.0f, 0.0f);  // eye: throughput; photon: flux
     Rng rng;
     while (true) {
@@ -505,10 +510,15 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
             depth = eye ? meta : (meta & 0xff);
             ndep = eye ? 0u : (uint32_t)(meta >> 8);
             trav_init(S, f3(a), f3(c), eye ? a.w : P.eps, __int_as_float(0x7f800000), st);
+            if (STACK) stack_init(S, sw);
         }
         if (__ballot_sync(0xffffffffu, i >= 0) == 0) break;
-        trav_steps(S, st, pend, i >= 0, cap);
-        if (i >= 0 && st.node < 0 && pend < 0) {
+        if (STACK)
+            stack_steps(S, st, sw, i >= 0, cap);
+        else
+            trav_steps(S, st, pend, i >= 0, cap);
+        const bool walked = STACK ? sw.node == kWalkDone : (st.node < 0 && pend < 0);
+        if (i >= 0 && walked) {
             const Hit h = walk_hit(S, st);
             float3 o = st.o, d = st.d;
             bool more = false;
@@ -522,10 +532,12 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
                 }
                 if (!more) D.pcount[id] = ndep;
             }
-            if (more)
+            if (more) {
                 trav_init(S, o, d, P.eps, __int_as_float(0x7f800000), st);
-            else
+                if (STACK) stack_init(S, sw);
+            } else {
                 i = -1;
+            }
         }
     }
 }
@@ -1066,6 +1078,7 @@ struct gsp_sppm {
     PathQ q[2]{};   // photon wavefront queues (np entries; full paths only)
     PathQ qe[2]{};  // eye wavefront queues (npix entries)
     int32_t gather_lanes = 8;  // lanes per hit point in the exact gather
+    int32_t traversal = GSP_TRAVERSAL_MTBVH;  // of the path kernel
     int64_t qcap = 0;
     int32_t eye_steps = 0;      // eye wavefront steps before the persistent path kernel
     int32_t photon_steps = 0;   // photon wavefront steps before the persistent path kernel
@@ -1354,17 +1367,20 @@ static void launch_gather_exact(int lanes, const GatherDev& G, const PassDev& P,
 }
 
 // Grid of k_paths: resident blocks on every SM, but no more warps than items.
-static int path_grid(int64_t items, int device) {
-    static int per_sm[64] = {0};
+static int path_grid(int64_t items, int device, bool stack) {
+    static int per_sm[2][64] = {{0}};
     static int sms[64] = {0};
     if (device < 0 || device >= 64) device = 0;
-    if (!per_sm[device]) {
+    if (!per_sm[stack][device]) {
         int b = 0;
         cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths, kTraceThreads, 0);
-        per_sm[device] = std::max(1, b);
+        if (stack)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<true>, kTraceThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<false>, kTraceThreads, 0);
+        per_sm[stack][device] = std::max(1, b);
     }
-    const int64_t full = (int64_t)std::max(1, sms[device]) * per_sm[device];
+    const int64_t full = (int64_t)std::max(1, sms[device]) * per_sm[stack][device];
     const int64_t need = (items + kTraceThreads - 1) / kTraceThreads;
     return (int)std::max<int64_t>(1, std::min(full, need));
 }
@@ -1429,9 +1445,16 @@ static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, co
     if (eye_left || ph_left) {
         const int64_t items = (eye_left ? r->npix : 0) + (ph_left ? r->np : 0);
         const DevScene S = gsp_dev_scene(r->scene);
-        k_paths<<<path_grid(items, r->scene->ctx->device), kTraceThreads, 0, st>>>(
-            S, P, r->qe[be & 1], O, eye_left ? r->counters + 4 + be % 3 : nullptr, r->q[ph_left ? bp & 1 : 0], D,
-            ph_left ? r->counters + 8 + bp % 3 : nullptr, r->counters + 12);
+        const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
+        const unsigned grid = (unsigned)path_grid(items, r->scene->ctx->device, stack);
+        const uint32_t* ne = eye_left ? r->counters + 4 + be % 3 : nullptr;
+        const uint32_t* npp = ph_left ? r->counters + 8 + bp % 3 : nullptr;
+        if (stack)
+            k_paths<true><<<grid, kTraceThreads, 0, st>>>(S, P, r->qe[be & 1], O, ne, r->q[ph_left ? bp & 1 : 0], D,
+                                                          npp, r->counters + 12);
+        else
+            k_paths<false><<<grid, kTraceThreads, 0, st>>>(S, P, r->qe[be & 1], O, ne, r->q[ph_left ? bp & 1 : 0], D,
+                                                           npp, r->counters + 12);
     }
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
@@ -1574,15 +1597,18 @@ static gsp_status passes_overlapped(gsp_sppm* r, int32_t npasses, cudaStream_t s
 }
 
 gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, float refine_factor,
-                         int32_t gather_lanes) {
+                         int32_t gather_lanes, int32_t traversal) {
     if (!r || eye_steps < 0 || eye_steps > 64 || photon_steps < 0 || photon_steps > kSlotsPerPath ||
         !(refine_factor >= 0.0f) ||
-        (gather_lanes != 0 && gather_lanes != 1 && gather_lanes != 4 && gather_lanes != 8 && gather_lanes != 16))
+        (gather_lanes != 0 && gather_lanes != 1 && gather_lanes != 4 && gather_lanes != 8 && gather_lanes != 16) ||
+        (traversal != 0 && traversal != GSP_TRAVERSAL_MTBVH && traversal != GSP_TRAVERSAL_STACK) ||
+        (traversal == GSP_TRAVERSAL_STACK && r->scene->bvh.depth >= kStackDepth))
         return GSP_ERR_INVALID_ARG;
     r->eye_steps = eye_steps;
     r->photon_steps = photon_steps;
     r->refine_factor = refine_factor;
     if (gather_lanes) r->gather_lanes = gather_lanes;
+    if (traversal) r->traversal = traversal;
     return GSP_OK;
 }
 
@@ -1847,8 +1873,10 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
     cudaError_t ce = cudaEventCreate(&a);
     if (ce == cudaSuccess) ce = cudaEventCreate(&z);
     gsp_status e = GSP_OK;
-    struct Cand { int32_t es, ps, gl; };
-    const Cand start{b->rs[0]->eye_steps, b->rs[0]->photon_steps, b->rs[0]->gather_lanes};
+    struct Cand { int32_t es, ps, gl, tr; };
+    const Cand start{b->rs[0]->eye_steps, b->rs[0]->photon_steps, b->rs[0]->gather_lanes, b->rs[0]->traversal};
+    bool stack_ok = true;
+    for (gsp_sppm* r : b->rs) stack_ok = stack_ok && r->scene->bvh.depth < kStackDepth;
     Cand pick = start;
     float best = INFINITY, first = INFINITY;
     int32_t ncand = 0;
@@ -1857,6 +1885,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
             r->eye_steps = c.es;
             r->photon_steps = c.ps;
             r->gather_lanes = c.gl;
+            r->traversal = c.tr;
         }
         if (b->exec) cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -1889,10 +1918,13 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
     const bool full = b->rs[0]->P.photon_mode == GSP_FULL_PATH;
     for (int32_t es : {0, 1})
         for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2} : std::vector<int32_t>{0})
-            if (es != start.es || ps != start.ps) trial({es, ps, start.gl});
+            if (es != start.es || ps != start.ps) trial({es, ps, start.gl, start.tr});
     const Cand steps = pick;
     for (int32_t gl : {4, 8, 16})
-        if (gl != start.gl) trial({steps.es, steps.ps, gl});
+        if (gl != start.gl) trial({steps.es, steps.ps, gl, start.tr});
+    const Cand lanes = pick;
+    for (int32_t tr : {GSP_TRAVERSAL_MTBVH, GSP_TRAVERSAL_STACK})
+        if (tr != start.tr && (tr != GSP_TRAVERSAL_STACK || stack_ok)) trial({lanes.es, lanes.ps, lanes.gl, tr});
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (a) cudaEventDestroy(a);
     if (z) cudaEventDestroy(z);
@@ -1910,6 +1942,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
         out->first_ms_per_pass = first;
         out->candidates = ncand;
         out->gather_lanes = pick.gl;
+        out->traversal = pick.tr;
     }
     return GSP_OK;
 }
@@ -1927,10 +1960,10 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreate(&a);
     if (ce == cudaSuccess) ce = cudaEventCreate(&z);
-    struct Cand { int32_t es, ps; float cell; int32_t gl; };
+    struct Cand { int32_t es, ps; float cell; int32_t gl, tr; };
     int32_t ncand = 0;
     float best = INFINITY, first = INFINITY;
-    Cand pick{r->eye_steps, r->photon_steps, r->P.cell_h, r->gather_lanes};
+    Cand pick{r->eye_steps, r->photon_steps, r->P.cell_h, r->gather_lanes, r->traversal};
     // Each candidate starts from a fresh state (radii r0), runs one untimed pass and times
     // trial_passes more, so every candidate sees the same radii.
     auto trial = [&](const Cand& c) {
@@ -1939,6 +1972,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         t->photon_steps = c.ps;
         t->inv_h = 1.0f / c.cell;
         t->gather_lanes = c.gl;
+        t->traversal = c.tr;
         ce = reset_state(t, st);
         if (ce != cudaSuccess) return;
         e = sppm_one_pass(t, st);
@@ -1958,20 +1992,25 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     };
     // stage 1: wavefront steps at the renderer's cell edge; stage 2: the cell edge (exact mode)
     const bool full = r->P.photon_mode == GSP_FULL_PATH;
-    const int32_t gl0 = r->gather_lanes;
-    trial({r->eye_steps, r->photon_steps, r->P.cell_h, gl0});  // the current settings first
+    const int32_t gl0 = r->gather_lanes, tr0 = r->traversal;
+    trial({r->eye_steps, r->photon_steps, r->P.cell_h, gl0, tr0});  // the current settings first
     for (int32_t es : {0, 1, 2})
         for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2, 4} : std::vector<int32_t>{0})
-            if (es != r->eye_steps || ps != r->photon_steps) trial({es, ps, r->P.cell_h, gl0});
+            if (es != r->eye_steps || ps != r->photon_steps) trial({es, ps, r->P.cell_h, gl0, tr0});
     if (r->P.hash_mode == GSP_EXACT) {
         // stage 2: the cell edge; stage 3: lanes per hit point in the gather
         const Cand steps = pick;
         for (float c : {2.0f, 1.5f, 1.0f, 0.75f, 0.5f})
-            if (c * r->P.r0 != r->P.cell_h) trial({steps.es, steps.ps, c * r->P.r0, gl0});
+            if (c * r->P.r0 != r->P.cell_h) trial({steps.es, steps.ps, c * r->P.r0, gl0, tr0});
         const Cand cell = pick;
         for (int32_t gl : {1, 4, 8, 16})
-            if (gl != gl0) trial({cell.es, cell.ps, cell.cell, gl});
+            if (gl != gl0) trial({cell.es, cell.ps, cell.cell, gl, tr0});
     }
+    // last stage: the path kernel's traversal
+    const Cand lanes = pick;
+    for (int32_t tr : {GSP_TRAVERSAL_MTBVH, GSP_TRAVERSAL_STACK})
+        if (tr != tr0 && (tr != GSP_TRAVERSAL_STACK || r->scene->bvh.depth < kStackDepth))
+            trial({lanes.es, lanes.ps, lanes.cell, lanes.gl, tr});
     if (st) cudaStreamDestroy(st);
     if (a) cudaEventDestroy(a);
     if (z) cudaEventDestroy(z);
@@ -1984,6 +2023,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     r->eye_steps = pick.es;
     r->photon_steps = pick.ps;
     r->gather_lanes = pick.gl;
+    r->traversal = pick.tr;
     r->inv_h = 1.0f / pick.cell;
     r->P.cell_h = pick.cell;
     if (out) {
@@ -1994,6 +2034,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         out->first_ms_per_pass = first;
         out->candidates = ncand;
         out->gather_lanes = pick.gl;
+        out->traversal = pick.tr;
     }
     return GSP_OK;
 }

@@ -28,6 +28,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "out of memory", -3: "CUDA runtim
           -6: "scene has no BVH", -7: "call order violated", -8: "checkpoint I/O failed",
           -9: "device buffer overflow"}
 FULL_PATH, REGEN = 0, 1
+TRAVERSAL_MTBVH, TRAVERSAL_STACK = 1, 2
 EXACT, STOCHASTIC = 0, 1
 
 # exported symbols of include/gsp.h
@@ -70,7 +71,7 @@ class BvhStats(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("eye_steps", C.c_int32), ("photon_steps", C.c_int32), ("cell_h", C.c_float),
                 ("ms_per_pass", C.c_float), ("first_ms_per_pass", C.c_float), ("candidates", C.c_int32),
-                ("gather_lanes", C.c_int32)]
+                ("gather_lanes", C.c_int32), ("traversal", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -125,7 +126,7 @@ def lib():
             L.gsp_sppm_sync.argtypes = [P]
             L.gsp_hash_grid_build.argtypes = [P, P, I64, C.c_float, I64, P, P, P]
             L.gsp_hash_grid_build_static.argtypes = [P, I64, C.c_float, I64, P, P, P]
-            L.gsp_sppm_tune.argtypes = [P, I32, I32, C.c_float, I32]
+            L.gsp_sppm_tune.argtypes = [P, I32, I32, C.c_float, I32, I32]
             L.gsp_sppm_enable_grad.argtypes = [P, I32]
             L.gsp_render_grad.argtypes = [P, P, P, P, P]
             L.gsp_scene_set_materials.argtypes = [P, P, I32]
@@ -323,8 +324,8 @@ def gsp_sppm_create(scene, params: dict):
     return h
 
 
-def gsp_sppm_tune(r, eye_steps=0, photon_steps=0, refine_factor=0.0, gather_lanes=0):
-    _check("gsp_sppm_tune", lib().gsp_sppm_tune(r, eye_steps, photon_steps, refine_factor, gather_lanes))
+def gsp_sppm_tune(r, eye_steps=0, photon_steps=0, refine_factor=0.0, gather_lanes=0, traversal=0):
+    _check("gsp_sppm_tune", lib().gsp_sppm_tune(r, eye_steps, photon_steps, refine_factor, gather_lanes, traversal))
 
 
 def gsp_sppm_enable_grad(r, max_passes):
@@ -498,8 +499,9 @@ class Renderer:
     def run(self, npasses=1, stream=None):
         gsp_sppm_pass(self.h, npasses, stream)
 
-    def tune(self, eye_steps=0, photon_steps=0, refine_factor=0.0, gather_lanes=0):
-        gsp_sppm_tune(self.h, eye_steps, photon_steps, refine_factor, gather_lanes)
+    def tune(self, eye_steps=0, photon_steps=0, refine_factor=0.0, gather_lanes=0, traversal=0):
+        """traversal: 0 keep, TRAVERSAL_MTBVH or TRAVERSAL_STACK (path kernel)."""
+        gsp_sppm_tune(self.h, eye_steps, photon_steps, refine_factor, gather_lanes, traversal)
 
     def autotune(self, trial_passes=2) -> dict:
         return gsp_sppm_autotune(self.h, trial_passes)

@@ -58,7 +58,8 @@ def test_batch_autotune_keeps_the_estimate(ctx):
     b = gsp.Batch(rs)
     res = b.autotune(trial_passes=1)
     assert res["eye_steps"] in (0, 1) and res["photon_steps"] in (0, 1, 2) and res["gather_lanes"] in (4, 8, 16)
-    assert 6 <= res["candidates"] <= 9 and res["ms_per_pass"] <= res["first_ms_per_pass"]
+    assert 6 <= res["candidates"] <= 10 and res["ms_per_pass"] <= res["first_ms_per_pass"]
+    assert res["traversal"] in (1, 2)
     b.run(3)
     torch.cuda.synchronize()
     for r, (img, n) in zip(rs, solo):
@@ -90,8 +91,8 @@ def test_autotune_keeps_the_estimate(ctx):
     a = ref.image().cpu().numpy()
     r = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
     res = r.autotune(trial_passes=1)
-    assert 12 <= res["candidates"] <= 20 and res["ms_per_pass"] <= res["first_ms_per_pass"]
-    assert res["gather_lanes"] in (1, 4, 8, 16)
+    assert 12 <= res["candidates"] <= 21 and res["ms_per_pass"] <= res["first_ms_per_pass"]
+    assert res["gather_lanes"] in (1, 4, 8, 16) and res["traversal"] in (1, 2)
     assert res["cell_h"] >= np.float32(0.5 * kw["r0_frac"] * sc.extent()) * 0.999
     r.run(3)
     b = r.image().cpu().numpy()

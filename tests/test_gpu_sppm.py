@@ -103,21 +103,23 @@ def test_overlapped_passes_equal_single_passes(ctx, photon_mode):
 
 
 def test_execution_settings_keep_the_image(ctx):
-    """Wavefront steps before the persistent path kernel give bit-identical images; the lanes per
-    hit point of the exact gather change only the summation order (identical counts)."""
+    """Wavefront steps before the persistent path kernel and its traversal (hit/miss links or
+    stack) give bit-identical images; the lanes per hit point of the exact gather change only
+    the summation order (identical counts)."""
     sc = I.full_scene(seed=9, width=80, height=64, plane_quads=40, sphere_n=8)
     s = gsp.Scene(ctx, sc)
     params = gsp.sppm_params(sc, 30000, seed=6, r0_frac=0.01)
     out = {}
-    for es, ps, lanes in [(1, 1, 8), (0, 0, 8), (2, 4, 8), (3, 2, 8), (0, 0, 1), (1, 1, 4), (1, 1, 16)]:
+    for es, ps, lanes, tr in [(1, 1, 8, 1), (0, 0, 8, 1), (2, 4, 8, 1), (3, 2, 8, 1), (0, 0, 8, 2), (1, 2, 8, 2),
+                              (0, 0, 1, 1), (1, 1, 4, 1), (1, 1, 16, 2)]:
         r = gsp.Renderer(s, params)
-        r.tune(es, ps, 0.0, lanes)
+        r.tune(es, ps, 0.0, lanes, tr)
         r.run(3)
         st = r.state()
-        out[(es, ps, lanes)] = (r.image().cpu().numpy(), st["N"].cpu().numpy())
+        out[(es, ps, lanes, tr)] = (r.image().cpu().numpy(), st["N"].cpu().numpy())
         r.close()
-    ref_img, ref_n = out[(1, 1, 8)]
-    for (es, ps, lanes), (img, n) in out.items():
+    ref_img, ref_n = out[(1, 1, 8, 1)]
+    for (es, ps, lanes, tr), (img, n) in out.items():
         assert np.array_equal(n, ref_n)
         if lanes == 8:
             assert np.array_equal(img, ref_img), (es, ps)
