@@ -372,7 +372,10 @@ def bench_sppm(args, ctx, dev, stream, pg):
     ms_tuned = timed_passes(tuned, k, stream)
     img_tuned = tuned.image(stream)
     same = bool(torch.equal(img, img_tuned))
+    npix, nphot = 512 * 512, 1 << 20
     out = {"passes_per_s": round(1000.0 / ms, 2), "ms_per_pass": round(ms, 3), "passes_timed": k,
+           # the paper's readout is complete paths per second (eye paths + photon paths)
+           "paths_per_s": round((npix + nphot) * 1000.0 / ms, 0),
            "autotuned": {"passes_per_s": round(1000.0 / ms_tuned, 2), "ms_per_pass": round(ms_tuned, 3),
                          "choice": {kk: (round(v, 5) if isinstance(v, float) else v) for kk, v in choice.items()},
                          "tuning_s": round(tune_s, 2)},

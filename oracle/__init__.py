@@ -24,7 +24,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gsp_oracle.cpp")
-_OUT = os.path.join(_HERE, "_build", "libgsp_oracle.so")
+# GSP_ORACLE_SANITIZE=1: a separate build with AddressSanitizer and UndefinedBehaviorSanitizer
+# (the host process must preload their runtimes; tests/test_sanitizers.py does that).
+_SANITIZE = os.environ.get("GSP_ORACLE_SANITIZE") == "1"
+_OUT = os.path.join(_HERE, "_build", "libgsp_oracle_asan.so" if _SANITIZE else "libgsp_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -59,6 +62,8 @@ def build(force: bool = False) -> str:
         tmp = _OUT + f".{os.getpid()}.tmp"
         cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
                "-fno-fast-math", "-pthread", _SRC, "-o", tmp]
+        if _SANITIZE:
+            cmd[3:3] = ["-fsanitize=address,undefined", "-fno-sanitize-recover=undefined", "-fno-omit-frame-pointer"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _OUT)
         return _OUT

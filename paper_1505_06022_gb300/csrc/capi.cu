@@ -174,6 +174,7 @@ int gsp_trace_grid(int device) {
 // flagged hits. ctr (2 u64) and rlist (n entries) belong to this call's stream.
 static void launch_trace(const gsp_scene* s, const float4* rays, int64_t n, int32_t* tri, float* t, float2* uv,
                          unsigned long long* ctr, int2* rlist, cudaStream_t st) {
+    NvtxRange nvtx("gsp: closest hit");
     const gspd::DevScene S = gsp_dev_scene(s);
     gspd::k_zero_u64x2<<<1, 1, 0, st>>>(ctr);
     const int grid = gsp_trace_grid(s->ctx->device);
@@ -453,6 +454,7 @@ gsp_status gsp_build_bvh(gsp_scene* s, const gsp_bvh_params* params, gsp_bvh_sta
         p.leaf_threshold > p.max_leaf || (p.link_sets != 1 && p.link_sets != 6))
         return GSP_ERR_INVALID_ARG;
     HostBVH bvh;
+    NvtxRange nvtx("gsp: host SAH build + threading");
     std::string err = bvh_build_host(s->verts.data(), s->nv, s->tris.data(), s->nt, p, bvh);
     if (!err.empty()) {
         gsp_set_last_error(err);

@@ -1,6 +1,7 @@
 // gsp_internal.h -- host-side structures shared by the library's translation units.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -89,6 +90,14 @@ struct gsp_scene {
 // Installs a BVH built elsewhere (host copies + device arrays the scene takes ownership of),
 // replacing the scene's current one.
 void gsp_scene_adopt_bvh(gsp_scene* s, HostBVH&& bvh, float4* d_nodes, float4* d_tris, float4* d_bin);
+
+// NVTX range around a host-side stage (header-only NVTX3: a no-op unless a profiler attaches).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define GSP_CUDA_TRY(expr)                                   \
     do {                                                     \

@@ -253,6 +253,7 @@ extern "C" gsp_status gsp_build_bvh_device(gsp_scene* s, int32_t link_sets, int3
     if (nt < 1 || nt > (int64_t(1) << 28)) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
     (void)cudaGetLastError();
+    NvtxRange nvtx("gsp: device LBVH build + threading");
     const int n = (int)nt;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t v = 0; v < s->nv; ++v)  // bounds of all vertices (Morton quantisation range)

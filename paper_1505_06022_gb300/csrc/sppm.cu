@@ -1436,6 +1436,7 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
 // Eye and photon passes of one pass (Sec. 2): both fronts, then one persistent kernel finishes
 // the eye and photon paths still going.
 static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, const DepositDev& D, cudaStream_t st) {
+    NvtxRange nvtx("gsp: eye + photon paths");
     int be = 0, bp = -1;
     gsp_status e = eye_front(r, P, O, st, be);
     if (e == GSP_OK) e = photon_front(r, P, D, st, bp);
@@ -1490,6 +1491,7 @@ static gsp_status trace_half(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
 
 // Gather half of a pass: deposit (exact mode) and the fused range query + progressive update.
 static gsp_status gather_half(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
+    NvtxRange nvtx("gsp: deposit + gather");
     GatherDev G{};
     G.hx = r->hx;
     G.hn = r->hn;
@@ -1695,6 +1697,7 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
         const int j = (int)(i & 1);
         use_buf(r, j);
         // replay pass i from its PRNG counters: the same hit points, photons and radii
+        NvtxRange nvtx("gsp: adjoint pass");
         const PassDev P = pass_params(r, i);
         const EyeOut O{r->hx, r->hn, r->hf, r->hd, r->hw};
         const DepositDev D{r->slots, r->pcount, nullptr, nullptr, 0, r->smat};
