@@ -549,37 +549,64 @@ struct RegenDev {
     unsigned long long* __restrict__ started;
 };
 
-__global__ void __launch_bounds__(128)
-k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool start = false;
-    if (j < P.np) {
-        Rng rng = rng_seed(P.seed, P.scene_id, 1u, pass_index(P), (uint64_t)j);
-        float4 a = R.ro[j], b = R.rd[j], c = R.rphi[j];
-        float3 o = f3(a), d = f3(b), phi = f3(c);
-        int32_t depth = __float_as_int(a.w);
-        bool alive = __float_as_int(b.w) != 0;
-        if (!alive) {
-            emit_photon(E, rng, o, d, phi);
-            depth = 0;
-            alive = true;
-            start = true;
+// One bounce per thread and pass (Sec. 3.3): thread j continues its stored path, or starts a new
+// one when the stored path has ended (N_e counts the starts), traces exactly one ray, deposits at
+// a diffuse hit and stores the path state for the next pass. Persistent, with per-lane refill
+// over the threads (counter *ctr) as the path kernel; STACK as in k_paths.
+template <bool STACK>
+__global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
+k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R, uint32_t* __restrict__ ctr) {
+    const int32_t cap = trav_cap(S);
+    WarpQueue wq;
+    wq.init((int32_t)P.np);
+    Trav st;
+    st.node = -1;
+    st.slot = -1;
+    StackWalk sw;
+    sw.node = kWalkDone;
+    sw.sp = 0;
+    int32_t j = -1, pend = -1, depth = 0;
+    uint32_t starts = 0;
+    float3 phi = make_float3(0.0f, 0.0f, 0.0f);
+    Rng rng;
+    while (true) {
+        const int32_t got = wq.take(j < 0, ctr);
+        if (got >= 0) {
+            j = got;
+            rng = rng_seed(P.seed, P.scene_id, 1u, pass_index(P), (uint64_t)j);
+            const float4 a = R.ro[j], b = R.rd[j], c = R.rphi[j];
+            float3 o = f3(a), d = f3(b);
+            phi = f3(c);
+            depth = __float_as_int(a.w);
+            if (__float_as_int(b.w) == 0) {  // the stored path has ended: start a new one
+                emit_photon(E, rng, o, d, phi);
+                depth = 0;
+                ++starts;
+            }
+            trav_init(S, o, d, P.eps, __int_as_float(0x7f800000), st);
+            if (STACK) stack_init(S, sw);
         }
-        uint32_t ndep = 0;
-        const Hit h = traverse<true>(S, o, d, P.eps, __int_as_float(0x7f800000));
-        if (h.id < 0) {
-            alive = false;
-        } else if (!photon_bounce(S, P, D, rng, h, o, d, phi, (uint32_t)j, (uint32_t)j, ndep)) {
-            alive = false;
-        } else if (++depth >= P.max_photon) {
-            alive = false;
+        if (__ballot_sync(0xffffffffu, j >= 0) == 0) break;
+        if (STACK)
+            stack_steps(S, st, sw, j >= 0, cap);
+        else
+            trav_steps(S, st, pend, j >= 0, cap);
+        const bool walked = STACK ? sw.node == kWalkDone : (st.node < 0 && pend < 0);
+        if (j >= 0 && walked) {
+            const Hit h = walk_hit(S, st);
+            float3 o = st.o, d = st.d;
+            uint32_t ndep = 0;
+            bool alive = h.id >= 0 && photon_bounce(S, P, D, rng, h, o, d, phi, (uint32_t)j, (uint32_t)j, ndep) &&
+                         ++depth < P.max_photon;
+            D.pcount[j] = ndep;
+            R.ro[j] = make_float4(o.x, o.y, o.z, __int_as_float(depth));
+            R.rd[j] = make_float4(d.x, d.y, d.z, __int_as_float(alive ? 1 : 0));
+            R.rphi[j] = make_float4(phi.x, phi.y, phi.z, 0.0f);
+            j = -1;
         }
-        D.pcount[j] = ndep;
-        R.ro[j] = make_float4(o.x, o.y, o.z, __int_as_float(depth));
-        R.rd[j] = make_float4(d.x, d.y, d.z, __int_as_float(alive ? 1 : 0));
-        R.rphi[j] = make_float4(phi.x, phi.y, phi.z, 0.0f);
     }
-    const unsigned int starts = __popc(__ballot_sync(0xffffffffu, start));
+    // paths started by this warp
+    for (int off = 16; off > 0; off >>= 1) starts += __shfl_xor_sync(0xffffffffu, starts, off);
     if ((threadIdx.x & 31) == 0 && starts) atomicAdd(R.started, (unsigned long long)starts);
 }
 
@@ -1352,8 +1379,8 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
 }
 
 // Renderer counters (uint32): [0] deposits of the pass, [4..6] eye queue lengths, [8..10] photon
-// queue lengths (three each, used in rotation), [12] work counter of k_paths, [7] pass index of a
-// replayed graph.
+// queue lengths (three each, used in rotation), [12] work counter of k_paths, [13] work counter of
+// k_photon_regen, [7] pass index of a replayed graph.
 static unsigned shade_blocks(int64_t n) { return (unsigned)std::min<int64_t>(blocks(n, 256), 4 * 152); }
 
 // Exact gather with `lanes` lanes per hit point (1, 4, 8 or 16).
@@ -1428,7 +1455,13 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
         }
     } else {
         RegenDev R{r->ro, r->rd, r->rphi, r->started};
-        k_photon_regen<<<blocks(r->np, 128), 128, 0, st>>>(S, E, P, D, R);
+        GSP_CUDA_TRY(cudaMemsetAsync(r->counters + 13, 0, sizeof(uint32_t), st));
+        const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
+        const unsigned grid = (unsigned)path_grid(r->np, r->scene->ctx->device, stack);
+        if (stack)
+            k_photon_regen<true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13);
+        else
+            k_photon_regen<false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13);
     }
     return GSP_OK;
 }
