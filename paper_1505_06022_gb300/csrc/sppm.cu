@@ -170,7 +170,7 @@ struct PathQ {
 };
 
 // A wavefront hit given as a leaf-ordered triangle slot: t from the triangle's plane in
-// double-float arithmetic (as for per-thread paths); returns the upload-order index.
+// double-float arithmetic (as in the persistent path kernel); returns the upload-order index.
 __device__ __forceinline__ int32_t slot_refine(const DevScene& S, float3 o, float3 d, Hit& h) {
     const int32_t id = __float_as_int(__ldg(S.tris + 3 * (int64_t)h.id).w);
     refine_plane(S.tris, S.shade, S.nlo, h.id, id, o, d, h.t);
@@ -1381,7 +1381,21 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
 // Renderer counters (uint32): [0] deposits of the pass, [4..6] eye queue lengths, [8..10] photon
 // queue lengths (three each, used in rotation), [12] work counter of k_paths, [13] work counter of
 // k_photon_regen, [7] pass index of a replayed graph.
-static unsigned shade_blocks(int64_t n) { return (unsigned)std::min<int64_t>(blocks(n, 256), 4 * 152); }
+static int sm_count(int device) {
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) device = 0;
+    if (!cached[device]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+        cached[device] = std::max(1, v);
+    }
+    return cached[device];
+}
+
+// Grid-stride kernels over a queue whose length is on the device: 4 blocks of 256 per SM.
+static unsigned shade_blocks(int64_t n, int device) {
+    return (unsigned)std::min<int64_t>(blocks(n, 256), 4 * (int64_t)sm_count(device));
+}
 
 // Exact gather with `lanes` lanes per hit point (1, 4, 8 or 16).
 static void launch_gather_exact(int lanes, const GatherDev& G, const PassDev& P, int64_t npix, cudaStream_t st) {
@@ -1425,7 +1439,7 @@ static gsp_status eye_front(gsp_sppm* r, const PassDev& P, const EyeOut& O, cuda
     for (b = 0; b < r->eye_steps && b <= r->P.max_eye_depth; ++b) {
         const PathQ& cur = r->qe[b & 1];
         GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->npix, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
-        k_eye_shade<<<shade_blocks(r->npix), 256, 0, st>>>(S, P, cur, r->qe[(b + 1) & 1], O, qn, b, tctr);
+        k_eye_shade<<<shade_blocks(r->npix, s->ctx->device), 256, 0, st>>>(S, P, cur, r->qe[(b + 1) & 1], O, qn, b, tctr);
     }
     return GSP_OK;
 }
@@ -1451,7 +1465,7 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
         for (b = 0; b < r->photon_steps && b < r->P.max_photon_depth; ++b) {
             const PathQ& cur = r->q[b & 1];
             GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->np, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
-            k_photon_shade<<<shade_blocks(r->np), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
+            k_photon_shade<<<shade_blocks(r->np, s->ctx->device), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
         }
     } else {
         RegenDev R{r->ro, r->rd, r->rphi, r->started};
@@ -1719,7 +1733,7 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
     const int32_t nmat = r->scene->nmat;
     GSP_CUDA_TRY(cudaMemsetAsync(r->gacc, 0, ((size_t)kMaxGradMats * 3 + 3) * sizeof(double), st));
     const float hp_cell = 2.0f * r->P.r0;
-    const int grid = 4 * 152;
+    const int grid = 4 * sm_count(r->scene->ctx->device);
     // Pass i + 1 is replayed on the tracing stream into the other trace buffers while the adjoint
     // kernels of pass i run on the caller's stream (the same double buffering as gsp_sppm_pass).
     gsp_status e = ensure_second_buffer(r);

@@ -32,9 +32,11 @@ def case():
     return sc, g, ga, gl
 
 
-def gpu_grad(ctx, sc, g):
+def gpu_grad(ctx, sc, g, **tune):
     s = gsp.Scene(ctx, sc)
     r = gsp.Renderer(s, gsp.sppm_params(sc, **KW))
+    if tune:
+        r.tune(**tune)
     r.enable_grad(PASSES)
     r.run(PASSES)
     before = r.image().clone()
@@ -117,3 +119,15 @@ def test_call_order_is_checked(ctx):
     with pytest.raises(gsp.GspError) as e:
         r2.run(1)  # radius history full
     assert e.value.code == -9
+
+
+def test_adjoint_does_not_depend_on_execution_settings(ctx, case):
+    """Wavefront steps and the path kernel's traversal give the same hits, hence the same
+    forward records and the same gradient up to the order of its atomic per-material sums."""
+    sc, g, _, _ = case
+    base = gpu_grad(ctx, sc, g)
+    for tune in (dict(traversal=gsp.TRAVERSAL_STACK), dict(eye_steps=1, photon_steps=2),
+                 dict(eye_steps=2, photon_steps=1, traversal=gsp.TRAVERSAL_STACK)):
+        ga, gl, _, _ = gpu_grad(ctx, sc, g, **tune)
+        np.testing.assert_allclose(ga, base[0], rtol=1e-5, atol=1e-6 * np.abs(base[0]).max())
+        np.testing.assert_allclose(gl, base[1], rtol=1e-5, atol=1e-6 * np.abs(base[1]).max())

@@ -154,11 +154,16 @@ def test_host_buffer_entry_matches_device_entry(ctx, full_size):
     t_p = torch.empty(n, dtype=torch.float32).pin_memory()
     uv_p = torch.empty((n, 2), dtype=torch.float32).pin_memory()
     gsp.gsp_trace_closest_hit_host(s.h, r_pin, tri_p, t_p, uv_p)
-    # pageable, without uv
+    # pageable, without uv, then with uv
     tri_n = np.empty(n, np.int32)
     t_n = np.empty(n, np.float32)
     gsp.gsp_trace_closest_hit_host(s.h, np.ascontiguousarray(rays), tri_n, t_n)
+    uv_n = np.empty((n, 2), np.float32)
+    tri_u = np.empty(n, np.int32)
+    t_u = np.empty(n, np.float32)
+    gsp.gsp_trace_closest_hit_host(s.h, np.ascontiguousarray(rays), tri_u, t_u, uv_n)
     ctx.sync()
+    assert np.array_equal(tri_u, want[0]) and np.array_equal(uv_n.view(np.int32), want[2].view(np.int32))
     assert np.array_equal(tri_p.numpy(), want[0]) and np.array_equal(t_p.numpy().view(np.int32), want[1].view(np.int32))
     assert np.array_equal(uv_p.numpy().view(np.int32), want[2].view(np.int32))
     assert np.array_equal(tri_n, want[0]) and np.array_equal(t_n.view(np.int32), want[1].view(np.int32))
