@@ -547,8 +547,9 @@ static gsp_status host_lanes_reserve(gsp_scene* s, int64_t cap, bool staged) {
 // transfer spreads over the traversal) and writes the hits to device buffers, which are copied
 // back while the other half is traced. Measured alternatives were slower on GB300 (4,194,304
 // rays): the traversal also writing its 4-byte results to host memory (3,390 Mrays/s against
-// 3,560 for one part), a copy of the rays before the traversal (2,640), and copy-engine
-// pipelines of 2^17-2^20-ray chunks (1,240-2,940). Other buffers: chunks through page-locked
+// 3,560 for one part), a copy of the rays before the traversal (2,640), copy-engine pipelines
+// of 2^17-2^20-ray chunks (1,240-2,940), and copying 50-100 % of the rays by copy engine while
+// the rest is traced in place (3,000-3,230). Other buffers: chunks through page-locked
 // staging buffers on three streams, the host filling and draining them while the device works
 // on other chunks.
 gsp_status gsp_trace_closest_hit_host(gsp_scene* s, const float* h_rays, int64_t n, int32_t* h_tri, float* h_t,
