@@ -577,7 +577,8 @@ def bench_batch(args, ctx, dev, stream):
            "graph_scene_passes_per_s": round(1000.0 * n / bat_ms, 1),
            "speedup": round(seq_ms / bat_ms, 3), "ms_per_batch_pass": round(bat_ms, 3), "passes_timed": k,
            "batch_autotune": {"choice": {kk: v for kk, v in choice.items()
-                                         if kk in ("eye_steps", "photon_steps", "gather_lanes", "traversal")},
+                                         if kk in ("eye_steps", "photon_steps", "gather_lanes", "traversal",
+                                                   "fused")},
                               "tuning_s": round(tune_s, 2)},
            "config": f"{n} scenes, 1e3-2e5 triangles log-uniform, image side in {{64,128,256,512}}, "
                      "262,144 photon paths/pass each, full paths + exact hash grid"}

@@ -321,6 +321,14 @@ void gsp_batch_destroy(gsp_batch* b);
 /* Runs npasses passes of every renderer of the batch on `stream`. */
 gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream);
 
+/* fused = 1: each batch pass runs the eye and photon fronts of all renderers in parallel
+ * branches, then ONE persistent launch that finishes every renderer's eye and photon paths
+ * (work items from all scenes in one queue: a warp's chunk names its renderer), then the
+ * deposits and gathers in parallel branches (default). fused = 0: a path launch per renderer
+ * inside its branch. Results are the same (bit for bit). Takes effect at the next pass (the graph
+ * is captured again). */
+gsp_status gsp_batch_tune(gsp_batch* b, int32_t fused);
+
 typedef struct {
     int32_t eye_steps, photon_steps; /* chosen wavefront steps */
     float cell_h;                    /* chosen hash cell edge (exact mode) */
@@ -329,6 +337,7 @@ typedef struct {
     int32_t candidates;              /* settings timed */
     int32_t gather_lanes;            /* chosen lanes per hit point in the exact gather (1, 4, 8, 16) */
     int32_t traversal;               /* chosen path-kernel traversal (GSP_TRAVERSAL_*) */
+    int32_t fused;                   /* batch: 1 = one fused path launch for all renderers */
 } gsp_tune_result;
 
 /* Times candidate execution settings that leave the estimate unchanged, each from a fresh state
@@ -343,8 +352,8 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
 
 /* Autotuning of a whole batch, before its first pass: times batch passes (one CUDA graph each)
  * under candidate settings applied to every renderer -- wavefront steps (eye 0-1, photon 0-2),
- * then lanes per hit point in the exact gather (4, 8, 16), then the path kernel's traversal --
- * and keeps the fastest. Each
+ * then lanes per hit point in the exact gather (4, 8, 16), then the path kernel's traversal, then
+ * the other batch form (gsp_batch_tune) with the steps searched again -- and keeps the fastest. Each
  * candidate runs one untimed and trial_passes timed passes, after which every renderer is back
  * to its initial state, so the renders that follow are those of untuned renderers (bit for bit
  * for the steps; the lanes change only a pixel's summation order). GSP_ERR_BAD_STATE if a

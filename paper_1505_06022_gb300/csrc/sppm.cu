@@ -542,6 +542,157 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// the eye and photon paths of many renderers in one persistent launch (batched passes)
+// ------------------------------------------------------------------------------------------
+// One renderer's share of a fused launch: its scene, pass, queues and outputs, where its item
+// counts live on the device, and its range of 64-item chunks in the launch's chunk sequence
+// (sized by capacity; chunks past the pass's actual counts are skipped).
+struct PathJob {
+    DevScene S;
+    PassDev P;
+    PathQ qe, qp;
+    EyeOut O;
+    DepositDev D;
+    const uint32_t* ne_ptr;  // null: no eye items
+    const uint32_t* np_ptr;  // null: no photon items
+    int32_t first_chunk, nchunks;
+};
+
+// Work distribution over the chunks of all jobs: as WarpQueue, but a chunk also names its job
+// (found by binary search over the jobs' chunk ranges), and its items are that job's local
+// item indices (eye items first, then photon items).
+struct MultiQueue {
+    int32_t total, static_end, pos, pend, job;
+    bool done;
+
+    __device__ __forceinline__ bool chunk(const PathJob* __restrict__ jobs, int32_t njobs, int32_t c) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].first_chunk <= c) lo = mid; else hi = mid - 1;
+        }
+        job = lo;
+        const PathJob& J = jobs[lo];
+        const int32_t items = (J.ne_ptr ? (int32_t)*J.ne_ptr : 0) + (J.np_ptr ? (int32_t)*J.np_ptr : 0);
+        pos = (c - J.first_chunk) * kTraceChunk;
+        pend = min(pos + kTraceChunk, items);
+        return pos < pend;
+    }
+
+    __device__ __forceinline__ void init(const PathJob* __restrict__ jobs, int32_t njobs, int32_t total_chunks) {
+        total = total_chunks;
+        const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+        static_end = (int32_t)min(warps, (int64_t)total);
+        const int32_t c = (int32_t)((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+        done = false;
+        pos = pend = 0;
+        job = 0;
+        if (c < total) chunk(jobs, njobs, c);
+    }
+
+    // Lanes with `need` set receive the next item of some job (-1 when all are exhausted); the
+    // job is `job` at the time of the return for every lane that received one in this call only
+    // if no chunk change happened after its assignment, so it is returned per lane.
+    __device__ __forceinline__ int32_t take(bool need, const PathJob* __restrict__ jobs, int32_t njobs, uint32_t* ctr,
+                                            int32_t& item_job) {
+        int32_t item = -1;
+        const uint32_t lt = lanemask_lt();
+        need = need && !done;
+        uint32_t m = __ballot_sync(0xffffffffu, need);
+        while (m) {
+            while (pos >= pend) {
+                uint32_t b = 0;
+                if (static_end < total && (threadIdx.x & 31) == 0) b = atomicAdd(ctr, 1u);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                const int64_t c = (int64_t)static_end + b;
+                if (c >= total) {
+                    done = true;
+                    return item;
+                }
+                chunk(jobs, njobs, (int32_t)c);
+            }
+            const int take = min(__popc(m), pend - pos);
+            const int rank = __popc(m & lt);
+            if (need && rank < take) {
+                item = pos + rank;
+                item_job = job;
+                need = false;
+            }
+            pos += take;
+            m = __ballot_sync(0xffffffffu, need);
+        }
+        return item;
+    }
+};
+
+template <bool STACK>
+__global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
+k_paths_multi(const PathJob* __restrict__ jobs, int32_t njobs, int32_t total_chunks, uint32_t* __restrict__ ctr) {
+    MultiQueue mq;
+    mq.init(jobs, njobs, total_chunks);
+    Trav st;
+    st.node = -1;
+    st.slot = -1;
+    StackWalk sw;
+    sw.node = kWalkDone;
+    sw.sp = 0;
+    int32_t i = -1, jb = 0, pend = -1, id = 0, depth = 0, cap = 0;
+    uint32_t ndep = 0;
+    bool eye = false;
+    float3 w = make_float3(0.0f, 0.0f, 0.0f);  // eye: throughput; photon: flux
+    Rng rng;
+    while (true) {
+        const int32_t got = mq.take(i < 0, jobs, njobs, ctr, jb);
+        if (got >= 0) {
+            const PathJob& J = jobs[jb];
+            const int32_t ne = J.ne_ptr ? (int32_t)*J.ne_ptr : 0;
+            i = got;
+            eye = got < ne;
+            const PathQ Q = eye ? J.qe : J.qp;
+            const size_t j = (size_t)(eye ? got : got - ne);
+            const float4 a = Q.ray[2 * j], c = Q.ray[2 * j + 1], ww = Q.w[j];
+            const int32_t meta = Q.meta[j];
+            w = f3(ww);
+            id = __float_as_int(ww.w);
+            rng = rng_from(Q.rng[j]);
+            depth = eye ? meta : (meta & 0xff);
+            ndep = eye ? 0u : (uint32_t)(meta >> 8);
+            cap = trav_cap(J.S);
+            trav_init(J.S, f3(a), f3(c), eye ? a.w : J.P.eps, __int_as_float(0x7f800000), st);
+            if (STACK) stack_init(J.S, sw);
+        }
+        if (__ballot_sync(0xffffffffu, i >= 0) == 0) break;
+        const PathJob& J = jobs[jb];
+        if (STACK)
+            stack_steps(J.S, st, sw, i >= 0, cap);
+        else
+            trav_steps(J.S, st, pend, i >= 0, cap);
+        const bool walked = STACK ? sw.node == kWalkDone : (st.node < 0 && pend < 0);
+        if (i >= 0 && walked) {
+            const Hit h = walk_hit(J.S, st);
+            float3 o = st.o, d = st.d;
+            bool more = false;
+            if (eye) {
+                more = h.id >= 0 && eye_interact(J.S, J.P, J.O, id, h, o, d, w, rng) && ++depth <= J.P.max_eye;
+            } else {
+                if (h.id >= 0) {
+                    const uint32_t pid = (uint32_t)id * kSlotsPerPath + depth;
+                    const uint32_t slot = (uint32_t)id * kSlotsPerPath + ndep;
+                    more = photon_bounce(J.S, J.P, J.D, rng, h, o, d, w, pid, slot, ndep) && ++depth < J.P.max_photon;
+                }
+                if (!more) J.D.pcount[id] = ndep;
+            }
+            if (more) {
+                trav_init(J.S, o, d, J.P.eps, __int_as_float(0x7f800000), st);
+                if (STACK) stack_init(J.S, sw);
+            } else {
+                i = -1;
+            }
+        }
+    }
+}
+
 struct RegenDev {
     float4* __restrict__ ro;    // {o.xyz, depth bits}
     float4* __restrict__ rd;    // {d.xyz, alive bits}
@@ -1482,27 +1633,41 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
 
 // Eye and photon passes of one pass (Sec. 2): both fronts, then one persistent kernel finishes
 // the eye and photon paths still going.
-static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, const DepositDev& D, cudaStream_t st) {
-    NvtxRange nvtx("gsp: eye + photon paths");
+// Both fronts of a pass; J describes the paths still going (J.nchunks == 0: none).
+static gsp_status paths_front(gsp_sppm* r, const PassDev& P, const EyeOut& O, const DepositDev& D, cudaStream_t st,
+                              PathJob& J) {
     int be = 0, bp = -1;
     gsp_status e = eye_front(r, P, O, st, be);
     if (e == GSP_OK) e = photon_front(r, P, D, st, bp);
     if (e != GSP_OK) return e;
     const bool eye_left = be <= r->P.max_eye_depth;
     const bool ph_left = bp >= 0 && bp < r->P.max_photon_depth;
-    if (eye_left || ph_left) {
-        const int64_t items = (eye_left ? r->npix : 0) + (ph_left ? r->np : 0);
-        const DevScene S = gsp_dev_scene(r->scene);
+    J.S = gsp_dev_scene(r->scene);
+    J.P = P;
+    J.qe = r->qe[be & 1];
+    J.qp = r->q[ph_left ? bp & 1 : 0];
+    J.O = O;
+    J.D = D;
+    J.ne_ptr = eye_left ? r->counters + 4 + be % 3 : nullptr;
+    J.np_ptr = ph_left ? r->counters + 8 + bp % 3 : nullptr;
+    J.first_chunk = 0;
+    const int64_t items = (eye_left ? r->npix : 0) + (ph_left ? r->np : 0);
+    J.nchunks = (int32_t)((items + kTraceChunk - 1) / kTraceChunk);
+    return GSP_OK;
+}
+
+static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, const DepositDev& D, cudaStream_t st) {
+    NvtxRange nvtx("gsp: eye + photon paths");
+    PathJob J;
+    gsp_status e = paths_front(r, P, O, D, st, J);
+    if (e != GSP_OK) return e;
+    if (J.nchunks > 0) {
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
-        const unsigned grid = (unsigned)path_grid(items, r->scene->ctx->device, stack);
-        const uint32_t* ne = eye_left ? r->counters + 4 + be % 3 : nullptr;
-        const uint32_t* npp = ph_left ? r->counters + 8 + bp % 3 : nullptr;
+        const unsigned grid = (unsigned)path_grid((int64_t)J.nchunks * kTraceChunk, r->scene->ctx->device, stack);
         if (stack)
-            k_paths<true><<<grid, kTraceThreads, 0, st>>>(S, P, r->qe[be & 1], O, ne, r->q[ph_left ? bp & 1 : 0], D,
-                                                          npp, r->counters + 12);
+            k_paths<true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12);
         else
-            k_paths<false><<<grid, kTraceThreads, 0, st>>>(S, P, r->qe[be & 1], O, ne, r->q[ph_left ? bp & 1 : 0], D,
-                                                           npp, r->counters + 12);
+            k_paths<false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12);
     }
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
@@ -1802,6 +1967,9 @@ struct gsp_batch {
     cudaStream_t cap = nullptr;  // private stream the graph is captured on (never the legacy stream)
     cudaGraphExec_t exec = nullptr;
     int32_t device = 0;
+    bool fused = true;           // all renderers' paths in one persistent launch (k_paths_multi)
+    PathJob* d_jobs = nullptr;   // fused: the renderers' job table
+    uint32_t* d_ctr = nullptr;   // fused: the path kernel's work counter
 };
 
 static void batch_free(gsp_batch* b) {
@@ -1810,11 +1978,11 @@ static void batch_free(gsp_batch* b) {
     for (auto e : b->joins) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_ctr);
     delete b;
 }
 
-// One pass of every renderer captured as a single CUDA graph: a branch per renderer, forked
-// from and joined to the capturing stream, so the scenes' kernels overlap on the GPU.
 // Back to the state of a new renderer (radii r0, nothing gathered, no pass run).
 static cudaError_t reset_state(gsp_sppm* t, cudaStream_t st) {
     t->passes = 0;
@@ -1825,7 +1993,80 @@ static cudaError_t reset_state(gsp_sppm* t, cudaStream_t st) {
     return e;
 }
 
+// Fused form of a batch pass: the eye and photon fronts of every renderer in parallel branches,
+// then ONE persistent k_paths_multi launch over all renderers' remaining paths, then the
+// deposits and gathers in parallel branches. The job table holds only pointers and device
+// counters, so it is written once, after the capture.
+static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st) {
+    const int n = (int)b->rs.size();
+    if (!b->d_jobs) {
+        GSP_CUDA_TRY(cudaMalloc(&b->d_jobs, (size_t)n * sizeof(PathJob)));
+        GSP_CUDA_TRY(cudaMalloc(&b->d_ctr, sizeof(uint32_t)));
+    }
+    bool stack = true;
+    for (gsp_sppm* r : b->rs) stack = stack && r->traversal == GSP_TRAVERSAL_STACK;
+    std::vector<PathJob> jobs(n);
+    std::vector<PassDev> passes(n);
+    GSP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    gsp_status e = GSP_OK;
+    cudaError_t ce = cudaEventRecord(b->fork, st);
+    for (int i = 0; i < n && ce == cudaSuccess && e == GSP_OK; ++i) {
+        gsp_sppm* r = b->rs[i];
+        passes[i] = pass_params(r, r->passes);
+        passes[i].pass_dev = r->counters + 7;
+        const EyeOut O{r->hx, r->hn, r->hf, r->hd, nullptr};
+        const DepositDev D{r->slots, r->pcount, r->entry, r->ecount, r->P.hash_mode == GSP_STOCHASTIC ? 1 : 0, nullptr};
+        ce = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        if (ce == cudaSuccess) e = paths_front(r, passes[i], O, D, b->streams[i], jobs[i]);
+        if (ce == cudaSuccess && e == GSP_OK) ce = cudaEventRecord(b->joins[i], b->streams[i]);
+        if (ce == cudaSuccess && e == GSP_OK) ce = cudaStreamWaitEvent(st, b->joins[i], 0);
+    }
+    int32_t total = 0;
+    for (auto& J : jobs) {
+        J.first_chunk = total;
+        total += J.nchunks;
+    }
+    if (ce == cudaSuccess && e == GSP_OK && total > 0) {
+        ce = cudaMemsetAsync(b->d_ctr, 0, sizeof(uint32_t), st);
+        const unsigned grid = (unsigned)path_grid((int64_t)total * kTraceChunk, b->device, stack);
+        if (ce == cudaSuccess) {
+            if (stack)
+                k_paths_multi<true><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr);
+            else
+                k_paths_multi<false><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr);
+            ce = cudaGetLastError();
+        }
+    }
+    if (ce == cudaSuccess && e == GSP_OK) ce = cudaEventRecord(b->fork, st);
+    for (int i = 0; i < n && ce == cudaSuccess && e == GSP_OK; ++i) {
+        gsp_sppm* r = b->rs[i];
+        ce = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+        if (ce == cudaSuccess) e = gather_half(r, passes[i], b->streams[i]);
+        if (ce == cudaSuccess && e == GSP_OK) {
+            k_add_u32<<<1, 1, 0, b->streams[i]>>>(r->counters + 7, 1u);
+            ce = cudaEventRecord(b->joins[i], b->streams[i]);
+        }
+        if (ce == cudaSuccess && e == GSP_OK) ce = cudaStreamWaitEvent(st, b->joins[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(st, &g);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess && e == GSP_OK) ce = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ce == cudaSuccess && e == GSP_OK)
+        ce = cudaMemcpy(b->d_jobs, jobs.data(), (size_t)n * sizeof(PathJob), cudaMemcpyHostToDevice);
+    if (e != GSP_OK) return e;
+    if (ce != cudaSuccess) {
+        gsp_set_last_error(cudaGetErrorString(ce));
+        return GSP_ERR_CUDA;
+    }
+    return GSP_OK;
+}
+
+// One pass of every renderer captured as a single CUDA graph: a branch per renderer, forked
+// from and joined to the capturing stream, so the scenes' kernels overlap on the GPU.
 static gsp_status batch_capture(gsp_batch* b, cudaStream_t st) {
+    if (b->fused) return batch_capture_fused(b, st);
     GSP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     gsp_status e = GSP_OK;
     cudaError_t ce = cudaEventRecord(b->fork, st);
@@ -1887,6 +2128,17 @@ gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** o
     return GSP_OK;
 }
 
+gsp_status gsp_batch_tune(gsp_batch* b, int32_t fused) {
+    if (!b || fused < 0 || fused > 1) return GSP_ERR_INVALID_ARG;
+    if (b->fused != (fused == 1) && b->exec) {
+        cudaSetDevice(b->device);
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;  // captured again at the next gsp_batch_pass
+    }
+    b->fused = fused == 1;
+    return GSP_OK;
+}
+
 void gsp_batch_destroy(gsp_batch* b) {
     if (!b) return;
     cudaSetDevice(b->device);
@@ -1923,8 +2175,9 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
     cudaError_t ce = cudaEventCreate(&a);
     if (ce == cudaSuccess) ce = cudaEventCreate(&z);
     gsp_status e = GSP_OK;
-    struct Cand { int32_t es, ps, gl, tr; };
-    const Cand start{b->rs[0]->eye_steps, b->rs[0]->photon_steps, b->rs[0]->gather_lanes, b->rs[0]->traversal};
+    struct Cand { int32_t es, ps, gl, tr; bool fused; };
+    const Cand start{b->rs[0]->eye_steps, b->rs[0]->photon_steps, b->rs[0]->gather_lanes, b->rs[0]->traversal,
+                     b->fused};
     bool stack_ok = true;
     for (gsp_sppm* r : b->rs) stack_ok = stack_ok && r->scene->bvh.depth < kStackDepth;
     Cand pick = start;
@@ -1937,6 +2190,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
             r->gather_lanes = c.gl;
             r->traversal = c.tr;
         }
+        b->fused = c.fused;
         if (b->exec) cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     };
@@ -1968,13 +2222,20 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
     const bool full = b->rs[0]->P.photon_mode == GSP_FULL_PATH;
     for (int32_t es : {0, 1})
         for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2} : std::vector<int32_t>{0})
-            if (es != start.es || ps != start.ps) trial({es, ps, start.gl, start.tr});
+            if (es != start.es || ps != start.ps) trial({es, ps, start.gl, start.tr, start.fused});
     const Cand steps = pick;
     for (int32_t gl : {4, 8, 16})
-        if (gl != start.gl) trial({steps.es, steps.ps, gl, start.tr});
+        if (gl != start.gl) trial({steps.es, steps.ps, gl, start.tr, start.fused});
     const Cand lanes = pick;
     for (int32_t tr : {GSP_TRAVERSAL_MTBVH, GSP_TRAVERSAL_STACK})
-        if (tr != start.tr && (tr != GSP_TRAVERSAL_STACK || stack_ok)) trial({lanes.es, lanes.ps, lanes.gl, tr});
+        if (tr != start.tr && (tr != GSP_TRAVERSAL_STACK || stack_ok))
+            trial({lanes.es, lanes.ps, lanes.gl, tr, start.fused});
+    // last: one fused path launch for all renderers, or a path launch per renderer; with the
+    // steps searched again for the other form (the best split moves)
+    const Cand form = pick;
+    for (int32_t es : {0, 1})
+        for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2} : std::vector<int32_t>{0})
+            trial({es, ps, form.gl, form.tr, !form.fused});
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (a) cudaEventDestroy(a);
     if (z) cudaEventDestroy(z);
@@ -1993,6 +2254,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
         out->candidates = ncand;
         out->gather_lanes = pick.gl;
         out->traversal = pick.tr;
+        out->fused = pick.fused ? 1 : 0;
     }
     return GSP_OK;
 }

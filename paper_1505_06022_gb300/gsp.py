@@ -39,7 +39,7 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
        "gsp_scene_set_materials", "gsp_batch_create", "gsp_batch_destroy", "gsp_batch_pass",
-       "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load", "gsp_batch_autotune"]
+       "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load", "gsp_batch_autotune", "gsp_batch_tune"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -71,7 +71,7 @@ class BvhStats(C.Structure):
 class TuneResult(C.Structure):
     _fields_ = [("eye_steps", C.c_int32), ("photon_steps", C.c_int32), ("cell_h", C.c_float),
                 ("ms_per_pass", C.c_float), ("first_ms_per_pass", C.c_float), ("candidates", C.c_int32),
-                ("gather_lanes", C.c_int32), ("traversal", C.c_int32)]
+                ("gather_lanes", C.c_int32), ("traversal", C.c_int32), ("fused", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -136,6 +136,7 @@ def lib():
             L.gsp_batch_pass.argtypes = [P, I32, P]
             L.gsp_sppm_autotune.argtypes = [P, I32, P]
             L.gsp_batch_autotune.argtypes = [P, I32, P]
+            L.gsp_batch_tune.argtypes = [P, I32]
             L.gsp_sppm_save.argtypes = [P, C.c_char_p]
             L.gsp_sppm_load.argtypes = [P, C.c_char_p]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
@@ -346,6 +347,10 @@ def gsp_sppm_autotune(r, trial_passes=2) -> dict:
     out = TuneResult()
     _check("gsp_sppm_autotune", lib().gsp_sppm_autotune(r, trial_passes, C.byref(out)))
     return out.as_dict()
+
+
+def gsp_batch_tune(b, fused):
+    _check("gsp_batch_tune", lib().gsp_batch_tune(b, 1 if fused else 0))
 
 
 def gsp_batch_autotune(b, trial_passes=2) -> dict:
@@ -577,6 +582,10 @@ class Batch:
 
     def autotune(self, trial_passes=2) -> dict:
         return gsp_batch_autotune(self.h, trial_passes)
+
+    def tune(self, fused):
+        """fused: one persistent path launch for all renderers per pass (else one per renderer)."""
+        gsp_batch_tune(self.h, fused)
 
     def close(self):
         if self.h:

@@ -27,7 +27,8 @@ def scenes():
     return out, kws
 
 
-def test_batch_graph_matches_individual_passes(ctx):
+@pytest.mark.parametrize("fused", [False, True])
+def test_batch_graph_matches_individual_passes(ctx, fused):
     scs, kws = scenes()
     solo = []
     for sc, kw in zip(scs, kws):
@@ -36,7 +37,9 @@ def test_batch_graph_matches_individual_passes(ctx):
         solo.append(r.image().cpu().numpy())
     rs = [gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw)) for sc, kw in zip(scs, kws)]
     rs[0].run(1)  # a renderer that already ran a pass joins the batch at its own pass index
+    rs[1].tune(1, 2)  # per-renderer wavefront settings differ inside one batch
     b = gsp.Batch(rs)
+    b.tune(fused)
     b.run(2)      # one captured graph, replayed twice: renderer 0 at 3 passes, the others at 2
     for r in rs[1:]:
         r.run(1)  # plain passes continue from where the graph left off
@@ -58,8 +61,8 @@ def test_batch_autotune_keeps_the_estimate(ctx):
     b = gsp.Batch(rs)
     res = b.autotune(trial_passes=1)
     assert res["eye_steps"] in (0, 1) and res["photon_steps"] in (0, 1, 2) and res["gather_lanes"] in (4, 8, 16)
-    assert 6 <= res["candidates"] <= 10 and res["ms_per_pass"] <= res["first_ms_per_pass"]
-    assert res["traversal"] in (1, 2)
+    assert 6 <= res["candidates"] <= 16 and res["ms_per_pass"] <= res["first_ms_per_pass"]
+    assert res["traversal"] in (1, 2) and res["fused"] in (0, 1)
     b.run(3)
     torch.cuda.synchronize()
     for r, (img, n) in zip(rs, solo):
