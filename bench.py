@@ -1,13 +1,19 @@
 #!/usr/bin/env python3
-"""Benchmark: closest-hit ray casting through the multiple-threaded BVH, plus an SPPM pass.
+"""Benchmark: closest-hit ray casting through the multiple-threaded BVH, plus the SPPM workloads.
 
 Default workload (one line of JSON on rank 0):
   * step = one gsp_trace_closest_hit call over 4,194,304 rays (2,097,152 coherent pinhole rays
     + 2,097,152 uniform random rays) against a 1,003,520-triangle displaced icosphere
     (SAH BVH, 16 bins, six hit/miss link sets). metric: closest-hit Mrays/s.
-  * "sppm_512": SPPM passes/s at 512x512 on a 247,234-triangle scene with 1M photons/pass.
-  * "e2e": the same ray casting through the C ABI with host buffers (host->device copy of the
-    rays and device->host copy of the hits inside the timed region).
+  * "e2e": the same rays through gsp_trace_closest_hit_host from pinned host memory (the
+    host->device transfer of the rays and the device->host copy of the hits inside the timed
+    region).
+  * "traversal_fig4": MTBVH vs TBVH vs stack traversal (Fig. 4) and the device BVH build.
+  * "sppm_512": SPPM passes/s at 512x512 on a 247,234-triangle scene with 1M photon paths/pass
+    (a 64-pass render; default and autotuned settings).
+  * "grad_256": backward/forward time of the path-replay adjoint (256x256, 8 passes).
+  * "batch_64": 64 scenes as one graph per pass vs one renderer after another.
+  * "sppm_modes": the paper's photon-pass / hashing variants at equal image error.
 Multi-GPU: every rank casts its own 4M rays (independent work, no collective on the data
 path); the value is all rays of all ranks over the slowest rank's time.
 

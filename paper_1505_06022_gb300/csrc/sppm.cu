@@ -1,15 +1,20 @@
 // sppm.cu -- stochastic progressive photon mapping on the device (Sec. 2, 3.3, 3.4).
 //
-// One pass = eye pass (first non-specular hit per pixel; emission seen directly is added to
-// the pixel's direct term), photon pass (whole paths, or one bounce per thread with path
-// regeneration), hash-grid deposit, and the fused range query + progressive update.
+// One pass = eye pass (first non-specular hit per pixel; emission seen directly is recorded as
+// the pass's direct term), photon pass (whole paths, or one bounce per thread with path
+// regeneration), hash-grid deposit, and the fused range query + progressive update (which also
+// folds the pass's direct term into the pixel state). The eye and photon passes are emission
+// kernels, optional wavefront steps, and one persistent path kernel (k_paths; k_paths_multi for
+// a batch of renderers); several passes overlap on two streams (passes_overlapped).
 //
 // Device layout (all library-owned, sized at creation):
 //   pixel state   st0[p] = {tau.rgb, N}, st1[p] = {direct.rgb, R}          32 B / pixel
-//   hit points    hx[p] = {x.xyz, material or -1}, hn[p] = {n_s.xyz, 0},
-//                 hf[p] = {w * albedo / pi, 0}                              48 B / pixel
-//   photon slots  slot s: {x.xyz, id}, {flux.rgb, octahedral direction}    32 B / deposit
+//   trace buffers two sets (the second made when passes overlap), each:
+//     hit points  hx[p] = {x.xyz, material or -1}, hn[p] = {n_s.xyz, 0},
+//                 hf[p] = {w * albedo / pi, 0}, hd[p] = {direct.rgb, 0}     64 B / pixel
+//     photons     slot s: {x.xyz, id}, {flux.rgb, octahedral direction}    32 B / deposit
 //                 path k owns slots [k*32, k*32+32) (one slot per thread in REGEN mode)
+//   queues        eye and photon wavefront queues, two of each (ping-pong)
 //   exact grid    bucket-sorted SoA copies spos[], spay[] + bucket starts bstart[T+1]
 //   stochastic    entry[T] = min(random depth bits << 32 | slot), ecount[T]
 #include <algorithm>
