@@ -22,7 +22,12 @@
  *    exceeds its step limit, an overflowing buffer) in a device status word; the next
  *    gsp_sppm_sync()/gsp_context_sync() returns the first such error.
  *  - Memory the library allocates itself (scene, BVH, SPPM state) lives in device memory of
- *    the context's device, sized at creation; no call allocates during a pass.
+ *    the context's device, sized at creation. A few buffers are made on first use and kept:
+ *    the second set of trace buffers when a call runs several passes (or a gradient replay),
+ *    the per-stream buffers of host-buffer tracing, a batch's job table; each entry point says
+ *    so. Nothing is allocated between the launches of a pass.
+ *  - Passes, batches and gradients use the handles' own extra streams internally; they are
+ *    ordered after earlier work on `stream`, and later work on `stream` is ordered after them.
  */
 #ifndef GSP_H_
 #define GSP_H_
@@ -257,7 +262,10 @@ void gsp_sppm_destroy(gsp_sppm* r);
 
 /* Runs `npasses` SPPM iterations on `stream`: eye pass (first non-specular hit per pixel,
  * emission seen directly), photon pass, hash-grid deposit, range query with the progressive
- * update N' = N + alpha M, R' = R sqrt((N + alpha M) / (N + M)), tau' = (tau + Phi) R'^2/R^2. */
+ * update N' = N + alpha M, R' = R sqrt((N + alpha M) / (N + M)), tau' = (tau + Phi) R'^2/R^2.
+ * With npasses >= 2 in exact mode, pass i + 1 is traced on the renderer's own stream into a
+ * second set of trace buffers (allocated at the first such call) while pass i is deposited and
+ * gathered on `stream`; the result equals npasses single-pass calls bit for bit. */
 gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
 
 /* Execution tuning of the passes. eye_steps / photon_steps: wavefront steps (closest hit of a
