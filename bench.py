@@ -294,6 +294,7 @@ def run_ours(args, world, rank, local):
 
     # ---- Fig. 4's traversal comparison, SPPM pass at 512x512, the gradient workload, the batch ----
     fig4 = bench_traversals(args, ctx, dev, stream, sc, scene, rays) if not args.skip_fig4 else None
+    cornell = bench_cornell(args, ctx, dev, stream, with_cpu(args, world, rank)) if not args.skip_sppm else None
     sppm = bench_sppm(args, ctx, dev, stream, pg) if not args.skip_sppm else None
     grad = bench_grad(args, ctx, dev, stream) if not args.skip_grad else None
     batch = bench_batch(args, ctx, dev, stream) if not args.skip_batch else None
@@ -326,6 +327,7 @@ def run_ours(args, world, rank, local):
             "wall_s_timed": round(wall, 4),
             "check": {"host_walk_agreement": round(agree, 5)},
             "traversal_fig4": fig4,
+            "sppm_cornell_64": cornell,
             "sppm_512": sppm,
             "grad_256": grad,
             "batch_64": batch,
@@ -352,6 +354,49 @@ def timed_passes(r, k, stream):
     torch.cuda.synchronize()
     r.sync()
     return e0.elapsed_time(e1) / k
+
+
+def oracle_sppm(sc, kw, passes, grad=False):
+    """The FP64 CPU oracle rendering `passes` passes of a configuration on all host cores (with
+    forward-mode derivatives when grad): (ms per pass, cores)."""
+    import oracle as O
+    o = O.Sppm(sc, O.default_params(sc, **kw))
+    if grad:
+        o.enable_grad()
+    t0 = time.perf_counter()
+    o.run(passes)
+    dt = time.perf_counter() - t0
+    return 1000.0 * dt / passes, O.nthreads_default()
+
+
+def with_cpu(args, world, rank):
+    return rank == 0 and world == 1 and not args.skip_cpu
+
+
+def bench_cornell(args, ctx, dev, stream, cpu):
+    """The small configuration (Cornell box, 64x64, 16,384 photons/pass, 4 passes, alpha 0.7,
+    r0 = 0.05 * diagonal, seed 1): a render of 4 passes on the GPU, and the oracle beside it."""
+    import torch
+    from paper_1505_06022_gb300 import gsp, inputs as I
+    sc = I.cornell_box(seed=1)
+    s = gsp.Scene(ctx, sc)
+    kw = dict(photons_per_pass=16384, seed=1)
+    warm = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
+    warm.run(4, stream)
+    torch.cuda.synchronize()
+    warm.close()
+    ms = []
+    for _ in range(5):
+        r = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
+        ms.append(timed_passes(r, 4, stream))
+        r.close()
+    out = {"ms_per_pass": round(statistics.median(ms), 4), "passes_per_s": round(1000.0 / statistics.median(ms), 1),
+           "config": "Cornell box 36 triangles, 64x64, 16,384 photons/pass, 4 passes, alpha 0.7, r0 = 0.05 * diagonal"}
+    if cpu:
+        oms, cores = oracle_sppm(sc, kw, 4)
+        out["cpu_oracle"] = {"ms_per_pass": round(oms, 2), "cores": cores, "passes": 4}
+    s.close()
+    return out
 
 
 def bench_sppm(args, ctx, dev, stream, pg):
@@ -388,6 +433,10 @@ def bench_sppm(args, ctx, dev, stream, pg):
            "config": "512x512, 247,234 triangles (displaced plane, glass/mirror/diffuse icospheres, area light), "
                      "1,048,576 photon paths/pass, alpha 0.7, r0 = 0.004 * diagonal, full paths + exact hash grid",
            "image_mean": round(float(img.mean()), 5), "autotuned_image_identical": same}
+    if with_cpu(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))):
+        oms, cores = oracle_sppm(sc, dict(photons_per_pass=1 << 20, seed=3, r0_frac=0.004), 2)
+        out["cpu_oracle"] = {"ms_per_pass": round(oms, 1), "passes_per_s": round(1000.0 / oms, 3), "cores": cores,
+                             "passes": 2, "sample": "the first 2 passes of the same render, FP64 oracle"}
     tuned.close()
     r.close()
     s.close()
@@ -436,13 +485,19 @@ def bench_grad(args, ctx, dev, stream):
             bwd.append(e[1].elapsed_time(e[2]))
         r.close()
     f, b = statistics.median(fwd), statistics.median(bwd)
-    return {"forward_ms": round(f, 3), "backward_ms": round(b, 3), "backward_over_forward": round(b / f, 3),
-            "grad_norm": round(float(ga.norm()), 6),
-            "settings": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in choice.items()
-                         if k in ("eye_steps", "photon_steps", "cell_h", "gather_lanes", "traversal")},
-            "config": "256x256, 50,770 triangles (displaced plane in 12 material regions + 4 icospheres), "
-                      "16 diffuse materials + light, 262,144 photon paths/pass, 8 passes, L2 loss vs a render "
-                      "at perturbed albedos; gradient w.r.t. 16 RGB albedos and the light's emission"}
+    out = {"forward_ms": round(f, 3), "backward_ms": round(b, 3), "backward_over_forward": round(b / f, 3),
+           "grad_norm": round(float(ga.norm()), 6),
+           "settings": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in choice.items()
+                        if k in ("eye_steps", "photon_steps", "cell_h", "gather_lanes", "traversal")},
+           "config": "256x256, 50,770 triangles (displaced plane in 12 material regions + 4 icospheres), "
+                     "16 diffuse materials + light, 262,144 photon paths/pass, 8 passes, L2 loss vs a render "
+                     "at perturbed albedos; gradient w.r.t. 16 RGB albedos and the light's emission"}
+    if with_cpu(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))):
+        # the oracle's gradient: FP64 forward-mode derivatives carried through the 8 passes
+        oms, cores = oracle_sppm(sc, dict(photons_per_pass=1 << 18, seed=4, r0_frac=0.004), passes, grad=True)
+        out["cpu_oracle"] = {"forward_with_gradient_ms": round(oms * passes, 1), "cores": cores,
+                             "sample": "the same 8 passes, FP64 forward-mode derivatives"}
+    return out
 
 
 def bench_traversals(args, ctx, dev, stream, sc, scene, rays):
@@ -588,6 +643,13 @@ def bench_batch(args, ctx, dev, stream):
                               "tuning_s": round(tune_s, 2)},
            "config": f"{n} scenes, 1e3-2e5 triangles log-uniform, image side in {{64,128,256,512}}, "
                      "262,144 photon paths/pass each, full paths + exact hash grid"}
+    if with_cpu(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))):
+        t = []
+        for i, sc in enumerate(scs[:4]):
+            oms, cores = oracle_sppm(sc, dict(photons_per_pass=1 << 18, seed=5 + i, r0_frac=0.004, scene_id=i), 1)
+            t.append(oms)
+        out["cpu_oracle"] = {"scene_passes_per_s": round(1000.0 * len(t) / sum(t), 2), "cores": cores,
+                             "sample": "one pass of each of the first 4 scenes, FP64 oracle"}
     b.close()
     for r in bat:
         r.close()
