@@ -30,7 +30,9 @@ def _nvcc() -> str:
 def _flags():
     # GSP_NVCC_EXTRA: extra nvcc arguments, e.g. -DGSP_PATH_MIN_BLOCKS=8 to sweep launch shapes
     extra = os.environ.get("GSP_NVCC_EXTRA", "").split()
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+    # -fmad=false: device arithmetic rounds as written (fused multiply-adds only where the source
+    # spells them out), so one device function gives identical bits in every kernel it is inlined in
+    return ARCH + ["-O3", "-fmad=false", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC] + extra
 
 

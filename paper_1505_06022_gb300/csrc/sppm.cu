@@ -98,10 +98,10 @@ __device__ __forceinline__ float3 cosine_dir(float3 n, float ua, float ub) {
     sincospif(2.0f * ub, &s, &c);  // angle 2 pi ub without rounding 2 pi ub first
     float3 t1, t2;
     onb(n, t1, t2);
-    return t1 * (r * c) + t2 * (r * s) + n * z;
+    return madd3(n, z, madd3(t2, r * s, t1 * (r * c)));
 }
 
-__device__ __forceinline__ float3 reflect3(float3 d, float3 n) { return d - n * (2.0f * dot3(d, n)); }
+__device__ __forceinline__ float3 reflect3(float3 d, float3 n) { return madd3(n, -2.0f * dot3(d, n), d); }
 
 // Smooth dielectric: reflection with the exact unpolarised Fresnel probability, else refraction.
 __device__ __forceinline__ float3 dielectric(float3 d, float3 n, float ior, float u) {
@@ -117,7 +117,7 @@ __device__ __forceinline__ float3 dielectric(float3 d, float3 n, float ior, floa
     const float rp = (n2 * cosi - n1 * cost) / (n2 * cosi + n1 * cost);
     const float F = 0.5f * (rs * rs + rp * rp);
     if (u < F) return reflect3(d, nf);
-    return d * eta + nf * (eta * cosi - cost);
+    return madd3(nf, __fmaf_rn(eta, cosi, -cost), d * eta);
 }
 
 // Octahedral unit-vector encoding, 2 x 16-bit snorm (Cigolle et al., JCGT 2014).
@@ -249,7 +249,7 @@ __device__ __forceinline__ bool eye_interact(const DevScene& S, const PassDev& P
         O.hd[p] = v;
     }
     if (m.type == GSP_EMITTER) return false;
-    const float3 x = o + d * h.t;
+    const float3 x = madd3(d, h.t, o);
     if (m.type == GSP_DIFFUSE) {
         const float3 ns = front ? n : n * -1.0f;
         const float3 f = mul3(w, m.albedo) * (1.0f / kPi);
@@ -376,7 +376,7 @@ __device__ __forceinline__ bool photon_bounce(const DevScene& S, const PassDev& 
     const float3 n = f3(sh);
     const Material m = load_mat(S, __float_as_int(sh.w));
     if (m.type == GSP_EMITTER) return false;
-    const float3 x = o + d * h.t;
+    const float3 x = madd3(d, h.t, o);
     if (m.type == GSP_DIFFUSE) {
         if (D.smat) D.smat[slot] = __float_as_int(sh.w);
         float4* rec = D.slots + 2 * (size_t)slot;

@@ -101,3 +101,28 @@ def test_autotune_keeps_the_estimate(ctx):
     b = r.image().cpu().numpy()
     # the same photons are gathered; only the summation order can differ with the cell size
     np.testing.assert_allclose(b, a, rtol=2e-5, atol=1e-7 * a.max())
+
+
+def test_full_size_batch_matches_individual_renderers(ctx):
+    """The batch configuration: 64 scenes (1k-200k triangles, 64^2-512^2, 2^18 photon paths per
+    pass each) as fused graph passes; 8 of the renderers checked bit for bit against the same
+    renderers run alone."""
+    scs = I.batch_scenes(64, seed=5)
+    scenes = [gsp.Scene(ctx, sc) for sc in scs]
+    mk = lambda i: gsp.Renderer(scenes[i], gsp.sppm_params(scs[i], 1 << 18, seed=5 + i, r0_frac=0.004, scene_id=i))
+    rs = [mk(i) for i in range(64)]
+    b = gsp.Batch(rs)
+    b.run(2)
+    torch.cuda.synchronize()
+    pick = np.random.default_rng(3).choice(64, 8, replace=False)
+    for i in pick:
+        rs[i].sync()
+        alone = mk(i)
+        alone.run(2)
+        assert np.array_equal(rs[i].image().cpu().numpy(), alone.image().cpu().numpy()), i
+        alone.close()
+    b.close()
+    for r in rs:
+        r.close()
+    for s in scenes:
+        s.close()

@@ -131,3 +131,53 @@ def test_adjoint_does_not_depend_on_execution_settings(ctx, case):
         ga, gl, _, _ = gpu_grad(ctx, sc, g, **tune)
         np.testing.assert_allclose(ga, base[0], rtol=1e-5, atol=1e-6 * np.abs(base[0]).max())
         np.testing.assert_allclose(gl, base[1], rtol=1e-5, atol=1e-6 * np.abs(base[1]).max())
+
+
+def test_full_size_gradient_configuration(ctx):
+    """The gradient configuration itself: 256x256, 50,770 triangles, 16 diffuse materials + a
+    light, 262,144 photon paths per pass, 8 passes, L2 loss against a render at perturbed
+    albedos. The adjoint against the FP64 oracle's gradient, and against central differences
+    of the GPU forward with h = 1e-3 on three albedo components."""
+    sc = I.grad_scene(seed=4)
+    kw = dict(photons_per_pass=1 << 18, seed=4, r0_frac=0.004)
+    passes = 8
+    s = gsp.Scene(ctx, sc)
+    tgt = sc.mats.copy()
+    tgt["albedo"] = np.clip(tgt["albedo"] * np.random.default_rng(40).uniform(0.8, 1.2, tgt["albedo"].shape), 0.05, 0.95)
+    gsp.gsp_scene_set_materials(s.h, tgt)
+    rt = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
+    rt.run(passes)
+    target = rt.image()
+    gsp.gsp_scene_set_materials(s.h, sc.mats)
+    r = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
+    r.enable_grad(passes)
+    r.run(passes)
+    g = (r.image() - target).contiguous()
+    ga, gl = (x.cpu().numpy() for x in r.grad(g))
+    g_np = g.cpu().numpy().astype(np.float64)
+    orc = O.Sppm(sc, O.default_params(sc, **kw))
+    orc.enable_grad()
+    orc.run(passes)
+    ga_o, gl_o = orc.grad(g_np)
+    diffuse = sc.mats["type"] == I.DIFFUSE
+    scale = np.abs(ga_o[diffuse]).max()
+    assert np.abs(ga[diffuse] - ga_o[diffuse]).max() <= 1e-3 * scale
+    np.testing.assert_allclose(gl, gl_o, rtol=1e-3, atol=1e-3 * np.abs(gl_o).max())
+
+    def objective(mats):
+        gsp.gsp_scene_set_materials(s.h, mats)
+        rr = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
+        rr.run(passes)
+        val = float(np.sum(g_np * rr.image().cpu().numpy().astype(np.float64)))
+        rr.close()
+        return val
+
+    h = 1e-3
+    for m, c in [(0, 0), (7, 1), (15, 2)]:
+        mp, mm = sc.mats.copy(), sc.mats.copy()
+        mp["albedo"][m, c] += h
+        mm["albedo"][m, c] -= h
+        dh = float(mp["albedo"][m, c]) - float(mm["albedo"][m, c])
+        fd = (objective(mp) - objective(mm)) / dh
+        assert abs(fd - ga[m, c]) <= 2e-3 * scale, (m, c, fd, ga[m, c])
+    gsp.gsp_scene_set_materials(s.h, sc.mats)
