@@ -107,6 +107,11 @@ def lib():
         L.orc_sppm_enable_grad.argtypes = [P]
         L.orc_sppm_grad.restype = I32
         L.orc_sppm_grad.argtypes = [P, P, P, P]
+        L.orc_mesh_set_attributes.restype = I32
+        L.orc_mesh_set_attributes.argtypes = [P, P, P, P, I64]
+        L.orc_sppm_set_texture.restype = I32
+        L.orc_sppm_set_texture.argtypes = [P, I32, P, I32, I32]
+        L.orc_sppm_surface.argtypes = [P, P, I64, P]
         _lib = L
     return _lib
 
@@ -178,6 +183,14 @@ class Mesh:
         if getattr(self, "h", None) and _lib is not None:
             _lib.orc_mesh_destroy(self.h)
             self.h = None
+
+    def set_attributes(self, normals=None, texcoords=None):
+        """Per-vertex normals [nv, 3] and texture coordinates [nv, 2] (either may be None)."""
+        self.normals = None if normals is None else np.ascontiguousarray(normals, np.float32)
+        self.texcoords = None if texcoords is None else np.ascontiguousarray(texcoords, np.float32)
+        if lib().orc_mesh_set_attributes(self.h, _p(self.normals), _p(self.texcoords), _p(self.tris),
+                                         len(self.tris)) != 0:
+            raise ValueError("oracle: a vertex normal is zero")
 
     def closest_hit(self, rays, brute=False, classify=True, nthreads=None):
         """Returns (id int32, t f64, u f64, v f64, nondeg int32 or None). id -1 = miss."""
@@ -253,6 +266,27 @@ class Sppm:
         self.w, self.h = self.cam.width, self.cam.height
         self.handle = lib().orc_sppm_create(self.mesh.h, C.cast(self.mats, C.c_void_p), len(self.mats),
                                             C.byref(self.cam), C.byref(self.params))
+        # shading data of the scene, if it has any (per-vertex normals, texture coordinates,
+        # albedo textures per material)
+        nrm, st = getattr(scene, "normals", None), getattr(scene, "texcoords", None)
+        if mesh is None and (nrm is not None or st is not None):
+            self.mesh.set_attributes(nrm, st)
+        for m, rgb in (getattr(scene, "textures", None) or {}).items():
+            self.set_texture(m, rgb)
+
+    def set_texture(self, mat: int, rgb):
+        """Albedo texture [h, w, 3] of diffuse material `mat`."""
+        rgb = np.ascontiguousarray(rgb, np.float32)
+        if lib().orc_sppm_set_texture(self.handle, int(mat), _p(rgb), rgb.shape[1], rgb.shape[0]) != 0:
+            raise ValueError("oracle: bad texture")
+
+    def surface(self, rays):
+        """Shading at each ray's closest hit: dict(id, u, v, ns [n, 3], tex [n, 3], smooth)."""
+        rays = np.ascontiguousarray(rays, np.float32)
+        out = np.zeros((len(rays), 10))
+        lib().orc_sppm_surface(self.handle, _p(rays), len(rays), _p(out))
+        return dict(id=out[:, 0].astype(np.int64), u=out[:, 1], v=out[:, 2], ns=out[:, 3:6], tex=out[:, 6:9],
+                    smooth=out[:, 9] > 0)
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -22,6 +22,10 @@
 //                     query + progressive density estimation; Hachisuka & Jensen 2009),
 //                     Sec. 3.3 (photon path regeneration), Sec. 3.4 (stochastic hashing with a
 //                     random depth per photon).
+//  * surface          Sec. 3.1's triangle record with a normal and texture coordinates per
+//                     vertex: the shading normal is the barycentric blend of the vertex
+//                     normals, normalised; the albedo of a diffuse material is multiplied by a
+//                     bilinear, wrapping lookup of its texture at the blended coordinates.
 //  Parity unpinned: none of the functions exported here; every one is pinned by a CPU test.
 #include <algorithm>
 #include <array>
@@ -146,10 +150,19 @@ struct BVHNode {
     int first, count; // triangle range in `order` (leaf)
 };
 
+// Per-vertex shading data of one triangle (Sec. 3.1 stores a normal and texture coordinates
+// with each vertex of a triangle).
+struct Shading {
+    bool normals;
+    V3 n[3];
+    double st[3][2];  // texture coordinates (s, t) of the three vertices
+};
+
 struct Mesh {
     std::vector<Tri> tris;
     std::vector<BVHNode> nodes;
     std::vector<int> order;
+    std::vector<Shading> shade;  // empty: face normals, no texture coordinates
 };
 
 void bvh_build(Mesh& M) {
@@ -421,6 +434,29 @@ void* orc_mesh_create(const float* verts, int64_t nv, const int32_t* tris, int64
 
 void orc_mesh_destroy(void* m) { delete (Mesh*)m; }
 
+// Per-vertex normals [nv][3] (NULL: face normals) and texture coordinates [nv][2] (NULL: none),
+// gathered per triangle through the index buffer. Returns -1 on a zero normal.
+int32_t orc_mesh_set_attributes(void* mesh, const float* normals, const float* st, const int32_t* tris,
+                                int64_t nt) {
+    Mesh& M = *(Mesh*)mesh;
+    if ((int64_t)M.tris.size() != nt) return -1;
+    M.shade.assign(nt, Shading{});
+    for (int64_t i = 0; i < nt; ++i) {
+        Shading& A = M.shade[i];
+        A.normals = normals != nullptr;
+        for (int k = 0; k < 3; ++k) {
+            const int64_t v = tris[3 * i + k];
+            if (normals) {
+                A.n[k] = {normals[3 * v], normals[3 * v + 1], normals[3 * v + 2]};
+                if (!(norm(A.n[k]) > 0)) return -1;
+            }
+            A.st[k][0] = st ? st[2 * v] : 0.0;
+            A.st[k][1] = st ? st[2 * v + 1] : 0.0;
+        }
+    }
+    return 0;
+}
+
 // rays: [n][8] = ox oy oz tmin dx dy dz tmax. mode 0 = brute force, 1 = oracle BVH.
 // nondeg may be null.
 void orc_closest_hit(void* mesh, const float* rays, int64_t n, int32_t mode, int32_t* out_id,
@@ -481,11 +517,19 @@ struct HitPoint {
     V3 x, n, w;
     int mat;
     Deriv dw;
+    V3 tex;  // texture factor of the albedo at the hit point (1 without a texture)
+};
+
+// Albedo texture of a material: rgb factors, row-major [h][w][3]; w = 0 means none.
+struct Texture {
+    int w = 0, h = 0;
+    std::vector<double> rgb;
 };
 
 struct Sppm {
     const Mesh* mesh;
     std::vector<orc_material> mats;
+    std::vector<Texture> tex;  // per material
     orc_camera cam;
     orc_sppm_params P;
     V3 eye, fwd, right, up;
@@ -556,6 +600,59 @@ V3 dielectric(const V3& d, const V3& n, double ior, float u) {
     return d * eta + nf * (eta * cosi - cost);
 }
 
+// Bilinear lookup with wrapping at texture coordinates (s, t): texel (i, j) covers
+// [i/w, (i+1)/w) x [j/h, (j+1)/h) and holds its value at the centre; between centres the four
+// nearest texels are blended with the usual bilinear weights, across the border with the texels
+// of the opposite side.
+V3 bilinear(const Texture& X, double s, double t) {
+    s -= std::floor(s);
+    t -= std::floor(t);
+    const double x = s * X.w - 0.5, y = t * X.h - 0.5;
+    const double x0 = std::floor(x), y0 = std::floor(y);
+    const double fx = x - x0, fy = y - y0;
+    auto wrap = [](int64_t i, int n) { return (int)(((i % n) + n) % n); };
+    const int i0 = wrap((int64_t)x0, X.w), i1 = wrap((int64_t)x0 + 1, X.w);
+    const int j0 = wrap((int64_t)y0, X.h), j1 = wrap((int64_t)y0 + 1, X.h);
+    auto T = [&](int i, int j) {
+        const double* q = &X.rgb[3 * ((size_t)j * X.w + i)];
+        return V3{q[0], q[1], q[2]};
+    };
+    return T(i0, j0) * ((1 - fx) * (1 - fy)) + T(i1, j0) * (fx * (1 - fy)) + T(i0, j1) * ((1 - fx) * fy) +
+           T(i1, j1) * (fx * fy);
+}
+
+// Shading at a hit: the shading normal (the blend of the vertex normals at the hit's
+// barycentrics, normalised and turned into the geometric normal's hemisphere; the face normal
+// without vertex normals) and the texture factor of a diffuse material's albedo.
+struct Surface {
+    V3 ns, tex;
+    bool smooth;  // ns comes from vertex normals
+};
+
+Surface surface(const Sppm& S, const Hit& h) {
+    const Tri& T = S.mesh->tris[h.id];
+    Surface sf{T.n, {1, 1, 1}, false};
+    if (S.mesh->shade.empty()) return sf;
+    const Shading& A = S.mesh->shade[h.id];
+    const double b0 = 1.0 - h.u - h.v, b1 = h.u, b2 = h.v;
+    if (A.normals) {
+        V3 n = A.n[0] * b0 + A.n[1] * b1 + A.n[2] * b2;
+        const double l = norm(n);
+        if (l > 0) {
+            n = n * (1.0 / l);
+            sf.ns = dot(n, T.n) < 0 ? n * -1.0 : n;
+            sf.smooth = true;
+        }
+    }
+    const Texture& X = S.tex[T.mat];
+    if (X.w > 0 && S.mats[T.mat].type == 0) {  // diffuse
+        const double s = A.st[0][0] * b0 + A.st[1][0] * b1 + A.st[2][0] * b2;
+        const double t = A.st[0][1] * b0 + A.st[1][1] * b1 + A.st[2][1] * b2;
+        sf.tex = bilinear(X, s, t);
+    }
+    return sf;
+}
+
 Hit trace(const Sppm& S, const V3& o, const V3& d, double tmin) {
     if (S.mesh->tris.size() <= 64) return closest_brute(*S.mesh, o, d, tmin, INFINITY);
     return closest_bvh(*S.mesh, o, d, tmin, INFINITY);
@@ -594,8 +691,9 @@ HitPoint eye_path(const Sppm& S, int64_t pix, V3& direct_add, double* ddirect_ad
         }
         if (m.type == EMITTER) break;
         V3 x = o + d * h.t;
+        const Surface sf = surface(S, h);
         if (m.type == DIFFUSE) {
-            hp = {true, x, front ? T.n : T.n * -1.0, w, T.mat, dw};
+            hp = {true, x, front ? T.n : T.n * -1.0, w, T.mat, dw, sf.tex};
             break;
         }
         if (m.type == MIRROR) {
@@ -607,10 +705,10 @@ HitPoint eye_path(const Sppm& S, int64_t pix, V3& direct_add, double* ddirect_ad
                 }
             }
             w = mul(w, albedo(m));
-            d = reflect(d, T.n);
+            d = reflect(d, sf.ns);
         } else {  // dielectric
             float uf = rng_next(rng);
-            d = dielectric(d, T.n, m.ior, uf);
+            d = dielectric(d, sf.ns, m.ior, uf);
         }
         o = x;
         tmin = S.P.eps;
@@ -650,24 +748,28 @@ Step photon_bounce(const Sppm& S, Rng& rng, const Hit& h, V3& o, V3& d, V3& phi,
     const orc_material& m = S.mats[T.mat];
     if (m.type == EMITTER) return STOP;
     V3 x = o + d * h.t;
+    const Surface sf = surface(S, h);
     if (m.type == DIFFUSE) {
         Photon p{x, d, phi, id, 0.0f, dphi ? *dphi : Deriv()};
         if (S.P.hash_mode == 1) p.z = rng_next(rng);
         out.push_back(p);
         float urr = rng_next(rng);
         if (!((double)urr < (double)S.P.rr_continue)) return STOP;
-        if (dphi) {  // phi' = phi * rho_m / p_c
+        if (dphi) {  // phi' = phi * rho_m * tex / p_c
             const double rr = (double)S.P.rr_continue, a[3] = {m.albedo[0], m.albedo[1], m.albedo[2]},
-                         pc[3] = {phi.x, phi.y, phi.z};
+                         pc[3] = {phi.x, phi.y, phi.z}, tx[3] = {sf.tex.x, sf.tex.y, sf.tex.z};
             for (int c = 0; c < 3; ++c) {
-                for (int j = 0; j < S.NG; ++j) (*dphi)[c * S.NG + j] *= a[c] / rr;
-                (*dphi)[c * S.NG + T.mat] += pc[c] / rr;
+                for (int j = 0; j < S.NG; ++j) (*dphi)[c * S.NG + j] *= a[c] * tx[c] / rr;
+                (*dphi)[c * S.NG + T.mat] += pc[c] * tx[c] / rr;
             }
         }
-        phi = mul(phi, albedo(m)) * (1.0 / (double)S.P.rr_continue);
-        V3 ns = dot(d, T.n) < 0 ? T.n : T.n * -1.0;
+        phi = mul(mul(phi, albedo(m)), sf.tex) * (1.0 / (double)S.P.rr_continue);
+        const bool fr = dot(d, T.n) < 0;
+        V3 ns = fr ? sf.ns : sf.ns * -1.0;
         float ua = rng_next(rng), ub = rng_next(rng);
         d = cosine_dir(ns, ua, ub);
+        // a direction sampled about a shading normal can point into the surface: the path ends
+        if (sf.smooth && !(dot(d, fr ? T.n : T.n * -1.0) > 0)) return STOP;
     } else if (m.type == MIRROR) {
         if (dphi) {  // phi' = phi * a_m
             const double a[3] = {m.albedo[0], m.albedo[1], m.albedo[2]}, pc[3] = {phi.x, phi.y, phi.z};
@@ -677,10 +779,10 @@ Step photon_bounce(const Sppm& S, Rng& rng, const Hit& h, V3& o, V3& d, V3& phi,
             }
         }
         phi = mul(phi, albedo(m));
-        d = reflect(d, T.n);
+        d = reflect(d, sf.ns);
     } else {
         float uf = rng_next(rng);
-        d = dielectric(d, T.n, m.ior, uf);
+        d = dielectric(d, sf.ns, m.ior, uf);
     }
     o = x;
     return CONTINUE;
@@ -786,13 +888,15 @@ void sppm_pass(Sppm& S, int nthreads) {
     // d(f * phi_k) for f = w * rho_{m_p} / pi (the hit point's weight), scaled by `scale`
     auto add_dflux = [&](const HitPoint& hp, const Photon& q, double scale, double* out) {
         const orc_material& m = S.mats[hp.mat];
-        const double a[3] = {m.albedo[0], m.albedo[1], m.albedo[2]}, wc[3] = {hp.w.x, hp.w.y, hp.w.z},
-                     pc[3] = {q.phi.x, q.phi.y, q.phi.z};
+        // f = w * rho_m * tex / pi: tex is a constant factor of the albedo
+        const double tx[3] = {hp.tex.x, hp.tex.y, hp.tex.z},
+                     a[3] = {m.albedo[0] * tx[0], m.albedo[1] * tx[1], m.albedo[2] * tx[2]},
+                     wc[3] = {hp.w.x, hp.w.y, hp.w.z}, pc[3] = {q.phi.x, q.phi.y, q.phi.z};
         for (int c = 0; c < 3; ++c) {
             const double f = wc[c] * a[c] / kPi;
             for (int j = 0; j < NG; ++j)
                 out[c * NG + j] += scale * (hp.dw[c * NG + j] * a[c] / kPi * pc[c] + f * q.dphi[c * NG + j]);
-            out[c * NG + hp.mat] += scale * wc[c] / kPi * pc[c];
+            out[c * NG + hp.mat] += scale * wc[c] * tx[c] / kPi * pc[c];
         }
     };
     const double h = S.P.cell_h;
@@ -824,7 +928,7 @@ void sppm_pass(Sppm& S, int nthreads) {
                             }
                         }
                 std::sort(acc.begin(), acc.end(), [&](int a2, int b2) { return ph[a2].id < ph[b2].id; });
-                V3 f = mul(hp.w, albedo(S.mats[hp.mat])) * (1.0 / kPi);
+                V3 f = mul(mul(hp.w, albedo(S.mats[hp.mat])), hp.tex) * (1.0 / kPi);
                 V3 sum{0, 0, 0};
                 for (int i : acc) sum = sum + mul(f, ph[i].phi);
                 if (S.grad)
@@ -862,7 +966,7 @@ void sppm_pass(Sppm& S, int nthreads) {
                     lo[k] = cell_of(comp(hp.x, k) - R, h);
                     hi[k] = cell_of(comp(hp.x, k) + R, h);
                 }
-                V3 f = mul(hp.w, albedo(S.mats[hp.mat])) * (1.0 / kPi);
+                V3 f = mul(mul(hp.w, albedo(S.mats[hp.mat])), hp.tex) * (1.0 / kPi);
                 V3 sum{0, 0, 0};
                 double M = 0;
                 for (int64_t cx = lo[0]; cx <= hi[0]; ++cx)
@@ -944,6 +1048,7 @@ void* orc_sppm_create(void* mesh, const orc_material* mats, int32_t nmat, const 
     S->R.assign(npix, (double)params->r0);
     S->tau.assign(3 * npix, 0.0);
     S->direct.assign(3 * npix, 0.0);
+    S->tex.assign(nmat, Texture{});
     int64_t np = params->photons_per_pass;
     S->ro.assign(np, V3{0, 0, 0});
     S->rd.assign(np, V3{0, 0, 0});
@@ -954,6 +1059,39 @@ void* orc_sppm_create(void* mesh, const orc_material* mats, int32_t nmat, const 
 }
 
 void orc_sppm_destroy(void* s) { delete (Sppm*)s; }
+
+// Albedo texture of material `mat`: rgb [h][w][3] (applies to diffuse materials).
+int32_t orc_sppm_set_texture(void* s, int32_t mat, const float* rgb, int32_t w, int32_t h) {
+    Sppm* S = (Sppm*)s;
+    if (mat < 0 || mat >= (int32_t)S->mats.size() || w < 1 || h < 1 || !rgb) return -1;
+    Texture& X = S->tex[mat];
+    X.w = w;
+    X.h = h;
+    X.rgb.assign(rgb, rgb + 3 * (size_t)w * h);
+    return 0;
+}
+
+// Shading at the closest hit of each ray [n][8]: out[n][10] = id, u, v, shading normal (3),
+// texture factor (3), 1 if the normal comes from vertex normals (id -1: no hit).
+void orc_sppm_surface(void* s, const float* rays, int64_t n, double* out) {
+    const Sppm& S = *(const Sppm*)s;
+    for (int64_t i = 0; i < n; ++i) {
+        const float* r = rays + 8 * i;
+        V3 o{r[0], r[1], r[2]}, d{r[4], r[5], r[6]};
+        const Mesh& M = *S.mesh;
+        Hit h = M.tris.size() <= 64 ? closest_brute(M, o, d, r[3], r[7]) : closest_bvh(M, o, d, r[3], r[7]);
+        double* q = out + 10 * i;
+        std::fill(q, q + 10, 0.0);
+        q[0] = h.id;
+        if (h.id < 0) continue;
+        const Surface sf = surface(S, h);
+        q[1] = h.u;
+        q[2] = h.v;
+        q[3] = sf.ns.x; q[4] = sf.ns.y; q[5] = sf.ns.z;
+        q[6] = sf.tex.x; q[7] = sf.tex.y; q[8] = sf.tex.z;
+        q[9] = sf.smooth ? 1.0 : 0.0;
+    }
+}
 
 int32_t orc_sppm_run(void* s, int32_t npasses, int32_t nthreads) {
     Sppm* S = (Sppm*)s;

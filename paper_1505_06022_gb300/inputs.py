@@ -11,6 +11,9 @@ Scene conventions shared by every consumer:
 * ``tri_mat`` int32  [nt]       material index per triangle
 * ``mats``   MATERIAL_DTYPE [nm] material table (type, albedo RGB, emission RGB, ior)
 * ``camera`` CAMERA_DTYPE  [1]  pinhole camera (eye, look-at point, up, vertical fov, w, h)
+* optional shading data: ``normals`` float32 [nv, 3] per-vertex normals, ``texcoords`` float32
+  [nv, 2] per-vertex texture coordinates, ``textures`` {material index: float32 [h, w, 3]}
+  albedo factors of diffuse materials
 
 Material types: DIFFUSE (two-sided Lambertian; may also emit from its front face), MIRROR,
 DIELECTRIC, EMITTER (one-sided Lambertian emitter that absorbs everything it receives).
@@ -47,6 +50,9 @@ class Scene:
     camera: np.ndarray
     name: str = "scene"
     info: dict = field(default_factory=dict)
+    normals: np.ndarray | None = None
+    texcoords: np.ndarray | None = None
+    textures: dict = field(default_factory=dict)
 
     @property
     def ntris(self) -> int:
@@ -321,6 +327,68 @@ def full_scene(seed: int = 3, width: int = 512, height: int = 512, plane_quads: 
     verts, tris, tri_mat = mb.build()
     cam = camera((0, 2.2, 5.0), (0, 0.4, 0), (0, 1, 0), 40.0, width, height)
     return Scene(verts, tris, tri_mat, np.concatenate(mats), cam, name=f"full{len(tris)}")
+
+
+def vertex_normals(verts, tris):
+    """Area-weighted average of the faces' normals around each vertex (float64, unit)."""
+    v = np.asarray(verts, np.float64)
+    t = np.asarray(tris, np.int64)
+    fn = np.cross(v[t[:, 1]] - v[t[:, 0]], v[t[:, 2]] - v[t[:, 0]])  # length = 2 * area
+    acc = np.zeros_like(v)
+    for k in range(3):
+        np.add.at(acc, t[:, k], fn)
+    return acc / np.linalg.norm(acc, axis=1, keepdims=True)
+
+
+def pattern_texture(size: int, seed: int, squares: int = 8) -> np.ndarray:
+    """Seeded RGB albedo factors in [0.35, 1]: a checkerboard of two random colours with a smooth
+    sinusoidal shading on top. float32 [size, size, 3]."""
+    rng = np.random.default_rng(seed)
+    c0, c1 = rng.uniform(0.5, 1.0, 3), rng.uniform(0.35, 0.7, 3)
+    j, i = np.meshgrid(np.arange(size), np.arange(size), indexing="ij")
+    check = ((i * squares // size) + (j * squares // size)) % 2
+    base = np.where(check[..., None] == 0, c0, c1)
+    f = rng.uniform(1.0, 3.0, 2)
+    shade = 0.85 + 0.15 * np.sin(2 * np.pi * (f[0] * i / size + f[1] * j / size))[..., None]
+    return np.clip(base * shade, 0.35, 1.0).astype(np.float32)
+
+
+def shaded_scene(seed: int = 6, width: int = 512, height: int = 512, plane_quads: int = 256,
+                 sphere_n: int = 44, tex_size: int = 256) -> Scene:
+    """The full scene's layout with per-vertex shading data: smooth normals on every sphere
+    (radial) and on the displaced plane (area-weighted), texture coordinates (the plane tiled
+    4 x 4, the spheres in longitude/latitude) and albedo textures on the plane and the diffuse
+    sphere. Defaults: 247,234 triangles, two 256^2 textures."""
+    rng = np.random.default_rng(seed)
+    mats = [material(DIFFUSE, rng.uniform(0.5, 0.9, 3)),
+            material(DIELECTRIC, (1, 1, 1), ior=1.5),
+            material(MIRROR, (0.9, 0.9, 0.9)),
+            material(DIFFUSE, rng.uniform(0.5, 0.9, 3)),
+            material(EMITTER, (0, 0, 0), (40.0, 38.0, 34.0))]
+    mb = _MeshBuilder()
+    nrm, st = [], []
+    half = 2.5
+    v, t = displaced_plane(plane_quads, half, seed, amp=0.04)
+    mb.add(v, t, 0)
+    nrm.append(vertex_normals(v, t))
+    st.append(np.stack([(v[:, 0] + half) / (2 * half) * 4.0, (v[:, 2] + half) / (2 * half) * 4.0], 1))
+    for k, (cx, cz) in enumerate([(-1.1, 0.0), (0.0, -0.8), (1.1, 0.3)]):
+        c = np.array([cx, 0.62, cz])
+        v, t = displaced_icosphere(sphere_n, seed + 10 + k, amp=0.0, center=c, radius=0.5)
+        mb.add(v, t, 1 + k)
+        n = (v - c) / np.linalg.norm(v - c, axis=1, keepdims=True)
+        nrm.append(n)
+        st.append(np.stack([0.5 + np.arctan2(n[:, 2], n[:, 0]) / (2 * np.pi),
+                            np.arccos(np.clip(n[:, 1], -1.0, 1.0)) / np.pi], 1))
+    s, y = 0.5, 3.0
+    mb.quad([-s, y, -s], [s, y, -s], [s, y, s], [-s, y, s], 4)
+    nrm.append(np.tile([0.0, -1.0, 0.0], (4, 1)))
+    st.append(np.zeros((4, 2)))
+    verts, tris, tri_mat = mb.build()
+    cam = camera((0, 2.2, 5.0), (0, 0.4, 0), (0, 1, 0), 40.0, width, height)
+    return Scene(verts, tris, tri_mat, np.concatenate(mats), cam, name=f"shaded{len(tris)}",
+                 normals=np.concatenate(nrm).astype(np.float32), texcoords=np.concatenate(st).astype(np.float32),
+                 textures={0: pattern_texture(tex_size, seed + 1), 3: pattern_texture(tex_size, seed + 2, 6)})
 
 
 def grad_scene(seed: int = 4, width: int = 256, height: int = 256, plane_quads: int = 128,
