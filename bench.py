@@ -11,6 +11,8 @@ Default workload (one line of JSON on rank 0):
   * "traversal_fig4": MTBVH vs TBVH vs stack traversal (Fig. 4) and the device BVH build.
   * "sppm_512": SPPM passes/s at 512x512 on a 247,234-triangle scene with 1M photon paths/pass
     (a 64-pass render; default and autotuned settings).
+  * "sppm_512_shaded": the 512x512 render with per-vertex normals, texture coordinates and albedo
+    textures, against the same geometry without them.
   * "grad_256": backward/forward time of the path-replay adjoint (256x256, 8 passes).
   * "batch_64": 64 scenes as one graph per pass vs one renderer after another.
   * "sppm_modes": the paper's photon-pass / hashing variants at equal image error.
@@ -296,6 +298,7 @@ def run_ours(args, world, rank, local):
     fig4 = bench_traversals(args, ctx, dev, stream, sc, scene, rays) if not args.skip_fig4 else None
     cornell = bench_cornell(args, ctx, dev, stream, with_cpu(args, world, rank)) if not args.skip_sppm else None
     sppm = bench_sppm(args, ctx, dev, stream, pg) if not args.skip_sppm else None
+    shaded = bench_shaded(args, ctx, dev, stream, pg) if not (args.skip_sppm or args.skip_shaded) else None
     grad = bench_grad(args, ctx, dev, stream) if not args.skip_grad else None
     batch = bench_batch(args, ctx, dev, stream) if not args.skip_batch else None
     modes = bench_modes(args, ctx, dev, stream) if not args.skip_modes else None
@@ -329,6 +332,7 @@ def run_ours(args, world, rank, local):
             "traversal_fig4": fig4,
             "sppm_cornell_64": cornell,
             "sppm_512": sppm,
+            "sppm_512_shaded": shaded,
             "grad_256": grad,
             "batch_64": batch,
             "sppm_modes": modes,
@@ -440,6 +444,42 @@ def bench_sppm(args, ctx, dev, stream, pg):
     tuned.close()
     r.close()
     s.close()
+    return out
+
+
+def bench_shaded(args, ctx, dev, stream, pg):
+    """The 512^2 SPPM render with per-vertex shading data (smooth normals on every surface,
+    texture coordinates, two 256^2 albedo textures) against the same geometry without it."""
+    import copy
+    import torch
+    from paper_1505_06022_gb300 import gsp, inputs as I
+    sc = I.shaded_scene(seed=6)
+    flat = copy.copy(sc)
+    flat.normals, flat.texcoords, flat.textures = None, None, {}
+    kw = dict(photons_per_pass=1 << 20, seed=6, r0_frac=0.004)
+    k = args.sppm_passes
+    out = {}
+    for name, scene in (("shaded", sc), ("no_shading_data", flat)):
+        s = gsp.Scene(ctx, scene)
+        params = gsp.sppm_params(scene, **kw)
+        warm = gsp.Renderer(s, params)
+        warm.run(3, stream)
+        torch.cuda.synchronize()
+        warm.close()
+        r = gsp.Renderer(s, params)
+        ms = max_over_ranks(timed_passes(r, k, stream), pg, dev)
+        out[name] = {"ms_per_pass": round(ms, 3), "passes_per_s": round(1000.0 / ms, 2)}
+        r.close()
+        s.close()
+    out["passes_timed"] = k
+    out["shading_cost"] = round(out["shaded"]["ms_per_pass"] / out["no_shading_data"]["ms_per_pass"], 3)
+    out["config"] = ("512x512, 247,234 triangles, smooth vertex normals (radial on the spheres, area-weighted on the "
+                     "plane), texture coordinates, 256^2 albedo textures on the plane and the diffuse sphere, "
+                     "1,048,576 photon paths/pass, r0 = 0.004 * diagonal, full paths + exact hash grid")
+    if with_cpu(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))):
+        oms, cores = oracle_sppm(sc, kw, 2)
+        out["cpu_oracle"] = {"ms_per_pass": round(oms, 1), "passes_per_s": round(1000.0 / oms, 3), "cores": cores,
+                             "passes": 2, "sample": "the first 2 passes of the shaded render, FP64 oracle"}
     return out
 
 
@@ -666,6 +706,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sppm-passes", type=int, default=64)
     ap.add_argument("--skip-sppm", action="store_true")
+    ap.add_argument("--skip-shaded", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-fig4", action="store_true")

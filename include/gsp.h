@@ -187,6 +187,31 @@ gsp_status gsp_scene_set_materials(gsp_scene* scene, const gsp_material* mats, i
  * worst-case work, and for testing the failure path without corrupting a BVH. */
 gsp_status gsp_scene_set_step_limit(gsp_scene* scene, int32_t max_box_tests);
 
+/* Per-vertex shading data (Sec. 3.1: the threaded BVH's triangle record carries a normal and
+ * texture coordinates at each vertex). Host arrays in upload order, copied:
+ *   normals   [nv][3] per-vertex normals of any nonzero length, or NULL (face normals)
+ *   texcoords [nv][2] per-vertex texture coordinates (s, t), or NULL (none)
+ * At a hit the shading normal is the blend of the triangle's three vertex normals with the hit's
+ * barycentric weights, normalised and turned into the geometric normal's hemisphere. It gives
+ * the directions of mirror and dielectric bounces and the axis of a diffuse photon bounce's
+ * cosine-distributed direction (a direction that points into the surface ends the photon path).
+ * The geometric normal still decides the side a ray arrives from (emission, the photon
+ * acceptance test). Both NULL removes the data. Takes effect for passes started afterwards (a
+ * batch graph captured earlier keeps what it captured).
+ * Errors: INVALID_ARG (non-finite value, zero normal); BAD_STATE (texcoords NULL while a
+ * material has a texture); OOM; CUDA. */
+gsp_status gsp_scene_set_attributes(gsp_scene* scene, const float* normals, const float* texcoords);
+
+/* Albedo texture of a DIFFUSE material: rgb [height][width][3] factors (finite, >= 0) that
+ * multiply the material's albedo. The lookup is bilinear with wrap-around at the blended texture
+ * coordinates: texel (i, j) covers [i/width, (i+1)/width) x [j/height, (j+1)/height) and holds
+ * its value at its centre. rgb NULL removes the texture. Host array, copied.
+ * Errors: INVALID_ARG (material out of range or not DIFFUSE, width or height outside 1..16384,
+ * more than 2^26 texels, a non-finite or negative value); BAD_STATE (the scene has no texture
+ * coordinates); OOM; CUDA. */
+gsp_status gsp_scene_set_texture(gsp_scene* scene, int32_t material, const float* rgb, int32_t width,
+                                 int32_t height);
+
 /* Builds the SAH BVH and its hit/miss links on the host (Sec. 3.1), packs them, and uploads
  * them to the device (replacing any previous BVH). params NULL = defaults. stats may be NULL. */
 gsp_status gsp_build_bvh(gsp_scene* scene, const gsp_bvh_params* params, gsp_bvh_stats* stats);

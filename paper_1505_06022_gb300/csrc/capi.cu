@@ -216,6 +216,9 @@ gspd::DevScene gsp_dev_scene(const gsp_scene* s) {
     d.shade = s->d_shade;
     d.nlo = s->d_nlo;
     d.mats = s->d_mats;
+    d.attr = s->d_attr;
+    d.texels = s->d_texels;
+    d.mtex = s->d_mtex;
     d.nnodes = s->bvh.nnodes;
     d.stride = s->bvh.stride;
     d.link_sets = s->bvh.link_sets;
@@ -320,6 +323,9 @@ void gsp_scene_destroy(gsp_scene* s) {
         cudaFree(s->d_mats);
         cudaFree(s->d_counter);
         cudaFree(s->d_rlist);
+        cudaFree(s->d_attr);
+        cudaFree(s->d_texels);
+        cudaFree(s->d_mtex);
         host_lanes_free(s);
     }
     delete s;
@@ -443,6 +449,104 @@ gsp_status gsp_scene_set_materials(gsp_scene* s, const gsp_material* mats, int32
 gsp_status gsp_scene_set_step_limit(gsp_scene* s, int32_t max_box_tests) {
     if (!s || max_box_tests < 0) return GSP_ERR_INVALID_ARG;
     s->step_limit = max_box_tests;
+    return GSP_OK;
+}
+
+gsp_status gsp_scene_set_attributes(gsp_scene* s, const float* normals, const float* texcoords) {
+    if (!s) return GSP_ERR_INVALID_ARG;
+    const int64_t nv = s->nv, nt = s->nt;
+    if (normals)
+        for (int64_t v = 0; v < nv; ++v) {
+            const float* n = normals + 3 * v;
+            if (!std::isfinite(n[0]) || !std::isfinite(n[1]) || !std::isfinite(n[2]) ||
+                (double)n[0] * n[0] + (double)n[1] * n[1] + (double)n[2] * n[2] == 0.0)
+                return GSP_ERR_INVALID_ARG;
+        }
+    if (texcoords)
+        for (int64_t i = 0; i < 2 * nv; ++i)
+            if (!std::isfinite(texcoords[i])) return GSP_ERR_INVALID_ARG;
+    if (!texcoords)
+        for (const auto& t : s->tex)
+            if (!t.empty()) {
+                gsp_set_last_error("gsp_scene_set_attributes: remove the scene's textures before its texture coordinates");
+                return GSP_ERR_BAD_STATE;
+            }
+    if (s->ctx) GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    (void)cudaGetLastError();
+    cudaFree(s->d_attr);
+    s->d_attr = nullptr;
+    s->has_texcoords = false;
+    if (!normals && !texcoords) return GSP_OK;
+    s->has_texcoords = texcoords != nullptr;
+    if (!s->ctx) return GSP_OK;
+    // gathered per triangle so that a hit reads its shading data with four aligned loads
+    std::vector<float4> rec(4 * (size_t)nt);
+    const int32_t flags = normals ? 1 : 0;
+    float ff;
+    std::memcpy(&ff, &flags, 4);
+    for (int64_t i = 0; i < nt; ++i) {
+        float t3[3];
+        for (int k = 0; k < 3; ++k) {
+            const int64_t v = s->tris[3 * i + k];
+            const float* n = normals ? normals + 3 * v : nullptr;
+            rec[4 * i + k] = float4{n ? n[0] : 0.0f, n ? n[1] : 0.0f, n ? n[2] : 0.0f, texcoords ? texcoords[2 * v] : 0.0f};
+            t3[k] = texcoords ? texcoords[2 * v + 1] : 0.0f;
+        }
+        rec[4 * i + 3] = float4{t3[0], t3[1], t3[2], ff};
+    }
+    GSP_CUDA_TRY(cudaMalloc(&s->d_attr, rec.size() * sizeof(float4)));
+    GSP_CUDA_TRY(cudaMemcpy(s->d_attr, rec.data(), rec.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    return GSP_OK;
+}
+
+gsp_status gsp_scene_set_texture(gsp_scene* s, int32_t material, const float* rgb, int32_t width, int32_t height) {
+    if (!s || material < 0 || material >= s->nmat) return GSP_ERR_INVALID_ARG;
+    if (rgb) {
+        if (s->mats[material].type != GSP_DIFFUSE || width < 1 || height < 1 || width > 16384 || height > 16384 ||
+            (int64_t)width * height > (int64_t(1) << 26))
+            return GSP_ERR_INVALID_ARG;
+        for (int64_t i = 0; i < 3 * (int64_t)width * height; ++i)
+            if (!std::isfinite(rgb[i]) || rgb[i] < 0.0f) return GSP_ERR_INVALID_ARG;
+        if (!s->has_texcoords) {
+            gsp_set_last_error("gsp_scene_set_texture: the scene has no texture coordinates (gsp_scene_set_attributes)");
+            return GSP_ERR_BAD_STATE;
+        }
+        int64_t others = 0;  // texel offsets are int32
+        for (int32_t m = 0; m < (int32_t)s->tex.size(); ++m)
+            if (m != material) others += (int64_t)s->tex[m].size();
+        if (others + (int64_t)width * height > INT32_MAX) return GSP_ERR_INVALID_ARG;
+    }
+    s->tex.resize(s->nmat);
+    s->tex_size.resize(s->nmat, int2{0, 0});
+    std::vector<float4>& t = s->tex[material];
+    t.clear();
+    s->tex_size[material] = int2{0, 0};
+    if (rgb) {
+        t.resize((size_t)width * height);
+        for (size_t i = 0; i < t.size(); ++i) t[i] = float4{rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], 0.0f};
+        s->tex_size[material] = int2{width, height};
+    }
+    if (!s->ctx) return GSP_OK;
+    GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    (void)cudaGetLastError();
+    cudaFree(s->d_texels);
+    cudaFree(s->d_mtex);
+    s->d_texels = nullptr;
+    s->d_mtex = nullptr;
+    int64_t total = 0;
+    std::vector<int4> mt(s->nmat, int4{0, 0, 0, 0});
+    for (int32_t m = 0; m < s->nmat; ++m) {
+        mt[m] = int4{(int32_t)total, s->tex_size[m].x, s->tex_size[m].y, 0};
+        total += (int64_t)s->tex[m].size();
+    }
+    if (total == 0) return GSP_OK;  // no material has a texture: kernels skip the lookup
+    GSP_CUDA_TRY(cudaMalloc(&s->d_texels, total * sizeof(float4)));
+    GSP_CUDA_TRY(cudaMalloc(&s->d_mtex, mt.size() * sizeof(int4)));
+    for (int32_t m = 0; m < s->nmat; ++m)
+        if (!s->tex[m].empty())
+            GSP_CUDA_TRY(cudaMemcpy(s->d_texels + mt[m].x, s->tex[m].data(), s->tex[m].size() * sizeof(float4),
+                                    cudaMemcpyHostToDevice));
+    GSP_CUDA_TRY(cudaMemcpy(s->d_mtex, mt.data(), mt.size() * sizeof(int4), cudaMemcpyHostToDevice));
     return GSP_OK;
 }
 

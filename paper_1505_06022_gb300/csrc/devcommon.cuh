@@ -106,6 +106,9 @@ struct DevScene {
     const float4* __restrict__ nlo;    // per triangle (upload order): FP32 remainder of the normal
     const float4* __restrict__ mats;   // 2 per material
     const float4* __restrict__ bin;    // child-pair layout of the same tree (stack traversal)
+    const float4* __restrict__ attr;   // per triangle (upload order): vertex normals + texture coordinates, or null
+    const float4* __restrict__ texels; // albedo textures
+    const int4* __restrict__ mtex;     // per material: {first texel, width, height, 0}, or null
     int64_t nnodes;
     int64_t stride;  // nodes per link set in memory (nnodes + 1 padding node)
     int32_t link_sets;
@@ -117,6 +120,7 @@ struct DevScene {
 struct Hit {
     int32_t id;  // triangle index in upload order, -1 = none
     float t, u, v;
+    int32_t slot;  // SPPM hits: the triangle's leaf-ordered slot (its vertices), -1 = not known
 };
 
 // Ray direction class for the multiple-threaded BVH (replaces Fig. 3's cubemap lookup):

@@ -67,6 +67,13 @@ struct gsp_scene {
     int64_t rlist_cap = 0;
     bool built = false;
     int32_t step_limit = 0;  // gsp_scene_set_step_limit (0 = the default cap)
+    // per-vertex shading data (gsp_scene_set_attributes, gsp_scene_set_texture)
+    float4* d_attr = nullptr;  // per triangle (upload order): {n0, s0}, {n1, s1}, {n2, s2}, {t0, t1, t2, flags}
+    bool has_texcoords = false;
+    std::vector<std::vector<float4>> tex;  // per material: texels {r, g, b, 0}, row-major (empty = none)
+    std::vector<int2> tex_size;            // per material: width, height
+    float4* d_texels = nullptr;            // every texture, one after the other
+    int4* d_mtex = nullptr;                // per material: {first texel, width, height, 0}; null if none
     HostBVH bvh;
     int64_t device_bytes = 0;
     // host-buffer tracing (gsp_trace_closest_hit_host): a pipeline of chunks over kHostLanes

@@ -177,6 +177,7 @@ struct PathQ {
 // A wavefront hit given as a leaf-ordered triangle slot: t from the triangle's plane in
 // double-float arithmetic (as in the persistent path kernel); returns the upload-order index.
 __device__ __forceinline__ int32_t slot_refine(const DevScene& S, float3 o, float3 d, Hit& h) {
+    h.slot = h.id;
     const int32_t id = __float_as_int(__ldg(S.tris + 3 * (int64_t)h.id).w);
     refine_plane(S.tris, S.shade, S.nlo, h.id, id, o, d, h.t);
     return id;
@@ -188,8 +189,90 @@ __device__ __forceinline__ Hit walk_hit(const DevScene& S, const Trav& st) {
     h.id = st.best;
     h.t = st.tbest;
     h.u = h.v = 0.0f;
+    h.slot = st.slot;
     if (st.slot >= 0) refine_plane(S.tris, S.shade, S.nlo, st.slot, h.id, st.o, st.d, h.t);
     return h;
+}
+
+// ------------------------------------------------------------------------------------------
+// per-vertex shading data (Sec. 3.1's triangle: a normal and texture coordinates per vertex)
+// ------------------------------------------------------------------------------------------
+struct Surf {
+    float3 ns;    // shading normal, in the geometric normal's hemisphere
+    float3 tex;   // factor of a diffuse albedo (1 without a texture)
+    bool smooth;  // ns blended from vertex normals
+};
+
+// Bilinear lookup with wrap-around of texture T = {first texel, w, h} at coordinates (s, t):
+// texel (i, j) holds its value at the centre of [i/w, (i+1)/w) x [j/h, (j+1)/h).
+__device__ __forceinline__ float3 tex_bilinear(const float4* __restrict__ texels, int4 T, float s, float t) {
+    s = s - floorf(s);
+    t = t - floorf(t);
+    const float x = s * (float)T.y - 0.5f, y = t * (float)T.z - 0.5f;
+    const float x0 = floorf(x), y0 = floorf(y);
+    const float fx = x - x0, fy = y - y0;
+    int i0 = (int)x0, j0 = (int)y0;  // -1 .. size - 1
+    if (i0 < 0) i0 += T.y;
+    if (j0 < 0) j0 += T.z;
+    const int i1 = i0 + 1 == T.y ? 0 : i0 + 1, j1 = j0 + 1 == T.z ? 0 : j0 + 1;
+    const float4* q = texels + T.x;
+    const float3 a = f3(__ldg(q + (int64_t)j0 * T.y + i0)), b = f3(__ldg(q + (int64_t)j0 * T.y + i1));
+    const float3 c = f3(__ldg(q + (int64_t)j1 * T.y + i0)), e = f3(__ldg(q + (int64_t)j1 * T.y + i1));
+    const float gx = 1.0f - fx, gy = 1.0f - fy;
+    return madd3(e, fx * fy, madd3(c, gx * fy, madd3(b, fx * gy, a * (gx * gy))));
+}
+
+// Shading from the per-vertex data of triangle `id` (vertices at leaf-ordered `slot`) for the
+// hit of ray (o, d) with geometric unit normal n: barycentric weights (Moller-Trumbore's u, v
+// for vertices 1 and 2; 1 - u - v for vertex 0), blended normal, texture lookup.
+__device__ __forceinline__ Surf surface_attr(const float4* __restrict__ attr, const float4* __restrict__ tris,
+                                          const float4* __restrict__ texels, const int4* __restrict__ mtex,
+                                          int32_t slot, int32_t id, float3 o, float3 d, float3 n, bool diffuse,
+                                          int32_t mid) {
+    Surf sf;
+    sf.ns = n;
+    sf.tex = make_float3(1.0f, 1.0f, 1.0f);
+    sf.smooth = false;
+    const float4* tv = tris + 3 * (int64_t)slot;
+    const float3 v0 = f3(__ldg(tv)), e1 = f3(__ldg(tv + 1)) - v0, e2 = f3(__ldg(tv + 2)) - v0;
+    const float3 p = cross3(d, e2);
+    const float f = 1.0f / dot3(e1, p);
+    const float3 s0 = o - v0;
+    const float b1 = f * dot3(s0, p), b2 = f * dot3(d, cross3(s0, e1)), b0 = 1.0f - b1 - b2;
+    const float4* a = attr + 4 * (int64_t)id;
+    const float4 a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2), a3 = __ldg(a + 3);
+    if (__float_as_int(a3.w) & 1) {
+        float3 nb = madd3(f3(a2), b2, madd3(f3(a1), b1, f3(a0) * b0));
+        const float l2 = dot3(nb, nb);
+        if (l2 > 0.0f) {
+            nb = nb * (1.0f / sqrtf(l2));
+            sf.ns = dot3(nb, n) < 0.0f ? nb * -1.0f : nb;
+            sf.smooth = true;
+        }
+    }
+    if (mtex && diffuse) {
+        const int4 T = __ldg(mtex + mid);
+        if (T.y > 0) {
+            const float s = __fmaf_rn(a2.w, b2, __fmaf_rn(a1.w, b1, a0.w * b0));
+            const float t = __fmaf_rn(a3.z, b2, __fmaf_rn(a3.y, b1, a3.x * b0));
+            sf.tex = tex_bilinear(texels, T, s, t);
+        }
+    }
+    return sf;
+}
+
+// Shading at hit h of ray (o, d) with geometric unit normal n and material m (index mid).
+// SHADE = false compiles the flat case only (kernels launched for scenes without shading data
+// keep the registers of the plain path).
+template <bool SHADE>
+__device__ __forceinline__ Surf surface(const DevScene& S, const Hit& h, float3 o, float3 d, float3 n,
+                                        const Material& m, int32_t mid) {
+    if (SHADE && S.attr) return surface_attr(S.attr, S.tris, S.texels, S.mtex, h.slot, h.id, o, d, n, m.type == GSP_DIFFUSE, mid);
+    Surf sf;
+    sf.ns = n;
+    sf.tex = make_float3(1.0f, 1.0f, 1.0f);
+    sf.smooth = false;
+    return sf;
 }
 
 // Appends the lanes with `keep` set to queue Q (warp-aggregated: one atomic per warp).
@@ -234,6 +317,7 @@ struct EyeOut {
 // direct term of this pass (one path per pixel, so no atomics);
 // a diffuse hit records the hit point and ends the path; a mirror or dielectric bends the ray
 // (returns true: the path continues from x along the new d).
+template <bool SHADE>
 __device__ __forceinline__ bool eye_interact(const DevScene& S, const PassDev& P, const EyeOut& O, int64_t p,
                                              const Hit& h, float3& o, float3& d, float3& w, Rng& rng) {
     const float4 sh = __ldg(S.shade + h.id);
@@ -250,20 +334,22 @@ __device__ __forceinline__ bool eye_interact(const DevScene& S, const PassDev& P
     }
     if (m.type == GSP_EMITTER) return false;
     const float3 x = madd3(d, h.t, o);
+    const Surf sf = surface<SHADE>(S, h, o, d, n, m, mid);
     if (m.type == GSP_DIFFUSE) {
         const float3 ns = front ? n : n * -1.0f;
-        const float3 f = mul3(w, m.albedo) * (1.0f / kPi);
+        const float3 wt = mul3(w, sf.tex);  // the hit point's weight without its albedo
+        const float3 f = mul3(wt, m.albedo) * (1.0f / kPi);
         O.hx[p] = make_float4(x.x, x.y, x.z, __int_as_float(mid));
         O.hn[p] = make_float4(ns.x, ns.y, ns.z, 0.0f);
         O.hf[p] = make_float4(f.x, f.y, f.z, 0.0f);
-        if (O.hw) O.hw[p] = make_float4(w.x, w.y, w.z, 0.0f);
+        if (O.hw) O.hw[p] = make_float4(wt.x, wt.y, wt.z, 0.0f);
         return false;
     }
     if (m.type == GSP_MIRROR) {
         w = mul3(w, m.albedo);
-        d = reflect3(d, n);
+        d = reflect3(d, sf.ns);
     } else {
-        d = dielectric(d, n, m.ior, rng_next(rng));
+        d = dielectric(d, sf.ns, m.ior, rng_next(rng));
     }
     o = x;
     return true;
@@ -302,6 +388,7 @@ k_eye_emit(CamDev C, PassDev P, PathQ Q, EyeOut O, uint32_t* __restrict__ qn, un
 }
 
 // Wavefront step b of the eye pass: shade the traced queue qn[b % 3], push continuing paths.
+template <bool SHADE>
 __global__ void __launch_bounds__(256)
 k_eye_shade(DevScene S, PassDev P, PathQ cur, PathQ nxt, EyeOut O, uint32_t* __restrict__ qn, int b,
             unsigned long long* __restrict__ trace_ctr) {
@@ -327,9 +414,10 @@ k_eye_shade(DevScene S, PassDev P, PathQ cur, PathQ nxt, EyeOut O, uint32_t* __r
             Hit h;
             h.id = cur.tri[i];
             h.t = cur.t[i];
+            h.slot = -1;
             if (h.id >= 0 && !P.tri_is_id) h.id = slot_refine(S, o, d, h);
             if (h.id >= 0) {
-                keep = eye_interact(S, P, O, p, h, o, d, w, rng) && depth + 1 <= P.max_eye;
+                keep = eye_interact<SHADE>(S, P, O, p, h, o, d, w, rng) && depth + 1 <= P.max_eye;
             }
         }
         queue_push(nxt, qn + (b + 1) % 3, keep, o, P.eps, d, w, p, rng, depth + 1);
@@ -369,6 +457,7 @@ struct DepositDev {
 };
 
 // One photon interaction at a hit. Returns false when the path ends.
+template <bool SHADE>
 __device__ __forceinline__ bool photon_bounce(const DevScene& S, const PassDev& P, const DepositDev& D,
                                               Rng& rng, const Hit& h, float3& o, float3& d, float3& phi,
                                               uint32_t id, uint32_t slot, uint32_t& ndep) {
@@ -377,6 +466,7 @@ __device__ __forceinline__ bool photon_bounce(const DevScene& S, const PassDev& 
     const Material m = load_mat(S, __float_as_int(sh.w));
     if (m.type == GSP_EMITTER) return false;
     const float3 x = madd3(d, h.t, o);
+    const Surf sf = surface<SHADE>(S, h, o, d, n, m, __float_as_int(sh.w));
     if (m.type == GSP_DIFFUSE) {
         if (D.smat) D.smat[slot] = __float_as_int(sh.w);
         float4* rec = D.slots + 2 * (size_t)slot;
@@ -392,15 +482,18 @@ __device__ __forceinline__ bool photon_bounce(const DevScene& S, const PassDev& 
         }
         const float urr = rng_next(rng);
         if (!(urr < P.rr)) return false;
-        phi = mul3(phi, m.albedo) * (1.0f / P.rr);
-        const float3 ns = dot3(d, n) < 0.0f ? n : n * -1.0f;
+        phi = mul3(mul3(phi, m.albedo), sf.tex) * (1.0f / P.rr);
+        const bool fr = dot3(d, n) < 0.0f;
+        const float3 ns = fr ? sf.ns : sf.ns * -1.0f;
         const float ua = rng_next(rng), ub = rng_next(rng);
         d = cosine_dir(ns, ua, ub);
+        // about a shading normal the direction can point into the surface: the path ends there
+        if (sf.smooth && !(dot3(d, fr ? n : n * -1.0f) > 0.0f)) return false;
     } else if (m.type == GSP_MIRROR) {
         phi = mul3(phi, m.albedo);
-        d = reflect3(d, n);
+        d = reflect3(d, sf.ns);
     } else {
-        d = dielectric(d, n, m.ior, rng_next(rng));
+        d = dielectric(d, sf.ns, m.ior, rng_next(rng));
     }
     o = x;
     return true;
@@ -432,6 +525,7 @@ k_photon_emit(EmitDev E, PassDev P, PathQ Q, uint32_t* __restrict__ pcount, uint
 
 // Wavefront step b of the photon pass: shade the traced queue qn[b % 3] (deposit, Russian
 // roulette, new direction) and push the paths that go on.
+template <bool SHADE>
 __global__ void __launch_bounds__(256)
 k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32_t* __restrict__ qn, int b,
                unsigned long long* __restrict__ trace_ctr) {
@@ -460,12 +554,13 @@ k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32
             Hit h;
             h.id = cur.tri[i];
             h.t = cur.t[i];
+            h.slot = -1;
             if (h.id >= 0 && !P.tri_is_id) h.id = slot_refine(S, o, d, h);
             if (h.id >= 0) {
                 const uint32_t id = (uint32_t)k * kSlotsPerPath + depth;
                 const uint32_t slot = (uint32_t)k * kSlotsPerPath + ndep;
                 const uint32_t before = ndep;
-                keep = photon_bounce(S, P, D, rng, h, o, d, phi, id, slot, ndep) && depth + 1 < P.max_photon;
+                keep = photon_bounce<SHADE>(S, P, D, rng, h, o, d, phi, id, slot, ndep) && depth + 1 < P.max_photon;
                 if (ndep != before) D.pcount[k] = ndep;
             }
         }
@@ -480,7 +575,7 @@ k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32
 // which start first, run beside the bulk of the photon work instead of after it. Eye entries
 // have depth <= max_eye, photon entries depth < max_photon (the host launches accordingly).
 // STACK: walk the child-pair layout with a stack (StackWalk) instead of the hit/miss links.
-template <bool STACK>
+template <bool STACK, bool SHADE>
 __global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
 k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ ne_ptr, PathQ qp, DepositDev D,
         const uint32_t* __restrict__ np_ptr, uint32_t* __restrict__ ctr) {
@@ -528,12 +623,12 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
             float3 o = st.o, d = st.d;
             bool more = false;
             if (eye) {
-                more = h.id >= 0 && eye_interact(S, P, O, id, h, o, d, w, rng) && ++depth <= P.max_eye;
+                more = h.id >= 0 && eye_interact<SHADE>(S, P, O, id, h, o, d, w, rng) && ++depth <= P.max_eye;
             } else {
                 if (h.id >= 0) {
                     const uint32_t pid = (uint32_t)id * kSlotsPerPath + depth;
                     const uint32_t slot = (uint32_t)id * kSlotsPerPath + ndep;
-                    more = photon_bounce(S, P, D, rng, h, o, d, w, pid, slot, ndep) && ++depth < P.max_photon;
+                    more = photon_bounce<SHADE>(S, P, D, rng, h, o, d, w, pid, slot, ndep) && ++depth < P.max_photon;
                 }
                 if (!more) D.pcount[id] = ndep;
             }
@@ -631,7 +726,7 @@ struct MultiQueue {
     }
 };
 
-template <bool STACK>
+template <bool STACK, bool SHADE>
 __global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
 k_paths_multi(const PathJob* __restrict__ jobs, int32_t njobs, int32_t total_chunks, uint32_t* __restrict__ ctr) {
     MultiQueue mq;
@@ -679,12 +774,12 @@ k_paths_multi(const PathJob* __restrict__ jobs, int32_t njobs, int32_t total_chu
             float3 o = st.o, d = st.d;
             bool more = false;
             if (eye) {
-                more = h.id >= 0 && eye_interact(J.S, J.P, J.O, id, h, o, d, w, rng) && ++depth <= J.P.max_eye;
+                more = h.id >= 0 && eye_interact<SHADE>(J.S, J.P, J.O, id, h, o, d, w, rng) && ++depth <= J.P.max_eye;
             } else {
                 if (h.id >= 0) {
                     const uint32_t pid = (uint32_t)id * kSlotsPerPath + depth;
                     const uint32_t slot = (uint32_t)id * kSlotsPerPath + ndep;
-                    more = photon_bounce(J.S, J.P, J.D, rng, h, o, d, w, pid, slot, ndep) && ++depth < J.P.max_photon;
+                    more = photon_bounce<SHADE>(J.S, J.P, J.D, rng, h, o, d, w, pid, slot, ndep) && ++depth < J.P.max_photon;
                 }
                 if (!more) J.D.pcount[id] = ndep;
             }
@@ -709,7 +804,7 @@ struct RegenDev {
 // one when the stored path has ended (N_e counts the starts), traces exactly one ray, deposits at
 // a diffuse hit and stores the path state for the next pass. Persistent, with per-lane refill
 // over the threads (counter *ctr) as the path kernel; STACK as in k_paths.
-template <bool STACK>
+template <bool STACK, bool SHADE>
 __global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
 k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R, uint32_t* __restrict__ ctr) {
     const int32_t cap = trav_cap(S);
@@ -752,7 +847,7 @@ k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R, uint3
             const Hit h = walk_hit(S, st);
             float3 o = st.o, d = st.d;
             uint32_t ndep = 0;
-            bool alive = h.id >= 0 && photon_bounce(S, P, D, rng, h, o, d, phi, (uint32_t)j, (uint32_t)j, ndep) &&
+            bool alive = h.id >= 0 && photon_bounce<SHADE>(S, P, D, rng, h, o, d, phi, (uint32_t)j, (uint32_t)j, ndep) &&
                          ++depth < P.max_photon;
             D.pcount[j] = ndep;
             R.ro[j] = make_float4(o.x, o.y, o.z, __int_as_float(depth));
@@ -1530,7 +1625,7 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
     P.max_photon = r->P.max_photon_depth;
     P.tmask = (uint32_t)(r->T - 1);
     P.np = r->np;
-    P.tri_is_id = r->refine_factor > 0.0f ? 1 : 0;
+    P.tri_is_id = r->refine_factor > 0.0f && !r->scene->d_attr ? 1 : 0;  // as eye_front / photon_front
     return P;
 }
 
@@ -1572,9 +1667,9 @@ static int path_grid(int64_t items, int device, bool stack) {
         int b = 0;
         cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
         if (stack)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<true>, kTraceThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<true, false>, kTraceThreads, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<false>, kTraceThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<false, false>, kTraceThreads, 0);
         per_sm[stack][device] = std::max(1, b);
     }
     const int64_t full = (int64_t)std::max(1, sms[device]) * per_sm[stack][device];
@@ -1589,13 +1684,18 @@ static gsp_status eye_front(gsp_sppm* r, const PassDev& P, const EyeOut& O, cuda
     const DevScene S = gsp_dev_scene(s);
     uint32_t* qn = r->counters + 4;
     unsigned long long* tctr = s->d_counter;
-    const bool list = r->refine_factor > 0.0f;  // 0: every hit is refined in the shade kernel
+    // 0: every hit is refined in the shade kernel (always with per-vertex shading data, which
+    // needs the hit's triangle slot for its barycentrics)
+    const bool list = r->refine_factor > 0.0f && !s->d_attr;
     const float rf = list ? r->refine_factor : INFINITY;
     k_eye_emit<<<blocks(r->npix, 256), 256, 0, st>>>(r->cam, P, r->qe[0], O, qn, tctr, r->counters + 12);
     for (b = 0; b < r->eye_steps && b <= r->P.max_eye_depth; ++b) {
         const PathQ& cur = r->qe[b & 1];
         GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->npix, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
-        k_eye_shade<<<shade_blocks(r->npix, s->ctx->device), 256, 0, st>>>(S, P, cur, r->qe[(b + 1) & 1], O, qn, b, tctr);
+        if (S.attr)
+            k_eye_shade<true><<<shade_blocks(r->npix, s->ctx->device), 256, 0, st>>>(S, P, cur, r->qe[(b + 1) & 1], O, qn, b, tctr);
+        else
+            k_eye_shade<false><<<shade_blocks(r->npix, s->ctx->device), 256, 0, st>>>(S, P, cur, r->qe[(b + 1) & 1], O, qn, b, tctr);
     }
     return GSP_OK;
 }
@@ -1608,7 +1708,7 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
     const DevScene S = gsp_dev_scene(s);
     uint32_t* qn = r->counters + 8;
     unsigned long long* tctr = s->d_counter;
-    const bool list = r->refine_factor > 0.0f;
+    const bool list = r->refine_factor > 0.0f && !s->d_attr;
     const float rf = list ? r->refine_factor : INFINITY;
     const EmitDev E{r->d_emit, r->d_cdf, r->nemit};
     if (D.stochastic) {
@@ -1621,7 +1721,10 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
         for (b = 0; b < r->photon_steps && b < r->P.max_photon_depth; ++b) {
             const PathQ& cur = r->q[b & 1];
             GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->np, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
-            k_photon_shade<<<shade_blocks(r->np, s->ctx->device), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
+            if (S.attr)
+                k_photon_shade<true><<<shade_blocks(r->np, s->ctx->device), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
+            else
+                k_photon_shade<false><<<shade_blocks(r->np, s->ctx->device), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
         }
     } else {
         RegenDev R{r->ro, r->rd, r->rphi, r->started};
@@ -1629,9 +1732,11 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
         const unsigned grid = (unsigned)path_grid(r->np, r->scene->ctx->device, stack);
         if (stack)
-            k_photon_regen<true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13);
+            S.attr ? k_photon_regen<true, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13)
+                   : k_photon_regen<true, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13);
         else
-            k_photon_regen<false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13);
+            S.attr ? k_photon_regen<false, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13)
+                   : k_photon_regen<false, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13);
     }
     return GSP_OK;
 }
@@ -1670,9 +1775,11 @@ static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, co
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
         const unsigned grid = (unsigned)path_grid((int64_t)J.nchunks * kTraceChunk, r->scene->ctx->device, stack);
         if (stack)
-            k_paths<true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12);
+            J.S.attr ? k_paths<true, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12)
+                     : k_paths<true, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12);
         else
-            k_paths<false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12);
+            J.S.attr ? k_paths<false, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12)
+                     : k_paths<false, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12);
     }
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
@@ -2008,8 +2115,11 @@ static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st) {
         GSP_CUDA_TRY(cudaMalloc(&b->d_jobs, (size_t)n * sizeof(PathJob)));
         GSP_CUDA_TRY(cudaMalloc(&b->d_ctr, sizeof(uint32_t)));
     }
-    bool stack = true;
-    for (gsp_sppm* r : b->rs) stack = stack && r->traversal == GSP_TRAVERSAL_STACK;
+    bool stack = true, shade = false;  // one launch for all: shading code if any scene has shading data
+    for (gsp_sppm* r : b->rs) {
+        stack = stack && r->traversal == GSP_TRAVERSAL_STACK;
+        shade = shade || r->scene->d_attr != nullptr;
+    }
     std::vector<PathJob> jobs(n);
     std::vector<PassDev> passes(n);
     GSP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -2036,9 +2146,11 @@ static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st) {
         const unsigned grid = (unsigned)path_grid((int64_t)total * kTraceChunk, b->device, stack);
         if (ce == cudaSuccess) {
             if (stack)
-                k_paths_multi<true><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr);
+                shade ? k_paths_multi<true, true><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr)
+                      : k_paths_multi<true, false><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr);
             else
-                k_paths_multi<false><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr);
+                shade ? k_paths_multi<false, true><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr)
+                      : k_paths_multi<false, false><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr);
             ce = cudaGetLastError();
         }
     }

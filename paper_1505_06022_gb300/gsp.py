@@ -39,7 +39,8 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_sppm_last_deposits", "gsp_sppm_sync", "gsp_rng_fill", "gsp_hash_grid_build",
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
        "gsp_scene_set_materials", "gsp_batch_create", "gsp_batch_destroy", "gsp_batch_pass",
-       "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load", "gsp_batch_autotune", "gsp_batch_tune"]
+       "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load", "gsp_batch_autotune", "gsp_batch_tune",
+       "gsp_scene_set_attributes", "gsp_scene_set_texture"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -110,6 +111,8 @@ def lib():
             L.gsp_build_bvh.argtypes = [P, P, P]
             L.gsp_build_bvh_device.argtypes = [P, I32, I32, P]
             L.gsp_scene_set_step_limit.argtypes = [P, I32]
+            L.gsp_scene_set_attributes.argtypes = [P, P, P]
+            L.gsp_scene_set_texture.argtypes = [P, I32, P, I32, I32]
             L.gsp_trace_closest_hit.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_trace_closest_hit_stack.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_trace_closest_hit_host.argtypes = [P, P, I64, P, P, P]
@@ -250,6 +253,24 @@ def gsp_build_bvh(scene, bins=16, leaf_threshold=4, max_leaf=7, link_sets=6) -> 
 
 def gsp_scene_set_step_limit(scene, max_box_tests):
     _check("gsp_scene_set_step_limit", lib().gsp_scene_set_step_limit(scene, max_box_tests))
+
+
+def gsp_scene_set_attributes(scene, normals=None, texcoords=None):
+    """Per-vertex normals float32 [nv, 3] and texture coordinates float32 [nv, 2] (None = none)."""
+    n = None if normals is None else np.ascontiguousarray(normals, np.float32)
+    st = None if texcoords is None else np.ascontiguousarray(texcoords, np.float32)
+    _check("gsp_scene_set_attributes", lib().gsp_scene_set_attributes(
+        scene, None if n is None else n.ctypes.data_as(C.c_void_p), None if st is None else st.ctypes.data_as(C.c_void_p)))
+
+
+def gsp_scene_set_texture(scene, material, rgb):
+    """Albedo texture float32 [h, w, 3] of a diffuse material (None removes it)."""
+    if rgb is None:
+        _check("gsp_scene_set_texture", lib().gsp_scene_set_texture(scene, int(material), None, 0, 0))
+        return
+    t = np.ascontiguousarray(rgb, np.float32)
+    _check("gsp_scene_set_texture", lib().gsp_scene_set_texture(scene, int(material), t.ctypes.data_as(C.c_void_p),
+                                                                t.shape[1], t.shape[0]))
 
 
 def gsp_build_bvh_device(scene, link_sets=6, max_leaf=4) -> dict:
@@ -461,6 +482,12 @@ class Scene:
             self.stats = gsp_build_bvh_device(self.h, bvh.get("link_sets", 6), bvh.get("max_leaf", 4))
         else:
             self.stats = gsp_build_bvh(self.h, **bvh)
+        # per-vertex shading data and albedo textures, when the input scene has them
+        nrm, st = getattr(scene, "normals", None), getattr(scene, "texcoords", None)
+        if nrm is not None or st is not None:
+            gsp_scene_set_attributes(self.h, nrm, st)
+        for m, rgb in (getattr(scene, "textures", None) or {}).items():
+            gsp_scene_set_texture(self.h, m, rgb)
 
     def trace(self, rays, stream=None, with_uv=False, method="mtbvh"):
         """Closest hits; method "mtbvh" (stackless, the scene's link sets) or "stack"."""

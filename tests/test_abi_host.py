@@ -167,3 +167,33 @@ def test_upload_rejects_bad_input():
         gsp.gsp_bvh_host_walk(h, I.random_rays(4, 0))
     assert e.value.code == -6
     gsp.gsp_scene_destroy(h)
+
+
+def test_shading_data_argument_checks_on_a_host_scene():
+    """gsp_scene_set_attributes / gsp_scene_set_texture validate on a host-only scene: zero or
+    non-finite normals, textures without texture coordinates or on a non-diffuse material, sizes,
+    negative texels, and coordinates that cannot be dropped while a texture uses them."""
+    sc = I.full_scene(width=8, height=8, plane_quads=4, sphere_n=2)
+    s = gsp.Scene(None, sc)
+    nv = len(sc.verts)
+    ok_n, ok_st = np.tile([0.0, 1.0, 0.0], (nv, 1)).astype(np.float32), np.zeros((nv, 2), np.float32)
+    tex = np.full((4, 4, 3), 0.5, np.float32)
+    for bad in (np.zeros((nv, 3), np.float32), np.full((nv, 3), np.nan, np.float32)):
+        with pytest.raises(gsp.GspError):
+            gsp.gsp_scene_set_attributes(s.h, bad, None)
+    with pytest.raises(gsp.GspError):
+        gsp.gsp_scene_set_attributes(s.h, None, np.full((nv, 2), np.inf, np.float32))
+    with pytest.raises(gsp.GspError):  # no texture coordinates
+        gsp.gsp_scene_set_texture(s.h, 0, tex)
+    gsp.gsp_scene_set_attributes(s.h, ok_n, ok_st)
+    for m, t in [(1, tex), (2, tex), (4, tex), (99, tex), (0, -tex), (0, np.zeros((0, 4, 3), np.float32))]:
+        with pytest.raises(gsp.GspError):  # dielectric, mirror, emitter, out of range, negative, empty
+            gsp.gsp_scene_set_texture(s.h, m, t)
+    gsp.gsp_scene_set_texture(s.h, 0, tex)
+    gsp.gsp_scene_set_texture(s.h, 3, tex)
+    with pytest.raises(gsp.GspError):  # textures still use the coordinates
+        gsp.gsp_scene_set_attributes(s.h, ok_n, None)
+    gsp.gsp_scene_set_texture(s.h, 0, None)
+    gsp.gsp_scene_set_texture(s.h, 3, None)
+    gsp.gsp_scene_set_attributes(s.h, None, None)
+    s.close()
