@@ -2394,7 +2394,11 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     float best = INFINITY, first = INFINITY;
     Cand pick{r->eye_steps, r->photon_steps, r->P.cell_h, r->gather_lanes, r->traversal};
     // Each candidate starts from a fresh state (radii r0), runs one untimed pass and times
-    // trial_passes more, so every candidate sees the same radii.
+    // trial_passes more, so every candidate sees the same radii. Several passes are timed the
+    // way gsp_sppm_pass runs them (overlapped in exact mode), which changes which settings win:
+    // the overlap hides the path kernel's tail.
+    const bool overlap = trial_passes >= 2 && r->P.hash_mode == GSP_EXACT;
+    if (overlap) e = ensure_second_buffer(t);
     auto trial = [&](const Cand& c) {
         if (ce != cudaSuccess || e != GSP_OK) return;
         t->eye_steps = c.es;
@@ -2407,7 +2411,10 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         e = sppm_one_pass(t, st);
         if (e != GSP_OK) return;
         ce = cudaEventRecord(a, st);
-        for (int32_t k = 0; k < trial_passes && e == GSP_OK; ++k) e = sppm_one_pass(t, st);
+        if (overlap)
+            e = passes_overlapped(t, trial_passes, st);
+        else
+            for (int32_t k = 0; k < trial_passes && e == GSP_OK; ++k) e = sppm_one_pass(t, st);
         if (ce == cudaSuccess) ce = cudaEventRecord(z, st);
         if (ce == cudaSuccess) ce = cudaEventSynchronize(z);
         float ms = 0.0f;
