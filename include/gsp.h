@@ -288,9 +288,11 @@ void gsp_sppm_destroy(gsp_sppm* r);
 /* Runs `npasses` SPPM iterations on `stream`: eye pass (first non-specular hit per pixel,
  * emission seen directly), photon pass, hash-grid deposit, range query with the progressive
  * update N' = N + alpha M, R' = R sqrt((N + alpha M) / (N + M)), tau' = (tau + Phi) R'^2/R^2.
- * With npasses >= 2 in exact mode, pass i + 1 is traced on the renderer's own stream into a
- * second set of trace buffers (allocated at the first such call) while pass i is deposited and
- * gathered on `stream`; the result equals npasses single-pass calls bit for bit. */
+ * With npasses >= 2 in exact mode, the passes are traced on two streams of the renderer's own,
+ * alternating between two sets of trace buffers and queues (the second allocated at the first
+ * such call): pass i + 1 is traced while the last paths of pass i are still being traced and
+ * while pass i is deposited and gathered on `stream`; the result equals npasses single-pass
+ * calls bit for bit. */
 gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
 
 /* Execution tuning of the passes. eye_steps / photon_steps: wavefront steps (closest hit of a

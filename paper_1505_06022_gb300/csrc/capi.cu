@@ -183,27 +183,16 @@ static void launch_trace(const gsp_scene* s, const float4* rays, int64_t n, int3
 }
 
 cudaError_t gsp_trace_queue(const gsp_scene* s, const float4* rays, int64_t max_n, const uint32_t* d_n, int32_t* tri,
-                            float* t, float refine_factor, bool zero_counters, bool out_slot, cudaStream_t st) {
+                            float* t, float refine_factor, bool zero_counters, bool out_slot, unsigned long long* ctr,
+                            int2* rlist, cudaStream_t st) {
     const gspd::DevScene S = gsp_dev_scene(s);
     const int grid = gsp_trace_grid(s->ctx->device);
     const bool list = refine_factor < INFINITY;
-    if (list || zero_counters) gspd::k_zero_u64x2<<<1, 1, 0, st>>>(s->d_counter);
-    gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, rays, max_n, d_n, tri, t, nullptr, s->d_counter, s->d_rlist,
-                                                  refine_factor, out_slot ? 1 : 0);
-    if (list) gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, rays, s->d_rlist, s->d_counter, t, nullptr);
+    if (list || zero_counters) gspd::k_zero_u64x2<<<1, 1, 0, st>>>(ctr);
+    gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, rays, max_n, d_n, tri, t, nullptr, ctr, rlist, refine_factor,
+                                                  out_slot ? 1 : 0);
+    if (list) gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, rays, rlist, ctr, t, nullptr);
     return cudaGetLastError();
-}
-
-cudaError_t gsp_scene_reserve_rays(gsp_scene* s, int64_t n) {
-    if (n <= s->rlist_cap) return cudaSuccess;
-    cudaError_t e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return e;
-    cudaFree(s->d_rlist);
-    s->d_rlist = nullptr;
-    s->rlist_cap = 0;
-    e = cudaMalloc(&s->d_rlist, (size_t)n * sizeof(int2));
-    if (e == cudaSuccess) s->rlist_cap = n;
-    return e;
 }
 
 gspd::DevScene gsp_dev_scene(const gsp_scene* s) {

@@ -33,7 +33,7 @@ gspd::DevScene gsp_dev_scene(const gsp_scene* s);
 // scene's trace counters are reset first); with refine_factor = INFINITY nothing is re-evaluated
 // and the counters are reset only if zero_counters is set (else the caller has reset them).
 // out_slot: tri receives the hit's leaf-ordered triangle slot instead of its upload-order index.
+// ctr (2 u64: next ray, list length) and rlist (max_n entries) belong to the caller.
 cudaError_t gsp_trace_queue(const gsp_scene* s, const float4* rays, int64_t max_n, const uint32_t* d_n, int32_t* tri,
-                            float* t, float refine_factor, bool zero_counters, bool out_slot, cudaStream_t st);
-// Grows the scene's FP64 re-evaluation list to hold n rays (synchronises the device first).
-cudaError_t gsp_scene_reserve_rays(gsp_scene* s, int64_t n);
+                            float* t, float refine_factor, bool zero_counters, bool out_slot, unsigned long long* ctr,
+                            int2* rlist, cudaStream_t st);

@@ -5,16 +5,18 @@
 // regeneration), hash-grid deposit, and the fused range query + progressive update (which also
 // folds the pass's direct term into the pixel state). The eye and photon passes are emission
 // kernels, optional wavefront steps, and one persistent path kernel (k_paths; k_paths_multi for
-// a batch of renderers); several passes overlap on two streams (passes_overlapped).
+// a batch of renderers); several passes overlap on three streams (passes_overlapped: two
+// tracing streams, one per trace set, and the caller's stream for the deposits and gathers).
 //
 // Device layout (all library-owned, sized at creation):
 //   pixel state   st0[p] = {tau.rgb, N}, st1[p] = {direct.rgb, R}          32 B / pixel
-//   trace buffers two sets (the second made when passes overlap), each:
+//   trace sets    two (the second made when passes overlap), each:
 //     hit points  hx[p] = {x.xyz, material or -1}, hn[p] = {n_s.xyz, 0},
 //                 hf[p] = {w * albedo / pi, 0}, hd[p] = {direct.rgb, 0}     64 B / pixel
 //     photons     slot s: {x.xyz, id}, {flux.rgb, octahedral direction}    32 B / deposit
 //                 path k owns slots [k*32, k*32+32) (one slot per thread in REGEN mode)
-//   queues        eye and photon wavefront queues, two of each (ping-pong)
+//     queues      eye and photon wavefront queues, two of each (ping-pong), their lengths,
+//                 the path kernel's work counter, the wavefront steps' trace counters
 //   exact grid    bucket-sorted SoA copies spos[], spay[] + bucket starts bstart[T+1]
 //   stochastic    entry[T] = min(random depth bits << 32 | slot), ecount[T]
 #include <algorithm>
@@ -1328,20 +1330,30 @@ struct gsp_sppm {
     float4* d_emit = nullptr;
     float* d_cdf = nullptr;
     float4 *st0 = nullptr, *st1 = nullptr;
-    // The outputs of a pass's eye and photon tracing, read by its deposit and gather. Two sets, so
-    // that the tracing of pass i + 1 can run while pass i is gathered (gsp_sppm_pass with
-    // several passes); the second set is allocated on first use. hx .. pcount alias the set in use.
+    // The tracing of a pass: its path queues and counters, and the outputs its deposit and gather
+    // read. Two sets, so that the tracing of pass i + 1 runs while pass i is gathered and while
+    // the longest paths of pass i are still being traced (gsp_sppm_pass with several passes);
+    // the second set is allocated on first use. hx .. rlist alias the set in use.
     struct TraceBuf {
         float4 *hx = nullptr, *hn = nullptr, *hf = nullptr, *hd = nullptr, *slots = nullptr;
         uint32_t* pcount = nullptr;
         float4* hw = nullptr;     // gradient replay: eye throughput per hit point
         int32_t* smat = nullptr;  // gradient replay: material under each deposit
+        PathQ q[2]{};             // photon wavefront queues, ping-pong (np entries; full paths only)
+        PathQ qe[2]{};            // eye wavefront queues (npix entries)
+        uint32_t* qctr = nullptr;  // [16]: eye queue lengths 4..6, photon 8..10, path-kernel work 12, regen 13
+        unsigned long long* tctr = nullptr;  // closest-hit counters of the wavefront steps
+        int2* rlist = nullptr;               // their FP64 refinement list (qcap entries)
     } tb[2];
     int cur = 0;
     float4 *hx = nullptr, *hn = nullptr, *hf = nullptr, *hd = nullptr;
     float4* slots = nullptr;
     uint32_t* pcount = nullptr;
-    cudaStream_t tstream = nullptr;  // tracing stream of overlapped passes
+    PathQ *q = nullptr, *qe = nullptr;
+    uint32_t* qctr = nullptr;
+    unsigned long long* tctr = nullptr;
+    int2* rlist = nullptr;
+    cudaStream_t tstream[2] = {nullptr, nullptr};  // tracing streams of overlapped passes, one per set
     cudaEvent_t ev_start = nullptr, ev_traced[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     uint32_t *poff = nullptr, *counters = nullptr;
     uint32_t *keys[2] = {nullptr, nullptr}, *vals[2] = {nullptr, nullptr};
@@ -1352,9 +1364,7 @@ struct gsp_sppm {
     float4 *ro = nullptr, *rd = nullptr, *rphi = nullptr;
     unsigned long long* started = nullptr;
     uint32_t* last_order = nullptr;  // sorted slot order of the last exact pass
-    // wavefront queues (ping-pong) and their tuning
-    PathQ q[2]{};   // photon wavefront queues (np entries; full paths only)
-    PathQ qe[2]{};  // eye wavefront queues (npix entries)
+    // tuning
     int32_t gather_lanes = 8;  // lanes per hit point in the exact gather
     int32_t traversal = GSP_TRAVERSAL_MTBVH;  // of the path kernel
     int64_t qcap = 0;
@@ -1401,6 +1411,35 @@ void use_buf(gsp_sppm* r, int j) {
     r->hd = r->tb[j].hd;
     r->slots = r->tb[j].slots;
     r->pcount = r->tb[j].pcount;
+    r->q = r->tb[j].q;
+    r->qe = r->tb[j].qe;
+    r->qctr = r->tb[j].qctr;
+    r->tctr = r->tb[j].tctr;
+    r->rlist = r->tb[j].rlist;
+}
+
+// The path queues and counters of trace set j.
+template <class AllocF>
+void alloc_trace_queues(gsp_sppm* r, int j, AllocF&& A) {
+    const int64_t nq = r->P.photon_mode == GSP_FULL_PATH ? r->np : 0;
+    auto& t = r->tb[j];
+    for (int b = 0; b < 2; ++b) {
+        A(&t.q[b].ray, 2 * nq);
+        A(&t.q[b].w, nq);
+        A(&t.q[b].rng, nq);
+        A(&t.q[b].meta, nq);
+        A(&t.q[b].tri, nq);
+        A(&t.q[b].t, nq);
+        A(&t.qe[b].ray, 2 * r->npix);
+        A(&t.qe[b].w, r->npix);
+        A(&t.qe[b].rng, r->npix);
+        A(&t.qe[b].meta, r->npix);
+        A(&t.qe[b].tri, r->npix);
+        A(&t.qe[b].t, r->npix);
+    }
+    A(&t.qctr, 16);
+    A(&t.tctr, 2);
+    A(&t.rlist, r->qcap);
 }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -1556,22 +1595,8 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     r->eye_steps = 0;     // no wavefront steps: the persistent path kernel (per-lane refill)
     r->photon_steps = 0;  // traces every bounce; a step costs a closest-hit launch over the whole
                           // queue plus a shade launch, and waits for its slowest ray
-    const int64_t nq = P.photon_mode == GSP_FULL_PATH ? r->np : 0;
-    for (int b = 0; b < 2; ++b) {
-        A(&r->q[b].ray, 2 * nq);
-        A(&r->q[b].w, nq);
-        A(&r->q[b].rng, nq);
-        A(&r->q[b].meta, nq);
-        A(&r->q[b].tri, nq);
-        A(&r->q[b].t, nq);
-        A(&r->qe[b].ray, 2 * r->npix);
-        A(&r->qe[b].w, r->npix);
-        A(&r->qe[b].rng, r->npix);
-        A(&r->qe[b].meta, r->npix);
-        A(&r->qe[b].tri, r->npix);
-        A(&r->qe[b].t, r->npix);
-    }
-    if (e == cudaSuccess) e = gsp_scene_reserve_rays(s, r->qcap);
+    alloc_trace_queues(r, 0, A);
+    use_buf(r, 0);
     if (P.photon_mode == GSP_REGEN) {
         A(&r->ro, r->np);
         A(&r->rd, r->np);
@@ -1604,7 +1629,8 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
 void gsp_sppm_destroy(gsp_sppm* r) {
     if (!r) return;
     cudaSetDevice(r->scene->ctx->device);
-    if (r->tstream) cudaStreamDestroy(r->tstream);
+    for (cudaStream_t t : r->tstream)
+        if (t) cudaStreamDestroy(t);
     for (cudaEvent_t ev : {r->ev_start, r->ev_traced[0], r->ev_traced[1], r->ev_free[0], r->ev_free[1]})
         if (ev) cudaEventDestroy(ev);
     free_all(r);
@@ -1682,16 +1708,16 @@ static int path_grid(int64_t items, int device, bool stack) {
 static gsp_status eye_front(gsp_sppm* r, const PassDev& P, const EyeOut& O, cudaStream_t st, int& b) {
     gsp_scene* s = r->scene;
     const DevScene S = gsp_dev_scene(s);
-    uint32_t* qn = r->counters + 4;
-    unsigned long long* tctr = s->d_counter;
+    uint32_t* qn = r->qctr + 4;
+    unsigned long long* tctr = r->tctr;
     // 0: every hit is refined in the shade kernel (always with per-vertex shading data, which
     // needs the hit's triangle slot for its barycentrics)
     const bool list = r->refine_factor > 0.0f && !s->d_attr;
     const float rf = list ? r->refine_factor : INFINITY;
-    k_eye_emit<<<blocks(r->npix, 256), 256, 0, st>>>(r->cam, P, r->qe[0], O, qn, tctr, r->counters + 12);
+    k_eye_emit<<<blocks(r->npix, 256), 256, 0, st>>>(r->cam, P, r->qe[0], O, qn, tctr, r->qctr + 12);
     for (b = 0; b < r->eye_steps && b <= r->P.max_eye_depth; ++b) {
         const PathQ& cur = r->qe[b & 1];
-        GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->npix, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
+        GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->npix, qn + b % 3, cur.tri, cur.t, rf, false, !list, tctr, r->rlist, st));
         if (S.attr)
             k_eye_shade<true><<<shade_blocks(r->npix, s->ctx->device), 256, 0, st>>>(S, P, cur, r->qe[(b + 1) & 1], O, qn, b, tctr);
         else
@@ -1706,8 +1732,8 @@ static gsp_status eye_front(gsp_sppm* r, const PassDev& P, const EyeOut& O, cuda
 static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& D, cudaStream_t st, int& b) {
     gsp_scene* s = r->scene;
     const DevScene S = gsp_dev_scene(s);
-    uint32_t* qn = r->counters + 8;
-    unsigned long long* tctr = s->d_counter;
+    uint32_t* qn = r->qctr + 8;
+    unsigned long long* tctr = r->tctr;
     const bool list = r->refine_factor > 0.0f && !s->d_attr;
     const float rf = list ? r->refine_factor : INFINITY;
     const EmitDev E{r->d_emit, r->d_cdf, r->nemit};
@@ -1717,10 +1743,10 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
     }
     b = -1;
     if (r->P.photon_mode == GSP_FULL_PATH) {
-        k_photon_emit<<<blocks(r->np, 256), 256, 0, st>>>(E, P, r->q[0], r->pcount, qn, tctr, r->counters + 12);
+        k_photon_emit<<<blocks(r->np, 256), 256, 0, st>>>(E, P, r->q[0], r->pcount, qn, tctr, r->qctr + 12);
         for (b = 0; b < r->photon_steps && b < r->P.max_photon_depth; ++b) {
             const PathQ& cur = r->q[b & 1];
-            GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->np, qn + b % 3, cur.tri, cur.t, rf, false, !list, st));
+            GSP_CUDA_TRY(gsp_trace_queue(s, cur.ray, r->np, qn + b % 3, cur.tri, cur.t, rf, false, !list, tctr, r->rlist, st));
             if (S.attr)
                 k_photon_shade<true><<<shade_blocks(r->np, s->ctx->device), 256, 0, st>>>(S, P, D, cur, r->q[(b + 1) & 1], qn, b, tctr);
             else
@@ -1728,15 +1754,15 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
         }
     } else {
         RegenDev R{r->ro, r->rd, r->rphi, r->started};
-        GSP_CUDA_TRY(cudaMemsetAsync(r->counters + 13, 0, sizeof(uint32_t), st));
+        GSP_CUDA_TRY(cudaMemsetAsync(r->qctr + 13, 0, sizeof(uint32_t), st));
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
         const unsigned grid = (unsigned)path_grid(r->np, r->scene->ctx->device, stack);
         if (stack)
-            S.attr ? k_photon_regen<true, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13)
-                   : k_photon_regen<true, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13);
+            S.attr ? k_photon_regen<true, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13)
+                   : k_photon_regen<true, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13);
         else
-            S.attr ? k_photon_regen<false, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13)
-                   : k_photon_regen<false, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->counters + 13);
+            S.attr ? k_photon_regen<false, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13)
+                   : k_photon_regen<false, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13);
     }
     return GSP_OK;
 }
@@ -1758,8 +1784,8 @@ static gsp_status paths_front(gsp_sppm* r, const PassDev& P, const EyeOut& O, co
     J.qp = r->q[ph_left ? bp & 1 : 0];
     J.O = O;
     J.D = D;
-    J.ne_ptr = eye_left ? r->counters + 4 + be % 3 : nullptr;
-    J.np_ptr = ph_left ? r->counters + 8 + bp % 3 : nullptr;
+    J.ne_ptr = eye_left ? r->qctr + 4 + be % 3 : nullptr;
+    J.np_ptr = ph_left ? r->qctr + 8 + bp % 3 : nullptr;
     J.first_chunk = 0;
     const int64_t items = (eye_left ? r->npix : 0) + (ph_left ? r->np : 0);
     J.nchunks = (int32_t)((items + kTraceChunk - 1) / kTraceChunk);
@@ -1775,11 +1801,11 @@ static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, co
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
         const unsigned grid = (unsigned)path_grid((int64_t)J.nchunks * kTraceChunk, r->scene->ctx->device, stack);
         if (stack)
-            J.S.attr ? k_paths<true, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12)
-                     : k_paths<true, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12);
+            J.S.attr ? k_paths<true, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
+                     : k_paths<true, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
         else
-            J.S.attr ? k_paths<false, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12)
-                     : k_paths<false, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->counters + 12);
+            J.S.attr ? k_paths<false, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
+                     : k_paths<false, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
     }
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
@@ -1866,9 +1892,9 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
     return GSP_OK;
 }
 
-// The second set of trace buffers, the tracing stream and its events, made on first use.
+// The second set of trace buffers, the tracing streams and their events, made on first use.
 static gsp_status ensure_second_buffer(gsp_sppm* r) {
-    if (r->tb[1].hx && (!r->grad || r->tb[1].hw)) return GSP_OK;
+    if (r->tb[1].hx && r->tb[1].qctr && (!r->grad || r->tb[1].hw)) return GSP_OK;
     cudaError_t e = cudaSuccess;
     auto A = [&](auto** p, int64_t n) {
         if (e == cudaSuccess && !*p) e = alloc(r, p, n);
@@ -1883,7 +1909,9 @@ static gsp_status ensure_second_buffer(gsp_sppm* r) {
         A(&r->tb[1].hw, r->npix);
         A(&r->tb[1].smat, r->slot_cap);
     }
-    if (e == cudaSuccess && !r->tstream) e = cudaStreamCreateWithFlags(&r->tstream, cudaStreamNonBlocking);
+    if (!r->tb[1].qctr) alloc_trace_queues(r, 1, A);
+    for (cudaStream_t& t : r->tstream)
+        if (e == cudaSuccess && !t) e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
     for (cudaEvent_t* ev : {&r->ev_start, &r->ev_traced[0], &r->ev_traced[1], &r->ev_free[0], &r->ev_free[1]})
         if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -1894,25 +1922,29 @@ static gsp_status ensure_second_buffer(gsp_sppm* r) {
     return GSP_OK;
 }
 
-// Several passes with the tracing of pass i + 1 (on the renderer's tracing stream, into the other
-// trace buffers) running while pass i is deposited and gathered on the caller's stream: the long
-// tail of the path kernel, when only the longest paths are still running, overlaps the previous
-// pass's sort and gather. Events order each buffer's reuse; results are those of one pass after
-// the other. Exact hashing only (stochastic hashing shares its table between the two halves).
+// Several passes, pass i traced on tracing stream i % 2 into trace set i % 2 while the caller's
+// stream deposits and gathers the pass before: the tracing of pass i + 1 starts as soon as its
+// set has been gathered (pass i - 1), so it runs beside the long tail of pass i's path kernel,
+// when only the longest paths are still going, and beside pass i's sort and gather. Events order
+// each set's reuse (and, with paths carried from pass to pass, the tracing itself); results are
+// those of one pass after the other. Exact hashing only (stochastic hashing shares its table
+// between the two halves).
 static gsp_status passes_overlapped(gsp_sppm* r, int32_t npasses, cudaStream_t st) {
     gsp_status se = ensure_second_buffer(r);
     if (se != GSP_OK) return se;
-    // the tracing stream starts after everything the caller queued before
+    // the tracing streams start after everything the caller queued before
     GSP_CUDA_TRY(cudaEventRecord(r->ev_start, st));
-    GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_start, 0));
+    for (cudaStream_t t : r->tstream) GSP_CUDA_TRY(cudaStreamWaitEvent(t, r->ev_start, 0));
+    const bool chained = r->P.photon_mode == GSP_REGEN;  // photon paths continue into the next pass
     for (int32_t i = 0; i < npasses; ++i) {
         const int j = i & 1;
         use_buf(r, j);
         const PassDev P = pass_params(r, r->passes);
-        if (i >= 2) GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_free[j], 0));  // pass i - 2 gathered
-        gsp_status e = trace_half(r, P, r->tstream);
+        if (i >= 2) GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream[j], r->ev_free[j], 0));  // pass i - 2 gathered
+        if (chained && i >= 1) GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream[j], r->ev_traced[j ^ 1], 0));
+        gsp_status e = trace_half(r, P, r->tstream[j]);
         if (e != GSP_OK) return e;
-        GSP_CUDA_TRY(cudaEventRecord(r->ev_traced[j], r->tstream));
+        GSP_CUDA_TRY(cudaEventRecord(r->ev_traced[j], r->tstream[j]));
         GSP_CUDA_TRY(cudaStreamWaitEvent(st, r->ev_traced[j], 0));
         e = gather_half(r, P, st);
         if (e != GSP_OK) return e;
@@ -2011,12 +2043,12 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
     GSP_CUDA_TRY(cudaMemsetAsync(r->gacc, 0, ((size_t)kMaxGradMats * 3 + 3) * sizeof(double), st));
     const float hp_cell = 2.0f * r->P.r0;
     const int grid = 4 * sm_count(r->scene->ctx->device);
-    // Pass i + 1 is replayed on the tracing stream into the other trace buffers while the adjoint
+    // Pass i + 1 is replayed on the other tracing stream into the other trace set while the adjoint
     // kernels of pass i run on the caller's stream (the same double buffering as gsp_sppm_pass).
     gsp_status e = ensure_second_buffer(r);
     if (e != GSP_OK) return e;
     GSP_CUDA_TRY(cudaEventRecord(r->ev_start, st));
-    GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_start, 0));
+    for (cudaStream_t t : r->tstream) GSP_CUDA_TRY(cudaStreamWaitEvent(t, r->ev_start, 0));
     for (int64_t i = 0; i < r->passes; ++i) {
         const int j = (int)(i & 1);
         use_buf(r, j);
@@ -2025,10 +2057,10 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
         const PassDev P = pass_params(r, i);
         const EyeOut O{r->hx, r->hn, r->hf, r->hd, r->hw};
         const DepositDev D{r->slots, r->pcount, nullptr, nullptr, 0, r->smat};
-        if (i >= 2) GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream, r->ev_free[j], 0));
-        e = stage_paths(r, P, O, D, r->tstream);
+        if (i >= 2) GSP_CUDA_TRY(cudaStreamWaitEvent(r->tstream[j], r->ev_free[j], 0));
+        e = stage_paths(r, P, O, D, r->tstream[j]);
         if (e != GSP_OK) return e;
-        GSP_CUDA_TRY(cudaEventRecord(r->ev_traced[j], r->tstream));
+        GSP_CUDA_TRY(cudaEventRecord(r->ev_traced[j], r->tstream[j]));
         GSP_CUDA_TRY(cudaStreamWaitEvent(st, r->ev_traced[j], 0));
         e = stage_deposit(r, P, st);
         if (e != GSP_OK) return e;
