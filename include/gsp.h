@@ -22,9 +22,10 @@
  *    exceeds its step limit, an overflowing buffer) in a device status word; the next
  *    gsp_sppm_sync()/gsp_context_sync() returns the first such error.
  *  - Memory the library allocates itself (scene, BVH, SPPM state) lives in device memory of
- *    the context's device, sized at creation. A few buffers are made on first use and kept:
- *    the second set of trace buffers when a call runs several passes (or a gradient replay),
- *    the per-stream buffers of host-buffer tracing, a batch's job table; each entry point says
+ *    the context's device, sized at creation (a renderer in exact mode makes both of its trace
+ *    sets then). A few buffers are made on first use and kept: the second trace set of a
+ *    renderer in stochastic mode when a gradient replay or a two-pass batch graph needs it,
+ *    the per-stream buffers of host-buffer tracing, a batch's job tables; each entry point says
  *    so. Nothing is allocated between the launches of a pass.
  *  - Passes, batches and gradients use the handles' own extra streams internally; they are
  *    ordered after earlier work on `stream`, and later work on `stream` is ordered after them.
@@ -289,10 +290,10 @@ void gsp_sppm_destroy(gsp_sppm* r);
  * emission seen directly), photon pass, hash-grid deposit, range query with the progressive
  * update N' = N + alpha M, R' = R sqrt((N + alpha M) / (N + M)), tau' = (tau + Phi) R'^2/R^2.
  * With npasses >= 2 in exact mode, the passes are traced on two streams of the renderer's own,
- * alternating between two sets of trace buffers and queues (the second allocated at the first
- * such call): pass i + 1 is traced while the last paths of pass i are still being traced and
- * while pass i is deposited and gathered on `stream`; the result equals npasses single-pass
- * calls bit for bit. */
+ * alternating between two sets of trace buffers and queues (both allocated by gsp_sppm_create in
+ * exact mode; nothing is allocated during a pass): pass i + 1 is traced while the last paths of
+ * pass i are still being traced and while pass i is deposited and gathered on `stream`; the
+ * result equals npasses single-pass calls bit for bit. */
 gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
 
 /* Execution tuning of the passes. eye_steps / photon_steps: wavefront steps (closest hit of a
@@ -353,7 +354,10 @@ typedef struct gsp_batch gsp_batch;
  * first gsp_batch_pass do not reach the captured graph. The renderers must outlive the batch. */
 gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** out);
 void gsp_batch_destroy(gsp_batch* b);
-/* Runs npasses passes of every renderer of the batch on `stream`. */
+/* Runs npasses passes of every renderer of the batch on `stream`. With one fused path launch
+ * (gsp_batch_tune) and exact hashing in every renderer, pairs of passes run as a second graph of
+ * two passes (captured at the first call that has a pair) in which the second pass is traced,
+ * into the renderers' other trace sets, beside the first; results are unchanged. */
 gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream);
 
 /* fused = 1: each batch pass runs the eye and photon fronts of all renderers in parallel

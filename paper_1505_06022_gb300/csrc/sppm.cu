@@ -10,7 +10,7 @@
 //
 // Device layout (all library-owned, sized at creation):
 //   pixel state   st0[p] = {tau.rgb, N}, st1[p] = {direct.rgb, R}          32 B / pixel
-//   trace sets    two (the second made when passes overlap), each:
+//   trace sets    two (both made at creation in exact mode), each:
 //     hit points  hx[p] = {x.xyz, material or -1}, hn[p] = {n_s.xyz, 0},
 //                 hf[p] = {w * albedo / pi, 0}, hd[p] = {direct.rgb, 0}     64 B / pixel
 //     photons     slot s: {x.xyz, id}, {flux.rgb, octahedral direction}    32 B / deposit
@@ -61,7 +61,9 @@ struct PassDev {
     int64_t np;
 };
 
-__device__ __forceinline__ uint32_t pass_index(const PassDev& P) { return P.pass_dev ? *P.pass_dev : P.pass; }
+// The pass index; in a replayed graph the device counter holds the graph's first pass and
+// P.pass the pass's place in the graph.
+__device__ __forceinline__ uint32_t pass_index(const PassDev& P) { return P.pass_dev ? *P.pass_dev + P.pass : P.pass; }
 
 struct Material {
     float3 albedo, emission;
@@ -1333,7 +1335,8 @@ struct gsp_sppm {
     // The tracing of a pass: its path queues and counters, and the outputs its deposit and gather
     // read. Two sets, so that the tracing of pass i + 1 runs while pass i is gathered and while
     // the longest paths of pass i are still being traced (gsp_sppm_pass with several passes);
-    // the second set is allocated on first use. hx .. rlist alias the set in use.
+    // both sets are made at creation in exact mode (else on first use). hx .. rlist alias the set
+    // in use.
     struct TraceBuf {
         float4 *hx = nullptr, *hn = nullptr, *hf = nullptr, *hd = nullptr, *slots = nullptr;
         uint32_t* pcount = nullptr;
@@ -1447,6 +1450,8 @@ inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 extern "C" {
+
+static gsp_status ensure_second_buffer(gsp_sppm* r);
 
 gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm** out) {
     if (!s || !params || !out) return GSP_ERR_INVALID_ARG;
@@ -1615,6 +1620,15 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         if (e == cudaSuccess) e = cudaMemset(r->rd, 0, r->np * sizeof(float4));
         if (e == cudaSuccess) e = cudaMemset(r->rphi, 0, r->np * sizeof(float4));
     }
+    // exact mode traces several passes into both trace sets: the second one is made now, so
+    // that no pass allocates
+    if (e == cudaSuccess && P.hash_mode == GSP_EXACT) {
+        const gsp_status se = ensure_second_buffer(r);
+        if (se != GSP_OK) {
+            gsp_sppm_destroy(r);
+            return se;
+        }
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         gsp_set_last_error(cudaGetErrorString(e));
@@ -1655,9 +1669,9 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
     return P;
 }
 
-// Renderer counters (uint32): [0] deposits of the pass, [4..6] eye queue lengths, [8..10] photon
-// queue lengths (three each, used in rotation), [12] work counter of k_paths, [13] work counter of
-// k_photon_regen, [7] pass index of a replayed graph.
+// Renderer counters (uint32): [0] deposits of the pass, [7] first pass index of a replayed graph.
+// Per trace set (qctr): [4..6] eye queue lengths, [8..10] photon queue lengths (three each, used
+// in rotation), [12] work counter of k_paths, [13] work counter of k_photon_regen.
 static int sm_count(int device) {
     static int cached[64] = {0};
     if (device < 0 || device >= 64) device = 0;
@@ -1881,7 +1895,10 @@ static gsp_status check_grad_room(gsp_sppm* r, int64_t npasses) {
 
 static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false) {
     PassDev P = pass_params(r, r->passes);
-    if (graph) P.pass_dev = r->counters + 7;
+    if (graph) {
+        P.pass_dev = r->counters + 7;
+        P.pass = 0;
+    }
     gsp_status e = check_grad_room(r, graph ? 0 : 1);
     if (e == GSP_OK) e = trace_half(r, P, st);
     if (e == GSP_OK) e = gather_half(r, P, st);
@@ -1892,7 +1909,8 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
     return GSP_OK;
 }
 
-// The second set of trace buffers, the tracing streams and their events, made on first use.
+// The second set of trace buffers, the tracing streams and their events (at creation in exact
+// mode, else on first use).
 static gsp_status ensure_second_buffer(gsp_sppm* r) {
     if (r->tb[1].hx && r->tb[1].qctr && (!r->grad || r->tb[1].hw)) return GSP_OK;
     cudaError_t e = cudaSuccess;
@@ -2106,22 +2124,33 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
 struct gsp_batch {
     std::vector<gsp_sppm*> rs;
     std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> joins;
-    cudaEvent_t fork = nullptr;
-    cudaStream_t cap = nullptr;  // private stream the graph is captured on (never the legacy stream)
-    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaEvent_t> joins, joins2;  // per renderer: ends of its branches (first, second pass)
+    cudaEvent_t fork = nullptr, paths[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;   // private stream the graphs are captured on (never the legacy stream)
+    cudaStream_t cap2 = nullptr;  // the second pass's path launch in a two-pass graph
+    cudaGraphExec_t exec = nullptr;   // one pass
+    cudaGraphExec_t exec2 = nullptr;  // fused: two passes, the second traced beside the first
     int32_t device = 0;
     bool fused = true;           // all renderers' paths in one persistent launch (k_paths_multi)
-    PathJob* d_jobs = nullptr;   // fused: the renderers' job table
-    uint32_t* d_ctr = nullptr;   // fused: the path kernel's work counter
+    PathJob* d_jobs = nullptr;   // fused: job tables, [0, n) one-pass graph, [n, 3n) two-pass graph
+    uint32_t* d_ctr = nullptr;   // fused: the path kernel's work counters (one per table)
 };
 
-static void batch_free(gsp_batch* b) {
+static void batch_drop_graphs(gsp_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->exec2) cudaGraphExecDestroy(b->exec2);
+    b->exec = b->exec2 = nullptr;
+}
+
+static void batch_free(gsp_batch* b) {
+    batch_drop_graphs(b);
     for (auto s : b->streams) cudaStreamDestroy(s);
     for (auto e : b->joins) cudaEventDestroy(e);
-    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto e : b->joins2) cudaEventDestroy(e);
+    for (cudaEvent_t e : {b->fork, b->paths[0], b->paths[1]})
+        if (e) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->cap2) cudaStreamDestroy(b->cap2);
     cudaFree(b->d_jobs);
     cudaFree(b->d_ctr);
     delete b;
@@ -2137,73 +2166,100 @@ static cudaError_t reset_state(gsp_sppm* t, cudaStream_t st) {
     return e;
 }
 
-// Fused form of a batch pass: the eye and photon fronts of every renderer in parallel branches,
+// Fused form of batch passes: the eye and photon fronts of every renderer in parallel branches,
 // then ONE persistent k_paths_multi launch over all renderers' remaining paths, then the
-// deposits and gathers in parallel branches. The job table holds only pointers and device
-// counters, so it is written once, after the capture.
-static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st) {
+// deposits and gathers in parallel branches. K = 2 captures two passes into one graph, pass k in
+// trace set k: the second pass's fronts and path launch depend on nothing of the first, so its
+// paths fill the SMs that the first path launch's tail leaves idle; each renderer's second gather
+// follows its first. The job tables hold only pointers and device counters, so they are written
+// once, after the capture.
+static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st, int K, cudaGraphExec_t* out) {
     const int n = (int)b->rs.size();
     if (!b->d_jobs) {
-        GSP_CUDA_TRY(cudaMalloc(&b->d_jobs, (size_t)n * sizeof(PathJob)));
-        GSP_CUDA_TRY(cudaMalloc(&b->d_ctr, sizeof(uint32_t)));
+        GSP_CUDA_TRY(cudaMalloc(&b->d_jobs, 3 * (size_t)n * sizeof(PathJob)));
+        GSP_CUDA_TRY(cudaMalloc(&b->d_ctr, 3 * sizeof(uint32_t)));
     }
+    if (K == 2)
+        for (gsp_sppm* r : b->rs) {  // both trace sets (made outside the capture)
+            gsp_status se = ensure_second_buffer(r);
+            if (se != GSP_OK) return se;
+        }
     bool stack = true, shade = false;  // one launch for all: shading code if any scene has shading data
     for (gsp_sppm* r : b->rs) {
         stack = stack && r->traversal == GSP_TRAVERSAL_STACK;
         shade = shade || r->scene->d_attr != nullptr;
     }
-    std::vector<PathJob> jobs(n);
-    std::vector<PassDev> passes(n);
+    const size_t base = K == 2 ? (size_t)n : 0;  // job tables and counters of this graph
+    std::vector<PathJob> jobs((size_t)K * n);
+    std::vector<PassDev> passes((size_t)K * n);
+    std::vector<int32_t> total(K, 0);
     GSP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     gsp_status e = GSP_OK;
     cudaError_t ce = cudaEventRecord(b->fork, st);
-    for (int i = 0; i < n && ce == cudaSuccess && e == GSP_OK; ++i) {
-        gsp_sppm* r = b->rs[i];
-        passes[i] = pass_params(r, r->passes);
-        passes[i].pass_dev = r->counters + 7;
-        const EyeOut O{r->hx, r->hn, r->hf, r->hd, nullptr};
-        const DepositDev D{r->slots, r->pcount, r->entry, r->ecount, r->P.hash_mode == GSP_STOCHASTIC ? 1 : 0, nullptr};
-        ce = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-        if (ce == cudaSuccess) e = paths_front(r, passes[i], O, D, b->streams[i], jobs[i]);
-        if (ce == cudaSuccess && e == GSP_OK) ce = cudaEventRecord(b->joins[i], b->streams[i]);
-        if (ce == cudaSuccess && e == GSP_OK) ce = cudaStreamWaitEvent(st, b->joins[i], 0);
-    }
-    int32_t total = 0;
-    for (auto& J : jobs) {
-        J.first_chunk = total;
-        total += J.nchunks;
-    }
-    if (ce == cudaSuccess && e == GSP_OK && total > 0) {
-        ce = cudaMemsetAsync(b->d_ctr, 0, sizeof(uint32_t), st);
-        const unsigned grid = (unsigned)path_grid((int64_t)total * kTraceChunk, b->device, stack);
-        if (ce == cudaSuccess) {
-            if (stack)
-                shade ? k_paths_multi<true, true><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr)
-                      : k_paths_multi<true, false><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr);
-            else
-                shade ? k_paths_multi<false, true><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr)
-                      : k_paths_multi<false, false><<<grid, kTraceThreads, 0, st>>>(b->d_jobs, n, total, b->d_ctr);
-            ce = cudaGetLastError();
+    for (int i = 0; i < n && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
+    if (ce == cudaSuccess && K == 2) ce = cudaStreamWaitEvent(b->cap2, b->fork, 0);
+    // fronts: per renderer, pass 0 then pass 1 on its branch
+    for (int k = 0; k < K && ce == cudaSuccess && e == GSP_OK; ++k)
+        for (int i = 0; i < n && ce == cudaSuccess && e == GSP_OK; ++i) {
+            gsp_sppm* r = b->rs[i];
+            use_buf(r, k);
+            PassDev& P = passes[(size_t)k * n + i];
+            P = pass_params(r, r->passes);
+            P.pass_dev = r->counters + 7;
+            P.pass = (uint32_t)k;
+            const EyeOut O{r->hx, r->hn, r->hf, r->hd, nullptr};
+            const DepositDev D{r->slots, r->pcount, r->entry, r->ecount, r->P.hash_mode == GSP_STOCHASTIC ? 1 : 0,
+                               nullptr};
+            e = paths_front(r, P, O, D, b->streams[i], jobs[(size_t)k * n + i]);
+            if (e == GSP_OK) ce = cudaEventRecord((k == 0 ? b->joins : b->joins2)[i], b->streams[i]);
         }
-    }
-    if (ce == cudaSuccess && e == GSP_OK) ce = cudaEventRecord(b->fork, st);
-    for (int i = 0; i < n && ce == cudaSuccess && e == GSP_OK; ++i) {
-        gsp_sppm* r = b->rs[i];
-        ce = cudaStreamWaitEvent(b->streams[i], b->fork, 0);
-        if (ce == cudaSuccess) e = gather_half(r, passes[i], b->streams[i]);
-        if (ce == cudaSuccess && e == GSP_OK) {
-            k_add_u32<<<1, 1, 0, b->streams[i]>>>(r->counters + 7, 1u);
-            ce = cudaEventRecord(b->joins[i], b->streams[i]);
+    // one path launch per pass, pass 1's on its own stream
+    for (int k = 0; k < K && ce == cudaSuccess && e == GSP_OK; ++k) {
+        cudaStream_t ps = k == 0 ? st : b->cap2;
+        for (int i = 0; i < n && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(ps, (k == 0 ? b->joins : b->joins2)[i], 0);
+        for (int i = 0; i < n; ++i) {
+            PathJob& J = jobs[(size_t)k * n + i];
+            J.first_chunk = total[k];
+            total[k] += J.nchunks;
         }
-        if (ce == cudaSuccess && e == GSP_OK) ce = cudaStreamWaitEvent(st, b->joins[i], 0);
+        uint32_t* ctr = b->d_ctr + (K == 2 ? 1 + k : 0);
+        const PathJob* jt = b->d_jobs + base + (size_t)k * n;
+        if (ce == cudaSuccess && total[k] > 0) {
+            ce = cudaMemsetAsync(ctr, 0, sizeof(uint32_t), ps);
+            const unsigned grid = (unsigned)path_grid((int64_t)total[k] * kTraceChunk, b->device, stack);
+            if (ce == cudaSuccess) {
+                if (stack)
+                    shade ? k_paths_multi<true, true><<<grid, kTraceThreads, 0, ps>>>(jt, n, total[k], ctr)
+                          : k_paths_multi<true, false><<<grid, kTraceThreads, 0, ps>>>(jt, n, total[k], ctr);
+                else
+                    shade ? k_paths_multi<false, true><<<grid, kTraceThreads, 0, ps>>>(jt, n, total[k], ctr)
+                          : k_paths_multi<false, false><<<grid, kTraceThreads, 0, ps>>>(jt, n, total[k], ctr);
+                ce = cudaGetLastError();
+            }
+        }
+        if (ce == cudaSuccess) ce = cudaEventRecord(b->paths[k], ps);
     }
+    // deposits and gathers: per renderer, pass 0 then pass 1 on its branch
+    for (int k = 0; k < K && ce == cudaSuccess && e == GSP_OK; ++k)
+        for (int i = 0; i < n && ce == cudaSuccess && e == GSP_OK; ++i) {
+            gsp_sppm* r = b->rs[i];
+            use_buf(r, k);
+            ce = cudaStreamWaitEvent(b->streams[i], b->paths[k], 0);
+            if (ce == cudaSuccess) e = gather_half(r, passes[(size_t)k * n + i], b->streams[i]);
+            if (ce == cudaSuccess && e == GSP_OK && k == K - 1) {
+                k_add_u32<<<1, 1, 0, b->streams[i]>>>(r->counters + 7, (uint32_t)K);
+                ce = cudaEventRecord(b->joins[i], b->streams[i]);
+                if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, b->joins[i], 0);
+            }
+        }
+    if (ce == cudaSuccess && e == GSP_OK && K == 2) ce = cudaStreamWaitEvent(st, b->paths[1], 0);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(st, &g);
     if (ce == cudaSuccess) ce = ee;
-    if (ce == cudaSuccess && e == GSP_OK) ce = cudaGraphInstantiate(&b->exec, g, 0);
+    if (ce == cudaSuccess && e == GSP_OK) ce = cudaGraphInstantiate(out, g, 0);
     if (g) cudaGraphDestroy(g);
     if (ce == cudaSuccess && e == GSP_OK)
-        ce = cudaMemcpy(b->d_jobs, jobs.data(), (size_t)n * sizeof(PathJob), cudaMemcpyHostToDevice);
+        ce = cudaMemcpy(b->d_jobs + base, jobs.data(), jobs.size() * sizeof(PathJob), cudaMemcpyHostToDevice);
     if (e != GSP_OK) return e;
     if (ce != cudaSuccess) {
         gsp_set_last_error(cudaGetErrorString(ce));
@@ -2215,7 +2271,7 @@ static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st) {
 // One pass of every renderer captured as a single CUDA graph: a branch per renderer, forked
 // from and joined to the capturing stream, so the scenes' kernels overlap on the GPU.
 static gsp_status batch_capture(gsp_batch* b, cudaStream_t st) {
-    if (b->fused) return batch_capture_fused(b, st);
+    if (b->fused) return batch_capture_fused(b, st, 1, &b->exec);
     GSP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     gsp_status e = GSP_OK;
     cudaError_t ce = cudaEventRecord(b->fork, st);
@@ -2238,6 +2294,15 @@ static gsp_status batch_capture(gsp_batch* b, cudaStream_t st) {
     return GSP_OK;
 }
 
+// Two-pass graphs need exact hashing everywhere: a stochastic pass resets its hash table in its
+// fronts, which the previous pass's photons may still be filling.
+static bool batch_pairs(const gsp_batch* b) {
+    if (!b->fused) return false;
+    for (const gsp_sppm* r : b->rs)
+        if (r->P.hash_mode != GSP_EXACT) return false;
+    return true;
+}
+
 extern "C" {
 
 gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** out) {
@@ -2258,14 +2323,19 @@ gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** o
     b->device = dev;
     b->rs.assign(renderers, renderers + n);
     cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (cudaEvent_t* ev : {&b->paths[0], &b->paths[1]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking);
     for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
         cudaStream_t s = nullptr;
-        cudaEvent_t j = nullptr;
+        cudaEvent_t j = nullptr, j2 = nullptr;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e == cudaSuccess) b->streams.push_back(s);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
         if (e == cudaSuccess) b->joins.push_back(j);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j2, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->joins2.push_back(j2);
     }
     (void)gsp_trace_grid(dev);  // fill the launch-size cache outside any capture
     if (e != cudaSuccess) {
@@ -2279,10 +2349,9 @@ gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** o
 
 gsp_status gsp_batch_tune(gsp_batch* b, int32_t fused) {
     if (!b || fused < 0 || fused > 1) return GSP_ERR_INVALID_ARG;
-    if (b->fused != (fused == 1) && b->exec) {
+    if (b->fused != (fused == 1)) {
         cudaSetDevice(b->device);
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;  // captured again at the next gsp_batch_pass
+        batch_drop_graphs(b);  // captured again at the next gsp_batch_pass
     }
     b->fused = fused == 1;
     return GSP_OK;
@@ -2302,12 +2371,19 @@ gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
     for (gsp_sppm* r : b->rs)
         if (r->grad && r->passes + npasses > r->grad_max_passes) return GSP_ERR_OVERFLOW;
     if (npasses == 0) return GSP_OK;
-    if (!b->exec) {
+    // pairs of passes as two-pass graphs where they apply, the rest one pass per graph
+    const int32_t pairs = batch_pairs(b) ? npasses / 2 : 0, singles = npasses - 2 * pairs;
+    if (pairs > 0 && !b->exec2) {
+        gsp_status e = batch_capture_fused(b, b->cap, 2, &b->exec2);  // capture runs nothing
+        if (e != GSP_OK) return e;
+    }
+    if (singles > 0 && !b->exec) {
         gsp_status e = batch_capture(b, b->cap);  // capture runs nothing; the graph launches on st
         if (e != GSP_OK) return e;
     }
     for (gsp_sppm* r : b->rs) k_store_u32<<<1, 1, 0, st>>>(r->counters + 7, (uint32_t)r->passes);
-    for (int32_t k = 0; k < npasses; ++k) GSP_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    for (int32_t k = 0; k < pairs; ++k) GSP_CUDA_TRY(cudaGraphLaunch(b->exec2, st));
+    for (int32_t k = 0; k < singles; ++k) GSP_CUDA_TRY(cudaGraphLaunch(b->exec, st));
     for (gsp_sppm* r : b->rs) r->passes += npasses;
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
@@ -2340,19 +2416,22 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
             r->traversal = c.tr;
         }
         b->fused = c.fused;
-        if (b->exec) cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
+        batch_drop_graphs(b);
     };
-    // Each candidate: capture its graph, one untimed batch pass, trial_passes timed ones, then
-    // every renderer back to its initial state.
+    // Each candidate: capture its graph, one untimed graph launch, then trial_passes timed passes
+    // the way gsp_batch_pass runs them (two-pass graphs where they apply), then every renderer
+    // back to its initial state.
     auto trial = [&](const Cand& c) {
         if (ce != cudaSuccess || e != GSP_OK) return;
         apply(c);
-        e = batch_capture(b, st);
-        for (int32_t k = 0; k <= trial_passes && e == GSP_OK && ce == cudaSuccess; ++k) {
+        const bool two = batch_pairs(b) && trial_passes >= 2;
+        e = two ? batch_capture_fused(b, st, 2, &b->exec2) : batch_capture(b, st);
+        cudaGraphExec_t g = two ? b->exec2 : b->exec;
+        const int32_t per = two ? 2 : 1, launches = (trial_passes + per - 1) / per;
+        for (int32_t k = 0; k <= launches && e == GSP_OK && ce == cudaSuccess; ++k) {
             if (k == 1) ce = cudaEventRecord(a, st);
-            for (gsp_sppm* r : b->rs) k_store_u32<<<1, 1, 0, st>>>(r->counters + 7, (uint32_t)k);
-            if (ce == cudaSuccess) ce = cudaGraphLaunch(b->exec, st);
+            for (gsp_sppm* r : b->rs) k_store_u32<<<1, 1, 0, st>>>(r->counters + 7, (uint32_t)(k * per));
+            if (ce == cudaSuccess) ce = cudaGraphLaunch(g, st);
         }
         if (ce == cudaSuccess && e == GSP_OK) ce = cudaEventRecord(z, st);
         if (ce == cudaSuccess) ce = cudaEventSynchronize(z);
@@ -2360,7 +2439,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
         if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, z);
         for (gsp_sppm* r : b->rs)
             if (ce == cudaSuccess) ce = reset_state(r, st);
-        ms /= (float)trial_passes;
+        ms /= (float)(launches * per);
         if (ncand++ == 0) first = ms;
         if (ms < best) {
             best = ms;
