@@ -10,10 +10,14 @@
 // float4 (32 bytes): {min.xyz, miss} and {max.xyz, leaf word}. A triangle is three float4:
 // {v0.xyz, triangle index}, {v1.xyz, 0}, {v2.xyz, 0}.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <mutex>
 #include <numeric>
+#include <thread>
 
 #include "gsp_internal.h"
 
@@ -56,33 +60,49 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
     if (nt >= (int64_t(1) << 28)) return "more than 2^28 triangles";
     const int bins = p.bins, leaf_thr = p.leaf_threshold, max_leaf = p.max_leaf;
 
+    // worker threads for the per-triangle pass, the subtrees and the link sets; the tree, and so
+    // every output array, is the same for any number of threads
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nthreads = nt < 65536 ? 1 : (int)std::min(64u, hw);
+    auto parallel_for = [&](int64_t n, auto&& fn) {  // fn(begin, end)
+        if (nthreads == 1 || n < 4096) return fn((int64_t)0, n);
+        std::vector<std::thread> th;
+        const int64_t per = (n + nthreads - 1) / nthreads;
+        for (int t = 0; t < nthreads; ++t) {
+            const int64_t a = t * per, b = std::min(n, a + per);
+            if (a < b) th.emplace_back([&fn, a, b] { fn(a, b); });
+        }
+        for (auto& x : th) x.join();
+    };
+
     // per-triangle bounds and centroids
     std::vector<float> tlo(3 * nt), thi(3 * nt), cen(3 * nt);
-    for (int64_t i = 0; i < nt; ++i) {
-        for (int k = 0; k < 3; ++k) {
-            float a = verts[3 * (int64_t)tris[3 * i] + k], b = verts[3 * (int64_t)tris[3 * i + 1] + k],
-                  c = verts[3 * (int64_t)tris[3 * i + 2] + k];
-            tlo[3 * i + k] = std::min({a, b, c});
-            thi[3 * i + k] = std::max({a, b, c});
-            cen[3 * i + k] = 0.5f * (tlo[3 * i + k] + thi[3 * i + k]);
-        }
-    }
+    parallel_for(nt, [&](int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i)
+            for (int k = 0; k < 3; ++k) {
+                float a = verts[3 * (int64_t)tris[3 * i] + k], b = verts[3 * (int64_t)tris[3 * i + 1] + k],
+                      c = verts[3 * (int64_t)tris[3 * i + 2] + k];
+                tlo[3 * i + k] = std::min({a, b, c});
+                thi[3 * i + k] = std::max({a, b, c});
+                cen[3 * i + k] = 0.5f * (tlo[3 * i + k] + thi[3 * i + k]);
+            }
+    });
     (void)nv;
     std::vector<int32_t> perm(nt);
     std::iota(perm.begin(), perm.end(), 0);
-    std::vector<BNode> nodes;
-    nodes.reserve(2 * nt / std::max(1, leaf_thr) + 16);
-    nodes.emplace_back();
+    // at most 2 nt - 1 nodes (every leaf holds a triangle); children are numbered after their
+    // parent, in whatever order the workers split them
+    std::vector<BNode> nodes((size_t)2 * nt);
+    std::atomic<int32_t> next_node{1};
+    std::atomic<int32_t> max_depth{1};
+    std::atomic<int64_t> leaves{0};
 
     struct Job { int32_t node, first, count, depth; };
-    std::vector<Job> stack{{0, 0, (int32_t)nt, 1}};
-    std::vector<Bin> binv(3 * bins), right(bins);
-    int32_t max_depth = 1;
-    int64_t leaves = 0;
-    while (!stack.empty()) {
-        Job j = stack.back();
-        stack.pop_back();
-        max_depth = std::max(max_depth, j.depth);
+    // Splits node j: its bounds, then a leaf, or the binned SAH split (cost = 1 + (A_L N_L +
+    // A_R N_R) / A_P) with the children's jobs handed to `push`.
+    auto split = [&](const Job& j, std::vector<Bin>& binv, std::vector<Bin>& right, auto&& push) {
+        int32_t d = max_depth.load(std::memory_order_relaxed);
+        while (j.depth > d && !max_depth.compare_exchange_weak(d, j.depth)) {}
         float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
         float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int32_t k = j.first; k < j.first + j.count; ++k) {
@@ -99,9 +119,8 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
         std::memcpy(nd.hi, bhi, sizeof bhi);
         nd.first = j.first;
         nd.count = j.count;
-        if (j.count <= leaf_thr) { ++leaves; continue; }
+        if (j.count <= leaf_thr) { ++leaves; return; }
 
-        // binned SAH over the centroid bounds: cost = 1 + (A_L N_L + A_R N_R) / A_P
         double best_cost = INFINITY;
         int best_axis = -1, best_split = -1;
         double ap = half_area(blo, bhi);
@@ -144,10 +163,10 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
         int32_t mid;
         if (best_axis < 0) {
             // every centroid coincides: split by position in the current order
-            if (j.count <= max_leaf) { ++leaves; continue; }
+            if (j.count <= max_leaf) { ++leaves; return; }
             mid = j.first + j.count / 2;
         } else {
-            if (j.count <= max_leaf && (double)j.count <= best_cost) { ++leaves; continue; }
+            if (j.count <= max_leaf && (double)j.count <= best_cost) { ++leaves; return; }
             const int a = best_axis;
             const float lo_a = clo[a], sc = scale[a];
             auto it = std::stable_partition(perm.begin() + j.first, perm.begin() + j.first + j.count,
@@ -158,15 +177,61 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
             mid = (int32_t)(it - perm.begin());
             if (mid == j.first || mid == j.first + j.count) mid = j.first + j.count / 2;
         }
-        int32_t l = (int32_t)nodes.size();
-        nodes.emplace_back();
-        nodes.emplace_back();
-        nodes[j.node].left = l;
-        nodes[j.node].right = l + 1;
-        nodes[j.node].count = 0;
-        stack.push_back({l + 1, mid, j.first + j.count - mid, j.depth + 1});
-        stack.push_back({l, j.first, mid - j.first, j.depth + 1});
+        const int32_t l = next_node.fetch_add(2);
+        nd.left = l;
+        nd.right = l + 1;
+        nd.count = 0;
+        push(Job{l + 1, mid, j.first + j.count - mid, j.depth + 1});
+        push(Job{l, j.first, mid - j.first, j.depth + 1});
+    };
+
+    // Workers share a stack of large jobs; a job below kLocal triangles is finished by the worker
+    // that takes it, depth first, without touching the shared stack.
+    constexpr int32_t kLocal = 4096;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<Job> shared{{0, 0, (int32_t)nt, 1}};
+    int64_t busy = 0;  // jobs taken and not finished (under mu)
+    auto worker = [&] {
+        std::vector<Bin> binv(3 * bins), right(bins);
+        std::vector<Job> local;
+        while (true) {
+            Job j;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return !shared.empty() || busy == 0; });
+                if (shared.empty()) return;  // nothing queued and nobody working: done
+                j = shared.back();
+                shared.pop_back();
+                ++busy;
+            }
+            local.clear();
+            local.push_back(j);
+            while (!local.empty()) {
+                Job k = local.back();
+                local.pop_back();
+                split(k, binv, right, [&](const Job& c) {
+                    if (c.count < kLocal || nthreads == 1) {
+                        local.push_back(c);
+                    } else {
+                        std::lock_guard<std::mutex> lk(mu);
+                        shared.push_back(c);
+                        cv.notify_one();
+                    }
+                });
+            }
+            std::lock_guard<std::mutex> lk(mu);
+            --busy;
+            if (busy == 0 && shared.empty()) cv.notify_all();
+        }
+    };
+    {
+        std::vector<std::thread> th;
+        for (int t = 1; t < nthreads; ++t) th.emplace_back(worker);
+        worker();
+        for (auto& x : th) x.join();
     }
+    nodes.resize((size_t)next_node.load());
     auto t1 = clk::now();
 
     // ---- threading: one preorder (and miss links) per link set ----
@@ -179,13 +244,12 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
     // node (a leaf) without using it; the padding box is empty and its links end the walk
     const int64_t stride = nn + 1;
     out.nodes.assign((size_t)sets * stride * 2, float4{0, 0, 0, 0});
-    std::vector<int32_t> pos(nn), st;
-    st.reserve(256);
-    for (int c = 0; c < sets; ++c) {
+    auto thread_set = [&](int c) {  // one link set, on its own worker
+        std::vector<int32_t> pos(nn), st;
+        st.reserve(256);
         const int axis = c / 2;
         const float sgn = (c % 2 == 0) ? 1.0f : -1.0f;
         int32_t counter = 0;
-        st.clear();
         st.push_back(0);
         while (!st.empty()) {
             int32_t n = st.back();
@@ -214,14 +278,22 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
             dst[2 * q] = float4{nd.lo[0], nd.lo[1], nd.lo[2], as_float(miss)};
             dst[2 * q + 1] = float4{nd.hi[0], nd.hi[1], nd.hi[2], as_float(word)};
         }
+    };
+    {
+        std::vector<std::thread> th;
+        for (int c = 1; c < sets; ++c) {
+            if (nthreads > 1) th.emplace_back(thread_set, c);
+            else thread_set(c);
+        }
+        thread_set(0);
+        for (auto& x : th) x.join();
     }
     auto t2 = clk::now();
 
     // ---- the same tree as child pairs (stack-based traversal), internal nodes in preorder ----
     {
-        std::vector<int32_t> ref(nn, 0);
+        std::vector<int32_t> ref(nn, 0), st;
         int32_t ni = 0;
-        st.clear();
         st.push_back(0);
         while (!st.empty()) {  // preorder numbering of the internal nodes
             int32_t n = st.back();
@@ -261,8 +333,8 @@ std::string bvh_build_host(const float* verts, int64_t nv, const int32_t* tris, 
     }
     out.nnodes = nn;
     out.stride = stride;
-    out.nleaves = leaves;
-    out.depth = max_depth;
+    out.nleaves = leaves.load();
+    out.depth = max_depth.load();
     out.link_sets = sets;
     out.build_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     out.thread_ms = std::chrono::duration<double, std::milli>(t2 - t1).count();
