@@ -1,5 +1,6 @@
-// Host BVH build and host walk under AddressSanitizer / UndefinedBehaviorSanitizer
-// (tests/test_sanitizers.py compiles this with the library's host build source).
+// Host BVH build and host walk under AddressSanitizer / UndefinedBehaviorSanitizer, and under
+// ThreadSanitizer for the build's worker threads (tests/test_sanitizers.py compiles this with the
+// library's host build source).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -17,7 +18,8 @@ int main() {
     int bad = 0;
     std::mt19937 rng(7);
     std::uniform_real_distribution<float> u(-1.0f, 1.0f);
-    for (int nt : {1, 2, 3, 17, 500, 4099}) {
+    // 70,001 triangles take the multi-threaded build (worker threads over subtrees and link sets)
+    for (int nt : {1, 2, 3, 17, 500, 4099, 70001}) {
         std::vector<float> v(9 * (size_t)nt);
         std::vector<int32_t> t(3 * (size_t)nt);
         for (int i = 0; i < nt; ++i) {
