@@ -53,11 +53,13 @@ TRACE_SOURCES = ["capi.cu", "devcommon.cuh", "launch.h", "persist.cuh", "gsp_int
 
 
 def trace_digest() -> str:
+    """Digest of the closest-hit kernel's sources and compile flags. Include directories are left
+    out: they are absolute paths, which differ between checkouts of the same sources."""
     h = hashlib.sha256()
     for name in TRACE_SOURCES:
         h.update(name.encode())
         h.update(open(os.path.join(CSRC, name), "rb").read())
-    h.update(" ".join(_flags()).encode())
+    h.update(" ".join(f for f in _flags() if not os.path.isabs(f)).encode())
     return h.hexdigest()[:16]
 
 
