@@ -569,6 +569,19 @@ static gsp_status stage_deposit(gsp_sppm* r, const PassDev& P, cudaStream_t st) 
     return GSP_OK;
 }
 
+// The pass's deposits in path order, without the hash grid: the list the adjoint's photon loop
+// walks (a grid would only order it).
+static gsp_status stage_deposit_list(gsp_sppm* r, cudaStream_t st) {
+    uint32_t* d_total = r->counters;
+    GSP_CUDA_TRY(gsp_scan_u32(r->pcount, r->poff, r->np, d_total, r->scan_tmp, st));
+    k_compact<<<blocks(r->np, 256), 256, 0, st>>>(r->slots, r->pcount, r->poff, r->np, r->slots_per_path, 0.0f, 0u,
+                                                  nullptr, r->vals[0], nullptr);
+    r->last_order = r->vals[0];
+    k_permute<<<1024, 256, 0, st>>>(r->slots, r->vals[0], d_total, r->spos, r->spay);
+    GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
 // One pass on stream st. In graph mode (a pass captured once and replayed) the pass index is read
 // from the device counter counters[7], which the pass advances itself, and the host count is left
 // to the caller.
@@ -806,7 +819,7 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
         if (e != GSP_OK) return e;
         GSP_CUDA_TRY(cudaEventRecord(r->ev_traced[j], r->tstream[j]));
         GSP_CUDA_TRY(cudaStreamWaitEvent(st, r->ev_traced[j], 0));
-        e = stage_deposit(r, P, st);
+        e = stage_deposit_list(r, st);
         if (e != GSP_OK) return e;
         e = gsp_grid_build_with(r->hx, r->npix, hp_cell, r->hp_T, r->hp_order, r->hp_bstart, r->hp_scratch, st, true);
         if (e != GSP_OK) return e;

@@ -11,6 +11,7 @@ namespace gspd {
 // ------------------------------------------------------------------------------------------
 // exact hash-grid deposit: compaction in id order, bucket keys, bucket counts
 // ------------------------------------------------------------------------------------------
+// keys == nullptr: the compaction alone (slot of each deposit in path order, no buckets).
 __global__ void __launch_bounds__(256)
 k_compact(const float4* __restrict__ slots, const uint32_t* __restrict__ pcount,
           const uint32_t* __restrict__ poff, int64_t np, int32_t slots_per_path, float inv_h,
@@ -21,10 +22,11 @@ k_compact(const float4* __restrict__ slots, const uint32_t* __restrict__ pcount,
     const uint32_t c = pcount[k], off = poff[k];
     for (uint32_t i = 0; i < c; ++i) {
         const uint32_t slot = (uint32_t)k * slots_per_path + i;
+        vals[off + i] = slot;
+        if (!keys) continue;
         const float4 a = slots[2 * (size_t)slot];
         const uint32_t b = bucket_of(f3(a), inv_h, tmask);
         keys[off + i] = b;
-        vals[off + i] = slot;
         atomicAdd(bcount + b, 1u);
     }
 }
