@@ -126,3 +126,34 @@ def test_full_size_batch_matches_individual_renderers(ctx):
         r.close()
     for s in scenes:
         s.close()
+
+
+def test_two_pass_graphs_match_individual_passes(ctx):
+    """Fused batches with exact hashing run pairs of passes as two-pass graphs (the second pass
+    traced beside the first, into the other trace sets) and an odd pass as a one-pass graph; with
+    one-bounce-per-pass photon paths the second pass's photon front follows the first's. Five
+    passes, then two more, must equal the renderers run alone."""
+    scs = [I.full_scene(seed=11, width=48, height=40, plane_quads=24, sphere_n=5),
+           I.cornell_box(seed=4, width=32, height=24),
+           I.grad_scene(seed=12, width=40, height=32, plane_quads=16, sphere_n=4)]
+    kws = [dict(photons_per_pass=12000, seed=7, r0_frac=0.01, scene_id=0),
+           dict(photons_per_pass=6000, seed=8, photon_mode=1, scene_id=1),
+           dict(photons_per_pass=9000, seed=9, r0_frac=0.02, scene_id=2)]
+    solo = []
+    for sc, kw in zip(scs, kws):
+        r = gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw))
+        r.run(7)
+        solo.append((r.image().cpu().numpy(), r.state()["N"].cpu().numpy()))
+    rs = [gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw)) for sc, kw in zip(scs, kws)]
+    b = gsp.Batch(rs)
+    b.tune(True)
+    b.run(5)
+    b.run(2)
+    torch.cuda.synchronize()
+    for r, (img, n) in zip(rs, solo):
+        r.sync()
+        st = r.state()
+        assert st["passes"] == 7
+        assert np.array_equal(st["N"].cpu().numpy(), n)
+        assert np.array_equal(r.image().cpu().numpy(), img)
+    b.close()
