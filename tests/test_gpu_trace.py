@@ -121,7 +121,8 @@ def full_size():
 @pytest.mark.parametrize("method", ["mtbvh", "stack"])
 def test_full_size_traversal_sampled(ctx, full_size, method):
     """The benchmark's workload and launch: all 4M rays in one call; the oracle checks a
-    stratified sample of 24,576 rays (both halves) with its FP64 BVH, and 256 by brute force."""
+    stratified sample of 24,576 rays (both halves) with its FP64 BVH, and 4,096 of them (256 for
+    the stack traversal) by brute force over all 1,003,520 triangles (4e9 FP64 tests)."""
     sc, rays = full_size
     tri, t, _, _ = gpu_trace(ctx, sc, rays, method=method)
     n = len(rays)
@@ -131,7 +132,7 @@ def test_full_size_traversal_sampled(ctx, full_size, method):
     mesh = O.Mesh(sc.verts, sc.tris)
     ids, tt, _, _, nd = mesh.closest_hit(rays[sample])
     parity_hits(tri[sample], t[sample], ids, tt, nd)
-    sub = sample[::96]
+    sub = sample[::6] if method == "mtbvh" else sample[::96]
     bids, btt, _, _, bnd = mesh.closest_hit(rays[sub], brute=True)
     parity_hits(tri[sub], t[sub], bids, btt, bnd)
     assert (tri >= 0).mean() > 0.2
