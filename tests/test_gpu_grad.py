@@ -181,3 +181,33 @@ def test_full_size_gradient_configuration(ctx):
         fd = (objective(mp) - objective(mm)) / dh
         assert abs(fd - ga[m, c]) <= 2e-3 * scale, (m, c, fd, ga[m, c])
     gsp.gsp_scene_set_materials(s.h, sc.mats)
+
+
+def test_gradient_after_batched_passes(ctx):
+    """Passes run through a fused batch (two-pass graphs, the pass index read from the device)
+    record the same radius history as plain passes, so the replayed gradient is the same."""
+    scs = [I.grad_scene(seed=13, width=32, height=24, plane_quads=16, sphere_n=3),
+           I.full_scene(seed=14, width=24, height=24, plane_quads=12, sphere_n=3)]
+    params = [gsp.sppm_params(scs[0], 6000, seed=3, r0_frac=0.03, scene_id=0),
+              gsp.sppm_params(scs[1], 5000, seed=4, r0_frac=0.03, scene_id=1)]
+    scenes = [gsp.Scene(ctx, sc) for sc in scs]
+    alone = gsp.Renderer(scenes[0], params[0])
+    alone.enable_grad(4)
+    alone.run(4)
+    img = alone.image()
+    g = (img - img.mean()).contiguous()
+    ga, gl = (x.cpu().numpy() for x in alone.grad(g))
+    rs = [gsp.Renderer(s, p) for s, p in zip(scenes, params)]
+    rs[0].enable_grad(4)
+    b = gsp.Batch(rs)
+    b.tune(True)
+    b.run(4)
+    torch.cuda.synchronize()
+    rs[0].sync()
+    assert torch.equal(rs[0].image(), img)
+    gb, glb = (x.cpu().numpy() for x in rs[0].grad(g))
+    np.testing.assert_allclose(gb, ga, rtol=1e-5, atol=1e-6 * np.abs(ga).max())
+    np.testing.assert_allclose(glb, gl, rtol=1e-5, atol=1e-6 * np.abs(gl).max())
+    with pytest.raises(gsp.GspError):
+        b.run(1)  # radius history full
+    b.close()
