@@ -351,7 +351,9 @@ typedef struct gsp_batch gsp_batch;
  * small and large scenes overlap on the GPU. The graph is captured at the first gsp_batch_pass
  * and replayed for every pass; each branch reads its pass index from the device. Results are
  * those of gsp_sppm_pass on each renderer. Tuning changes (gsp_sppm_tune/autotune) made after the
- * first gsp_batch_pass do not reach the captured graph. The renderers must outlive the batch. */
+ * first gsp_batch_pass do not reach the captured graph. A scene change that moves or resizes its
+ * device data (a new BVH, new shading data, a step limit) makes the next gsp_batch_pass capture
+ * again. The renderers must outlive the batch. */
 gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** out);
 void gsp_batch_destroy(gsp_batch* b);
 /* Runs npasses passes of every renderer of the batch on `stream`. With one fused path launch

@@ -873,7 +873,29 @@ struct gsp_batch {
     bool fused = true;           // all renderers' paths in one persistent launch (k_paths_multi)
     PathJob* d_jobs = nullptr;   // fused: job tables, [0, n) one-pass graph, [n, 3n) two-pass graph
     uint32_t* d_ctr = nullptr;   // fused: the path kernel's work counters (one per table)
+    std::vector<DevScene> captured;  // each renderer's scene as the graphs baked it in
 };
+
+// Whether every renderer's scene still has the device description the graphs were captured
+// with (a new BVH, new shading data or a new step limit changes it; replaying would then read
+// freed or stale buffers).
+static bool batch_scenes_unchanged(const gsp_batch* b) {
+    if (b->captured.size() != b->rs.size()) return false;
+    for (size_t i = 0; i < b->rs.size(); ++i) {
+        const DevScene x = gsp_dev_scene(b->rs[i]->scene), &y = b->captured[i];
+        if (x.nodes != y.nodes || x.tris != y.tris || x.shade != y.shade || x.nlo != y.nlo || x.mats != y.mats ||
+            x.bin != y.bin || x.attr != y.attr || x.texels != y.texels || x.mtex != y.mtex || x.nnodes != y.nnodes ||
+            x.stride != y.stride || x.link_sets != y.link_sets || x.bin_root != y.bin_root ||
+            x.step_limit != y.step_limit || x.status != y.status)
+            return false;
+    }
+    return true;
+}
+
+static void batch_note_scenes(gsp_batch* b) {
+    b->captured.clear();
+    for (gsp_sppm* r : b->rs) b->captured.push_back(gsp_dev_scene(r->scene));
+}
 
 static void batch_drop_graphs(gsp_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1110,15 +1132,18 @@ gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
     for (gsp_sppm* r : b->rs)
         if (r->grad && r->passes + npasses > r->grad_max_passes) return GSP_ERR_OVERFLOW;
     if (npasses == 0) return GSP_OK;
+    if ((b->exec || b->exec2) && !batch_scenes_unchanged(b)) batch_drop_graphs(b);
     // pairs of passes as two-pass graphs where they apply, the rest one pass per graph
     const int32_t pairs = batch_pairs(b) ? npasses / 2 : 0, singles = npasses - 2 * pairs;
     if (pairs > 0 && !b->exec2) {
         gsp_status e = batch_capture_fused(b, b->cap, 2, &b->exec2);  // capture runs nothing
         if (e != GSP_OK) return e;
+        batch_note_scenes(b);
     }
     if (singles > 0 && !b->exec) {
         gsp_status e = batch_capture(b, b->cap);  // capture runs nothing; the graph launches on st
         if (e != GSP_OK) return e;
+        batch_note_scenes(b);
     }
     for (gsp_sppm* r : b->rs) k_store_u32<<<1, 1, 0, st>>>(r->counters + 7, (uint32_t)r->passes);
     for (int32_t k = 0; k < pairs; ++k) GSP_CUDA_TRY(cudaGraphLaunch(b->exec2, st));

@@ -157,3 +157,37 @@ def test_two_pass_graphs_match_individual_passes(ctx):
         assert np.array_equal(st["N"].cpu().numpy(), n)
         assert np.array_equal(r.image().cpu().numpy(), img)
     b.close()
+
+
+@pytest.mark.parametrize("fused", [False, True])
+def test_batch_recaptures_after_a_scene_changes(ctx, fused):
+    """A new BVH (host SAH with one link set, then the device build) and new shading data move a
+    scene's device buffers; the next batch pass captures its graphs again instead of replaying
+    ones that point at the old buffers. Closest hits, and so images, do not depend on the tree."""
+    scs = [I.shaded_scene(seed=16, width=40, height=32, plane_quads=16, sphere_n=4, tex_size=16),
+           I.full_scene(seed=17, width=32, height=32, plane_quads=16, sphere_n=4)]
+    kws = [dict(photons_per_pass=8000, seed=2, r0_frac=0.02, scene_id=0),
+           dict(photons_per_pass=8000, seed=3, r0_frac=0.02, scene_id=1)]
+    solo = []
+    for sc, kw in zip(scs, kws):
+        r = gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw))
+        r.run(6)
+        solo.append(r.image().cpu().numpy())
+    scenes = [gsp.Scene(ctx, sc) for sc in scs]
+    rs = [gsp.Renderer(s, gsp.sppm_params(sc, **kw)) for s, sc, kw in zip(scenes, scs, kws)]
+    b = gsp.Batch(rs)
+    b.tune(fused)
+    b.run(2)
+    gsp.gsp_build_bvh(scenes[0].h, link_sets=1)
+    gsp.gsp_scene_set_attributes(scenes[0].h, scs[0].normals, scs[0].texcoords)  # same data, new buffer
+    for m, rgb in scs[0].textures.items():
+        gsp.gsp_scene_set_texture(scenes[0].h, m, rgb)
+    b.run(2)
+    gsp.gsp_build_bvh_device(scenes[1].h)
+    b.run(2)
+    torch.cuda.synchronize()
+    for r, want in zip(rs, solo):
+        r.sync()
+        assert r.state()["passes"] == 6
+        assert np.array_equal(r.image().cpu().numpy(), want)
+    b.close()
