@@ -299,6 +299,18 @@ __device__ __forceinline__ void trav_leaf(const DevScene& S, Trav& st, int32_t f
     }
 }
 
+// 64 bytes at a 32-byte aligned address (two adjacent nodes, or a node's two child boxes) as two
+// 256-bit read-only vector loads (sm_100 and later): half the load instructions of four 128-bit
+// loads on the traversal's dependent fetch.
+__device__ __forceinline__ void ldg64(const float4* p, float4& A, float4& B, float4& C, float4& D) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(A.x), "=f"(A.y), "=f"(A.z), "=f"(A.w), "=f"(B.x), "=f"(B.y), "=f"(B.z), "=f"(B.w)
+        : "l"(p));
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8+32];"
+        : "=f"(C.x), "=f"(C.y), "=f"(C.z), "=f"(C.w), "=f"(D.x), "=f"(D.y), "=f"(D.z), "=f"(D.w)
+        : "l"(p));
+}
+
 // Box test of a node {A, B} = {min.xyz, miss | max.xyz, leaf word} against [tmin, best t]
 // (conservative FP32 slab test). Returns true on a hit; `word` and `miss` receive the links.
 __device__ __forceinline__ bool box_hit(const Trav& st, const float4& A, const float4& B, int32_t& word, int32_t& miss) {
@@ -332,8 +344,8 @@ __device__ __forceinline__ bool box_entry(const Trav& st, float3 lo, float3 hi, 
 // otherwise follow the miss link. The node after the current one in preorder (the first child
 // of an internal node) comes with the same fetch, so a descent tests two boxes per step.
 __device__ __forceinline__ void trav_step(const DevScene& S, Trav& st) {
-    const float4* np = st.nodes + 2 * st.node;
-    const float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2), D = __ldg(np + 3);
+    float4 A, B, C, D;
+    ldg64(st.nodes + 2 * st.node, A, B, C, D);
     int32_t word, miss;
     if (!box_hit(st, A, B, word, miss)) {
         st.node = miss;

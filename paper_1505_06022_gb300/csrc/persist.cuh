@@ -77,8 +77,8 @@ __device__ __forceinline__ void trav_steps(const DevScene& S, Trav& st, int32_t&
         if (active && st.node >= 0) {
             // one fetch brings the node and the next node in preorder (its first child when it
             // is internal, usually in the same cache line); both boxes can be tested
-            const float4* np = st.nodes + 2 * st.node;
-            const float4 A = __ldg(np), B = __ldg(np + 1), C = __ldg(np + 2), D = __ldg(np + 3);
+            float4 A, B, C, D;
+            ldg64(st.nodes + 2 * st.node, A, B, C, D);
             st.steps += 1;
             int32_t word, miss;
             if (st.steps > cap) {
@@ -158,8 +158,8 @@ __device__ __forceinline__ void stack_steps(const DevScene& S, Trav& st, StackWa
             w.node = kWalkDone;
         } else if (active && w.node != kWalkDone) {
             if (w.node >= 0) {
-                const float4* q = S.bin + 4 * (int64_t)w.node;
-                const float4 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2), a3 = __ldg(q + 3);
+                float4 a0, a1, a2, a3;
+                ldg64(S.bin + 4 * (int64_t)w.node, a0, a1, a2, a3);
                 float tl, tr;
                 const bool hl = box_entry(st, f3(a0), f3(a1), tl);
                 const bool hr = box_entry(st, f3(a2), f3(a3), tr);
