@@ -424,21 +424,27 @@ static void launch_gather_exact(int lanes, const GatherDev& G, const PassDev& P,
     }
 }
 
-// Grid of k_paths: resident blocks on every SM, but no more warps than items.
-static int path_grid(int64_t items, int device, bool stack) {
-    static int per_sm[2][64] = {{0}};
+// Grid of k_paths (multi: of k_paths_multi): resident blocks on every SM, but no more warps than
+// items.
+static int path_grid(int64_t items, int device, bool stack, bool multi = false) {
+    static int per_sm[2][2][64] = {{{0}}};
     static int sms[64] = {0};
     if (device < 0 || device >= 64) device = 0;
-    if (!per_sm[stack][device]) {
+    int& ps = per_sm[multi][stack][device];
+    if (!ps) {
         int b = 0;
         cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
-        if (stack)
+        if (multi && stack)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths_multi<true, false>, kTraceThreads, 0);
+        else if (multi)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths_multi<false, false>, kTraceThreads, 0);
+        else if (stack)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<true, false>, kTraceThreads, 0);
         else
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<false, false>, kTraceThreads, 0);
-        per_sm[stack][device] = std::max(1, b);
+        ps = std::max(1, b);
     }
-    const int64_t full = (int64_t)std::max(1, sms[device]) * per_sm[stack][device];
+    const int64_t full = (int64_t)std::max(1, sms[device]) * ps;
     const int64_t need = (items + kTraceThreads - 1) / kTraceThreads;
     return (int)std::max<int64_t>(1, std::min(full, need));
 }
@@ -987,7 +993,7 @@ static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st, int K, cuda
         const PathJob* jt = b->d_jobs + base + (size_t)k * n;
         if (ce == cudaSuccess && total[k] > 0) {
             ce = cudaMemsetAsync(ctr, 0, sizeof(uint32_t), ps);
-            const unsigned grid = (unsigned)path_grid((int64_t)total[k] * kTraceChunk, b->device, stack);
+            const unsigned grid = (unsigned)path_grid((int64_t)total[k] * kTraceChunk, b->device, stack, true);
             if (ce == cudaSuccess) {
                 if (stack)
                     shade ? k_paths_multi<true, true><<<grid, kTraceThreads, 0, ps>>>(jt, n, total[k], ctr)

@@ -708,7 +708,7 @@ struct MultiQueue {
 };
 
 template <bool STACK, bool SHADE>
-__global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
+__global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MULTI_MIN_BLOCKS)
 k_paths_multi(const PathJob* __restrict__ jobs, int32_t njobs, int32_t total_chunks, uint32_t* __restrict__ ctr) {
     MultiQueue mq;
     mq.init(jobs, njobs, total_chunks);
