@@ -424,24 +424,22 @@ static void launch_gather_exact(int lanes, const GatherDev& G, const PassDev& P,
     }
 }
 
-// Grid of k_paths (multi: of k_paths_multi): resident blocks on every SM, but no more warps than
-// items.
-static int path_grid(int64_t items, int device, bool stack, bool multi = false) {
-    static int per_sm[2][2][64] = {{{0}}};
+// Grid of a persistent path kernel (k_paths, or k_paths_multi when multi, of the given
+// instantiation): resident blocks on every SM, but no more warps than items.
+static int path_grid(int64_t items, int device, bool stack, bool shade, bool multi = false) {
+    static int per_sm[2][2][2][64] = {};
     static int sms[64] = {0};
     if (device < 0 || device >= 64) device = 0;
-    int& ps = per_sm[multi][stack][device];
+    int& ps = per_sm[multi][stack][shade][device];
     if (!ps) {
+        const void* const kernels[2][2][2] = {
+            {{(const void*)k_paths<false, false>, (const void*)k_paths<false, true>},
+             {(const void*)k_paths<true, false>, (const void*)k_paths<true, true>}},
+            {{(const void*)k_paths_multi<false, false>, (const void*)k_paths_multi<false, true>},
+             {(const void*)k_paths_multi<true, false>, (const void*)k_paths_multi<true, true>}}};
         int b = 0;
         cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
-        if (multi && stack)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths_multi<true, false>, kTraceThreads, 0);
-        else if (multi)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths_multi<false, false>, kTraceThreads, 0);
-        else if (stack)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<true, false>, kTraceThreads, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_paths<false, false>, kTraceThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernels[multi][stack][shade], kTraceThreads, 0);
         ps = std::max(1, b);
     }
     const int64_t full = (int64_t)std::max(1, sms[device]) * ps;
@@ -502,7 +500,7 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
         RegenDev R{r->ro, r->rd, r->rphi, r->started};
         GSP_CUDA_TRY(cudaMemsetAsync(r->qctr + 13, 0, sizeof(uint32_t), st));
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
-        const unsigned grid = (unsigned)path_grid(r->np, r->scene->ctx->device, stack);
+        const unsigned grid = (unsigned)path_grid(r->np, r->scene->ctx->device, stack, false);
         if (stack)
             S.attr ? k_photon_regen<true, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13)
                    : k_photon_regen<true, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13);
@@ -545,7 +543,7 @@ static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, co
     if (e != GSP_OK) return e;
     if (J.nchunks > 0) {
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
-        const unsigned grid = (unsigned)path_grid((int64_t)J.nchunks * kTraceChunk, r->scene->ctx->device, stack);
+        const unsigned grid = (unsigned)path_grid((int64_t)J.nchunks * kTraceChunk, r->scene->ctx->device, stack, J.S.attr != nullptr);
         if (stack)
             J.S.attr ? k_paths<true, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
                      : k_paths<true, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
@@ -993,7 +991,7 @@ static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st, int K, cuda
         const PathJob* jt = b->d_jobs + base + (size_t)k * n;
         if (ce == cudaSuccess && total[k] > 0) {
             ce = cudaMemsetAsync(ctr, 0, sizeof(uint32_t), ps);
-            const unsigned grid = (unsigned)path_grid((int64_t)total[k] * kTraceChunk, b->device, stack, true);
+            const unsigned grid = (unsigned)path_grid((int64_t)total[k] * kTraceChunk, b->device, stack, shade, true);
             if (ce == cudaSuccess) {
                 if (stack)
                     shade ? k_paths_multi<true, true><<<grid, kTraceThreads, 0, ps>>>(jt, n, total[k], ctr)

@@ -557,7 +557,7 @@ k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32
 // have depth <= max_eye, photon entries depth < max_photon (the host launches accordingly).
 // STACK: walk the child-pair layout with a stack (StackWalk) instead of the hit/miss links.
 template <bool STACK, bool SHADE>
-__global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
+__global__ void __launch_bounds__(kTraceThreads, SHADE ? GSP_PATH_SHADE_MIN_BLOCKS : GSP_PATH_MIN_BLOCKS)
 k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ ne_ptr, PathQ qp, DepositDev D,
         const uint32_t* __restrict__ np_ptr, uint32_t* __restrict__ ctr) {
     const int32_t cap = trav_cap(S);
@@ -708,7 +708,7 @@ struct MultiQueue {
 };
 
 template <bool STACK, bool SHADE>
-__global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MULTI_MIN_BLOCKS)
+__global__ void __launch_bounds__(kTraceThreads, SHADE ? GSP_PATH_SHADE_MIN_BLOCKS : GSP_PATH_MULTI_MIN_BLOCKS)
 k_paths_multi(const PathJob* __restrict__ jobs, int32_t njobs, int32_t total_chunks, uint32_t* __restrict__ ctr) {
     MultiQueue mq;
     mq.init(jobs, njobs, total_chunks);
