@@ -20,12 +20,6 @@ constexpr int kTraceThreads = 128;
 #ifndef GSP_PATH_MIN_BLOCKS
 #define GSP_PATH_MIN_BLOCKS 8
 #endif
-#ifndef GSP_PATH_SHADE_MIN_BLOCKS  // path kernels of scenes with shading data (72 registers)
-#define GSP_PATH_SHADE_MIN_BLOCKS 7
-#endif
-#ifndef GSP_PATH_MULTI_MIN_BLOCKS  // the multi-scene path kernel: 70 registers without spills
-#define GSP_PATH_MULTI_MIN_BLOCKS 7
-#endif
 constexpr int kTraceChunk = GSP_TRACE_CHUNK;           // rays a warp takes from the global counter at once
 constexpr int kTraceInner = GSP_TRACE_INNER;           // traversal steps between refills
 constexpr int kTraceLeafBatch = GSP_TRACE_LEAF_BATCH;  // pending leaves that trigger a warp-wide leaf test

@@ -9,6 +9,14 @@
 #include "launch.h"
 #include "persist.cuh"
 
+// resident blocks per SM of the path kernels beside GSP_PATH_MIN_BLOCKS (launch.h)
+#ifndef GSP_PATH_SHADE_MIN_BLOCKS  // path kernels of scenes with shading data (72 registers)
+#define GSP_PATH_SHADE_MIN_BLOCKS 7
+#endif
+#ifndef GSP_PATH_MULTI_MIN_BLOCKS  // the multi-scene path kernel: 70 registers without spills
+#define GSP_PATH_MULTI_MIN_BLOCKS 7
+#endif
+
 namespace gspd {
 
 constexpr float kPi = 3.14159265358979323846f;
