@@ -54,7 +54,7 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* 
         if (fin) {
             float u = 0.0f, v = 0.0f;
             if (st.slot >= 0)
-                flag = hit_error_factor(S.tris + 3 * st.slot, st.o, st.d, st.tbest, u, v) > refine_factor;
+                flag = hit_needs_refine(S.tris + 3 * st.slot, st.o, st.d, st.tbest, refine_factor, uv != nullptr, u, v);
             __stcs(tri + ray, out_slot ? st.slot : st.best);
             __stcs(tout + ray, st.best >= 0 ? st.tbest : __int_as_float(0x7f800000));
             if (uv) __stcs(uv + ray, make_float2(u, v));
@@ -105,7 +105,7 @@ k_trace_stack(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* _
         if (fin) {
             float u = 0.0f, v = 0.0f;
             if (st.slot >= 0)
-                flag = hit_error_factor(S.tris + 3 * st.slot, st.o, st.d, st.tbest, u, v) > refine_factor;
+                flag = hit_needs_refine(S.tris + 3 * st.slot, st.o, st.d, st.tbest, refine_factor, uv != nullptr, u, v);
             __stcs(tri + ray, st.best);
             __stcs(tout + ray, st.best >= 0 ? st.tbest : __int_as_float(0x7f800000));
             if (uv) __stcs(uv + ray, make_float2(u, v));

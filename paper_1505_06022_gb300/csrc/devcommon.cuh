@@ -133,7 +133,7 @@ __device__ __forceinline__ int ray_class(float3 d) {
 }
 
 __device__ __forceinline__ float safe_inv(float d) {
-    return 1.0f / (fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d);
+    return __frcp_rn(fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d);
 }
 
 // 1 + 2 gamma_3 with gamma_n = n u / (1 - n u), u = 2^-24: the far-plane scale that makes the
@@ -179,6 +179,27 @@ __device__ __forceinline__ float hit_error_factor(const float4* __restrict__ tri
     const float l1s = fabsf(s.x) + fabsf(s.y) + fabsf(s.z);
     const float l1e = (fabsf(e1.x) + fabsf(e1.y) + fabsf(e1.z)) * (fabsf(e2.x) + fabsf(e2.y) + fabsf(e2.z));
     return (l1s / (t * l1d) + 1.0f) * l1e * l1d / fabsf(det);
+}
+
+// hit_error_factor(...) > rf without its divisions: with L1 norms and t > 0 the test is
+// (|s| + t |d|) |e1| |e2| > rf t |det|. FP32 (u, v) only when want_uv (else left as they are).
+__device__ __forceinline__ bool hit_needs_refine(const float4* __restrict__ tri, float3 o, float3 d, float t,
+                                                 float rf, bool want_uv, float& u, float& v) {
+    const float4 A = __ldg(tri), B = __ldg(tri + 1), C = __ldg(tri + 2);
+    const float3 v0 = f3(A);
+    const float3 e1 = f3(B) - v0, e2 = f3(C) - v0;
+    const float3 p = cross3(d, e2);
+    const float det = dot3(e1, p);
+    const float3 s = o - v0;
+    if (want_uv) {
+        const float f = 1.0f / det;
+        u = f * dot3(s, p);
+        v = f * dot3(d, cross3(s, e1));
+    }
+    const float l1d = fabsf(d.x) + fabsf(d.y) + fabsf(d.z);
+    const float l1s = fabsf(s.x) + fabsf(s.y) + fabsf(s.z);
+    const float l1e = (fabsf(e1.x) + fabsf(e1.y) + fabsf(e1.z)) * (fabsf(e2.x) + fabsf(e2.y) + fabsf(e2.z));
+    return (l1s + t * l1d) * l1e > rf * t * fabsf(det);
 }
 
 // Hits whose estimated amplification exceeds this are re-evaluated in FP64 (expected FP32
