@@ -450,7 +450,12 @@ gsp_status gsp_hash_grid_build(gsp_context* ctx, const float* d_pos, int64_t n, 
  *  - n <= GSP_GRID_STATIC_MAX_POINTS and table_size <= GSP_GRID_STATIC_MAX_TABLE, otherwise
  *    GSP_ERR_INVALID_ARG with the limits in gsp_last_error_message();
  *  - the first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *    that device current; make that first call before any stream capture;
+ *    that device current, and so does the first call after the current context has changed (a
+ *    cudaDeviceReset, or another context made current through the driver API, loads the library's
+ *    device image again); make such a call before any stream capture: during a capture it fails
+ *    with GSP_ERR_BAD_STATE;
+ *  - an error left pending by earlier CUDA work on the calling thread is reported (GSP_ERR_CUDA,
+ *    message in gsp_last_error_message()) before anything is launched;
  *  - every call uses the same array, which keeps the previous call's contents (whatever must
  *    start at zero is cleared by the call itself); calls whose device work overlaps, on any
  *    streams, race on it and must be serialised by the caller.

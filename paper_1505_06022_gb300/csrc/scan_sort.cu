@@ -13,6 +13,7 @@ constexpr int kThreads = 256;
 constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;
 constexpr int kSortBlocks = 512;
+static_assert(kTile == kGspScanTile && kSortBlocks == kGspSortBlocks, "scratch sizes in scan_sort.h follow these");
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_scatter(const uint32_t* __res
 
 }  // namespace
 
-int64_t gsp_scan_temp_elems(int64_t n) { return (n + kTile - 1) / kTile + 1; }
+int64_t gsp_scan_temp_elems(int64_t n) { return gsp_scan_temp_elems_c(n); }
 
 cudaError_t gsp_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total,
                          uint32_t* temp, cudaStream_t st) {
@@ -185,7 +186,7 @@ cudaError_t gsp_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t*
     return cudaGetLastError();
 }
 
-int64_t gsp_sort_hist_elems() { return 256 * (int64_t)kSortBlocks; }
+int64_t gsp_sort_hist_elems() { return kGspSortHistElems; }
 
 cudaError_t gsp_radix_sort_u32(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
                                const uint32_t* d_n, int bits, uint32_t* hist, uint32_t* temp,

@@ -1368,10 +1368,18 @@ static bool ck_write(FILE* f, const void* d_src, size_t bytes, std::vector<char>
     return fwrite(buf.data(), 1, bytes, f) == bytes;
 }
 
-static bool ck_read(FILE* f, void* d_dst, size_t bytes, std::vector<char>& buf) {
-    buf.resize(bytes);
-    if (fread(buf.data(), 1, bytes, f) != bytes) return false;
-    return !bytes || cudaMemcpy(d_dst, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+// One section of a checkpoint read into host memory; copied to d_dst only once every section of
+// the file has been read (a short or corrupt file leaves the renderer as it was).
+struct CkSection {
+    void* d_dst;
+    std::vector<char> data;
+};
+
+static bool ck_read(FILE* f, void* d_dst, size_t bytes, std::vector<CkSection>& out) {
+    CkSection c{d_dst, std::vector<char>(bytes)};
+    if (fread(c.data.data(), 1, bytes, f) != bytes) return false;
+    out.push_back(std::move(c));
+    return true;
 }
 
 gsp_status gsp_sppm_save(gsp_sppm* r, const char* path) {
@@ -1405,7 +1413,7 @@ gsp_status gsp_sppm_load(gsp_sppm* r, const char* path) {
     char magic[8];
     int64_t hdr[7];
     gsp_sppm_params P, mine = r->P;
-    std::vector<char> buf;
+    std::vector<CkSection> sec;
     gsp_status st = GSP_OK;
     const bool read_ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkMagic, 8) == 0 &&
                          fread(hdr, sizeof hdr, 1, f) == 1 && fread(&P, sizeof P, 1, f) == 1;
@@ -1419,19 +1427,27 @@ gsp_status gsp_sppm_load(gsp_sppm* r, const char* path) {
         gsp_set_last_error("gsp_sppm_load: the checkpoint was written by a renderer with other parameters");
         st = GSP_ERR_BAD_STATE;
     } else {
-        bool ok = ck_read(f, r->st0, r->npix * sizeof(float4), buf) && ck_read(f, r->st1, r->npix * sizeof(float4), buf);
+        bool ok = ck_read(f, r->st0, r->npix * sizeof(float4), sec) && ck_read(f, r->st1, r->npix * sizeof(float4), sec);
         if (ok && r->P.photon_mode == GSP_REGEN)
-            ok = ck_read(f, r->ro, r->np * sizeof(float4), buf) && ck_read(f, r->rd, r->np * sizeof(float4), buf) &&
-                 ck_read(f, r->rphi, r->np * sizeof(float4), buf) &&
-                 ck_read(f, r->started, sizeof(unsigned long long), buf);
+            ok = ck_read(f, r->ro, r->np * sizeof(float4), sec) && ck_read(f, r->rd, r->np * sizeof(float4), sec) &&
+                 ck_read(f, r->rphi, r->np * sizeof(float4), sec) &&
+                 ck_read(f, r->started, sizeof(unsigned long long), sec);
         if (ok && hdr[6] > 0)
-            ok = ck_read(f, r->rhist, (size_t)hdr[6] * r->npix * sizeof(float), buf) &&
-                 ck_read(f, r->shist, (size_t)hdr[6] * r->npix * sizeof(float4), buf);
-        if (ok) r->passes = hdr[3];
-        st = ok ? GSP_OK : GSP_ERR_IO;
+            ok = ck_read(f, r->rhist, (size_t)hdr[6] * r->npix * sizeof(float), sec) &&
+                 ck_read(f, r->shist, (size_t)hdr[6] * r->npix * sizeof(float4), sec);
+        ok = ok && fgetc(f) == EOF;  // nothing may follow the last section
+        if (!ok) {
+            gsp_set_last_error("gsp_sppm_load: the checkpoint is short or has trailing data; the renderer is unchanged");
+            st = GSP_ERR_IO;
+        }
     }
     fclose(f);
-    return st;
+    if (st != GSP_OK) return st;
+    // the whole file has been read: only now is the renderer's state replaced
+    for (const CkSection& c : sec)
+        if (!c.data.empty()) GSP_CUDA_TRY(cudaMemcpy(c.d_dst, c.data.data(), c.data.size(), cudaMemcpyHostToDevice));
+    r->passes = hdr[3];
+    return GSP_OK;
 }
 
 gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream) {
@@ -1501,10 +1517,7 @@ int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity) {
 
 // Scratch (uint32 words) of a hash-grid build over n points with T buckets: key/value
 // ping-pong buffers, the radix histogram, scan partials and the device copy of n.
-int64_t gsp_grid_scratch_words(int64_t n, int64_t T) {
-    return 4 * n + gsp_sort_hist_elems() +
-           std::max(gsp_scan_temp_elems(T), gsp_scan_temp_elems(gsp_sort_hist_elems())) + 64;
-}
+int64_t gsp_grid_scratch_words(int64_t n, int64_t T) { return gsp_grid_scratch_words_c(n, T); }
 
 // Exact hash grid of n points: keys -> counts -> in-place bucket scan -> stable radix sort.
 gsp_status gsp_grid_build_with(const float4* pos, int64_t n, float cell_h, int64_t T, uint32_t* order,

@@ -73,3 +73,30 @@ def test_mismatched_checkpoint_is_refused(ctx, tmp_path):
     with pytest.raises(gsp.GspError) as e:
         other.load(str(tmp_path / "missing.bin"))
     assert e.value.code == -8
+
+
+def test_short_or_padded_checkpoint_leaves_the_renderer_unchanged(ctx, tmp_path):
+    sc = I.cornell_box(width=24, height=16)
+    s = gsp.Scene(ctx, sc)
+    params = gsp.sppm_params(sc, 2000, seed=5)
+    src = gsp.Renderer(s, params)
+    src.run(3)
+    path = tmp_path / "ck.bin"
+    src.save(str(path))
+    data = path.read_bytes()
+    r = gsp.Renderer(s, params)
+    r.run(1)
+    before = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in r.state().items()}
+    for bad in (data[: len(data) - 20], data + b"\0" * 16):  # cut in the last section / trailing bytes
+        bp = tmp_path / "bad.bin"
+        bp.write_bytes(bad)
+        with pytest.raises(gsp.GspError) as e:
+            r.load(str(bp))
+        assert e.value.code == -8
+        after = r.state()
+        assert after["passes"] == 1
+        for k, v in before.items():
+            if hasattr(v, "clone"):
+                assert torch.equal(after[k], v), k
+    r.load(str(path))  # the intact file still loads
+    assert r.state()["passes"] == 3

@@ -1,7 +1,7 @@
 """The allocation-free hash-grid build (for callers that cannot allocate device memory, such as
 hosts whose device memory belongs to another allocator, or loops that must not block on
 cudaMalloc) gives the same grid as the allocating entry point, on consecutive calls that reuse its
-static scratch.
+static scratch, up to its largest point count and table size, and allocates nothing.
 
 Kept in a file that pytest collects last, so a run that stops at the first failure has run
 every other test before this one."""
@@ -37,6 +37,34 @@ def test_static_build_matches_allocating_build_twice():
         assert torch.equal(order, want_order)
         assert torch.equal(starts, want_starts)
         assert int(starts[-1]) == n
+    ctx.close()
+
+
+def test_static_build_at_its_largest_sizes_on_a_side_stream_allocates_nothing():
+    ctx = gsp.Context(0)
+    torch.cuda.set_device(0)
+    n, T = gsp.GRID_STATIC_MAX_POINTS, gsp.GRID_STATIC_MAX_TABLE
+    pos = cloud(n, 3)
+    want_order, want_starts = gsp.gsp_hash_grid_build(ctx.h, pos, 0.003, T)
+    order = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    starts = torch.full((T + 1,), -7, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    gsp.gsp_hash_grid_build_static(pos, 0.003, T, order, starts, side)  # loads and looks up once
+    side.synchronize()
+    assert torch.equal(order, want_order) and torch.equal(starts, want_starts)
+    # a second call on the same stream: neither torch nor the driver sees an allocation
+    order.fill_(-7)
+    starts.fill_(-7)
+    torch.cuda.synchronize()
+    allocs = torch.cuda.memory_stats()["allocation.all.allocated"]
+    free0, _ = torch.cuda.mem_get_info()
+    gsp.gsp_hash_grid_build_static(pos, 0.003, T, order, starts, side)
+    side.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_stats()["allocation.all.allocated"] == allocs
+    assert free1 == free0
+    assert torch.equal(order, want_order) and torch.equal(starts, want_starts)
     ctx.close()
 
 
