@@ -112,6 +112,8 @@ def lib():
         L.orc_sppm_set_texture.restype = I32
         L.orc_sppm_set_texture.argtypes = [P, I32, P, I32, I32]
         L.orc_sppm_surface.argtypes = [P, P, I64, P]
+        L.orc_sah_split.restype = I32
+        L.orc_sah_split.argtypes = [P, P, P, I64, I32, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -202,6 +204,23 @@ class Mesh:
         lib().orc_closest_hit(self.h, _p(rays), n, 0 if brute else 1, _p(ids), _p(t), _p(u), _p(v),
                               _p(nd), nthreads or nthreads_default())
         return ids, t, u, v, nd
+
+
+def sah_split(verts, tris, subset, bins=16):
+    """Binned SAH split of the triangles `subset` (Sec. 3.1): None if no boundary leaves both
+    sides non-empty, else dict(axis, boundary, cost, left = the subset's triangles in bins below
+    the boundary); `near` = smallest centroid distance from an interior bin boundary (bin widths)."""
+    v = np.ascontiguousarray(verts, np.float32)
+    t = np.ascontiguousarray(tris, np.int32)
+    sub = np.ascontiguousarray(subset, np.int32)
+    ax, b, cost, near = C.c_int32(), C.c_int32(), C.c_double(), C.c_double()
+    left = np.zeros(len(sub), np.int32)
+    ok = lib().orc_sah_split(_p(v), _p(t), _p(sub), len(sub), bins, C.byref(ax), C.byref(b), C.byref(cost),
+                             C.byref(near), _p(left))
+    if not ok:
+        return dict(split=False, near=near.value)
+    return dict(split=True, axis=ax.value, boundary=b.value, cost=cost.value, near=near.value,
+                left=sub[left.astype(bool)])
 
 
 def mt(v0, v1, v2, ray):

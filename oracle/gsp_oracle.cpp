@@ -15,6 +15,8 @@
 //                     textbook MLCG s' = a*s mod m. Per-stream seeding is counter-based
 //                     (splitmix64, Steele/Lea/Flood 2014) instead of host xorshift (Sec. 3.2).
 //  * mt_intersect     Moller-Trumbore ray/triangle test (the leaf test of Fig. 3), FP64.
+//  * sah split        the binned SAH split of Sec. 3.1's top-down build (Wald 2007), every
+//                     candidate evaluated from scratch; the library's host build must pick it.
 //  * closest hit      brute force over every triangle (definition of the closest hit) with
 //                     the lexicographic (t, id) minimum; a simple median-split BVH with a stack
 //                     is used only for speed and is checked against brute force by the tests.
@@ -475,6 +477,88 @@ void orc_closest_hit(void* mesh, const float* rays, int64_t n, int32_t mode, int
             if (nondeg) nondeg[i] = classify(M, mode == 0, o, d, tmin, tmax, h) ? 1 : 0;
         }
     });
+}
+
+// Binned SAH split of a set of triangles (Sec. 3.1 builds the tree top-down with the surface
+// area heuristic on the CPU, after Wald 2007), written out plainly: the centroid of a triangle
+// is the centre of its bounding box; along each axis whose centroid extent is positive the
+// centroid range is cut into `bins` equal bins (a centroid at the top end belongs to the last
+// bin); each boundary b = 1 .. bins-1 splits the set into the triangles of bins < b (left) and
+// of bins >= b (right); its cost is 1 + (A_L N_L + A_R N_R) / A_P with A the surface area of the
+// bounding box of the triangles on each side and of the whole set. Every (axis, boundary) with
+// two non-empty sides is evaluated from scratch; the cheapest wins, the first in (axis,
+// boundary) order on ties. Returns 1 and (axis, boundary, cost) if such a split exists, else 0;
+// left[i] = 1 if subset[i] goes to the left side of the split. *near_bin receives the smallest distance, in bin widths, of any centroid from an interior bin
+// boundary on any axis (a build that bins in FP32 may put such a centroid in the other bin).
+int32_t orc_sah_split(const float* verts, const int32_t* tris, const int32_t* subset, int64_t n,
+                      int32_t bins, int32_t* out_axis, int32_t* out_boundary, double* out_cost,
+                      double* near_bin, int32_t* left) {
+    std::vector<V3> lo(n), hi(n), cen(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t t = subset[i];
+        V3 p[3];
+        for (int k = 0; k < 3; ++k) {
+            const float* q = verts + 3 * (int64_t)tris[3 * t + k];
+            p[k] = {(double)q[0], (double)q[1], (double)q[2]};
+        }
+        lo[i] = {std::min({p[0].x, p[1].x, p[2].x}), std::min({p[0].y, p[1].y, p[2].y}),
+                 std::min({p[0].z, p[1].z, p[2].z})};
+        hi[i] = {std::max({p[0].x, p[1].x, p[2].x}), std::max({p[0].y, p[1].y, p[2].y}),
+                 std::max({p[0].z, p[1].z, p[2].z})};
+        cen[i] = (lo[i] + hi[i]) * 0.5;
+    }
+    auto area = [](const V3& a, const V3& b) {
+        const double dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+        return 2.0 * (dx * dy + dy * dz + dz * dx);
+    };
+    V3 plo{INFINITY, INFINITY, INFINITY}, phi{-INFINITY, -INFINITY, -INFINITY};
+    V3 clo = plo, chi = phi;
+    for (int64_t i = 0; i < n; ++i) {
+        plo = {std::min(plo.x, lo[i].x), std::min(plo.y, lo[i].y), std::min(plo.z, lo[i].z)};
+        phi = {std::max(phi.x, hi[i].x), std::max(phi.y, hi[i].y), std::max(phi.z, hi[i].z)};
+        clo = {std::min(clo.x, cen[i].x), std::min(clo.y, cen[i].y), std::min(clo.z, cen[i].z)};
+        chi = {std::max(chi.x, cen[i].x), std::max(chi.y, cen[i].y), std::max(chi.z, cen[i].z)};
+    }
+    const double ap = area(plo, phi);
+    double best = INFINITY, nearest = INFINITY;
+    int best_axis = -1, best_b = -1;
+    std::vector<int> bin(n), best_bin;
+    for (int a = 0; a < 3; ++a) {
+        const double ext = comp(chi, a) - comp(clo, a);
+        if (!(ext > 0)) continue;
+        for (int64_t i = 0; i < n; ++i) {
+            const double q = bins * (comp(cen[i], a) - comp(clo, a)) / ext;
+            bin[i] = std::min(bins - 1, (int)std::floor(q));
+            const double dist = std::fabs(q - std::round(q));
+            if (q > 0.5 && q < bins - 0.5) nearest = std::min(nearest, dist);
+        }
+        for (int b = 1; b < bins; ++b) {
+            V3 llo{INFINITY, INFINITY, INFINITY}, lhi{-INFINITY, -INFINITY, -INFINITY};
+            V3 rlo = llo, rhi = lhi;
+            int64_t nl = 0, nr = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                V3 &L = bin[i] < b ? llo : rlo, &H = bin[i] < b ? lhi : rhi;
+                L = {std::min(L.x, lo[i].x), std::min(L.y, lo[i].y), std::min(L.z, lo[i].z)};
+                H = {std::max(H.x, hi[i].x), std::max(H.y, hi[i].y), std::max(H.z, hi[i].z)};
+                (bin[i] < b ? nl : nr) += 1;
+            }
+            if (nl == 0 || nr == 0) continue;
+            const double c = 1.0 + (area(llo, lhi) * (double)nl + area(rlo, rhi) * (double)nr) / ap;
+            if (c < best) {
+                best = c;
+                best_axis = a;
+                best_b = b;
+                best_bin = bin;
+            }
+        }
+    }
+    *near_bin = nearest;
+    if (best_axis < 0) return 0;
+    *out_axis = best_axis;
+    *out_boundary = best_b;
+    *out_cost = best;
+    for (int64_t i = 0; i < n; ++i) left[i] = best_bin[i] < best_b ? 1 : 0;
+    return 1;
 }
 
 // Moller-Trumbore on one triangle (for closed-form tests).

@@ -444,3 +444,98 @@ def batch_scenes(count: int = 64, seed: int = 5):
         sc.name = f"batch{i}"
         out.append(sc)
     return out
+
+
+# ----------------------------------------------------------------------------------------
+# small specular scenes with closed-form answers (mirror and glass branches)
+# ----------------------------------------------------------------------------------------
+
+def _rotated_box(mb, center, half, angles, mat):
+    """A box of half extents `half`, rotated by `angles` (radians, about x then y) around its
+    centre, outward faces."""
+    ax, ay = angles
+    rx = np.array([[1, 0, 0], [0, np.cos(ax), -np.sin(ax)], [0, np.sin(ax), np.cos(ax)]])
+    ry = np.array([[np.cos(ay), 0, np.sin(ay)], [0, 1, 0], [-np.sin(ay), 0, np.cos(ay)]])
+    c = np.array([[x, y, z] for z in (-1, 1) for y in (-1, 1) for x in (-1, 1)], np.float64)
+    c = c[[0, 1, 3, 2, 4, 5, 7, 6]]  # the corner order of _MeshBuilder.box
+    v = (c * np.asarray(half)) @ (ry @ rx).T + np.asarray(center, np.float64)
+    faces = [[0, 3, 2, 1], [4, 5, 6, 7], [0, 4, 7, 3], [1, 2, 6, 5], [0, 1, 5, 4], [3, 7, 6, 2]]
+    tris = []
+    for a, b, cc, d in faces:
+        tris += [[a, b, cc], [a, cc, d]]
+    mb.add(v, tris, mat)
+
+
+def specular_furnace_scene(albedo: float = 0.5, le: float = 1.0, n: int = 32, sphere_n: int = 12,
+                           width: int = 12, height: int = 12, mirror_albedo=(1.0, 1.0, 1.0),
+                           glass_albedo=(0.3, 0.3, 0.3)) -> Scene:
+    """The white furnace (closed unit icosphere wound inward, every wall triangle a diffuse
+    emitter of radiance `le` with albedo `albedo`) with a mirror sphere of radius 0.22 and a
+    rotated glass box (IOR 1.5, half extents 0.2 x 0.16 x 0.12) in front of a camera at the centre
+    looking down -z. A ray inside a box always leaves it again (internal reflections at one pair of
+    faces keep its angle to the others), unlike a faceted sphere, which can trap light by total
+    internal reflection. The glass albedo is not used by the method (a dielectric only reflects or
+    refracts); it is set to 0.3 on purpose."""
+    mb = _MeshBuilder()
+    v, t = icosphere_unit(n)
+    mb.add(v, t[:, [0, 2, 1]], 0)  # walls, normals toward the centre
+    v, t = icosphere_unit(sphere_n)
+    mb.add(v * 0.22 + np.array([-0.3, -0.05, -0.45]), t, 1)
+    _rotated_box(mb, (0.3, 0.05, -0.45), (0.2, 0.16, 0.12), (0.45, 0.6), 2)
+    verts, tris, tri_mat = mb.build()
+    mats = np.concatenate([material(DIFFUSE, (albedo,) * 3, (le,) * 3), material(MIRROR, mirror_albedo),
+                           material(DIELECTRIC, glass_albedo, ior=1.5)])
+    cam = camera((0, 0, 0), (0, 0, -1), (0, 1, 0), 60.0, width, height)
+    return Scene(verts, tris, tri_mat, mats, cam, name=f"specular_furnace{albedo}")
+
+
+def mirror_view_scene(mirror_albedo=(0.9, 0.6, 0.3), le=(4.0, 5.0, 6.0), width: int = 8, height: int = 8) -> Scene:
+    """A camera at height 0.5 looking straight down at a 20 x 20 mirror floor (y = 0) under a
+    20 x 20 emitter ceiling (y = 1) facing down: every eye ray reflects once into the emitter."""
+    mb = _MeshBuilder()
+    S = 10.0
+    mb.quad([-S, 0, -S], [-S, 0, S], [S, 0, S], [S, 0, -S], 0)  # normal +y
+    mb.quad([-S, 1, -S], [S, 1, -S], [S, 1, S], [-S, 1, S], 1)  # normal -y
+    verts, tris, tri_mat = mb.build()
+    mats = np.concatenate([material(MIRROR, mirror_albedo), material(EMITTER, emission=le)])
+    cam = camera((0.3, 0.5, 0.2), (0.3, 0.0, 0.2001), (0, 0, 1), 30.0, width, height)
+    return Scene(verts, tris, tri_mat, mats, cam, name="mirror_view")
+
+
+def mirror_corridor_scene(length: int, mirror_albedo=(0.95, 0.9, 0.85), le=(3.0, 3.0, 3.0)) -> Scene:
+    """Two parallel mirrors (y = 0 facing up, y = 1 facing down) from x = -1 to x = `length`, an
+    emitter wall at x = `length` facing -x, and a one-pixel camera at (0, 0.5, 0) with a tiny field
+    of view looking up at 45 degrees along +x: its ray meets the mirrors at x = 0.5, 1.5, ...,
+    `length` - 0.5 (`length` reflections) and then the emitter at height 0.5."""
+    mb = _MeshBuilder()
+    X = float(length)
+    z0, z1 = -0.7, 1.0  # quad diagonals cross z = 0 away from the reflection points
+    mb.quad([-1, 0, z0], [-1, 0, z1], [X, 0, z1], [X, 0, z0], 0)  # normal +y
+    mb.quad([-1, 1, z0], [X, 1, z0], [X, 1, z1], [-1, 1, z1], 0)  # normal -y
+    mb.quad([X, -0.5, z0], [X, -0.5, z1], [X, 1.5, z1], [X, 1.5, z0], 1)  # normal -x
+    verts, tris, tri_mat = mb.build()
+    mats = np.concatenate([material(MIRROR, mirror_albedo), material(EMITTER, emission=le)])
+    cam = camera((0, 0.5, 0), (1, 1.5, 0), (0, 0, 1), 0.01, 1, 1)
+    return Scene(verts, tris, tri_mat, mats, cam, name=f"mirror_corridor{length}")
+
+
+def photon_mirror_scene(mirror_albedo=(0.9, 0.6, 0.3), le: float = 5.0, light: float = 0.2,
+                        mirror: bool = True, glass_albedo=(0.3, 0.3, 0.3)) -> Scene:
+    """A `light` x `light` emitter at y = 1 facing down over a 40 x 40 floor at y = 0, under a
+    diffuse ceiling at y = 2 facing down; a camera looks up at the ceiling. mirror=True: the floor
+    is a mirror of albedo `mirror_albedo`, so a photon reflects once before it lands on the
+    ceiling. mirror=False: the floor is diffuse and a 40 x 40 glass slab (IOR 1.5, y in
+    [0.3, 0.5]) lies between the light and the floor."""
+    mb = _MeshBuilder()
+    S, h = 20.0, light / 2
+    mb.quad([-S, 0, -S], [-S, 0, S], [S, 0, S], [S, 0, -S], 0)  # floor, normal +y
+    mb.quad([-S, 2, -S], [S, 2, -S], [S, 2, S], [-S, 2, S], 1)  # ceiling, normal -y
+    mb.quad([-h, 1, -h], [h, 1, -h], [h, 1, h], [-h, 1, h], 2)  # light, normal -y
+    if not mirror:
+        mb.box((-S, 0.3, -S), (S, 0.5, S), 3)
+    verts, tris, tri_mat = mb.build()
+    floor = material(MIRROR, mirror_albedo) if mirror else material(DIFFUSE, (0.5, 0.5, 0.5))
+    mats = np.concatenate([floor, material(DIFFUSE, (0.6, 0.6, 0.6)), material(EMITTER, emission=(le,) * 3),
+                           material(DIELECTRIC, glass_albedo, ior=1.5)])
+    cam = camera((0.0, 1.5, 0.0), (0.0, 2.0, 0.0001), (0, 0, 1), 60.0, 4, 4)
+    return Scene(verts, tris, tri_mat, mats, cam, name="photon_mirror" if mirror else "photon_glass")

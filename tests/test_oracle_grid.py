@@ -34,3 +34,20 @@ def test_points_of_one_cell_share_a_bucket_and_cells_spread():
     # the flag marks coordinates on a cell face
     face = np.array([[(5 - 0.381966) * h, 0.1, 0.1]], np.float32)
     assert O.hash_grid(face, h, 64)[3][0] == 1
+
+
+def test_teschner_buckets_by_hand():
+    # Teschner et al. 2003: (ix * 73856093) ^ (iy * 19349663) ^ (iz * 83492791) in 32-bit
+    # arithmetic, then mod the table size. Worked by hand:
+    #   cell (1, 2, 3):   73856093 ^ 38699326 ^ 250478373 = 147163718; mod 2^20 = 363078
+    #   cell (-1, 0, 5):  (2^32 - 73856093) ^ 0 ^ 417463955 = 4221111203 ^ 417463955
+    #                     = 3816355120; mod 2^20 = 587056
+    #   cell (7, -3, -2): 516992651 ^ 4236918307 ^ 4127981714 = 341217338; mod 2^16 = 36922
+    # A wrong constant, + instead of ^, or a negative cell that does not wrap mod 2^32 fails.
+    h = 0.25
+    cells = np.array([[1, 2, 3], [-1, 0, 5], [7, -3, -2]], np.float64)
+    pts = ((cells + 0.5 - 0.381966) * h).astype(np.float32)  # cell centres of the shifted lattice
+    b, _, _, near = O.hash_grid(pts[:2], h, 1 << 20)
+    assert list(b) == [363078, 587056] and not near.any()
+    b, _, _, _ = O.hash_grid(pts[2:], h, 1 << 16)
+    assert list(b) == [36922]

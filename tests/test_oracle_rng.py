@@ -86,6 +86,31 @@ def test_seeded_states_in_range_and_distinct():
         assert not np.array_equal(O.rng_seed(*args), base)
 
 
+def test_seeded_state_by_hand():
+    # The counter-based seeding of reading 3, worked through for (seed 1, scene 2, domain 1,
+    # pass 3, id 12345) with SplitMix64 (pinned above by its published outputs):
+    #   h0 = sm(1)                           = 0x910a2dec89025cc1
+    #   h1 = sm(h0 ^ 2)                      = 0xbcd9dbb49673066b
+    #   h2 = sm(h1 ^ (1 << 32 | 3))          = 0x7aa7cf351a3f1a78
+    #   h3 = sm(h2 ^ 12345)                  = 0xc54337904c97fb00
+    #   h4 = sm(h3)                          = 0xf3963e55104aacf9
+    #   s_i = 1 + (32-bit word i of (h3 low, h3 high, h4 low, h4 high)) mod (m_i - 1)
+    #       = 1 + 0x4c97fb00 mod 4194286, 1 + 0xc5433790 mod 4194276,
+    #         1 + 0x104aacf9 mod 4194190, 1 + 0xf3963e55 mod 4194166
+    #       = 1577093, 232925, 707052, 1592162
+    # A swapped word order, a missing +1, mod m instead of m - 1, or the pass and domain packed
+    # the other way round fails.
+    sm = O.splitmix64
+    h0 = sm(1)
+    h1 = sm(h0 ^ 2)
+    h2 = sm(h1 ^ ((1 << 32) | 3))
+    h3 = sm(h2 ^ 12345)
+    h4 = sm(h3)
+    assert [h0, h1, h2, h3, h4] == [0x910a2dec89025cc1, 0xbcd9dbb49673066b, 0x7aa7cf351a3f1a78,
+                                    0xc54337904c97fb00, 0xf3963e55104aacf9]
+    assert list(O.rng_seed(1, 2, 1, 3, 12345)) == [1577093, 232925, 707052, 1592162]
+
+
 def test_uniformity_and_independence():
     scipy_stats = pytest.importorskip("scipy.stats")
     u = O.rng_draws(1, 0, 1, 0, np.arange(1 << 14), 64).astype(np.float64)  # 2^20 draws
