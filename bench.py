@@ -38,14 +38,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# FP32 instructions of the traversal kernel, counted from its source: per node visit 6 FSUB,
-# 6 FMUL, 6 FMIN/FMAX per axis, 3 FMAX + 2 FMIN for the interval, 1 FMUL + 1 FMIN for the
-# conservative far plane, 1 compare; per triangle test (Moller-Trumbore) about 40.
-OPS_PER_NODE = 26
-OPS_PER_TRI = 40
+# Work model of a closest-hit query (the measurement plan's cost model): per node visit a 32-byte
+# node and 12 FP32 operations (the slab test), per triangle test a 48-byte triangle and 30 FP32
+# operations (Moller-Trumbore), per ray a 32-byte ray in and an 8-byte hit out. Roofline time =
+# max(bytes / memory bandwidth, flops / FP32 peak), FP32 peak = SMs x 128 lanes x 2 x clock.
+FLOPS_PER_NODE = 12
+FLOPS_PER_TRI = 30
 BYTES_PER_NODE = 32
 BYTES_PER_TRI = 48
 BYTES_PER_RAY_IO = 32 + 8
+FALLBACK_HBM_GBS = 6800.0
 
 
 def load_peaks():
@@ -266,25 +268,15 @@ def run_ours(args, world, rank, local):
     htri, _, vis, tests = scene.host_walk(rays_h[chk])
     agree = float(np.mean(htri == tri_pin.numpy()[chk]))
 
-    # ---- roofline of the traversal kernel (FP32 ALU) ----
+    # ---- roofline of the traversal: max(bytes / bandwidth, flops / FP32 peak) ----
     peaks = load_peaks()
+    tiers = measure_tiers(ctx)
     wk = stratified(n, 65536, seed=6)
     _, _, visw, testw = scene.host_walk(rays_h[wk])
     v_node, v_tri = float(visw.mean()), float(testw.mean())
-    ops = (OPS_PER_NODE * v_node + OPS_PER_TRI * v_tri) * n
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
-    peak_tops = sm_count * 128 * sm_max * 1e6 / 1e12
-    achieved = ops / (ms_step / 1000.0) / 1e12
-    algo_bytes_ray = BYTES_PER_NODE * v_node + BYTES_PER_TRI * v_tri + BYTES_PER_RAY_IO
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tops, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / peak_tops, 4), "traffic": None,
-                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (measured max SM clock)",
-                "ops_per_ray": round(OPS_PER_NODE * v_node + OPS_PER_TRI * v_tri, 2),
-                "node_visits_per_ray": round(v_node, 3), "tri_tests_per_ray": round(v_tri, 3),
-                "algorithmic_bytes_per_ray": round(algo_bytes_ray, 1),
-                "algorithmic_GBps": round(algo_bytes_ray * n / (ms_step / 1000.0) / 1e9, 1),
-                "hbm_peak_GBps": (peaks or {}).get("hbm_gbs")}
+    roofline = traversal_roofline(v_node, v_tri, n, ms_step, sm_count, peaks, tiers)
+    rl = {"peaks": peaks, "tiers": tiers, "sm_count": sm_count}
     traffic_file = os.path.join(ROOT, "profiles", "trace_traffic.json")
     if os.path.exists(traffic_file):
         try:
@@ -297,10 +289,10 @@ def run_ours(args, world, rank, local):
     # ---- Fig. 4's traversal comparison, SPPM pass at 512x512, the gradient workload, the batch ----
     fig4 = bench_traversals(args, ctx, dev, stream, sc, scene, rays) if not args.skip_fig4 else None
     cornell = bench_cornell(args, ctx, dev, stream, with_cpu(args, world, rank)) if not args.skip_sppm else None
-    sppm = bench_sppm(args, ctx, dev, stream, pg) if not args.skip_sppm else None
+    sppm = bench_sppm(args, ctx, dev, stream, pg, rl) if not args.skip_sppm else None
     shaded = bench_shaded(args, ctx, dev, stream, pg) if not (args.skip_sppm or args.skip_shaded) else None
-    grad = bench_grad(args, ctx, dev, stream) if not args.skip_grad else None
-    batch = bench_batch(args, ctx, dev, stream) if not args.skip_batch else None
+    grad = bench_grad(args, ctx, dev, stream, rl) if not args.skip_grad else None
+    batch = bench_batch(args, ctx, dev, stream, rl) if not args.skip_batch else None
     modes = bench_modes(args, ctx, dev, stream) if not args.skip_modes else None
 
     # ---- CPU baseline: the oracle on the same workload ----
@@ -342,6 +334,98 @@ def run_ours(args, world, rank, local):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def measure_tiers(ctx):
+    """Read bandwidth of L2 (streaming over 32 and 48 MB buffers, resident after a warm-up pass;
+    the larger rate is the L2 peak) and of HBM (4 GiB), from the library's microbenchmark."""
+    from paper_1505_06022_gb300 import gsp
+    l2 = {f"{mb}MB": round(gsp.gsp_measure_read_bandwidth(ctx.h, mb << 20, 300), 1) for mb in (32, 48)}
+    hbm = round(gsp.gsp_measure_read_bandwidth(ctx.h, 4 << 30, 3), 1)
+    return {"l2_read_gbs": l2, "l2_peak_gbs": max(l2.values()), "hbm_read_gbs": hbm}
+
+
+def fp32_peak_tflops(sm_count, peaks):
+    sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
+    return sm_count * 128 * 2 * sm_max * 1e6 / 1e12, sm_max
+
+
+def traversal_roofline(v_node, v_tri, n, ms, sm_count, peaks, tiers):
+    """The bench line's roofline block for closest hit: algorithmic bytes and flops of n rays with
+    v_node node visits and v_tri triangle tests per ray, against the call's time `ms`."""
+    bytes_ray = BYTES_PER_NODE * v_node + BYTES_PER_TRI * v_tri + BYTES_PER_RAY_IO
+    flops_ray = FLOPS_PER_NODE * v_node + FLOPS_PER_TRI * v_tri
+    hbm = (peaks or {}).get("hbm_gbs")
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (copy), of measured"
+    if not hbm:
+        hbm, hbm_src = FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+    fp32, sm_max = fp32_peak_tflops(sm_count, peaks)
+    s = ms / 1000.0
+    t_hbm = bytes_ray * n / (hbm * 1e9)
+    t_flop = flops_ray * n / (fp32 * 1e12)
+    achieved = bytes_ray * n / s / 1e9
+    l2 = tiers["l2_peak_gbs"]
+    return {"bound": "hbm" if t_hbm >= t_flop else "alu", "achieved": round(achieved, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": hbm_src,
+            "roofline_ms": round(1000 * max(t_hbm, t_flop), 4), "kernel_ms": round(ms, 4),
+            "kernel_timing": "CUDA events around the whole closest-hit call (k_trace and the two small "
+                             "launches beside it)",
+            "l2": {"peak": l2, "frac": round(achieved / l2, 4), "unit": "GB/s",
+                   "source": "gsp_measure_read_bandwidth, buffers of 32 and 48 MB resident in L2"},
+            "fp32": {"achieved": round(flops_ray * n / s / 1e12, 3), "peak": round(fp32, 2), "unit": "TFLOP/s",
+                     "frac": round(flops_ray * n / s / 1e12 / fp32, 4),
+                     "source": f"{sm_count} SMs x 128 FP32 lanes x 2 (FMA) x {sm_max:.0f} MHz"},
+            "node_visits_per_ray": round(v_node, 3), "tri_tests_per_ray": round(v_tri, 3),
+            "algorithmic_bytes_per_ray": round(bytes_ray, 1), "flops_per_ray": round(flops_ray, 1),
+            "algorithmic_bytes_per_launch": int(round(bytes_ray * n)), "tiers": tiers}
+
+
+# Work model of an SPPM pass (the measurement plan's per-pass figures): every traced ray as a
+# closest-hit query above; 3 x 32 bytes per deposit (written, sorted, read back); 32 bytes per
+# photon a gather reads and 72 bytes per pixel (hit point and progressive state). The adjoint adds
+# 20 bytes per hit point its photon-centric gather reads and 96 bytes per pixel (hit-point grid,
+# radius and flux history, loss gradient).
+def sppm_work(c, npix, passes, adjoint=False):
+    npix, passes = int(npix), int(passes)
+    rays = c["eye_rays"] + c["photon_rays"]
+    parts = {"traversal": BYTES_PER_NODE * c["node_visits"] + BYTES_PER_TRI * c["tri_tests"] + BYTES_PER_RAY_IO * rays,
+             "deposit": 3 * 32 * c["deposits"],
+             "gather": 32 * c["photons_scanned"] + 72 * npix * passes}
+    if adjoint:
+        parts["adjoint_gather"] = 20 * c["hit_points_scanned"] + 96 * npix * passes
+    flops = FLOPS_PER_NODE * c["node_visits"] + FLOPS_PER_TRI * c["tri_tests"]
+    return sum(parts.values()), flops, parts
+
+
+def work_roofline(nbytes, flops, seconds, rl, counts=None, parts=None, per=None):
+    """Roofline block of a whole workload: algorithmic bytes and flops over its measured time."""
+    peaks, tiers, sm_count = rl["peaks"], rl["tiers"], rl["sm_count"]
+    hbm = (peaks or {}).get("hbm_gbs") or FALLBACK_HBM_GBS
+    fp32, _ = fp32_peak_tflops(sm_count, peaks)
+    achieved = nbytes / seconds / 1e9
+    t_hbm, t_flop = nbytes / (hbm * 1e9), flops / (fp32 * 1e12)
+    out = {"bound": "hbm" if t_hbm >= t_flop else "alu", "achieved": round(achieved, 1), "peak": hbm,
+           "unit": "GB/s", "frac": round(achieved / hbm, 4),
+           "l2": {"peak": tiers["l2_peak_gbs"], "frac": round(achieved / tiers["l2_peak_gbs"], 4)},
+           "fp32": {"achieved": round(flops / seconds / 1e12, 3), "peak": round(fp32, 2), "unit": "TFLOP/s",
+                    "frac": round(flops / seconds / 1e12 / fp32, 4)},
+           "algorithmic_bytes": int(nbytes), "flops": int(flops)}
+    if per:
+        out["per"] = per
+    if parts:
+        out["bytes_by_stage"] = {k: int(v) for k, v in parts.items()}
+    if counts:
+        out["work_counts"] = counts
+    return out
+
+
+def counted_passes(r, k, warm=0):
+    """Work counts of k passes of renderer r (after `warm` uncounted passes)."""
+    if warm:
+        r.run(warm)
+    r.count_work(True)
+    r.run(k)
+    return r.count_work(False)
 
 
 def gsp_kernel_digest():
@@ -403,7 +487,7 @@ def bench_cornell(args, ctx, dev, stream, cpu):
     return out
 
 
-def bench_sppm(args, ctx, dev, stream, pg):
+def bench_sppm(args, ctx, dev, stream, pg, rl):
     import torch
     from paper_1505_06022_gb300 import gsp, inputs as I
     sc = I.full_scene(seed=3)
@@ -437,6 +521,14 @@ def bench_sppm(args, ctx, dev, stream, pg):
            "config": "512x512, 247,234 triangles (displaced plane, glass/mirror/diffuse icospheres, area light), "
                      "1,048,576 photon paths/pass, alpha 0.7, r0 = 0.004 * diagonal, full paths + exact hash grid",
            "image_mean": round(float(img.mean()), 5), "autotuned_image_identical": same}
+    # the same k passes once more with the work counted (untimed): the roofline of the timed render
+    cr = gsp.Renderer(s, params)
+    counts = counted_passes(cr, k)
+    cr.close()
+    nbytes, flops, parts = sppm_work(counts, npix, k)
+    out["roofline"] = work_roofline(nbytes, flops, k * ms / 1000.0, rl, counts, parts,
+                                    per="the 64-pass render at the default settings")
+    out["autotuned"]["roofline_frac"] = round(nbytes / (k * ms_tuned / 1000.0) / 1e9 / out["roofline"]["peak"], 4)
     if with_cpu(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))):
         oms, cores = oracle_sppm(sc, dict(photons_per_pass=1 << 20, seed=3, r0_frac=0.004), 2)
         out["cpu_oracle"] = {"ms_per_pass": round(oms, 1), "passes_per_s": round(1000.0 / oms, 3), "cores": cores,
@@ -483,7 +575,7 @@ def bench_shaded(args, ctx, dev, stream, pg):
     return out
 
 
-def bench_grad(args, ctx, dev, stream):
+def bench_grad(args, ctx, dev, stream, rl):
     """Backward/forward time of the path-replay adjoint: 256x256, 50,770 triangles, 16 diffuse
     materials, 262,144 photon paths/pass, 8 passes, L2 loss against a render at perturbed albedos."""
     import torch
@@ -524,9 +616,25 @@ def bench_grad(args, ctx, dev, stream):
             fwd.append(e[0].elapsed_time(e[1]))
             bwd.append(e[1].elapsed_time(e[2]))
         r.close()
+    # work of the forward and of the backward (the replay and the adjoint gathers), counted untimed
+    r = gsp.Renderer(s, params)
+    r.tune(0, 0, 0.0, choice["gather_lanes"], 1)
+    r.enable_grad(passes)
+    r.count_work(True)
+    r.run(passes, stream)
+    img = r.image(stream)
+    cf = r.count_work(True)
+    r.grad((img - target).contiguous(), stream)
+    cb = r.count_work(False)
+    r.close()
     f, b = statistics.median(fwd), statistics.median(bwd)
+    npix = 256 * 256
+    fb, ff, fparts = sppm_work(cf, npix, passes)
+    bb, bf, bparts = sppm_work(cb, npix, passes, adjoint=True)
     out = {"forward_ms": round(f, 3), "backward_ms": round(b, 3), "backward_over_forward": round(b / f, 3),
            "grad_norm": round(float(ga.norm()), 6),
+           "roofline": {"forward": work_roofline(fb, ff, f / 1000.0, rl, cf, fparts),
+                        "backward": work_roofline(bb, bf, b / 1000.0, rl, cb, bparts)},
            "settings": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in choice.items()
                         if k in ("eye_steps", "photon_steps", "cell_h", "gather_lanes", "traversal")},
            "config": "256x256, 50,770 triangles (displaced plane in 12 material regions + 4 icospheres), "
@@ -633,7 +741,7 @@ def bench_modes(args, ctx, dev, stream):
             "error_target": f"relative RMSE {target} (64 passes of full paths + exact grid)"}
 
 
-def bench_batch(args, ctx, dev, stream):
+def bench_batch(args, ctx, dev, stream, rl):
     """64 scenes (1k-200k triangles log-uniform, 64^2-512^2): scene-passes per second as one CUDA
     graph per pass (settings from the batch autotuner) vs the same renderers run one after
     another, k passes each (the same photons gathered)."""
@@ -673,10 +781,24 @@ def bench_batch(args, ctx, dev, stream):
     for r in bat:
         r.sync()
     n = len(scs)
+    # work of the timed passes (passes 2 .. k + 1 of every scene), counted on renderers run alone
+    # (a batched pass does the same work; batched passes are not counted)
+    tot = None
+    npix_sum = 0
+    for i, (sc_, scn) in enumerate(zip(scs, scenes)):
+        cr = gsp.Renderer(scn, gsp.sppm_params(sc_, 1 << 18, seed=5 + i, r0_frac=0.004, scene_id=i))
+        c = counted_passes(cr, k, warm=2)
+        cr.close()
+        tot = c if tot is None else {kk: tot[kk] + c[kk] for kk in c}
+        npix_sum += int(sc_.camera[0]["width"]) * int(sc_.camera[0]["height"])
+    nbytes, flops, parts = sppm_work(tot, npix_sum, k)
     out = {"scenes": n, "triangles": [int(min(sc.ntris for sc in scs)), int(max(sc.ntris for sc in scs))],
            "sequential_scene_passes_per_s": round(1000.0 * n / seq_ms, 1),
            "graph_scene_passes_per_s": round(1000.0 * n / bat_ms, 1),
            "speedup": round(seq_ms / bat_ms, 3), "ms_per_batch_pass": round(bat_ms, 3), "passes_timed": k,
+           "roofline": work_roofline(nbytes, flops, k * bat_ms / 1000.0, rl, tot, parts, per="the timed batch passes"),
+           "sequential_roofline_frac": round(nbytes / (k * seq_ms / 1000.0) / 1e9 /
+                                             ((rl["peaks"] or {}).get("hbm_gbs") or FALLBACK_HBM_GBS), 4),
            "batch_autotune": {"choice": {kk: v for kk, v in choice.items()
                                          if kk in ("eye_steps", "photon_steps", "gather_lanes", "traversal",
                                                    "fused")},

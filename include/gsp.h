@@ -401,6 +401,33 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
  * renderer has run a pass or has gradients enabled. out may be NULL (cell_h reports renderer 0's). */
 gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_result* out);
 
+/* ---- work counters (the algorithmic work of a pass, for rooflines) ------------------------- */
+
+/* Indices of the work counts: eye rays traced (primary and specular continuations), photon rays
+ * traced, node box tests, triangle tests (Fig. 3's two intersect calls), photon deposits, hit
+ * points gathered, photons read by the gathers (candidates of the range query), hit points read
+ * by the adjoint's photon-centric gather. */
+#define GSP_WORK_EYE_RAYS 0
+#define GSP_WORK_PHOTON_RAYS 1
+#define GSP_WORK_NODE_VISITS 2
+#define GSP_WORK_TRI_TESTS 3
+#define GSP_WORK_DEPOSITS 4
+#define GSP_WORK_HIT_POINTS 5
+#define GSP_WORK_PHOTONS_SCANNED 6
+#define GSP_WORK_HIT_POINTS_SCANNED 7
+#define GSP_WORK_COUNTS 8
+
+/* Counting the work of this renderer's passes (the paper has no counterpart: the counts give
+ * the bytes and operations a pass must move, against which its time is held). Synchronises the
+ * device, copies the counts accumulated since the previous call to h_counts [GSP_WORK_COUNTS]
+ * (if not NULL), zeroes them, and switches counting on (on != 0) or off for the passes and
+ * gradients that follow. Counting costs a few atomics per warp and per hit point; the estimate is
+ * unchanged. It covers the persistent path kernels with the stackless traversal: GSP_ERR_BAD_STATE
+ * if the renderer traces some bounces as wavefront steps or walks with a stack
+ * (gsp_sppm_tune), and while it counts, gsp_sppm_tune to those settings, gsp_sppm_autotune,
+ * gsp_batch_autotune and gsp_batch_pass with this renderer fail with GSP_ERR_BAD_STATE. */
+gsp_status gsp_sppm_count_work(gsp_sppm* r, int32_t on, uint64_t* h_counts);
+
 /* ---- gradient of an image loss (path-replay adjoint) ------------------------------------- */
 
 /* Prepares gradients: every pass from now on records the radius each pixel gathered with and
@@ -464,6 +491,17 @@ gsp_status gsp_hash_grid_build(gsp_context* ctx, const float* d_pos, int64_t n, 
 #define GSP_GRID_STATIC_MAX_TABLE 16777216
 gsp_status gsp_hash_grid_build_static(const float* d_pos, int64_t n, float cell_h, int64_t table_size,
                                       uint32_t* d_order, uint32_t* d_bstart, void* stream);
+
+/* ---- measurement --------------------------------------------------------------------------- */
+
+/* Read bandwidth of the memory tier a buffer of `bytes` lives in (the paper has no counterpart:
+ * this supplies the L2 peak against which the traversal of Sec. 3.1 is held). Allocates a
+ * zero-filled device buffer of `bytes` (a multiple of 16, at least 16 KiB) on the context's device,
+ * streams it once untimed, then `reps` times in one timed launch (16-byte loads that bypass L1;
+ * one grid of 2,048 threads per SM), and frees it. *gbps = bytes * reps / time / 1e9. A buffer
+ * well below the L2 size measures L2; one many times larger measures HBM. Synchronises the device.
+ * GSP_ERR_OOM if the buffer does not fit. */
+gsp_status gsp_measure_read_bandwidth(gsp_context* ctx, int64_t bytes, int32_t reps, double* gbps);
 
 #ifdef __cplusplus
 }

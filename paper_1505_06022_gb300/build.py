@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libgsp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "sppm.cu", "scan_sort.cu", "grid_static.cu", "lbvh.cu", "bvh_build.cpp"]
+SOURCES = ["capi.cu", "sppm.cu", "scan_sort.cu", "grid_static.cu", "lbvh.cu", "membench.cu", "bvh_build.cpp"]
 
 
 def _nvcc() -> str:

@@ -40,6 +40,7 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* 
     wq.init((int32_t)n);  // ray indices fit in 31 bits (the entry point rejects larger batches)
     int32_t ray = -1;
     int32_t pend = -1;  // leaf word of a postponed leaf, -1 = none
+    uint32_t ntri = 0;  // not reported by this kernel
     while (true) {
         const int32_t got = wq.take(ray < 0, ctr);
         if (got >= 0) {
@@ -48,7 +49,7 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* 
             trav_init(S, f3(a), f3(b), a.w, b.w, st);
         }
         if (__ballot_sync(0xffffffffu, ray >= 0) == 0) break;
-        trav_steps(S, st, pend, ray >= 0, cap);
+        trav_steps(S, st, pend, ray >= 0, cap, ntri);
         const bool fin = ray >= 0 && st.node < 0 && pend < 0;
         bool flag = false;
         if (fin) {

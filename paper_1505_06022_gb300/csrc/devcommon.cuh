@@ -137,8 +137,21 @@ __device__ __forceinline__ float safe_inv(float d) {
 }
 
 // 1 + 2 gamma_3 with gamma_n = n u / (1 - n u), u = 2^-24: the far-plane scale that makes the
-// FP32 slab test conservative (Ize 2013).
+// FP32 slab test conservative against relative rounding errors (Ize 2013).
 #define GSP_ROBUST_FAR 1.0000003576278687f
+
+// Three-input minimum and maximum (one instruction each on sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 
 // The triangle is chosen in FP32. Its t can lose relative accuracy when the ray origin is far
 // from the triangle compared with t, or the ray is grazing (cancellation in o - v0 and in det);
@@ -332,32 +345,35 @@ __device__ __forceinline__ void ldg64(const float4* p, float4& A, float4& B, flo
         : "l"(p));
 }
 
-// Box test of a node {A, B} = {min.xyz, miss | max.xyz, leaf word} against [tmin, best t]
-// (conservative FP32 slab test). Returns true on a hit; `word` and `miss` receive the links.
-__device__ __forceinline__ bool box_hit(const Trav& st, const float4& A, const float4& B, int32_t& word, int32_t& miss) {
-    const float3 o = st.o, inv = st.inv;
-    const float t0x = __fmul_rn(A.x - o.x, inv.x), t1x = __fmul_rn(B.x - o.x, inv.x);
-    const float t0y = __fmul_rn(A.y - o.y, inv.y), t1y = __fmul_rn(B.y - o.y, inv.y);
-    const float t0z = __fmul_rn(A.z - o.z, inv.z), t1z = __fmul_rn(B.z - o.z, inv.z);
-    const float tn = fmaxf(st.tmin, fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z)));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
-    tf = fminf(st.tbest, tf * GSP_ROBUST_FAR);
-    miss = __float_as_int(A.w);
-    word = __float_as_int(B.w);
-    return tn <= tf;
-}
-
-// Slab test of the box [lo, hi] against [tmin, best t] as box_hit; on a hit tn is the entry
-// distance (stack-based traversal orders children by it).
-__device__ __forceinline__ bool box_entry(const Trav& st, float3 lo, float3 hi, float& tn) {
+// Slab test of the box [lo, hi] against [tmin, best t] (Fig. 3's intersect(node.aabb, ray)):
+// t = (b - o) inv per plane, three-input min and max for the interval, the far end scaled by
+// GSP_ROBUST_FAR; conservative. On a hit tn is the entry distance. (The fused form
+// t = b inv + (-o inv) saves six instructions per box but errs in absolute terms by about
+// u |o inv|, which needs a per-plane pad held in six more registers per ray; on GB300 the spills
+// and lost residency that cost made the traversal slower: 5,132 against 5,217 Mrays/s.)
+__device__ __forceinline__ bool slab(const Trav& st, float3 lo, float3 hi, float& tn) {
     const float3 o = st.o, inv = st.inv;
     const float t0x = __fmul_rn(lo.x - o.x, inv.x), t1x = __fmul_rn(hi.x - o.x, inv.x);
     const float t0y = __fmul_rn(lo.y - o.y, inv.y), t1y = __fmul_rn(hi.y - o.y, inv.y);
     const float t0z = __fmul_rn(lo.z - o.z, inv.z), t1z = __fmul_rn(hi.z - o.z, inv.z);
-    tn = fmaxf(st.tmin, fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fminf(t0z, t1z)));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
-    tf = fminf(st.tbest, tf * GSP_ROBUST_FAR);
-    return tn <= tf;
+    tn = max3f(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), st.tmin));
+    const float tf = min3f(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fmaxf(t0z, t1z));
+    return tn <= fminf(st.tbest, __fmul_rn(tf, GSP_ROBUST_FAR));
+}
+
+// Box test of a node {A, B} = {min.xyz, miss | max.xyz, leaf word} against [tmin, best t].
+// Returns true on a hit; `word` and `miss` receive the links.
+__device__ __forceinline__ bool box_hit(const Trav& st, const float4& A, const float4& B, int32_t& word, int32_t& miss) {
+    float tn;
+    miss = __float_as_int(A.w);
+    word = __float_as_int(B.w);
+    return slab(st, f3(A), f3(B), tn);
+}
+
+// Slab test of the box [lo, hi] as box_hit, with the entry distance (stack-based traversal
+// orders children by it).
+__device__ __forceinline__ bool box_entry(const Trav& st, float3 lo, float3 hi, float& tn) {
+    return slab(st, lo, hi, tn);
 }
 
 // One step of the stackless traversal (Fig. 3): on a box hit follow the hit link (index + 1),

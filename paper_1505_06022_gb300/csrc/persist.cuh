@@ -69,8 +69,10 @@ struct WarpQueue {
 // visit more nodes, never skip the winner); when it meets a second leaf it waits. The warp tests
 // all pending leaves together when kTraceLeafBatch lanes hold one, when a lane waits, or when a
 // lane's walk has ended. A walk is over when st.node < 0 and pend < 0. `cap` bounds the box
-// tests of one walk (corrupt links end the walk with GSP_ERR_TRAVERSAL_LIMIT).
-__device__ __forceinline__ void trav_steps(const DevScene& S, Trav& st, int32_t& pend, bool active, int32_t cap) {
+// tests of one walk (corrupt links end the walk with GSP_ERR_TRAVERSAL_LIMIT). ntri counts the
+// triangle tests (callers that do not read it lose the count to dead-code elimination).
+__device__ __forceinline__ void trav_steps(const DevScene& S, Trav& st, int32_t& pend, bool active, int32_t cap,
+                                           uint32_t& ntri) {
 #pragma unroll 1
     for (int it = 0; it < kTraceInner; ++it) {
         bool waiting = false;
@@ -116,6 +118,7 @@ __device__ __forceinline__ void trav_steps(const DevScene& S, Trav& st, int32_t&
         if (urgent || __popc(pm) >= kTraceLeafBatch) {
             if (pend >= 0) {
                 trav_leaf(S, st, pend >> 3, pend & 7);
+                ntri += (uint32_t)(pend & 7);
                 pend = -1;
             }
         }
@@ -189,6 +192,18 @@ __device__ __forceinline__ void stack_steps(const DevScene& S, Trav& st, StackWa
         }
         if (__ballot_sync(0xffffffffu, active && w.node != kWalkDone) == 0) break;
     }
+}
+
+// Work counters of an SPPM pass (uint64 each, in this order; the C header names them
+// GSP_WORK_*): eye rays, photon rays, node box tests, triangle tests, deposits, hit points
+// gathered, photons scanned by the gathers, hit points scanned by the adjoint gather.
+enum { kWorkEyeRays, kWorkPhotonRays, kWorkNodes, kWorkTris, kWorkDeposits, kWorkHits, kWorkScanned,
+       kWorkHitsScanned, kWorkCounts };
+
+// Adds a per-lane count to work[k]: one atomic per warp. Every lane of the warp must call it.
+__device__ __forceinline__ void work_add_warp(unsigned long long* work, int k, uint32_t v) {
+    const uint32_t sum = __reduce_add_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(work + k, (unsigned long long)sum);
 }
 
 __device__ __forceinline__ int32_t trav_cap(const DevScene& S) {

@@ -46,6 +46,13 @@ int64_t gsp_grid_scratch_words(int64_t n, int64_t T);
 gsp_status gsp_grid_build_with(const float4* pos, int64_t n, float cell_h, int64_t T, uint32_t* order,
                                uint32_t* bstart, uint32_t* scratch, cudaStream_t st, bool skip_invalid);
 
+static_assert(kWorkCounts == GSP_WORK_COUNTS && kWorkEyeRays == GSP_WORK_EYE_RAYS &&
+                  kWorkPhotonRays == GSP_WORK_PHOTON_RAYS && kWorkNodes == GSP_WORK_NODE_VISITS &&
+                  kWorkTris == GSP_WORK_TRI_TESTS && kWorkDeposits == GSP_WORK_DEPOSITS &&
+                  kWorkHits == GSP_WORK_HIT_POINTS && kWorkScanned == GSP_WORK_PHOTONS_SCANNED &&
+                  kWorkHitsScanned == GSP_WORK_HIT_POINTS_SCANNED,
+              "the work counters of the kernels are the ones gsp.h names");
+
 struct gsp_sppm {
     gsp_scene* scene = nullptr;
     gsp_sppm_params P{};
@@ -93,6 +100,8 @@ struct gsp_sppm {
     float4 *ro = nullptr, *rd = nullptr, *rphi = nullptr;
     unsigned long long* started = nullptr;
     uint32_t* last_order = nullptr;  // sorted slot order of the last exact pass
+    unsigned long long* work = nullptr;  // work counters (kWorkCounts), see gsp_sppm_count_work
+    bool count_work = false;
     // tuning
     int32_t gather_lanes = 8;  // lanes per hit point in the exact gather
     int32_t traversal = GSP_TRAVERSAL_MTBVH;  // of the path kernel
@@ -305,6 +314,7 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     A(&r->poff, r->np);
     A(&r->counters, 16);
     A(&r->started, 1);
+    A(&r->work, kWorkCounts);
     const int64_t scan_tmp = std::max({gsp_scan_temp_elems(r->np), gsp_scan_temp_elems(r->T),
                                        gsp_scan_temp_elems(gsp_sort_hist_elems())});
     A(&r->scan_tmp, scan_tmp);
@@ -392,6 +402,7 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
     P.tmask = (uint32_t)(r->T - 1);
     P.np = r->np;
     P.tri_is_id = r->refine_factor > 0.0f && !r->scene->d_attr ? 1 : 0;  // as eye_front / photon_front
+    P.work = r->count_work ? r->work : nullptr;
     return P;
 }
 
@@ -433,8 +444,8 @@ static int path_grid(int64_t items, int device, bool stack, bool shade, bool mul
     int& ps = per_sm[multi][stack][shade][device];
     if (!ps) {
         const void* const kernels[2][2][2] = {
-            {{(const void*)k_paths<false, false>, (const void*)k_paths<false, true>},
-             {(const void*)k_paths<true, false>, (const void*)k_paths<true, true>}},
+            {{(const void*)k_paths<false, false, false>, (const void*)k_paths<false, true, false>},
+             {(const void*)k_paths<true, false, false>, (const void*)k_paths<true, true, false>}},
             {{(const void*)k_paths_multi<false, false>, (const void*)k_paths_multi<false, true>},
              {(const void*)k_paths_multi<true, false>, (const void*)k_paths_multi<true, true>}}};
         int b = 0;
@@ -502,11 +513,14 @@ static gsp_status photon_front(gsp_sppm* r, const PassDev& P, const DepositDev& 
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
         const unsigned grid = (unsigned)path_grid(r->np, r->scene->ctx->device, stack, false);
         if (stack)
-            S.attr ? k_photon_regen<true, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13)
-                   : k_photon_regen<true, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13);
+            S.attr ? k_photon_regen<true, true, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13)
+                   : k_photon_regen<true, false, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13);
+        else if (P.work)  // counting the work (never with the stack walk)
+            S.attr ? k_photon_regen<false, true, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13)
+                   : k_photon_regen<false, false, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13);
         else
-            S.attr ? k_photon_regen<false, true><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13)
-                   : k_photon_regen<false, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13);
+            S.attr ? k_photon_regen<false, true, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13)
+                   : k_photon_regen<false, false, false><<<grid, kTraceThreads, 0, st>>>(S, E, P, D, R, r->qctr + 13);
     }
     return GSP_OK;
 }
@@ -545,11 +559,14 @@ static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, co
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
         const unsigned grid = (unsigned)path_grid((int64_t)J.nchunks * kTraceChunk, r->scene->ctx->device, stack, J.S.attr != nullptr);
         if (stack)
-            J.S.attr ? k_paths<true, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
-                     : k_paths<true, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
+            J.S.attr ? k_paths<true, true, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
+                     : k_paths<true, false, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
+        else if (P.work)  // counting the work (never with the stack walk)
+            J.S.attr ? k_paths<false, true, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
+                     : k_paths<false, false, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
         else
-            J.S.attr ? k_paths<false, true><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
-                     : k_paths<false, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
+            J.S.attr ? k_paths<false, true, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
+                     : k_paths<false, false, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
     }
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
@@ -624,6 +641,7 @@ static gsp_status gather_half(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
         G.bstart = r->bstart;
         launch_gather_exact(r->gather_lanes, G, P, r->npix, st);
     }
+    if (P.work) k_work_add<<<1, 1, 0, st>>>(P.work + kWorkDeposits, r->counters);
     GSP_CUDA_TRY(cudaGetLastError());
     return GSP_OK;
 }
@@ -723,11 +741,31 @@ gsp_status gsp_sppm_tune(gsp_sppm* r, int32_t eye_steps, int32_t photon_steps, f
         (traversal != 0 && traversal != GSP_TRAVERSAL_MTBVH && traversal != GSP_TRAVERSAL_STACK) ||
         (traversal == GSP_TRAVERSAL_STACK && r->scene->bvh.depth >= kStackDepth))
         return GSP_ERR_INVALID_ARG;
+    if (r->count_work && (eye_steps || photon_steps || traversal == GSP_TRAVERSAL_STACK)) {
+        gsp_set_last_error("gsp_sppm_tune: work is counted in the persistent stackless path kernels only");
+        return GSP_ERR_BAD_STATE;
+    }
     r->eye_steps = eye_steps;
     r->photon_steps = photon_steps;
     r->refine_factor = refine_factor;
     if (gather_lanes) r->gather_lanes = gather_lanes;
     if (traversal) r->traversal = traversal;
+    return GSP_OK;
+}
+
+gsp_status gsp_sppm_count_work(gsp_sppm* r, int32_t on, uint64_t* h_counts) {
+    if (!r) return GSP_ERR_INVALID_ARG;
+    if (on && (r->eye_steps || r->photon_steps || r->traversal == GSP_TRAVERSAL_STACK)) {
+        gsp_set_last_error("gsp_sppm_count_work: work is counted in the persistent stackless path kernels only "
+                           "(no wavefront steps, traversal GSP_TRAVERSAL_MTBVH)");
+        return GSP_ERR_BAD_STATE;
+    }
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    GSP_CUDA_TRY(cudaDeviceSynchronize());
+    if (h_counts)
+        GSP_CUDA_TRY(cudaMemcpy(h_counts, r->work, kWorkCounts * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    GSP_CUDA_TRY(cudaMemset(r->work, 0, kWorkCounts * sizeof(unsigned long long)));
+    r->count_work = on != 0;
     return GSP_OK;
 }
 
@@ -844,6 +882,8 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
         A.order = r->last_order;
         A.d_total = r->counters;
         A.badj = r->badj;
+        A.work = r->count_work ? r->work : nullptr;
+        if (A.work) k_work_add<<<1, 1, 0, st>>>(A.work + kWorkDeposits, r->counters);
         k_adj_photons<8><<<grid * 8, 128, 0, st>>>(A);
         k_adj_pixels<<<grid, 256, 0, st>>>(r->hx, r->hw, A.rhist, r->shist + (size_t)i * r->npix, d_dloss_dimg,
                                            r->npix, r->gacc, nmat);
@@ -1133,8 +1173,13 @@ gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
     GSP_CUDA_TRY(cudaSetDevice(b->device));
     (void)cudaGetLastError();
     cudaStream_t st = (cudaStream_t)stream;
-    for (gsp_sppm* r : b->rs)
+    for (gsp_sppm* r : b->rs) {
         if (r->grad && r->passes + npasses > r->grad_max_passes) return GSP_ERR_OVERFLOW;
+        if (r->count_work) {
+            gsp_set_last_error("gsp_batch_pass: a renderer counts its work (batched passes are not counted)");
+            return GSP_ERR_BAD_STATE;
+        }
+    }
     if (npasses == 0) return GSP_OK;
     if ((b->exec || b->exec2) && !batch_scenes_unchanged(b)) batch_drop_graphs(b);
     // pairs of passes as two-pass graphs where they apply, the rest one pass per graph
@@ -1160,7 +1205,7 @@ gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
 gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_result* out) {
     if (!b || trial_passes < 1) return GSP_ERR_INVALID_ARG;
     for (gsp_sppm* r : b->rs)
-        if (r->passes != 0 || r->grad) return GSP_ERR_BAD_STATE;
+        if (r->passes != 0 || r->grad || r->count_work) return GSP_ERR_BAD_STATE;
     GSP_CUDA_TRY(cudaSetDevice(b->device));
     (void)cudaGetLastError();
     cudaStream_t st = b->cap;
@@ -1257,6 +1302,10 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
 
 gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out) {
     if (!r || trial_passes < 1) return GSP_ERR_INVALID_ARG;
+    if (r->count_work) {
+        gsp_set_last_error("gsp_sppm_autotune: the renderer counts its work (its settings must stay put)");
+        return GSP_ERR_BAD_STATE;
+    }
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
     (void)cudaGetLastError();
     gsp_sppm* t = nullptr;

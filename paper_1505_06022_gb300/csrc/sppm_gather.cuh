@@ -149,10 +149,12 @@ __global__ void __launch_bounds__(128) k_gather_stoch(GatherDev G, PassDev P) {
     float3 acc = make_float3(0.0f, 0.0f, 0.0f);
     uint32_t buckets[27];
     const int nb = query_buckets(x, R, P.inv_h, P.tmask, buckets);
+    uint32_t scanned = 0;
     for (int q = 0; q < nb; ++q) {
         const uint32_t b = buckets[q];
         const uint32_t cnt = G.ecount[b];
         if (cnt == 0) continue;
+        ++scanned;
         const uint32_t slot = (uint32_t)(G.entry[b] & 0xffffffffull);
         const float4 a = __ldg(G.slots + 2 * (size_t)slot);
         const float4 c = __ldg(G.slots + 2 * (size_t)slot + 1);
@@ -165,6 +167,10 @@ __global__ void __launch_bounds__(128) k_gather_stoch(GatherDev G, PassDev P) {
     progressive_update(s0, s1, M, mul3(f, acc), P.alpha);
     G.st0[p] = s0;
     G.st1[p] = s1;
+    if (P.work) {
+        atomicAdd(P.work + kWorkHits, 1ull);
+        atomicAdd(P.work + kWorkScanned, (unsigned long long)scanned);
+    }
 }
 
 // Exact range query + progressive update, a group of L lanes per hit point. The group visits
@@ -197,12 +203,14 @@ __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
     cell_range(x.z, R, P.inv_h, lz, hz);
     float M = 0.0f;
     float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+    uint32_t scanned = 0;  // this lane's photons read (work counter)
     for (int32_t ix = lx; ix <= hx; ++ix)
         for (int32_t iy = ly; iy <= hy; ++iy)
             for (int32_t iz = lz; iz <= hz; ++iz) {
                 const uint32_t b = cell_hash(ix, iy, iz, P.tmask);
                 const uint32_t e = __ldg(G.bstart + b + 1);
                 for (uint32_t i = __ldg(G.bstart + b) + gl; i < e; i += L) {
+                    ++scanned;
                     const float4 a = __ldg(G.spos + i);
                     const float3 dx = f3(a) - x;
                     if (!(dot3(dx, dx) < R2p)) continue;
@@ -224,8 +232,16 @@ __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
             acc.y += __shfl_xor_sync(gmask, acc.y, off, L);
             acc.z += __shfl_xor_sync(gmask, acc.z, off, L);
         }
+        if (P.work) {
+#pragma unroll
+            for (int off = L / 2; off > 0; off >>= 1) scanned += __shfl_xor_sync(gmask, scanned, off, L);
+        }
     }
     if (gl != 0) return;
+    if (P.work) {
+        atomicAdd(P.work + kWorkHits, 1ull);
+        atomicAdd(P.work + kWorkScanned, (unsigned long long)scanned);
+    }
     if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
     if (G.shist) G.shist[(size_t)pass_index(P) * G.npix + p] = make_float4(acc.x, acc.y, acc.z, 0.0f);
     float4 s0 = G.st0[p], s1 = G.st1[p];
@@ -257,6 +273,7 @@ struct AdjDev {
     const uint32_t* __restrict__ order; // sorted deposit -> photon slot
     const uint32_t* __restrict__ d_total;
     float4* __restrict__ badj;          // per slot: B_k, the weight of Phi_k in the loss
+    unsigned long long* work;           // work counters, or null
 };
 
 // Photon-centric adjoint gather. For deposit k the hit points that gathered it in the forward
@@ -280,12 +297,14 @@ __global__ void __launch_bounds__(128) k_adj_photons(AdjDev A) {
         cell_range(xk.y, A.rmax, A.inv_hp, ly, hy);
         cell_range(xk.z, A.rmax, A.inv_hp, lz, hz);
         float3 B = make_float3(0.0f, 0.0f, 0.0f);
+        uint32_t scanned = 0;
         for (int32_t ix = lx; ix <= hx; ++ix)
             for (int32_t iy = ly; iy <= hy; ++iy)
                 for (int32_t iz = lz; iz <= hz; ++iz) {
                     const uint32_t b = cell_hash(ix, iy, iz, A.hp_mask);
                     const uint32_t e = __ldg(A.hp_bstart + b + 1);
                     for (uint32_t j = __ldg(A.hp_bstart + b) + gl; j < e; j += L) {
+                        ++scanned;
                         const uint32_t p = __ldg(A.hp_order + j);
                         const float4 hxp = __ldg(A.hx + p);
                         if (__float_as_int(hxp.w) < 0) continue;
@@ -306,6 +325,7 @@ __global__ void __launch_bounds__(128) k_adj_photons(AdjDev A) {
             B.z += __shfl_xor_sync(gmask, B.z, off, L);
         }
         if (gl == 0) A.badj[A.order[i]] = make_float4(B.x, B.y, B.z, 0.0f);
+        if (A.work) atomicAdd(A.work + kWorkHitsScanned, (unsigned long long)scanned);
     }
 }
 
@@ -449,6 +469,8 @@ __global__ void k_grid_keys(const float4* __restrict__ pos, int64_t n, float inv
 __global__ void k_store_u32(uint32_t* p, uint32_t v) { *p = v; }
 
 __global__ void k_add_u32(uint32_t* p, uint32_t v) { *p += v; }
+
+__global__ void k_work_add(unsigned long long* p, const uint32_t* v) { *p += *v; }
 
 __global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;

@@ -44,6 +44,7 @@ struct PassDev {
     int32_t max_eye, max_photon;
     uint32_t tmask;
     int64_t np;
+    unsigned long long* work;  // work counters (kWork*), null unless the renderer counts its work
 };
 
 // The pass index; in a replayed graph the device counter holds the graph's first pass and
@@ -564,7 +565,9 @@ k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32
 // which start first, run beside the bulk of the photon work instead of after it. Eye entries
 // have depth <= max_eye, photon entries depth < max_photon (the host launches accordingly).
 // STACK: walk the child-pair layout with a stack (StackWalk) instead of the hit/miss links.
-template <bool STACK, bool SHADE>
+// COUNT: add the work of the launch to P.work (the instantiation used only while counting, so
+// that the counters take no registers in the others).
+template <bool STACK, bool SHADE, bool COUNT>
 __global__ void __launch_bounds__(kTraceThreads, SHADE ? GSP_PATH_SHADE_MIN_BLOCKS : GSP_PATH_MIN_BLOCKS)
 k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ ne_ptr, PathQ qp, DepositDev D,
         const uint32_t* __restrict__ np_ptr, uint32_t* __restrict__ ctr) {
@@ -584,6 +587,7 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
     sw.sp = 0;
     float3 w = make_float3(0.0f, 0.0f, 0.0f);  // eye: throughput; photon: flux
     Rng rng;
+    uint32_t c_eye = 0, c_ph = 0, c_nodes = 0, c_tris = 0;  // work of this lane
     while (true) {
         const int32_t got = wq.take(i < 0, ctr);
         if (got >= 0) {
@@ -605,12 +609,17 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
         if (STACK)
             stack_steps(S, st, sw, i >= 0, cap);
         else
-            trav_steps(S, st, pend, i >= 0, cap);
+            trav_steps(S, st, pend, i >= 0, cap, c_tris);
         const bool walked = STACK ? sw.node == kWalkDone : (st.node < 0 && pend < 0);
         if (i >= 0 && walked) {
             const Hit h = walk_hit(S, st);
             float3 o = st.o, d = st.d;
             bool more = false;
+            if (COUNT) {
+                c_nodes += (uint32_t)st.steps;
+                c_eye += eye ? 1u : 0u;
+                c_ph += eye ? 0u : 1u;
+            }
             if (eye) {
                 more = h.id >= 0 && eye_interact<SHADE>(S, P, O, id, h, o, d, w, rng) && ++depth <= P.max_eye;
             } else {
@@ -628,6 +637,12 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
                 i = -1;
             }
         }
+    }
+    if (COUNT) {  // the whole warp leaves the loop together
+        work_add_warp(P.work, kWorkEyeRays, c_eye);
+        work_add_warp(P.work, kWorkPhotonRays, c_ph);
+        work_add_warp(P.work, kWorkNodes, c_nodes);
+        work_add_warp(P.work, kWorkTris, c_tris);
     }
 }
 
@@ -753,10 +768,11 @@ k_paths_multi(const PathJob* __restrict__ jobs, int32_t njobs, int32_t total_chu
         }
         if (__ballot_sync(0xffffffffu, i >= 0) == 0) break;
         const PathJob& J = jobs[jb];
+        uint32_t ntri = 0;  // work is not counted in batched passes
         if (STACK)
             stack_steps(J.S, st, sw, i >= 0, cap);
         else
-            trav_steps(J.S, st, pend, i >= 0, cap);
+            trav_steps(J.S, st, pend, i >= 0, cap, ntri);
         const bool walked = STACK ? sw.node == kWalkDone : (st.node < 0 && pend < 0);
         if (i >= 0 && walked) {
             const Hit h = walk_hit(J.S, st);
@@ -792,8 +808,8 @@ struct RegenDev {
 // One bounce per thread and pass (Sec. 3.3): thread j continues its stored path, or starts a new
 // one when the stored path has ended (N_e counts the starts), traces exactly one ray, deposits at
 // a diffuse hit and stores the path state for the next pass. Persistent, with per-lane refill
-// over the threads (counter *ctr) as the path kernel; STACK as in k_paths.
-template <bool STACK, bool SHADE>
+// over the threads (counter *ctr) as the path kernel; STACK and COUNT as in k_paths.
+template <bool STACK, bool SHADE, bool COUNT>
 __global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
 k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R, uint32_t* __restrict__ ctr) {
     const int32_t cap = trav_cap(S);
@@ -807,6 +823,7 @@ k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R, uint3
     sw.sp = 0;
     int32_t j = -1, pend = -1, depth = 0;
     uint32_t starts = 0;
+    uint32_t c_ph = 0, c_nodes = 0, c_tris = 0;  // work of this lane
     float3 phi = make_float3(0.0f, 0.0f, 0.0f);
     Rng rng;
     while (true) {
@@ -830,9 +847,13 @@ k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R, uint3
         if (STACK)
             stack_steps(S, st, sw, j >= 0, cap);
         else
-            trav_steps(S, st, pend, j >= 0, cap);
+            trav_steps(S, st, pend, j >= 0, cap, c_tris);
         const bool walked = STACK ? sw.node == kWalkDone : (st.node < 0 && pend < 0);
         if (j >= 0 && walked) {
+            if (COUNT) {
+                c_ph += 1;
+                c_nodes += (uint32_t)st.steps;
+            }
             const Hit h = walk_hit(S, st);
             float3 o = st.o, d = st.d;
             uint32_t ndep = 0;
@@ -848,6 +869,11 @@ k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R, uint3
     // paths started by this warp
     for (int off = 16; off > 0; off >>= 1) starts += __shfl_xor_sync(0xffffffffu, starts, off);
     if ((threadIdx.x & 31) == 0 && starts) atomicAdd(R.started, (unsigned long long)starts);
+    if (COUNT) {
+        work_add_warp(P.work, kWorkPhotonRays, c_ph);
+        work_add_warp(P.work, kWorkNodes, c_nodes);
+        work_add_warp(P.work, kWorkTris, c_tris);
+    }
 }
 
 }  // namespace gspd

@@ -40,7 +40,7 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
        "gsp_scene_set_materials", "gsp_batch_create", "gsp_batch_destroy", "gsp_batch_pass",
        "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load", "gsp_batch_autotune", "gsp_batch_tune",
-       "gsp_scene_set_attributes", "gsp_scene_set_texture"]
+       "gsp_scene_set_attributes", "gsp_scene_set_texture", "gsp_measure_read_bandwidth", "gsp_sppm_count_work"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -143,6 +143,8 @@ def lib():
             L.gsp_sppm_save.argtypes = [P, C.c_char_p]
             L.gsp_sppm_load.argtypes = [P, C.c_char_p]
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
+            L.gsp_measure_read_bandwidth.argtypes = [P, I64, I32, C.POINTER(C.c_double)]
+            L.gsp_sppm_count_work.argtypes = [P, I32, P]
             _lib = L
     return _lib
 
@@ -211,6 +213,24 @@ def gsp_hash_grid_build(ctx, pos, cell_h, table_size, order=None, bstart=None, s
                                    _stream(stream))
     _check("gsp_hash_grid_build", rc)
     return order, bstart
+
+
+WORK_COUNTS = ["eye_rays", "photon_rays", "node_visits", "tri_tests", "deposits", "hit_points",
+               "photons_scanned", "hit_points_scanned"]
+
+
+def gsp_sppm_count_work(r, on):
+    """Counts accumulated since the previous call (dict by WORK_COUNTS name); then counting on/off."""
+    out = (C.c_uint64 * len(WORK_COUNTS))()
+    _check("gsp_sppm_count_work", lib().gsp_sppm_count_work(r, 1 if on else 0, out))
+    return dict(zip(WORK_COUNTS, (int(v) for v in out)))
+
+
+def gsp_measure_read_bandwidth(ctx, nbytes, reps):
+    """GB/s of a streaming read over a device buffer of `nbytes` (L2 below its size, HBM above)."""
+    out = C.c_double()
+    _check("gsp_measure_read_bandwidth", lib().gsp_measure_read_bandwidth(ctx, int(nbytes), int(reps), C.byref(out)))
+    return out.value
 
 
 def gsp_hash_grid_build_static(pos, cell_h, table_size, order, bstart, stream=None):
@@ -559,6 +579,10 @@ class Renderer:
 
     def last_deposits(self):
         return gsp_sppm_last_deposits(self.h)
+
+    def count_work(self, on):
+        """Work counts of the passes since the previous call; then counting on or off."""
+        return gsp_sppm_count_work(self.h, on)
 
     def save(self, path):
         gsp_sppm_save(self.h, path)
