@@ -323,6 +323,17 @@ gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream);
 gsp_status gsp_sppm_state(gsp_sppm* r, float* d_N, float* d_R, float* d_tau, float* d_direct,
                           double* h_counts, void* stream);
 
+/* The inverse of gsp_sppm_state: replaces the per-pixel progressive state (the N, R, tau update
+ * of Sec. 2 and the direct term) from caller device arrays d_N [h*w], d_R [h*w] (each > 0),
+ * d_tau [h*w][3], d_direct [h*w][3] (all required), and the pass count by `passes`; the next
+ * pass continues from that state with pass index `passes` (the PRNG is keyed by it). For
+ * restarting a render from a state computed elsewhere (a checkpoint written by other software,
+ * or a reference renderer's state, so that one pass can be compared from identical state).
+ * Whole photon paths only (GSP_ERR_BAD_STATE in the one-bounce mode, whose photon paths are not
+ * part of this state, and after gsp_sppm_enable_grad). Ordered on `stream`. */
+gsp_status gsp_sppm_set_state(gsp_sppm* r, const float* d_N, const float* d_R, const float* d_tau,
+                              const float* d_direct, int64_t passes, void* stream);
+
 /* Diagnostics of the last pass (host arrays, synchronises): number of photon deposits, and if
  * h_ids is not NULL (capacity given by the previous return value) their ids in ascending
  * order. Returns the count as a non-negative int64 or a negative gsp_status. */

@@ -1535,6 +1535,21 @@ gsp_status gsp_sppm_state(gsp_sppm* r, float* d_N, float* d_R, float* d_tau, flo
     return GSP_OK;
 }
 
+gsp_status gsp_sppm_set_state(gsp_sppm* r, const float* d_N, const float* d_R, const float* d_tau,
+                              const float* d_direct, int64_t passes, void* stream) {
+    if (!r || !d_N || !d_R || !d_tau || !d_direct || passes < 0 || passes > UINT32_MAX) return GSP_ERR_INVALID_ARG;
+    if (r->P.photon_mode != GSP_FULL_PATH || r->grad) {
+        gsp_set_last_error("gsp_sppm_set_state: whole photon paths only, and not with gradients enabled");
+        return GSP_ERR_BAD_STATE;
+    }
+    GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    k_set_state<<<blocks(r->npix, 256), 256, 0, (cudaStream_t)stream>>>(r->st0, r->st1, r->npix, d_N, d_R, d_tau,
+                                                                       d_direct);
+    GSP_CUDA_TRY(cudaGetLastError());
+    r->passes = passes;
+    return GSP_OK;
+}
+
 int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity) {
     if (!r) return GSP_ERR_INVALID_ARG;
     if (cudaSetDevice(r->scene->ctx->device) != cudaSuccess) return GSP_ERR_CUDA;

@@ -440,6 +440,15 @@ __global__ void k_state(const float4* __restrict__ st0, const float4* __restrict
     if (direct) { direct[3 * p] = b.x; direct[3 * p + 1] = b.y; direct[3 * p + 2] = b.z; }
 }
 
+__global__ void k_set_state(float4* __restrict__ st0, float4* __restrict__ st1, int64_t npix,
+                            const float* __restrict__ N, const float* __restrict__ R, const float* __restrict__ tau,
+                            const float* __restrict__ direct) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    st0[p] = make_float4(tau[3 * p], tau[3 * p + 1], tau[3 * p + 2], N[p]);
+    st1[p] = make_float4(direct[3 * p], direct[3 * p + 1], direct[3 * p + 2], R[p]);
+}
+
 __global__ void k_init_state(float4* st0, float4* st1, int64_t npix, float r0) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;

@@ -40,7 +40,8 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_hash_grid_build_static", "gsp_sppm_tune", "gsp_sppm_enable_grad", "gsp_render_grad",
        "gsp_scene_set_materials", "gsp_batch_create", "gsp_batch_destroy", "gsp_batch_pass",
        "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load", "gsp_batch_autotune", "gsp_batch_tune",
-       "gsp_scene_set_attributes", "gsp_scene_set_texture", "gsp_measure_read_bandwidth", "gsp_sppm_count_work"]
+       "gsp_scene_set_attributes", "gsp_scene_set_texture", "gsp_measure_read_bandwidth", "gsp_sppm_count_work",
+       "gsp_sppm_set_state"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -145,6 +146,7 @@ def lib():
             L.gsp_rng_fill.argtypes = [P, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P, I64, I32, P, P]
             L.gsp_measure_read_bandwidth.argtypes = [P, I64, I32, C.POINTER(C.c_double)]
             L.gsp_sppm_count_work.argtypes = [P, I32, P]
+            L.gsp_sppm_set_state.argtypes = [P, P, P, P, P, I64, P]
             _lib = L
     return _lib
 
@@ -443,6 +445,11 @@ def gsp_sppm_state(r, N=None, R=None, tau=None, direct=None, stream=None):
     return int(counts[0]), float(counts[1])
 
 
+def gsp_sppm_set_state(r, N, R, tau, direct, passes, stream=None):
+    _check("gsp_sppm_set_state", lib().gsp_sppm_set_state(r, _dev(N), _dev(R), _dev(tau), _dev(direct),
+                                                          int(passes), _stream(stream)))
+
+
 def gsp_sppm_last_deposits(r):
     n = lib().gsp_sppm_last_deposits(r, None, 0)
     if n < 0:
@@ -579,6 +586,11 @@ class Renderer:
 
     def last_deposits(self):
         return gsp_sppm_last_deposits(self.h)
+
+    def set_state(self, N, R, tau, direct, passes, stream=None):
+        """Replace the progressive state (device float32 arrays shaped as state() returns them)."""
+        c = lambda t: t.contiguous()
+        gsp_sppm_set_state(self.h, c(N), c(R), c(tau), c(direct), passes, stream)
 
     def count_work(self, on):
         """Work counts of the passes since the previous call; then counting on or off."""

@@ -539,3 +539,21 @@ def photon_mirror_scene(mirror_albedo=(0.9, 0.6, 0.3), le: float = 5.0, light: f
                            material(DIELECTRIC, glass_albedo, ior=1.5)])
     cam = camera((0.0, 1.5, 0.0), (0.0, 2.0, 0.0001), (0, 0, 1), 60.0, 4, 4)
     return Scene(verts, tris, tri_mat, mats, cam, name="photon_mirror" if mirror else "photon_glass")
+
+
+def rotated(scene: Scene, ax: float, ay: float, center=(0.5, 0.5, 0.5)) -> Scene:
+    """The scene turned about `center` by `ax` radians about x, then `ay` about y (geometry,
+    vertex normals and camera alike), so that its planar walls are no longer axis planes."""
+    rx = np.array([[1, 0, 0], [0, np.cos(ax), -np.sin(ax)], [0, np.sin(ax), np.cos(ax)]])
+    ry = np.array([[np.cos(ay), 0, np.sin(ay)], [0, 1, 0], [-np.sin(ay), 0, np.cos(ay)]])
+    M = ry @ rx
+    c = np.asarray(center, np.float64)
+    turn = lambda p: (np.asarray(p, np.float64) - c) @ M.T + c
+    cam = scene.camera.copy()
+    cam["eye"] = turn(cam["eye"][0])
+    cam["look"] = turn(cam["look"][0])
+    cam["up"] = np.asarray(cam["up"][0], np.float64) @ M.T
+    nrm = None if scene.normals is None else (scene.normals.astype(np.float64) @ M.T).astype(np.float32)
+    return Scene(turn(scene.verts).astype(np.float32), scene.tris.copy(), scene.tri_mat.copy(), scene.mats.copy(),
+                 cam, name=scene.name + "_rotated", normals=nrm, texcoords=scene.texcoords,
+                 textures=dict(scene.textures))

@@ -43,3 +43,45 @@ def image_parity_boundary(gpu, ref, n_gpu, n_ref, alpha, rtol=1e-3, min_frac=0.9
     assert frac >= min_frac, f"only {frac:.5f} of pixels within {rtol} (worst {rel.max():.3g})"
     assert unexplained <= max_unexplained, f"{unexplained:.5f} of pixels off by more than one boundary photon"
     return frac, unexplained
+
+
+# the hash grid's lattice shift (cell = floor(x / h + 0.381966)), the same on both sides
+CELL_OFFSET = 0.381966
+
+
+def _cell_buckets(cells, h, T):
+    """Buckets of integer cells [n, 3], through the oracle's hash of their centres."""
+    import oracle as O
+    centres = ((np.asarray(cells, np.float64) + 0.5 - CELL_OFFSET) * h).astype(np.float32)
+    return O.hash_grid(centres, h, T)[0]
+
+
+def stochastic_uncertain_pixels(deposits_x, hit_x, valid, R, h, T):
+    """Pixels whose stochastic-hashing gather may differ between FP32 and FP64 for want of a
+    rounding: a deposit within rounding of a cell face (the oracle's near flag) may fall into
+    either cell, changing the survivor and the count of both cells' buckets; every pixel whose
+    query cells (those overlapping x +- R) hash to such a bucket is uncertain. Returns a bool mask
+    over pixels and the number of deposits near a face."""
+    import oracle as O
+    x = np.asarray(deposits_x, np.float64)
+    near = O.hash_grid(x.astype(np.float32), h, T)[3].astype(bool)
+    flagged = np.zeros(len(hit_x), bool)
+    if not near.any():
+        return flagged, 0
+    q = x[near] / h + CELL_OFFSET
+    tol = 1e-5 + 1e-6 * np.abs(q)  # the near flag's band, in cells
+    lo, hi = np.floor(q - tol).astype(np.int64), np.floor(q + tol).astype(np.int64)
+    cells = {tuple(int(c) for c in (cx, cy, cz))
+             for a, b in zip(lo, hi)
+             for cx in range(a[0], b[0] + 1) for cy in range(a[1], b[1] + 1) for cz in range(a[2], b[2] + 1)}
+    bad = set(_cell_buckets(np.array(sorted(cells)), h, T).tolist())
+    hx = np.asarray(hit_x, np.float64)
+    Rv = np.asarray(R, np.float64)[:, None]
+    qlo = np.floor((hx - Rv) / h + CELL_OFFSET).astype(np.int64)
+    qhi = np.floor((hx + Rv) / h + CELL_OFFSET).astype(np.int64)
+    assert np.all(qhi - qlo <= 1), "query ranges of more than two cells per axis (cell edge below 2 R)"
+    corners = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)])
+    cand = np.minimum(qlo[:, None, :] + corners[None], qhi[:, None, :])  # [npix, 8, 3]
+    b = _cell_buckets(cand.reshape(-1, 3), h, T).reshape(len(hx), 8)
+    flagged = np.isin(b, np.array(sorted(bad))).any(axis=1) & np.asarray(valid, bool)
+    return flagged, int(near.sum())

@@ -191,3 +191,28 @@ def test_batch_recaptures_after_a_scene_changes(ctx, fused):
         assert r.state()["passes"] == 6
         assert np.array_equal(r.image().cpu().numpy(), want)
     b.close()
+
+
+def test_batch_scenes_against_the_oracle(ctx):
+    """The four cheapest of the 64-scene batch workload (1-4k triangles, 64^2-128^2 pixels,
+    2^18 photon paths per pass, r0 = 0.004 * diagonal, scene ids from their place in the batch)
+    rendered by one fused batch (one persistent path launch, a two-pass graph) for 2 passes,
+    each image against the FP64 oracle at the plain bar."""
+    import oracle as O
+    from gpu_util import image_parity
+    scs = I.batch_scenes(64, seed=5)
+    cost = [sc.ntris * int(sc.camera[0]["width"]) * int(sc.camera[0]["height"]) for sc in scs]
+    sel = [int(i) for i in np.argsort(cost)[:4]]
+    kw = [dict(photons_per_pass=1 << 18, seed=5 + i, r0_frac=0.004, scene_id=i) for i in sel]
+    rs = [gsp.Renderer(gsp.Scene(ctx, scs[i]), gsp.sppm_params(scs[i], **k)) for i, k in zip(sel, kw)]
+    b = gsp.Batch(rs)
+    b.tune(True)
+    b.run(2)
+    torch.cuda.synchronize()
+    for r, i, k in zip(rs, sel, kw):
+        r.sync()
+        orc = O.Sppm(scs[i], O.default_params(scs[i], **k))
+        orc.run(2)
+        assert r.state()["Ne"] == orc.state()["Ne"]
+        image_parity(r.image().cpu().numpy(), orc.image())
+    b.close()

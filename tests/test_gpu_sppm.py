@@ -4,7 +4,7 @@ import pytest
 
 import oracle as O
 from paper_1505_06022_gb300 import gsp, inputs as I
-from gpu_util import image_parity
+from gpu_util import image_parity, stochastic_uncertain_pixels
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,8 +45,8 @@ def test_cornell_deposit_ids_match(ctx):
     _, orc, r, _ = render_both(ctx, sc, 1, photons_per_pass=16384, seed=3)
     gid = r.last_deposits()
     oid = np.sort(orc.last_photons()["ids"])
-    diff = np.setxor1d(gid, oid)
-    assert len(diff) <= 2e-4 * len(oid), f"{len(diff)} of {len(oid)} deposit ids differ"
+    assert len(oid) > 30000
+    assert np.array_equal(np.sort(gid), oid)  # every photon path deposits at the same vertices
 
 
 @pytest.mark.parametrize("cell_frac", [0.25, 0.6, 1.0, 3.0])
@@ -154,6 +154,91 @@ def test_full_scene_one_pass_parity(ctx):
     kw = dict(photons_per_pass=1 << 20, seed=3, r0_frac=0.004)
     img, orc, r, st = render_both(ctx, sc, 2, **kw)
     image_parity(img, orc.state()["image"])
+
+
+@pytest.mark.parametrize("photon_mode", [gsp.FULL_PATH, gsp.REGEN])
+def test_stochastic_hashing_on_tilted_walls_with_the_near_face_guard(ctx, photon_mode):
+    """Stochastic hashing (Sec. 3.4) on a Cornell box turned off the axes, so that deposits
+    fall at every offset from the cell faces. Pixels whose gather may differ for want of a
+    rounding (stochastic_uncertain_pixels, accumulated over the passes) are excluded and
+    reported; the rest must meet the plain bar."""
+    # 256^2 with the benchmark's radius (r0 = 0.004 * diagonal): a cell spans a few pixels, so
+    # a bucket the guard marks touches few of them
+    sc = I.rotated(I.cornell_box(seed=1, width=256, height=256), 0.31, 0.52)
+    kw = dict(photons_per_pass=65536, seed=2, r0_frac=0.004, photon_mode=photon_mode, hash_mode=gsp.STOCHASTIC)
+    params = gsp.sppm_params(sc, **kw)
+    r = gsp.Renderer(gsp.Scene(ctx, sc), params)
+    orc = O.Sppm(sc, O.default_params(sc, **kw))
+    h, T = params["cell_h"], params["table_size"]
+    uncertain = np.zeros(256 * 256, bool)
+    near_total = 0
+    for _ in range(4):
+        R = orc.state()["R"].reshape(-1)
+        orc.run(1)
+        r.run(1)
+        g = orc.last_gather()
+        flag, near = stochastic_uncertain_pixels(orc.last_photons()["x"], g["x"], g["valid"], R, h, T)
+        uncertain |= flag
+        near_total += near
+    img, ref = r.image().cpu().numpy(), orc.image()
+    keep = ~uncertain
+    print(f"deposits near a cell face: {near_total}; uncertain pixels: {uncertain.mean():.4f}")
+    assert near_total > 0 and uncertain.mean() <= 0.1
+    image_parity(img.reshape(-1, 3)[keep], ref.reshape(-1, 3)[keep])
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def test_full_size_64_passes_in_lockstep_with_the_oracle(ctx):
+    """The benchmark's render (512x512, 247,234 triangles, 2^20 photon paths per pass, r0 =
+    0.004 * diagonal) over all of its 64 passes. Before every pass the GPU renderer takes the
+    oracle's progressive state (N, R, tau, direct), so each pass is compared from identical state
+    at the radii of that pass: every one must meet the plain bar. Run freely, FP32 and FP64 photon
+    positions (about 1e-7 of the scene apart) put a photon on one side or the other of a pixel's
+    radius now and then, and such a pixel keeps a slightly different radius from then on; the
+    free-running image is compared with a bar that allows for that accumulation."""
+    sc = I.full_scene()
+    kw = dict(photons_per_pass=1 << 20, seed=3, r0_frac=0.004)
+    s = gsp.Scene(ctx, sc)
+    params = gsp.sppm_params(sc, **kw)
+    step = gsp.Renderer(s, params)
+    orc = O.Sppm(sc, O.default_params(sc, **kw))
+    fracs = []
+    for i in range(64):
+        st = orc.state()
+        step.set_state(to_dev(st["N"]), to_dev(st["R"]), to_dev(st["tau"]), to_dev(st["direct"]), i)
+        step.run(1)
+        orc.run(1)
+        fracs.append(image_parity(step.image().cpu().numpy(), orc.image()))
+    assert min(fracs) >= 0.999
+    free = gsp.Renderer(s, params)
+    free.run(64)
+    img, ref = free.image().cpu().numpy().astype(np.float64), orc.image()
+    rel = (np.abs(img - ref) / np.maximum(np.abs(ref), 1e-6 * ref.mean())).reshape(-1, 3).max(axis=1)
+    print(f"lockstep: worst pass {min(fracs):.5f} of pixels within 1e-3; free-running 64 passes: "
+          f"{np.mean(rel <= 1e-3):.5f} within 1e-3, {np.mean(rel <= 1e-2):.5f} within 1e-2")
+    assert np.mean(rel <= 1e-3) >= 0.985 and np.mean(rel <= 1e-2) >= 0.998, (np.mean(rel <= 1e-3), np.mean(rel <= 1e-2))
+
+
+def test_set_state_round_trip_and_checks(ctx):
+    sc = I.cornell_box(width=24, height=16)
+    s = gsp.Scene(ctx, sc)
+    params = gsp.sppm_params(sc, 3000, seed=8)
+    a = gsp.Renderer(s, params)
+    a.run(3)
+    st = a.state()
+    b = gsp.Renderer(s, params)
+    b.set_state(st["N"], st["R"], st["tau"], st["direct"], st["passes"])
+    assert torch.equal(b.image(), a.image())
+    a.run(2)
+    b.run(2)
+    assert torch.equal(b.image(), a.image())  # the next passes continue from the same state
+    regen = gsp.Renderer(s, gsp.sppm_params(sc, 3000, seed=8, photon_mode=gsp.REGEN))
+    with pytest.raises(gsp.GspError) as e:
+        regen.set_state(st["N"], st["R"], st["tau"], st["direct"], 3)
+    assert e.value.code == -7
 
 
 def test_edge_cases(ctx):
