@@ -173,6 +173,11 @@ __global__ void __launch_bounds__(128) k_gather_stoch(GatherDev G, PassDev P) {
     }
 }
 
+#ifndef GSP_GATHER_BATCH
+#define GSP_GATHER_BATCH 4
+#endif
+constexpr int kGatherBatch = GSP_GATHER_BATCH;  // candidate positions a gather lane has in flight
+
 // Exact range query + progressive update, a group of L lanes per hit point. The group visits
 // every cell overlapping the box x +- R (any number per axis, so the cell may be smaller than the
 // radius); its lanes split each bucket's photons (consecutive, coalesced), and a photon that passes
@@ -209,17 +214,28 @@ __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
             for (int32_t iz = lz; iz <= hz; ++iz) {
                 const uint32_t b = cell_hash(ix, iy, iz, P.tmask);
                 const uint32_t e = __ldg(G.bstart + b + 1);
-                for (uint32_t i = __ldg(G.bstart + b) + gl; i < e; i += L) {
-                    ++scanned;
-                    const float4 a = __ldg(G.spos + i);
-                    const float3 dx = f3(a) - x;
-                    if (!(dot3(dx, dx) < R2p)) continue;
-                    if (cell_of(a.x, P.inv_h) != ix || cell_of(a.y, P.inv_h) != iy || cell_of(a.z, P.inv_h) != iz)
-                        continue;  // a colliding cell's photon, counted when its own cell is visited
-                    const float4 c = __ldg(G.spay + i);
-                    if (!photon_accept(f3(a), x, R, __float_as_uint(c.w), n)) continue;
-                    M += 1.0f;
-                    acc = acc + f3(c);
+                // kGatherBatch of the lane's candidates fetched before any is tested, so that a
+                // dense bucket costs kGatherBatch times fewer round trips to L2; they are then
+                // tested in the lane's order, as one at a time would
+                for (uint32_t i = __ldg(G.bstart + b) + gl; i < e; i += kGatherBatch * L) {
+                    float4 a[kGatherBatch];
+#pragma unroll
+                    for (int u = 0; u < kGatherBatch; ++u)
+                        if (i + u * L < e) a[u] = __ldg(G.spos + i + u * L);
+#pragma unroll
+                    for (int u = 0; u < kGatherBatch; ++u) {
+                        if (i + u * L >= e) break;
+                        ++scanned;
+                        const float3 dx = f3(a[u]) - x;
+                        if (!(dot3(dx, dx) < R2p)) continue;
+                        if (cell_of(a[u].x, P.inv_h) != ix || cell_of(a[u].y, P.inv_h) != iy ||
+                            cell_of(a[u].z, P.inv_h) != iz)
+                            continue;  // a colliding cell's photon, counted when its own cell is visited
+                        const float4 c = __ldg(G.spay + i + u * L);
+                        if (!photon_accept(f3(a[u]), x, R, __float_as_uint(c.w), n)) continue;
+                        M += 1.0f;
+                        acc = acc + f3(c);
+                    }
                 }
             }
     if (L > 1) {
