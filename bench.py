@@ -506,7 +506,7 @@ def bench_sppm(args, ctx, dev, stream, pg, rl):
     # autotune times its candidates on a temporary renderer: `tuned` itself is still at pass 0
     tuned = gsp.Renderer(s, params)
     t0 = time.perf_counter()
-    choice = tuned.autotune(trial_passes=2)
+    choice = tuned.autotune(trial_passes=6)
     tune_s = time.perf_counter() - t0
     ms_tuned = timed_passes(tuned, k, stream)
     img_tuned = tuned.image(stream)

@@ -100,6 +100,7 @@ struct gsp_sppm {
     float4 *ro = nullptr, *rd = nullptr, *rphi = nullptr;
     unsigned long long* started = nullptr;
     uint32_t* last_order = nullptr;  // sorted slot order of the last exact pass
+    uint32_t* heavy = nullptr;  // exact gather: hit points with long queries (k_gather_heavy), npix entries
     unsigned long long* work = nullptr;  // work counters (kWorkCounts), see gsp_sppm_count_work
     bool count_work = false;
     // tuning
@@ -328,6 +329,7 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         A(&r->bstart, r->T + 1);
         A(&r->spos, r->slot_cap);
         A(&r->spay, r->slot_cap);
+        A(&r->heavy, r->npix);
     } else {
         A(&r->entry, r->T);
         A(&r->ecount, r->T);
@@ -406,7 +408,8 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
     return P;
 }
 
-// Renderer counters (uint32): [0] deposits of the pass, [7] first pass index of a replayed graph.
+// Renderer counters (uint32): [0] deposits of the pass, [7] first pass index of a replayed graph,
+// [10] hit points listed for k_gather_heavy.
 // Per trace set (qctr): [4..6] eye queue lengths, [8..10] photon queue lengths (three each, used
 // in rotation), [12] work counter of k_paths, [13] work counter of k_photon_regen.
 static int sm_count(int device) {
@@ -639,7 +642,12 @@ static gsp_status gather_half(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
         G.spos = r->spos;
         G.spay = r->spay;
         G.bstart = r->bstart;
+        // long queries are listed by k_gather_exact and served by whole blocks (counters[10] counts them)
+        G.heavy = r->heavy;
+        G.nheavy = r->counters + 10;
+        GSP_CUDA_TRY(cudaMemsetAsync(G.nheavy, 0, sizeof(uint32_t), st));
         launch_gather_exact(r->gather_lanes, G, P, r->npix, st);
+        k_gather_heavy<<<2 * sm_count(r->scene->ctx->device), kHeavyThreads, 0, st>>>(G, P);
     }
     if (P.work) k_work_add<<<1, 1, 0, st>>>(P.work + kWorkDeposits, r->counters);
     GSP_CUDA_TRY(cudaGetLastError());
@@ -1202,6 +1210,11 @@ gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
     return GSP_OK;
 }
 
+// The autotuners keep their current choice unless a candidate is faster by more than 3 %: their
+// trials are a few passes from a fresh state, whose timings vary by a few percent and whose radii
+// are those of a render's first passes, so a smaller gain is as likely to be noise as real.
+constexpr float kTuneMargin = 0.97f;
+
 gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_result* out) {
     if (!b || trial_passes < 1) return GSP_ERR_INVALID_ARG;
     for (gsp_sppm* r : b->rs)
@@ -1254,7 +1267,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
             if (ce == cudaSuccess) ce = reset_state(r, st);
         ms /= (float)(launches * per);
         if (ncand++ == 0) first = ms;
-        if (ms < best) {
+        if (ms < best * kTuneMargin) {  // a clear gain only: trial timings vary by a few percent
             best = ms;
             pick = c;
         }
@@ -1349,7 +1362,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, z);
         ms /= (float)trial_passes;
         if (ncand++ == 0) first = ms;
-        if (ms < best) {
+        if (ms < best * kTuneMargin) {  // a clear gain only: trial timings vary by a few percent
             best = ms;
             pick = c;
         }

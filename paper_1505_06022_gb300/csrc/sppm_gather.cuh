@@ -56,6 +56,8 @@ struct GatherDev {
     const float4* __restrict__ spos;
     const float4* __restrict__ spay;
     const uint32_t* __restrict__ bstart;
+    uint32_t* __restrict__ heavy;   // optional: hit points whose query goes to k_gather_heavy
+    uint32_t* __restrict__ nheavy;  // their count (zeroed before k_gather_exact)
     // stochastic
     const float4* __restrict__ slots;
     const unsigned long long* __restrict__ entry;
@@ -178,12 +180,99 @@ __global__ void __launch_bounds__(128) k_gather_stoch(GatherDev G, PassDev P) {
 #endif
 constexpr int kGatherBatch = GSP_GATHER_BATCH;  // candidate positions a gather lane has in flight
 
+// The cells of an exact range query: those overlapping the box x +- R.
+struct QueryCells {
+    int32_t lx, hx, ly, hy, lz, hz;
+};
+
+__device__ __forceinline__ QueryCells query_cells(float3 x, float R, float inv_h) {
+    QueryCells q;
+    cell_range(x.x, R, inv_h, q.lx, q.hx);
+    cell_range(x.y, R, inv_h, q.ly, q.hy);
+    cell_range(x.z, R, inv_h, q.lz, q.hz);
+    return q;
+}
+
+// Photons in the buckets of the query's cells: the length of the range query.
+__device__ __forceinline__ uint32_t query_cost(const GatherDev& G, const PassDev& P, const QueryCells& q) {
+    uint32_t cost = 0;
+    for (int32_t ix = q.lx; ix <= q.hx; ++ix)
+        for (int32_t iy = q.ly; iy <= q.hy; ++iy)
+            for (int32_t iz = q.lz; iz <= q.hz; ++iz) {
+                const uint32_t b = cell_hash(ix, iy, iz, P.tmask);
+                cost += __ldg(G.bstart + b + 1) - __ldg(G.bstart + b);
+            }
+    return cost;
+}
+
+// One lane's share of an exact range query split over S lanes: lane gl takes every S-th photon of
+// each visited cell's bucket. A photon that passes the distance test counts only while its own
+// cell is the one being visited, so a photon whose bucket several visited cells share (hash
+// collisions) counts once. kGatherBatch of the lane's candidates are fetched before any is
+// tested, so that a dense bucket costs kGatherBatch times fewer round trips to L2; they are then
+// tested in the lane's order, as one at a time would.
+__device__ __forceinline__ void gather_lane(const GatherDev& G, const PassDev& P, const QueryCells& q, float3 x,
+                                            float3 n, float R, int gl, int S, float& M, float3& acc,
+                                            uint32_t& scanned) {
+    const float R2p = R * R * 1.0001f;  // cheap pre-test, then the exact one
+    for (int32_t ix = q.lx; ix <= q.hx; ++ix)
+        for (int32_t iy = q.ly; iy <= q.hy; ++iy)
+            for (int32_t iz = q.lz; iz <= q.hz; ++iz) {
+                const uint32_t b = cell_hash(ix, iy, iz, P.tmask);
+                const uint32_t e = __ldg(G.bstart + b + 1);
+                for (uint32_t i = __ldg(G.bstart + b) + gl; i < e; i += kGatherBatch * S) {
+                    float4 a[kGatherBatch];
+#pragma unroll
+                    for (int u = 0; u < kGatherBatch; ++u)
+                        if (i + u * S < e) a[u] = __ldg(G.spos + i + u * S);
+#pragma unroll
+                    for (int u = 0; u < kGatherBatch; ++u) {
+                        if (i + u * S >= e) break;
+                        ++scanned;
+                        const float3 dx = f3(a[u]) - x;
+                        if (!(dot3(dx, dx) < R2p)) continue;
+                        if (cell_of(a[u].x, P.inv_h) != ix || cell_of(a[u].y, P.inv_h) != iy ||
+                            cell_of(a[u].z, P.inv_h) != iz)
+                            continue;  // a colliding cell's photon, counted when its own cell is visited
+                        const float4 c = __ldg(G.spay + i + u * S);
+                        if (!photon_accept(f3(a[u]), x, R, __float_as_uint(c.w), n)) continue;
+                        M += 1.0f;
+                        acc = acc + f3(c);
+                    }
+                }
+            }
+}
+
+// The end of hit point p's gather: the pass's direct term, the gradient records, the progressive
+// update with the gathered count M and flux sum acc.
+__device__ __forceinline__ void gather_finish(const GatherDev& G, const PassDev& P, int64_t p, float R, float M,
+                                              float3 acc, uint32_t scanned) {
+    if (P.work) {
+        atomicAdd(P.work + kWorkHits, 1ull);
+        atomicAdd(P.work + kWorkScanned, (unsigned long long)scanned);
+    }
+    if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
+    if (G.shist) G.shist[(size_t)pass_index(P) * G.npix + p] = make_float4(acc.x, acc.y, acc.z, 0.0f);
+    float4 s0 = G.st0[p], s1 = G.st1[p];
+    add_direct(s1, G.hd[p]);
+    progressive_update(s0, s1, M, mul3(f3(G.hf[p]), acc), P.alpha);
+    G.st0[p] = s0;
+    G.st1[p] = s1;
+}
+
+// A query longer than this many photons per lane of its group goes to k_gather_heavy.
+#ifndef GSP_HEAVY_PER_LANE
+#define GSP_HEAVY_PER_LANE 128
+#endif
+constexpr uint32_t kHeavyPerLane = GSP_HEAVY_PER_LANE;
+
 // Exact range query + progressive update, a group of L lanes per hit point. The group visits
 // every cell overlapping the box x +- R (any number per axis, so the cell may be smaller than the
-// radius); its lanes split each bucket's photons (consecutive, coalesced), and a photon that passes
-// the distance test counts only while its own cell is the one being visited, so a photon whose
-// bucket several visited cells share (hash collisions) counts once. Lane sums are combined by a
-// fixed butterfly, so the result does not depend on scheduling.
+// radius) and its lanes split each bucket's photons (gather_lane; consecutive, coalesced). Lane
+// sums are combined by a fixed butterfly, so the result does not depend on scheduling. With a
+// heavy list (G.heavy), a hit point whose query is longer than kHeavyPerLane photons per lane (the
+// dense spots of a caustic, up to twenty times the median) is listed for k_gather_heavy instead:
+// left to one group it would keep its SM busy long after the others are done.
 template <int L>
 __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
     static_assert(L >= 1 && L <= 32 && (L & (L - 1)) == 0, "group size");
@@ -200,44 +289,16 @@ __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
         return;
     }
     const float3 x = f3(hxp);
-    const float3 n = f3(G.hn[p]);
-    const float R = G.st1[p].w, R2p = R * R * 1.0001f;  // cheap pre-test, then the exact one
-    int32_t lx, hx, ly, hy, lz, hz;
-    cell_range(x.x, R, P.inv_h, lx, hx);
-    cell_range(x.y, R, P.inv_h, ly, hy);
-    cell_range(x.z, R, P.inv_h, lz, hz);
+    const float R = G.st1[p].w;
+    const QueryCells q = query_cells(x, R, P.inv_h);
+    if (G.heavy && query_cost(G, P, q) > kHeavyPerLane * L) {  // the whole group leaves together
+        if (gl == 0) G.heavy[atomicAdd(G.nheavy, 1u)] = (uint32_t)p;
+        return;
+    }
     float M = 0.0f;
     float3 acc = make_float3(0.0f, 0.0f, 0.0f);
     uint32_t scanned = 0;  // this lane's photons read (work counter)
-    for (int32_t ix = lx; ix <= hx; ++ix)
-        for (int32_t iy = ly; iy <= hy; ++iy)
-            for (int32_t iz = lz; iz <= hz; ++iz) {
-                const uint32_t b = cell_hash(ix, iy, iz, P.tmask);
-                const uint32_t e = __ldg(G.bstart + b + 1);
-                // kGatherBatch of the lane's candidates fetched before any is tested, so that a
-                // dense bucket costs kGatherBatch times fewer round trips to L2; they are then
-                // tested in the lane's order, as one at a time would
-                for (uint32_t i = __ldg(G.bstart + b) + gl; i < e; i += kGatherBatch * L) {
-                    float4 a[kGatherBatch];
-#pragma unroll
-                    for (int u = 0; u < kGatherBatch; ++u)
-                        if (i + u * L < e) a[u] = __ldg(G.spos + i + u * L);
-#pragma unroll
-                    for (int u = 0; u < kGatherBatch; ++u) {
-                        if (i + u * L >= e) break;
-                        ++scanned;
-                        const float3 dx = f3(a[u]) - x;
-                        if (!(dot3(dx, dx) < R2p)) continue;
-                        if (cell_of(a[u].x, P.inv_h) != ix || cell_of(a[u].y, P.inv_h) != iy ||
-                            cell_of(a[u].z, P.inv_h) != iz)
-                            continue;  // a colliding cell's photon, counted when its own cell is visited
-                        const float4 c = __ldg(G.spay + i + u * L);
-                        if (!photon_accept(f3(a[u]), x, R, __float_as_uint(c.w), n)) continue;
-                        M += 1.0f;
-                        acc = acc + f3(c);
-                    }
-                }
-            }
+    gather_lane(G, P, q, x, f3(G.hn[p]), R, gl, L, M, acc, scanned);
     if (L > 1) {
         const int lane = threadIdx.x & 31;
         const uint32_t gmask = (L == 32 ? 0xffffffffu : ((1u << L) - 1u)) << (lane & ~(L - 1));
@@ -253,18 +314,60 @@ __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
             for (int off = L / 2; off > 0; off >>= 1) scanned += __shfl_xor_sync(gmask, scanned, off, L);
         }
     }
-    if (gl != 0) return;
-    if (P.work) {
-        atomicAdd(P.work + kWorkHits, 1ull);
-        atomicAdd(P.work + kWorkScanned, (unsigned long long)scanned);
+    if (gl == 0) gather_finish(G, P, p, R, M, acc, scanned);
+}
+
+// The listed heavy queries, a block of kHeavyThreads per hit point (persistent over the list):
+// the same lane split as k_gather_exact with kHeavyThreads lanes, lane sums combined by a fixed
+// butterfly in each warp and then warp by warp in order, so the result does not depend on
+// scheduling either.
+constexpr int kHeavyThreads = 256;
+
+__global__ void __launch_bounds__(kHeavyThreads) k_gather_heavy(GatherDev G, PassDev P) {
+    __shared__ float s_sum[kHeavyThreads / 32][4];
+    __shared__ uint32_t s_scan[kHeavyThreads / 32];
+    const uint32_t count = *G.nheavy;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t j = blockIdx.x; j < count; j += gridDim.x) {
+        const int64_t p = G.heavy[j];
+        const float3 x = f3(G.hx[p]);
+        const float R = G.st1[p].w;
+        const QueryCells q = query_cells(x, R, P.inv_h);
+        float M = 0.0f;
+        float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+        uint32_t scanned = 0;
+        gather_lane(G, P, q, x, f3(G.hn[p]), R, threadIdx.x, kHeavyThreads, M, acc, scanned);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            M += __shfl_xor_sync(0xffffffffu, M, off);
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
+            scanned += __shfl_xor_sync(0xffffffffu, scanned, off);
+        }
+        if (lane == 0) {
+            s_sum[warp][0] = M;
+            s_sum[warp][1] = acc.x;
+            s_sum[warp][2] = acc.y;
+            s_sum[warp][3] = acc.z;
+            s_scan[warp] = scanned;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            M = 0.0f;
+            acc = make_float3(0.0f, 0.0f, 0.0f);
+            scanned = 0;
+            for (int w = 0; w < kHeavyThreads / 32; ++w) {
+                M += s_sum[w][0];
+                acc.x += s_sum[w][1];
+                acc.y += s_sum[w][2];
+                acc.z += s_sum[w][3];
+                scanned += s_scan[w];
+            }
+            gather_finish(G, P, p, R, M, acc, scanned);
+        }
+        __syncthreads();
     }
-    if (G.rhist) G.rhist[(size_t)pass_index(P) * G.npix + p] = R;
-    if (G.shist) G.shist[(size_t)pass_index(P) * G.npix + p] = make_float4(acc.x, acc.y, acc.z, 0.0f);
-    float4 s0 = G.st0[p], s1 = G.st1[p];
-    add_direct(s1, G.hd[p]);
-    progressive_update(s0, s1, M, mul3(f3(G.hf[p]), acc), P.alpha);
-    G.st0[p] = s0;
-    G.st1[p] = s1;
 }
 
 // ------------------------------------------------------------------------------------------
