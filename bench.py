@@ -801,7 +801,7 @@ def bench_batch(args, ctx, dev, stream, rl):
                                              ((rl["peaks"] or {}).get("hbm_gbs") or FALLBACK_HBM_GBS), 4),
            "batch_autotune": {"choice": {kk: v for kk, v in choice.items()
                                          if kk in ("eye_steps", "photon_steps", "gather_lanes", "traversal",
-                                                   "fused")},
+                                                   "fused", "cell_h")},
                               "tuning_s": round(tune_s, 2)},
            "config": f"{n} scenes, 1e3-2e5 triangles log-uniform, image side in {{64,128,256,512}}, "
                      "262,144 photon paths/pass each, full paths + exact hash grid"}

@@ -398,18 +398,22 @@ typedef struct {
  * wavefront steps (0-2 and 0, 1, 2, 4), then in exact mode the hash cell edge (2, 1.5, 1, 0.75
  * or 0.5 times r0; smaller cells scan fewer photons but more buckets), then the lanes that share
  * one hit point's range query (1, 4, 8 or 16), then the path kernel's traversal (hit/miss links
- * or stack). Cell edge and lanes change only the order in which a pixel sums its photons. out
- * may be NULL. */
+ * or stack), replacing its current choice only for a gain above 3 %. Cell edge and lanes change
+ * only the order in which a pixel sums its photons. out may be NULL. */
 gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result* out);
 
 /* Autotuning of a whole batch, before its first pass: times batch passes (one CUDA graph each)
  * under candidate settings applied to every renderer -- wavefront steps (eye 0-1, photon 0-2),
- * then lanes per hit point in the exact gather (4, 8, 16), then the path kernel's traversal, then
- * the other batch form (gsp_batch_tune) with the steps searched again -- and keeps the fastest. Each
- * candidate runs one untimed and trial_passes timed passes, after which every renderer is back
- * to its initial state, so the renders that follow are those of untuned renderers (bit for bit
- * for the steps; the lanes change only a pixel's summation order). GSP_ERR_BAD_STATE if a
- * renderer has run a pass or has gradients enabled. out may be NULL (cell_h reports renderer 0's). */
+ * then the hash cell edge of the exact-mode renderers (2, 1.5, 1 or 0.75 times each renderer's
+ * own r0; a stochastic renderer's edge is part of its estimate and stays), then lanes per hit point
+ * in the exact gather (4, 8, 16), then the path kernel's traversal, then the other batch form
+ * (gsp_batch_tune) with the steps searched again -- and keeps the fastest, replacing its current
+ * choice only for a gain above 3 % (trial timings vary by a few percent). Each candidate runs one
+ * untimed and trial_passes timed passes, after which every renderer is back to its initial state,
+ * so the renders that follow are those of untuned renderers (bit for bit for the steps and the
+ * traversal; the cell edge and the lanes change only a pixel's summation order). GSP_ERR_BAD_STATE
+ * if a renderer has run a pass, has gradients enabled or counts its work. out may be NULL (cell_h
+ * reports renderer 0's). */
 gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_result* out);
 
 /* ---- work counters (the algorithmic work of a pass, for rooflines) ------------------------- */

@@ -329,7 +329,8 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         A(&r->bstart, r->T + 1);
         A(&r->spos, r->slot_cap);
         A(&r->spay, r->slot_cap);
-        A(&r->heavy, r->npix);
+        // the heavy-query split pays on large images; on small ones its extra launch costs more
+        if (r->npix >= kHeavyMinPixels) A(&r->heavy, r->npix);
     } else {
         A(&r->entry, r->T);
         A(&r->ecount, r->T);
@@ -643,11 +644,13 @@ static gsp_status gather_half(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
         G.spay = r->spay;
         G.bstart = r->bstart;
         // long queries are listed by k_gather_exact and served by whole blocks (counters[10] counts them)
-        G.heavy = r->heavy;
-        G.nheavy = r->counters + 10;
-        GSP_CUDA_TRY(cudaMemsetAsync(G.nheavy, 0, sizeof(uint32_t), st));
+        if (r->heavy) {
+            G.heavy = r->heavy;
+            G.nheavy = r->counters + 10;
+            GSP_CUDA_TRY(cudaMemsetAsync(G.nheavy, 0, sizeof(uint32_t), st));
+        }
         launch_gather_exact(r->gather_lanes, G, P, r->npix, st);
-        k_gather_heavy<<<2 * sm_count(r->scene->ctx->device), kHeavyThreads, 0, st>>>(G, P);
+        if (r->heavy) k_gather_heavy<<<2 * sm_count(r->scene->ctx->device), kHeavyThreads, 0, st>>>(G, P);
     }
     if (P.work) k_work_add<<<1, 1, 0, st>>>(P.work + kWorkDeposits, r->counters);
     GSP_CUDA_TRY(cudaGetLastError());
@@ -1226,20 +1229,33 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
     cudaError_t ce = cudaEventCreate(&a);
     if (ce == cudaSuccess) ce = cudaEventCreate(&z);
     gsp_status e = GSP_OK;
-    struct Cand { int32_t es, ps, gl, tr; bool fused; };
+    // cf: hash cell edge of the exact-mode renderers as a multiple of each one's r0 (0: the edge
+    // each had before tuning); a stochastic renderer's cell edge is part of its estimate and stays
+    struct Cand { int32_t es, ps, gl, tr; bool fused; float cf; };
     const Cand start{b->rs[0]->eye_steps, b->rs[0]->photon_steps, b->rs[0]->gather_lanes, b->rs[0]->traversal,
-                     b->fused};
+                     b->fused, 0.0f};
+    std::vector<float> cell0;
+    bool any_exact = false;
+    for (gsp_sppm* r : b->rs) {
+        cell0.push_back(r->P.cell_h);
+        any_exact = any_exact || r->P.hash_mode == GSP_EXACT;
+    }
     bool stack_ok = true;
     for (gsp_sppm* r : b->rs) stack_ok = stack_ok && r->scene->bvh.depth < kStackDepth;
     Cand pick = start;
     float best = INFINITY, first = INFINITY;
     int32_t ncand = 0;
     auto apply = [&](const Cand& c) {
-        for (gsp_sppm* r : b->rs) {
+        for (size_t i = 0; i < b->rs.size(); ++i) {
+            gsp_sppm* r = b->rs[i];
             r->eye_steps = c.es;
             r->photon_steps = c.ps;
             r->gather_lanes = c.gl;
             r->traversal = c.tr;
+            if (r->P.hash_mode == GSP_EXACT) {
+                r->P.cell_h = c.cf > 0.0f ? c.cf * r->P.r0 : cell0[i];
+                r->inv_h = 1.0f / r->P.cell_h;
+            }
         }
         b->fused = c.fused;
         batch_drop_graphs(b);
@@ -1276,20 +1292,23 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
     const bool full = b->rs[0]->P.photon_mode == GSP_FULL_PATH;
     for (int32_t es : {0, 1})
         for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2} : std::vector<int32_t>{0})
-            if (es != start.es || ps != start.ps) trial({es, ps, start.gl, start.tr, start.fused});
+            if (es != start.es || ps != start.ps) trial({es, ps, start.gl, start.tr, start.fused, 0.0f});
     const Cand steps = pick;
+    if (any_exact)  // the exact-mode cell edge (a multiple of each renderer's r0)
+        for (float cf : {2.0f, 1.5f, 1.0f, 0.75f}) trial({steps.es, steps.ps, start.gl, start.tr, start.fused, cf});
+    const Cand cell = pick;
     for (int32_t gl : {4, 8, 16})
-        if (gl != start.gl) trial({steps.es, steps.ps, gl, start.tr, start.fused});
+        if (gl != start.gl) trial({cell.es, cell.ps, gl, start.tr, start.fused, cell.cf});
     const Cand lanes = pick;
     for (int32_t tr : {GSP_TRAVERSAL_MTBVH, GSP_TRAVERSAL_STACK})
         if (tr != start.tr && (tr != GSP_TRAVERSAL_STACK || stack_ok))
-            trial({lanes.es, lanes.ps, lanes.gl, tr, start.fused});
+            trial({lanes.es, lanes.ps, lanes.gl, tr, start.fused, lanes.cf});
     // last: one fused path launch for all renderers, or a path launch per renderer; with the
     // steps searched again for the other form (the best split moves)
     const Cand form = pick;
     for (int32_t es : {0, 1})
         for (int32_t ps : full ? std::vector<int32_t>{0, 1, 2} : std::vector<int32_t>{0})
-            trial({es, ps, form.gl, form.tr, !form.fused});
+            trial({es, ps, form.gl, form.tr, !form.fused, form.cf});
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (a) cudaEventDestroy(a);
     if (z) cudaEventDestroy(z);

@@ -265,6 +265,8 @@ __device__ __forceinline__ void gather_finish(const GatherDev& G, const PassDev&
 #define GSP_HEAVY_PER_LANE 128
 #endif
 constexpr uint32_t kHeavyPerLane = GSP_HEAVY_PER_LANE;
+// Images below this many pixels gather without the split (its second launch costs more there).
+constexpr int64_t kHeavyMinPixels = 256 * 256;
 
 // Exact range query + progressive update, a group of L lanes per hit point. The group visits
 // every cell overlapping the box x +- R (any number per axis, so the cell may be smaller than the

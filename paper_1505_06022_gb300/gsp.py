@@ -665,18 +665,14 @@ class Batch:
 def sppm_params(scene, photons_per_pass, seed=1, alpha=0.7, r0=None, r0_frac=0.05, photon_mode=FULL_PATH,
                 hash_mode=EXACT, cell_h=None, table_size=None, rr_continue=0.8, eps_frac=1e-4,
                 max_eye_depth=16, max_photon_depth=32, scene_id=0) -> dict:
-    """SPPM parameters for a scene; radius and ray offset scale with the scene's diagonal."""
+    """SPPM parameters for a scene; radius and ray offset scale with the scene's diagonal. The
+    hash cell edge and table size are left to the library (0: its defaults) unless given."""
     ext = scene.extent()
     r0 = float(np.float32(r0 if r0 is not None else r0_frac * ext))
-    cell_h = float(np.float32(cell_h if cell_h is not None else 2.0 * r0))
-    if table_size is None:
-        table_size = 1
-        while table_size < 2 * photons_per_pass:
-            table_size *= 2
-    return dict(photons_per_pass=int(photons_per_pass), table_size=int(table_size), seed=int(seed),
+    return dict(photons_per_pass=int(photons_per_pass), table_size=int(table_size or 0), seed=int(seed),
                 alpha=float(np.float32(alpha)), r0=r0, rr_continue=float(np.float32(rr_continue)),
-                cell_h=cell_h, eps=float(np.float32(eps_frac * ext)), photon_mode=int(photon_mode),
-                hash_mode=int(hash_mode), max_eye_depth=int(max_eye_depth),
+                cell_h=float(np.float32(cell_h)) if cell_h else 0.0, eps=float(np.float32(eps_frac * ext)),
+                photon_mode=int(photon_mode), hash_mode=int(hash_mode), max_eye_depth=int(max_eye_depth),
                 max_photon_depth=int(max_photon_depth), scene_id=int(scene_id))
 
 

@@ -166,10 +166,10 @@ def test_stochastic_hashing_on_tilted_walls_with_the_near_face_guard(ctx, photon
     # a bucket the guard marks touches few of them
     sc = I.rotated(I.cornell_box(seed=1, width=256, height=256), 0.31, 0.52)
     kw = dict(photons_per_pass=65536, seed=2, r0_frac=0.004, photon_mode=photon_mode, hash_mode=gsp.STOCHASTIC)
-    params = gsp.sppm_params(sc, **kw)
-    r = gsp.Renderer(gsp.Scene(ctx, sc), params)
-    orc = O.Sppm(sc, O.default_params(sc, **kw))
-    h, T = params["cell_h"], params["table_size"]
+    r = gsp.Renderer(gsp.Scene(ctx, sc), gsp.sppm_params(sc, **kw))
+    oparams = O.default_params(sc, **kw)  # the hash grid's cell edge and table size (both sides' defaults)
+    orc = O.Sppm(sc, oparams)
+    h, T = oparams["cell_h"], oparams["table_size"]
     uncertain = np.zeros(256 * 256, bool)
     near_total = 0
     for _ in range(4):
