@@ -490,9 +490,11 @@ def bench_cornell(args, ctx, dev, stream, cpu):
 def bench_sppm(args, ctx, dev, stream, pg, rl):
     import torch
     from paper_1505_06022_gb300 import gsp, inputs as I
-    sc = I.full_scene(seed=3)
+    side = args.sppm_side  # 512 for the benchmark; smaller sides only for profiling captures
+    sc = I.full_scene(seed=3, width=side, height=side)
     s = gsp.Scene(ctx, sc)
-    params = gsp.sppm_params(sc, 1 << 20, seed=3, r0_frac=0.004)
+    nphot = (1 << 20) * side * side // (512 * 512)
+    params = gsp.sppm_params(sc, nphot, seed=3, r0_frac=0.004)
     warm = gsp.Renderer(s, params)
     warm.run(3, stream)
     torch.cuda.synchronize()
@@ -511,15 +513,15 @@ def bench_sppm(args, ctx, dev, stream, pg, rl):
     ms_tuned = timed_passes(tuned, k, stream)
     img_tuned = tuned.image(stream)
     same = bool(torch.equal(img, img_tuned))
-    npix, nphot = 512 * 512, 1 << 20
+    npix = side * side
     out = {"passes_per_s": round(1000.0 / ms, 2), "ms_per_pass": round(ms, 3), "passes_timed": k,
            # the paper's readout is complete paths per second (eye paths + photon paths)
            "paths_per_s": round((npix + nphot) * 1000.0 / ms, 0),
            "autotuned": {"passes_per_s": round(1000.0 / ms_tuned, 2), "ms_per_pass": round(ms_tuned, 3),
                          "choice": {kk: (round(v, 5) if isinstance(v, float) else v) for kk, v in choice.items()},
                          "tuning_s": round(tune_s, 2)},
-           "config": "512x512, 247,234 triangles (displaced plane, glass/mirror/diffuse icospheres, area light), "
-                     "1,048,576 photon paths/pass, alpha 0.7, r0 = 0.004 * diagonal, full paths + exact hash grid",
+           "config": f"{side}x{side}, 247,234 triangles (displaced plane, glass/mirror/diffuse icospheres, area light), "
+                     f"{nphot:,} photon paths/pass, alpha 0.7, r0 = 0.004 * diagonal, full paths + exact hash grid",
            "image_mean": round(float(img.mean()), 5), "autotuned_image_identical": same}
     # the same k passes once more with the work counted (untimed): the roofline of the timed render
     cr = gsp.Renderer(s, params)
@@ -530,7 +532,7 @@ def bench_sppm(args, ctx, dev, stream, pg, rl):
                                     per="the 64-pass render at the default settings")
     out["autotuned"]["roofline_frac"] = round(nbytes / (k * ms_tuned / 1000.0) / 1e9 / out["roofline"]["peak"], 4)
     if with_cpu(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))):
-        oms, cores = oracle_sppm(sc, dict(photons_per_pass=1 << 20, seed=3, r0_frac=0.004), 2)
+        oms, cores = oracle_sppm(sc, dict(photons_per_pass=nphot, seed=3, r0_frac=0.004), 2)
         out["cpu_oracle"] = {"ms_per_pass": round(oms, 1), "passes_per_s": round(1000.0 / oms, 3), "cores": cores,
                              "passes": 2, "sample": "the first 2 passes of the same render, FP64 oracle"}
     tuned.close()
@@ -827,6 +829,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sppm-passes", type=int, default=64)
+    ap.add_argument("--sppm-side", type=int, default=512,
+                    help="image side of the full-scene SPPM section (512 = the benchmark; smaller sides, with "
+                         "photons scaled by the pixel count, only for profiling captures)")
     ap.add_argument("--skip-sppm", action="store_true")
     ap.add_argument("--skip-shaded", action="store_true")
     ap.add_argument("--skip-grad", action="store_true")

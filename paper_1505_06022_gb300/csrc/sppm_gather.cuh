@@ -260,7 +260,9 @@ __device__ __forceinline__ void gather_finish(const GatherDev& G, const PassDev&
     G.st1[p] = s1;
 }
 
-// A query longer than this many photons per lane of its group goes to k_gather_heavy.
+// A query longer than this many photons per lane of its group (of at least 8 lanes: with fewer,
+// so many queries would qualify that the second launch would do most of the work) goes to
+// k_gather_heavy.
 #ifndef GSP_HEAVY_PER_LANE
 #define GSP_HEAVY_PER_LANE 128
 #endif
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(128) k_gather_exact(GatherDev G, PassDev P) {
     const float3 x = f3(hxp);
     const float R = G.st1[p].w;
     const QueryCells q = query_cells(x, R, P.inv_h);
-    if (G.heavy && query_cost(G, P, q) > kHeavyPerLane * L) {  // the whole group leaves together
+    if (G.heavy && query_cost(G, P, q) > kHeavyPerLane * (L < 8 ? 8 : L)) {  // the whole group leaves together
         if (gl == 0) G.heavy[atomicAdd(G.nheavy, 1u)] = (uint32_t)p;
         return;
     }
