@@ -408,7 +408,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
  * own r0; a stochastic renderer's edge is part of its estimate and stays), then lanes per hit point
  * in the exact gather (4, 8, 16), then the path kernel's traversal, then the other batch form
  * (gsp_batch_tune) with the steps searched again -- and keeps the fastest, replacing its current
- * choice only for a gain above 3 % (trial timings vary by a few percent). Each candidate runs one
+ * choice only for a gain above 1 % (its trials are whole-batch passes, steady to well under that). Each candidate runs one
  * untimed and trial_passes timed passes, after which every renderer is back to its initial state,
  * so the renders that follow are those of untuned renderers (bit for bit for the steps and the
  * traversal; the cell edge and the lanes change only a pixel's summation order). GSP_ERR_BAD_STATE

@@ -1213,10 +1213,12 @@ gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
     return GSP_OK;
 }
 
-// The autotuners keep their current choice unless a candidate is faster by more than 3 %: their
-// trials are a few passes from a fresh state, whose timings vary by a few percent and whose radii
-// are those of a render's first passes, so a smaller gain is as likely to be noise as real.
+// The autotuners keep their current choice unless a candidate is clearly faster: a renderer's
+// trials are a few short passes from a fresh state, whose timings vary by a few percent and whose
+// radii are those of a render's first passes, so it asks for 3 %; a batch's trials are whole-batch
+// passes of many milliseconds, steady to well under a percent, so it asks for 1 %.
 constexpr float kTuneMargin = 0.97f;
+constexpr float kBatchTuneMargin = 0.99f;
 
 gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_result* out) {
     if (!b || trial_passes < 1) return GSP_ERR_INVALID_ARG;
@@ -1283,7 +1285,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
             if (ce == cudaSuccess) ce = reset_state(r, st);
         ms /= (float)(launches * per);
         if (ncand++ == 0) first = ms;
-        if (ms < best * kTuneMargin) {  // a clear gain only: trial timings vary by a few percent
+        if (ms < best * kBatchTuneMargin) {  // a clear gain only (kBatchTuneMargin)
             best = ms;
             pick = c;
         }

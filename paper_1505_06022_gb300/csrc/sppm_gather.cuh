@@ -267,8 +267,10 @@ __device__ __forceinline__ void gather_finish(const GatherDev& G, const PassDev&
 #define GSP_HEAVY_PER_LANE 128
 #endif
 constexpr uint32_t kHeavyPerLane = GSP_HEAVY_PER_LANE;
-// Images below this many pixels gather without the split (its second launch costs more there).
-constexpr int64_t kHeavyMinPixels = 256 * 256;
+// Images below this many pixels gather without the split: at 256^2 it only breaks even (the
+// gather 67-71 us against 57 + 11 us), and in a batch of many smaller images its extra launches
+// cost more than they save.
+constexpr int64_t kHeavyMinPixels = 512 * 512;
 
 // Exact range query + progressive update, a group of L lanes per hit point. The group visits
 // every cell overlapping the box x +- R (any number per axis, so the cell may be smaller than the
