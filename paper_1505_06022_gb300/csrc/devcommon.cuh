@@ -304,27 +304,34 @@ __device__ __forceinline__ void trav_init(const DevScene& S, float3 o, float3 d,
     st.nodes = S.nodes + (size_t)c * (size_t)S.stride * 2;
 }
 
+// Moller-Trumbore test of one triangle (vertices P.xyz, V1.xyz, V2.xyz): true when the ray's
+// line meets it (det != 0, u >= 0, v >= 0, u + v <= 1); t is the distance in units of |d|.
+__device__ __forceinline__ bool tri_hit(float3 o, float3 d, const float4& P, const float4& V1, const float4& V2,
+                                        float& t) {
+    const float3 v0 = f3(P);
+    const float3 e1 = f3(V1) - v0, e2 = f3(V2) - v0;
+    const float3 p = cross3(d, e2);
+    const float det = dot3(e1, p);
+    if (det == 0.0f) return false;
+    const float f = 1.0f / det;
+    const float3 s = o - v0;
+    const float u = f * dot3(s, p);
+    const float3 q = cross3(s, e1);
+    const float v = f * dot3(d, q);
+    t = f * dot3(e2, q);
+    return u >= 0.0f && v >= 0.0f && u + v <= 1.0f;
+}
+
 // Moller-Trumbore on the triangles [first, first + cnt) of the leaf-ordered triangle array,
 // keeping the lexicographic (t, triangle index) minimum over tmin < t < best t.
 __device__ __forceinline__ void trav_leaf(const DevScene& S, Trav& st, int32_t first, int32_t cnt) {
-    const float3 o = st.o, d = st.d;
     for (int32_t k = 0; k < cnt; ++k) {
         const float4 P = __ldg(S.tris + 3 * (first + k));
         const float4 V1 = __ldg(S.tris + 3 * (first + k) + 1);
         const float4 V2 = __ldg(S.tris + 3 * (first + k) + 2);
-        const float3 v0 = f3(P);
-        const float3 e1 = f3(V1) - v0, e2 = f3(V2) - v0;
-        const float3 p = cross3(d, e2);
-        const float det = dot3(e1, p);
-        if (det == 0.0f) continue;
-        const float f = 1.0f / det;
-        const float3 s = o - v0;
-        const float u = f * dot3(s, p);
-        const float3 q = cross3(s, e1);
-        const float v = f * dot3(d, q);
-        const float t = f * dot3(e2, q);
+        float t;
         const int32_t id = __float_as_int(P.w);
-        if (u >= 0.0f && v >= 0.0f && u + v <= 1.0f && t > st.tmin &&
+        if (tri_hit(st.o, st.d, P, V1, V2, t) && t > st.tmin &&
             (t < st.tbest || (t == st.tbest && st.best >= 0 && id < st.best))) {
             st.tbest = t;
             st.best = id;
@@ -342,6 +349,13 @@ __device__ __forceinline__ void ldg64(const float4* p, float4& A, float4& B, flo
         : "l"(p));
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8+32];"
         : "=f"(C.x), "=f"(C.y), "=f"(C.z), "=f"(C.w), "=f"(D.x), "=f"(D.y), "=f"(D.z), "=f"(D.w)
+        : "l"(p));
+}
+
+// One 32-byte node at a 32-byte aligned address as one 256-bit read-only vector load.
+__device__ __forceinline__ void ldg32(const float4* p, float4& A, float4& B) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(A.x), "=f"(A.y), "=f"(A.z), "=f"(A.w), "=f"(B.x), "=f"(B.y), "=f"(B.z), "=f"(B.w)
         : "l"(p));
 }
 

@@ -126,6 +126,111 @@ __device__ __forceinline__ void trav_steps(const DevScene& S, Trav& st, int32_t&
     }
 }
 
+// The tail of a warp's work: once its queue is exhausted and a single lane still has a ray, the
+// whole warp walks that ray (coop_walk). A stackless walk only moves forward in preorder (a box
+// hit leads to the next node, a miss to a later one), so the 32 lanes fetch and test the 32
+// nodes from the current one on, one node each, and the walk then follows the hit and miss
+// links through that window in registers, fetching again only when a link leaves it; a leaf's
+// triangles are tested one per lane. The nodes visited and the hit found are those of the
+// one-lane walk (a box in the window is retested against the best t found since it was
+// fetched), but the chain of dependent fetches is several times shorter: the last ray of a
+// launch no longer waits for one node fetch per box test.
+
+// Makes every lane's walk state a copy of lane src's.
+__device__ __forceinline__ void trav_bcast(Trav& st, int src) {
+    const uint32_t F = 0xffffffffu;
+    st.o = make_float3(__shfl_sync(F, st.o.x, src), __shfl_sync(F, st.o.y, src), __shfl_sync(F, st.o.z, src));
+    st.d = make_float3(__shfl_sync(F, st.d.x, src), __shfl_sync(F, st.d.y, src), __shfl_sync(F, st.d.z, src));
+    st.inv = make_float3(__shfl_sync(F, st.inv.x, src), __shfl_sync(F, st.inv.y, src), __shfl_sync(F, st.inv.z, src));
+    st.tmin = __shfl_sync(F, st.tmin, src);
+    st.tbest = __shfl_sync(F, st.tbest, src);
+    st.best = __shfl_sync(F, st.best, src);
+    st.slot = __shfl_sync(F, st.slot, src);
+    st.node = __shfl_sync(F, st.node, src);
+    st.steps = __shfl_sync(F, st.steps, src);
+    st.nodes = (const float4*)__shfl_sync(F, (unsigned long long)st.nodes, src);
+}
+
+// Leaf test of a warp-uniform walk state, one triangle per lane: the same acceptance as
+// trav_leaf (whose sequential updates keep the lexicographic (t, index) minimum, so the winner
+// is that minimum over the accepted triangles); -0 and +0 compare equal, as there.
+__device__ __forceinline__ void coop_leaf(const float4* __restrict__ tris, Trav& st, int32_t first, int32_t cnt) {
+    const uint32_t F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float t = 0.0f;
+    int32_t id = 0;
+    bool ok = false;
+    if (lane < cnt) {
+        const float4 P = __ldg(tris + 3 * (first + lane));
+        const float4 V1 = __ldg(tris + 3 * (first + lane) + 1);
+        const float4 V2 = __ldg(tris + 3 * (first + lane) + 2);
+        id = __float_as_int(P.w);
+        ok = tri_hit(st.o, st.d, P, V1, V2, t) && t > st.tmin &&
+             (t < st.tbest || (t == st.tbest && st.best >= 0 && id < st.best));
+    }
+    if (__ballot_sync(F, ok) == 0) return;
+    uint32_t key = 0xffffffffu;  // t as an unsigned key in float order
+    if (ok) {
+        const uint32_t b = __float_as_uint(t + 0.0f);
+        key = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    }
+    const uint32_t kmin = __reduce_min_sync(F, key);
+    const bool tie = ok && key == kmin;
+    const uint32_t imin = __reduce_min_sync(F, tie ? (uint32_t)id : 0xffffffffu);
+    const int win = __ffs(__ballot_sync(F, tie && (uint32_t)id == imin)) - 1;
+    st.tbest = __shfl_sync(F, t, win);
+    st.best = (int32_t)imin;
+    st.slot = first + win;
+}
+
+// Walks lane owner's ray to its end with the whole warp (every lane must call it; lanes other
+// than owner hold no ray). Returns the owner's final state, with node = -1, in every lane.
+// Not inlined: the callers' traversal loops keep their registers, the call costs only at the
+// end of a launch. tris, nnodes and status are the scene's.
+static __device__ __noinline__ Trav coop_walk(const float4* __restrict__ tris, int64_t nnodes, int32_t* status, Trav st,
+                                              int32_t pend, int owner, int32_t cap) {
+    const uint32_t F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    trav_bcast(st, owner);
+    const int32_t pw = __shfl_sync(F, pend, owner);
+    if (pw >= 0) coop_leaf(tris, st, pw >> 3, pw & 7);
+    int32_t cur = st.node;
+    while (cur >= 0) {
+        const int32_t ws = cur;
+        bool hit = false;
+        float tn = 0.0f;
+        int32_t word = -1, miss = -1;
+        if ((int64_t)ws + lane < nnodes) {
+            float4 A, B;
+            ldg32(st.nodes + 2 * ((int64_t)ws + lane), A, B);
+            miss = __float_as_int(A.w);
+            word = __float_as_int(B.w);
+            hit = slab(st, f3(A), f3(B), tn);
+        }
+        const uint32_t hm = __ballot_sync(F, hit);
+        do {
+            const int k = cur - ws;
+            const float tk = __shfl_sync(F, tn, k);
+            const int32_t wk = __shfl_sync(F, word, k), mk = __shfl_sync(F, miss, k);
+            if (++st.steps > cap) {
+                if (lane == owner) report(status, -4);
+                cur = -1;
+            } else if (((hm >> k) & 1u) && tk <= st.tbest) {
+                if (wk >= 0) {
+                    coop_leaf(tris, st, wk >> 3, wk & 7);
+                    cur = mk;
+                } else {
+                    cur = cur + 1;
+                }
+            } else {
+                cur = mk;
+            }
+        } while (cur >= 0 && (uint32_t)(cur - ws) < 32u);
+    }
+    st.node = -1;
+    return st;
+}
+
 // Stack-based near-first walk of the child-pair layout (the comparison traversal of Fig. 4):
 // one 64-byte fetch brings both children's boxes, the nearer hit child is visited next and the
 // other pushed with its entry distance, and popped entries farther than the best hit so far are

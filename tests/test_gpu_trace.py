@@ -171,3 +171,34 @@ def test_host_buffer_entry_matches_device_entry(ctx, full_size):
     # a small call after a large one reuses the lanes
     gsp.gsp_trace_closest_hit_host(s.h, np.ascontiguousarray(rays[:1000]), tri_n[:1000], t_n[:1000])
     assert np.array_equal(tri_n[:1000], want[0][:1000])
+
+
+def test_warp_walk_of_a_lone_last_ray(ctx):
+    """When a warp has no rays left to take and one lane still walks, the whole warp walks that
+    ray through windows of 32 nodes. Rays traced one per call go almost entirely that way; their
+    ids and t are bit-identical to the same rays traced in one launch, and agree with the
+    oracle. The rays are the longest walks of the sample (the ones a launch ends on) plus
+    ordinary ones."""
+    sc = I.traversal_sphere(n=64, seed=5)  # 81,920 triangles
+    rays = I.traversal_rays(128, 64, n_random=8192, seed=36)
+    s = gsp.Scene(ctx, sc)
+    _, _, vis, _ = s.host_walk(rays)
+    pick = np.concatenate([np.argsort(-vis, kind="stable")[:192], np.arange(0, len(rays), 257)])
+    sub = np.ascontiguousarray(rays[pick])
+    d = torch.from_numpy(sub).cuda()
+    tri_all, t_all = s.trace(d)
+    tri_one = torch.empty_like(tri_all)
+    t_one = torch.empty_like(t_all)
+    for i in range(len(sub)):
+        a, b = s.trace(d[i:i + 1])
+        tri_one[i:i + 1] = a
+        t_one[i:i + 1] = b
+    torch.cuda.synchronize()
+    ctx.sync()
+    tri_all, t_all = tri_all.cpu().numpy(), t_all.cpu().numpy()
+    tri_one, t_one = tri_one.cpu().numpy(), t_one.cpu().numpy()
+    assert vis[pick[:192]].min() > 4 * vis.mean()
+    assert np.array_equal(tri_one, tri_all)
+    assert np.array_equal(t_one.view(np.int32), t_all.view(np.int32))
+    ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(sub)
+    parity_hits(tri_one, t_one, ids, tt, nd)
