@@ -72,7 +72,7 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* 
         if (wq.done) {  // no rays left to take: a ray left alone in the warp is walked by all lanes
             const uint32_t act = __ballot_sync(0xffffffffu, ray >= 0);
             if (act && !(act & (act - 1))) {
-                st = coop_walk(S.tris, S.nnodes, S.status, st, pend, __ffs(act) - 1, cap);
+                st = coop_walk(S.tris, S.nnodes, S.status, st, pend, __ffs(act) - 1, cap).st;
                 pend = -1;
             }
         }

@@ -352,13 +352,6 @@ __device__ __forceinline__ void ldg64(const float4* p, float4& A, float4& B, flo
         : "l"(p));
 }
 
-// One 32-byte node at a 32-byte aligned address as one 256-bit read-only vector load.
-__device__ __forceinline__ void ldg32(const float4* p, float4& A, float4& B) {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=f"(A.x), "=f"(A.y), "=f"(A.z), "=f"(A.w), "=f"(B.x), "=f"(B.y), "=f"(B.z), "=f"(B.w)
-        : "l"(p));
-}
-
 // Slab test of the box [lo, hi] against [tmin, best t] (Fig. 3's intersect(node.aabb, ray)):
 // t = (b - o) inv per plane, three-input min and max for the interval, the far end scaled by
 // GSP_ROBUST_FAR; conservative. On a hit tn is the entry distance. (The fused form

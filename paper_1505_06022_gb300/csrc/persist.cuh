@@ -183,17 +183,27 @@ __device__ __forceinline__ void coop_leaf(const float4* __restrict__ tris, Trav&
     st.slot = first + win;
 }
 
+// Result of coop_walk: the walk's final state (node = -1) and the triangles it tested.
+struct CoopWalk {
+    Trav st;
+    uint32_t ntri;
+};
+
 // Walks lane owner's ray to its end with the whole warp (every lane must call it; lanes other
-// than owner hold no ray). Returns the owner's final state, with node = -1, in every lane.
-// Not inlined: the callers' traversal loops keep their registers, the call costs only at the
-// end of a launch. tris, nnodes and status are the scene's.
-static __device__ __noinline__ Trav coop_walk(const float4* __restrict__ tris, int64_t nnodes, int32_t* status, Trav st,
-                                              int32_t pend, int owner, int32_t cap) {
+// than owner hold no ray). Every lane receives the owner's final state. Not inlined: the
+// callers' traversal loops keep their registers, the call costs only at the end of a launch.
+// tris, nnodes and status are the scene's.
+static __device__ __noinline__ CoopWalk coop_walk(const float4* __restrict__ tris, int64_t nnodes, int32_t* status,
+                                                  Trav st, int32_t pend, int owner, int32_t cap) {
     const uint32_t F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     trav_bcast(st, owner);
     const int32_t pw = __shfl_sync(F, pend, owner);
-    if (pw >= 0) coop_leaf(tris, st, pw >> 3, pw & 7);
+    uint32_t ntri = 0;
+    if (pw >= 0) {
+        coop_leaf(tris, st, pw >> 3, pw & 7);
+        ntri += (uint32_t)(pw & 7);
+    }
     int32_t cur = st.node;
     while (cur >= 0) {
         const int32_t ws = cur;
@@ -201,8 +211,7 @@ static __device__ __noinline__ Trav coop_walk(const float4* __restrict__ tris, i
         float tn = 0.0f;
         int32_t word = -1, miss = -1;
         if ((int64_t)ws + lane < nnodes) {
-            float4 A, B;
-            ldg32(st.nodes + 2 * ((int64_t)ws + lane), A, B);
+            const float4 A = __ldg(st.nodes + 2 * ((int64_t)ws + lane)), B = __ldg(st.nodes + 2 * ((int64_t)ws + lane) + 1);
             miss = __float_as_int(A.w);
             word = __float_as_int(B.w);
             hit = slab(st, f3(A), f3(B), tn);
@@ -218,6 +227,7 @@ static __device__ __noinline__ Trav coop_walk(const float4* __restrict__ tris, i
             } else if (((hm >> k) & 1u) && tk <= st.tbest) {
                 if (wk >= 0) {
                     coop_leaf(tris, st, wk >> 3, wk & 7);
+                    ntri += (uint32_t)(wk & 7);
                     cur = mk;
                 } else {
                     cur = cur + 1;
@@ -228,7 +238,7 @@ static __device__ __noinline__ Trav coop_walk(const float4* __restrict__ tris, i
         } while (cur >= 0 && (uint32_t)(cur - ws) < 32u);
     }
     st.node = -1;
-    return st;
+    return CoopWalk{st, ntri};
 }
 
 // Stack-based near-first walk of the child-pair layout (the comparison traversal of Fig. 4):

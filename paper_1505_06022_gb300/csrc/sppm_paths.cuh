@@ -637,6 +637,16 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
                 i = -1;
             }
         }
+        if (!STACK && wq.done) {  // nothing left to take: a path left alone in the warp walks with all lanes
+            const uint32_t act = __ballot_sync(0xffffffffu, i >= 0);
+            if (act && !(act & (act - 1)) && __shfl_sync(0xffffffffu, max(st.node, pend), __ffs(act) - 1) >= 0) {
+                const int owner = __ffs(act) - 1;
+                const CoopWalk r = coop_walk(S.tris, S.nnodes, S.status, st, pend, owner, cap);
+                st = r.st;
+                pend = -1;
+                if (COUNT && (threadIdx.x & 31) == owner) c_tris += r.ntri;
+            }
+        }
     }
     if (COUNT) {  // the whole warp leaves the loop together
         work_add_warp(P.work, kWorkEyeRays, c_eye);
