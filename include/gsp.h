@@ -46,7 +46,7 @@ enum {
     GSP_ERR_INVALID_ARG = -1,     /* a pointer, size or parameter is out of range */
     GSP_ERR_OOM = -2,             /* a device or host allocation failed */
     GSP_ERR_CUDA = -3,            /* a CUDA runtime call failed */
-    GSP_ERR_TRAVERSAL_LIMIT = -4, /* a traversal exceeded 2 * nodes + 8 steps (corrupt links) */
+    GSP_ERR_TRAVERSAL_LIMIT = -4, /* a traversal exceeded its bound on box tests (corrupt links, or gsp_scene_set_step_limit) */
     GSP_ERR_TIMEOUT = -5,         /* a bounded device wait gave up */
     GSP_ERR_NOT_BUILT = -6,       /* the scene has no BVH yet (call gsp_build_bvh) */
     GSP_ERR_BAD_STATE = -7,       /* call order violated, e.g. render_grad before a forward */
