@@ -7,7 +7,7 @@ The arithmetic lives in ``gsp_oracle.cpp`` (FP64 geometry and density estimation
 output). This module only builds that file with gcc and marshals numpy arrays.
 
 Non-degenerate rays (where the FP32 GPU triangle id must equal the FP64 oracle id bit for bit),
-judged in FP64: the winner's barycentric margin min(u, v, 1-u-v) exceeds 1e-6; its
+decided in FP64: the winner's barycentric margin min(u, v, 1-u-v) exceeds 1e-6; its
 |det| / (|e1| |e2| |d|) exceeds 1e-7; its t is more than 1e-5 (relative) away from tmin and
 tmax; and every other triangle whose barycentric margin is at least -1e-6 and whose t lies in
 the ray's range is more than 1e-5 (relative) away in t and not in front of the winner. A ray that
