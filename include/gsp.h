@@ -330,7 +330,10 @@ gsp_status gsp_sppm_state(gsp_sppm* r, float* d_N, float* d_R, float* d_tau, flo
  * restarting a render from a state computed elsewhere (a checkpoint written by other software,
  * or a reference renderer's state, so that one pass can be compared from identical state).
  * Whole photon paths only (GSP_ERR_BAD_STATE in the one-bounce mode, whose photon paths are not
- * part of this state, and after gsp_sppm_enable_grad). Ordered on `stream`. */
+ * part of this state, and after gsp_sppm_enable_grad). Every value is checked first: N finite
+ * and >= 0, R finite in (0, r0], tau and direct finite and >= 0 (a larger radius would make the
+ * exact gather visit cells without bound); otherwise GSP_ERR_INVALID_ARG and the renderer is
+ * unchanged. Synchronises `stream` (to read the check). */
 gsp_status gsp_sppm_set_state(gsp_sppm* r, const float* d_N, const float* d_R, const float* d_tau,
                               const float* d_direct, int64_t passes, void* stream);
 
@@ -350,7 +353,8 @@ gsp_status gsp_sppm_save(gsp_sppm* r, const char* path);
  * checkpoint has gradient records, with gradients enabled for at least as many passes). The PRNG
  * is keyed by the pass index, so passes after a load give bit for bit the result of an
  * uninterrupted run. GSP_ERR_BAD_STATE if the parameters differ, GSP_ERR_IO if the file is
- * unreadable or short. */
+ * unreadable, short, followed by other data, or holds a pixel state no render reaches (the
+ * values gsp_sppm_set_state checks); in each case the renderer is unchanged. */
 gsp_status gsp_sppm_load(gsp_sppm* r, const char* path);
 
 /* ---- many scenes per launch, CUDA graphs, autotuning ------------------------------------ */

@@ -410,7 +410,8 @@ static PassDev pass_params(const gsp_sppm* r, int64_t pass) {
 }
 
 // Renderer counters (uint32): [0] deposits of the pass, [7] first pass index of a replayed graph,
-// [10] hit points listed for k_gather_heavy.
+// [10] hit points listed for k_gather_heavy, [11] out-of-range pixels of a state given to
+// gsp_sppm_set_state.
 // Per trace set (qctr): [4..6] eye queue lengths, [8..10] photon queue lengths (three each, used
 // in rotation), [12] work counter of k_paths, [13] work counter of k_photon_regen.
 static int sm_count(int device) {
@@ -1458,6 +1459,19 @@ struct CkSection {
     std::vector<char> data;
 };
 
+// Whether a pixel state (st0 = {tau, N}, st1 = {direct, R}) holds only values a render can reach:
+// N finite and >= 0, R finite in (0, r0], tau and the direct sums finite and >= 0.
+static bool state_in_range(const float4* st0, const float4* st1, int64_t npix, float r0) {
+    auto fin = [](float v) { return std::isfinite(v) && v >= 0.0f; };
+    for (int64_t p = 0; p < npix; ++p) {
+        const float4 a = st0[p], b = st1[p];
+        if (!(fin(a.x) && fin(a.y) && fin(a.z) && fin(a.w) && fin(b.x) && fin(b.y) && fin(b.z) &&
+              std::isfinite(b.w) && b.w > 0.0f && b.w <= r0))
+            return false;
+    }
+    return true;
+}
+
 static bool ck_read(FILE* f, void* d_dst, size_t bytes, std::vector<CkSection>& out) {
     CkSection c{d_dst, std::vector<char>(bytes)};
     if (fread(c.data.data(), 1, bytes, f) != bytes) return false;
@@ -1522,6 +1536,11 @@ gsp_status gsp_sppm_load(gsp_sppm* r, const char* path) {
         if (!ok) {
             gsp_set_last_error("gsp_sppm_load: the checkpoint is short or has trailing data; the renderer is unchanged");
             st = GSP_ERR_IO;
+        } else if (!state_in_range((const float4*)sec[0].data.data(), (const float4*)sec[1].data.data(), r->npix,
+                                   r->P.r0)) {
+            gsp_set_last_error("gsp_sppm_load: the checkpoint's pixel state is out of range (N < 0, R outside (0, r0] "
+                               "or values not finite); the renderer is unchanged");
+            st = GSP_ERR_IO;
         }
     }
     fclose(f);
@@ -1577,8 +1596,20 @@ gsp_status gsp_sppm_set_state(gsp_sppm* r, const float* d_N, const float* d_R, c
         return GSP_ERR_BAD_STATE;
     }
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
-    k_set_state<<<blocks(r->npix, 256), 256, 0, (cudaStream_t)stream>>>(r->st0, r->st1, r->npix, d_N, d_R, d_tau,
-                                                                       d_direct);
+    // every value is checked before any is taken (a radius above r0 would make a gather visit
+    // cells without bound): counters[11] counts the pixels out of range
+    const cudaStream_t st = (cudaStream_t)stream;
+    GSP_CUDA_TRY(cudaMemsetAsync(r->counters + 11, 0, sizeof(uint32_t), st));
+    k_check_state<<<blocks(r->npix, 256), 256, 0, st>>>(r->npix, d_N, d_R, d_tau, d_direct, r->P.r0, r->counters + 11);
+    uint32_t bad = 0;
+    GSP_CUDA_TRY(cudaMemcpyAsync(&bad, r->counters + 11, sizeof bad, cudaMemcpyDeviceToHost, st));
+    GSP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad) {
+        gsp_set_last_error("gsp_sppm_set_state: N must be finite and >= 0, R finite in (0, r0], tau and the direct "
+                           "sums finite and >= 0; the renderer is unchanged");
+        return GSP_ERR_INVALID_ARG;
+    }
+    k_set_state<<<blocks(r->npix, 256), 256, 0, st>>>(r->st0, r->st1, r->npix, d_N, d_R, d_tau, d_direct);
     GSP_CUDA_TRY(cudaGetLastError());
     r->passes = passes;
     return GSP_OK;

@@ -565,6 +565,20 @@ __global__ void k_state(const float4* __restrict__ st0, const float4* __restrict
     if (direct) { direct[3 * p] = b.x; direct[3 * p + 1] = b.y; direct[3 * p + 2] = b.z; }
 }
 
+// Counts in *bad the pixels of a progressive state outside the values a render can reach: N
+// finite and >= 0, R finite in (0, r0], tau and the direct sums finite and >= 0.
+__global__ void k_check_state(int64_t npix, const float* __restrict__ N, const float* __restrict__ R,
+                              const float* __restrict__ tau, const float* __restrict__ direct, float r0,
+                              uint32_t* __restrict__ bad) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    bool ok = isfinite(N[p]) && N[p] >= 0.0f && isfinite(R[p]) && R[p] > 0.0f && R[p] <= r0;
+    for (int c = 0; c < 3; ++c)
+        ok = ok && isfinite(tau[3 * p + c]) && tau[3 * p + c] >= 0.0f && isfinite(direct[3 * p + c]) &&
+             direct[3 * p + c] >= 0.0f;
+    if (!ok) atomicAdd(bad, 1u);
+}
+
 __global__ void k_set_state(float4* __restrict__ st0, float4* __restrict__ st1, int64_t npix,
                             const float* __restrict__ N, const float* __restrict__ R, const float* __restrict__ tau,
                             const float* __restrict__ direct) {

@@ -161,13 +161,21 @@ def _host(a, dtype):
     return a, a.ctypes.data_as(C.c_void_p)
 
 
-def _dev(t):
-    """Device pointer of a torch CUDA tensor (or None)."""
+def _dev(t, dtypes=None, numel=None, what="tensor"):
+    """Device pointer of a torch CUDA tensor (or None). dtypes: accepted element types by name
+    ("float32", "int32", ...); numel: the fewest elements the call reads or writes."""
     if t is None:
         return None
     if not t.is_cuda or not t.is_contiguous():
-        raise ValueError("expected a contiguous CUDA tensor")
+        raise ValueError(f"{what}: expected a contiguous CUDA tensor")
+    if dtypes is not None and str(t.dtype).replace("torch.", "") not in dtypes:
+        raise TypeError(f"{what}: expected {' or '.join(dtypes)} elements, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{what}: expected at least {numel} elements, got {t.numel()}")
     return C.c_void_p(t.data_ptr())
+
+
+F32, I32 = ("float32",), ("int32",)
 
 
 def _stream(stream):
@@ -197,8 +205,9 @@ def gsp_rng_fill(ctx, seed, scene, domain, pass_, ids, ndraw, out=None, stream=N
     import torch
     if out is None:
         out = torch.empty((ids.shape[0], ndraw), dtype=torch.float32, device=ids.device)
-    rc = lib().gsp_rng_fill(ctx, seed, scene, domain, pass_, _dev(ids), ids.shape[0], ndraw, _dev(out),
-                            _stream(stream))
+    n = ids.shape[0]
+    rc = lib().gsp_rng_fill(ctx, seed, scene, domain, pass_, _dev(ids, ("int64", "uint64"), n, "ids"), n, ndraw,
+                            _dev(out, F32, n * ndraw, "out"), _stream(stream))
     _check("gsp_rng_fill", rc)
     return out
 
@@ -211,7 +220,8 @@ def gsp_hash_grid_build(ctx, pos, cell_h, table_size, order=None, bstart=None, s
         order = torch.empty(n, dtype=torch.int32, device=pos.device)
     if bstart is None:
         bstart = torch.empty(table_size + 1, dtype=torch.int32, device=pos.device)
-    rc = lib().gsp_hash_grid_build(ctx, _dev(pos), n, cell_h, table_size, _dev(order), _dev(bstart),
+    rc = lib().gsp_hash_grid_build(ctx, _dev(pos, F32, 4 * n, "pos"), n, cell_h, table_size,
+                                   _dev(order, I32, n, "order"), _dev(bstart, I32, table_size + 1, "bstart"),
                                    _stream(stream))
     _check("gsp_hash_grid_build", rc)
     return order, bstart
@@ -237,8 +247,10 @@ def gsp_measure_read_bandwidth(ctx, nbytes, reps):
 
 def gsp_hash_grid_build_static(pos, cell_h, table_size, order, bstart, stream=None):
     """Allocation-free hash-grid build on the current device; order/bstart are caller tensors."""
-    rc = lib().gsp_hash_grid_build_static(_dev(pos), pos.shape[0], cell_h, table_size, _dev(order),
-                                          _dev(bstart), _stream(stream))
+    n = pos.shape[0]
+    rc = lib().gsp_hash_grid_build_static(_dev(pos, F32, 4 * n, "pos"), n, cell_h, table_size,
+                                          _dev(order, I32, n, "order"), _dev(bstart, I32, table_size + 1, "bstart"),
+                                          _stream(stream))
     _check("gsp_hash_grid_build_static", rc)
     return order, bstart
 
@@ -304,14 +316,16 @@ def gsp_build_bvh_device(scene, link_sets=6, max_leaf=4) -> dict:
 def gsp_trace_closest_hit(scene, rays, tri, t, uv=None, stream=None):
     """rays: CUDA float32 [n, 8]; tri: CUDA int32 [n]; t: CUDA float32 [n]; uv: [n, 2] or None."""
     n = rays.shape[0]
-    rc = lib().gsp_trace_closest_hit(scene, _dev(rays), n, _dev(tri), _dev(t), _dev(uv), _stream(stream))
+    rc = lib().gsp_trace_closest_hit(scene, _dev(rays, F32, 8 * n, "rays"), n, _dev(tri, I32, n, "tri"),
+                                     _dev(t, F32, n, "t"), _dev(uv, F32, 2 * n, "uv"), _stream(stream))
     _check("gsp_trace_closest_hit", rc)
 
 
 def gsp_trace_closest_hit_stack(scene, rays, tri, t, uv=None, stream=None):
     """As gsp_trace_closest_hit, by stack-based near-first traversal of the same tree."""
     n = rays.shape[0]
-    rc = lib().gsp_trace_closest_hit_stack(scene, _dev(rays), n, _dev(tri), _dev(t), _dev(uv), _stream(stream))
+    rc = lib().gsp_trace_closest_hit_stack(scene, _dev(rays, F32, 8 * n, "rays"), n, _dev(tri, I32, n, "tri"),
+                                           _dev(t, F32, n, "t"), _dev(uv, F32, 2 * n, "uv"), _stream(stream))
     _check("gsp_trace_closest_hit_stack", rc)
 
 
@@ -377,7 +391,8 @@ def gsp_sppm_enable_grad(r, max_passes):
 
 
 def gsp_render_grad(r, dloss_dimg, grad_albedo, grad_emission, stream=None):
-    rc = lib().gsp_render_grad(r, _dev(dloss_dimg), _dev(grad_albedo), _dev(grad_emission), _stream(stream))
+    rc = lib().gsp_render_grad(r, _dev(dloss_dimg, F32, what="dloss_dimg"), _dev(grad_albedo, F32, what="grad_albedo"),
+                               _dev(grad_emission, F32, 3, "grad_emission"), _stream(stream))
     _check("gsp_render_grad", rc)
 
 
@@ -434,20 +449,23 @@ def gsp_sppm_pass(r, npasses=1, stream=None):
 
 
 def gsp_sppm_image(r, rgb, stream=None):
-    _check("gsp_sppm_image", lib().gsp_sppm_image(r, _dev(rgb), _stream(stream)))
+    _check("gsp_sppm_image", lib().gsp_sppm_image(r, _dev(rgb, F32, what="rgb"), _stream(stream)))
 
 
 def gsp_sppm_state(r, N=None, R=None, tau=None, direct=None, stream=None):
     counts = np.zeros(2, np.float64)
-    rc = lib().gsp_sppm_state(r, _dev(N), _dev(R), _dev(tau), _dev(direct),
+    rc = lib().gsp_sppm_state(r, _dev(N, F32, what="N"), _dev(R, F32, what="R"), _dev(tau, F32, what="tau"),
+                              _dev(direct, F32, what="direct"),
                               counts.ctypes.data_as(C.c_void_p), _stream(stream))
     _check("gsp_sppm_state", rc)
     return int(counts[0]), float(counts[1])
 
 
 def gsp_sppm_set_state(r, N, R, tau, direct, passes, stream=None):
-    _check("gsp_sppm_set_state", lib().gsp_sppm_set_state(r, _dev(N), _dev(R), _dev(tau), _dev(direct),
-                                                          int(passes), _stream(stream)))
+    _check("gsp_sppm_set_state", lib().gsp_sppm_set_state(r, _dev(N, F32, what="N"), _dev(R, F32, what="R"),
+                                                          _dev(tau, F32, what="tau"),
+                                                          _dev(direct, F32, what="direct"), int(passes),
+                                                          _stream(stream)))
 
 
 def gsp_sppm_last_deposits(r):
@@ -589,6 +607,10 @@ class Renderer:
 
     def set_state(self, N, R, tau, direct, passes, stream=None):
         """Replace the progressive state (device float32 arrays shaped as state() returns them)."""
+        npix = self.w * self.h_px
+        for t, k, name in ((N, 1, "N"), (R, 1, "R"), (tau, 3, "tau"), (direct, 3, "direct")):
+            if t.numel() != k * npix:
+                raise ValueError(f"set_state: {name} has {t.numel()} elements, expected {k * npix}")
         c = lambda t: t.contiguous()
         gsp_sppm_set_state(self.h, c(N), c(R), c(tau), c(direct), passes, stream)
 

@@ -1,5 +1,7 @@
 """Checkpoint / resume: passes after gsp_sppm_load reproduce an uninterrupted run bit for bit
 (the PRNG is keyed by the pass index), in both photon modes; mismatched renderers are refused."""
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -87,7 +89,14 @@ def test_short_or_padded_checkpoint_leaves_the_renderer_unchanged(ctx, tmp_path)
     r = gsp.Renderer(s, params)
     r.run(1)
     before = {k: (v.clone() if hasattr(v, "clone") else v) for k, v in r.state().items()}
-    for bad in (data[: len(data) - 20], data + b"\0" * 16):  # cut in the last section / trailing bytes
+    # a radius above r0 or a NaN count in the pixel state (a gather would visit cells without bound)
+    npix = 24 * 16
+    st0 = 8 + 7 * 8 + C.sizeof(gsp.SppmParams)  # magic, header, parameters, then st0 and st1
+    big_r = bytearray(data)
+    big_r[st0 + npix * 16 + 5 * 16 + 12: st0 + npix * 16 + 5 * 16 + 16] = np.float32(2 * params["r0"]).tobytes()
+    nan_n = bytearray(data)
+    nan_n[st0 + 7 * 16 + 12: st0 + 7 * 16 + 16] = np.float32("nan").tobytes()
+    for bad in (data[: len(data) - 20], data + b"\0" * 16, bytes(big_r), bytes(nan_n)):
         bp = tmp_path / "bad.bin"
         bp.write_bytes(bad)
         with pytest.raises(gsp.GspError) as e:

@@ -144,6 +144,33 @@ def test_full_size_shaded_scene_parity(ctx):
     image_parity_boundary(img, ref["image"], st["N"].cpu().numpy(), ref["N"], alpha=np.float32(0.7))
 
 
+def test_full_size_shaded_scene_in_lockstep_with_the_oracle(ctx):
+    """The same shaded scene over 4 passes, each started from the oracle's progressive state
+    (N, R, tau, direct), so that rounding differences of one pass cannot carry into the next.
+    From the second pass on, every pass meets the plain bar (1e-3 on 99.9 % of pixels). The first
+    starts from N = 0, where one photon on the other side of a radius moves a pixel by several
+    percent; it is held to the one-photon form of the bar. The same holds for the scene without
+    shading data (measured at this seed: first pass 99.88 %, later passes 99.95-99.97 %)."""
+    sc = I.shaded_scene()
+    kw = dict(photons_per_pass=1 << 20, seed=6, r0_frac=0.004)
+    s = gsp.Scene(ctx, sc)
+    step = gsp.Renderer(s, gsp.sppm_params(sc, **kw))
+    orc = O.Sppm(sc, O.default_params(sc, **kw))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    fracs = []
+    for i in range(4):
+        st = orc.state()
+        step.set_state(dev(st["N"]), dev(st["R"]), dev(st["tau"]), dev(st["direct"]), i)
+        step.run(1)
+        orc.run(1)
+        img, ref = step.image().cpu().numpy(), orc.image()
+        if i == 0:
+            image_parity_boundary(img, ref, step.state()["N"].cpu().numpy(), orc.state()["N"], alpha=np.float32(0.7))
+        else:
+            fracs.append(image_parity(img, ref))
+    assert min(fracs) >= 0.999
+
+
 def test_shading_argument_errors(ctx):
     sc = I.cornell_box(width=8, height=8)
     s = gsp.Scene(ctx, sc)

@@ -239,6 +239,22 @@ def test_set_state_round_trip_and_checks(ctx):
     with pytest.raises(gsp.GspError) as e:
         regen.set_state(st["N"], st["R"], st["tau"], st["direct"], 3)
     assert e.value.code == -7
+    # values no render reaches are refused before any is taken (a radius above r0 would make a
+    # gather visit cells without bound), and the renderer is left as it was
+    want = b.image().clone()
+    for name, idx, val in (("R", (0, 0), 2 * params["r0"]), ("R", (3, 4), 0.0), ("N", (1, 2), float("nan")),
+                           ("N", (2, 2), -1.0), ("tau", (5, 5, 1), -1.0), ("direct", (4, 7, 2), float("inf"))):
+        bad = {k: st[k].clone() for k in ("N", "R", "tau", "direct")}
+        bad[name][idx] = val
+        with pytest.raises(gsp.GspError) as e:
+            b.set_state(bad["N"], bad["R"], bad["tau"], bad["direct"], 9)
+        assert e.value.code == -1, name
+    assert torch.equal(b.image(), want) and b.state()["passes"] == 5
+    # element type and size are checked by the binding
+    with pytest.raises(TypeError):
+        b.set_state(st["N"].double(), st["R"], st["tau"], st["direct"], 3)
+    with pytest.raises(ValueError):
+        b.set_state(st["N"][:4], st["R"], st["tau"], st["direct"], 3)
 
 
 def test_edge_cases(ctx):

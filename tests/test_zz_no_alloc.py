@@ -77,5 +77,12 @@ def test_static_build_rejects_sizes_beyond_its_scratch():
         gsp.gsp_hash_grid_build_static(pos, 0.1, 64, order, starts)
     small = torch.zeros((16, 4), device="cuda")
     big_table = gsp.GRID_STATIC_MAX_TABLE * 2
-    with pytest.raises(gsp.GspError, match="static scratch"):
-        gsp.gsp_hash_grid_build_static(small, 0.1, big_table, order[:16], torch.empty(2, device="cuda"))
+    # the binding refuses a bucket-start buffer shorter than the table before calling the library
+    with pytest.raises(ValueError, match="bstart"):
+        gsp.gsp_hash_grid_build_static(small, 0.1, big_table, order[:16], torch.empty(2, dtype=torch.int32, device="cuda"))
+    # the library itself refuses the table size (called directly, past the binding's checks)
+    import ctypes as C
+    rc = gsp.lib().gsp_hash_grid_build_static(C.c_void_p(small.data_ptr()), 16, C.c_float(0.1), big_table,
+                                              C.c_void_p(order.data_ptr()), C.c_void_p(starts.data_ptr()),
+                                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -1 and "static scratch" in gsp.lib().gsp_last_error_message().decode()
