@@ -233,6 +233,70 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
     e = __fmaf_rn(a, b, -p);
 }
 
+// Double-float numbers hi + lo (|lo| <= ulp(hi) / 2) and the few operations the emission kernels
+// need, after Dekker (Numer. Math. 18, 1971), built on the error-free sum and product above: about
+// 44 bits of precision at FP32 instruction cost. A result rounded to FP32 (its hi) is the FP32
+// rounding of the exact value except within about 2^-20 of a tie.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    float p, e;
+    two_prod(a.hi, b, p, e);
+    return fast_two_sum(p, __fmaf_rn(a.lo, b, e));
+}
+
+__device__ __forceinline__ DF two_sum_df(float a, float b) {
+    DF r;
+    two_sum(a, b, r.hi, r.lo);
+    return r;
+}
+
+// a / b: the FP32 quotient plus its correction from the exact remainder a.hi - q b.
+__device__ __forceinline__ DF df_div_f(DF a, float b) {
+    const float q = __fdiv_rn(a.hi, b);
+    const float r = __fadd_rn(__fmaf_rn(-q, b, a.hi), a.lo);
+    return fast_two_sum(q, __fdiv_rn(r, b));
+}
+
+// 1 / sqrt(a) for a > 0: the FP32 value refined by one Newton step y + y (1 - a y^2) / 2 in
+// double-float arithmetic.
+__device__ __forceinline__ DF df_rsqrt(DF a) {
+    const float y = __frsqrt_rn(a.hi);
+    float yh, yl;
+    two_prod(y, y, yh, yl);
+    const DF t = df_mul(a, DF{yh, yl});
+    const DF e = df_add(DF{1.0f, 0.0f}, DF{-t.hi, -t.lo});
+    return df_add(DF{y, 0.0f}, df_mul_f(e, 0.5f * y));
+}
+
+// sqrt(a) for a >= 0: the FP32 root plus its correction from the exact residual a - s^2.
+__device__ __forceinline__ DF df_sqrt(float a) {
+    const float s = __fsqrt_rn(a);
+    if (!(s > 0.0f)) return DF{s, 0.0f};
+    return fast_two_sum(s, __fdiv_rn(__fmaf_rn(-s, s, a), __fadd_rn(s, s)));
+}
+
 // (nh + nl) . (vh + vl) as a normalised double-float hi + lo (|lo| <= ulp(hi) / 2): the
 // products nh * vh exactly, the cross terms once rounded, nl * vl dropped. Normalising matters
 // when the dot product cancels: the quotient below corrects only to first order in lo / hi.

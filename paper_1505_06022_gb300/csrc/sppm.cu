@@ -275,7 +275,7 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     r->slots_per_path = P.photon_mode == GSP_FULL_PATH ? kSlotsPerPath : 1;
     r->slot_cap = r->np * r->slots_per_path;
     r->nemit = ne;
-    {  // camera basis in FP64, rounded once
+    {  // camera basis in FP64, passed on as double-float pairs
         const gsp_camera& c = s->cam;
         double eye[3] = {c.eye[0], c.eye[1], c.eye[2]}, f[3], rt[3], up[3];
         for (int k = 0; k < 3; ++k) f[k] = (double)c.look[k] - eye[k];
@@ -291,11 +291,19 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         up[1] = rt[2] * f[0] - rt[0] * f[2];
         up[2] = rt[0] * f[1] - rt[1] * f[0];
         r->cam.eye = make_float3((float)eye[0], (float)eye[1], (float)eye[2]);
-        r->cam.fwd = make_double3(f[0], f[1], f[2]);
-        r->cam.right = make_double3(rt[0], rt[1], rt[2]);
-        r->cam.up = make_double3(up[0], up[1], up[2]);
-        r->cam.th = std::tan((double)c.vfov_deg * M_PI / 180.0 / 2.0);
-        r->cam.aspect = (double)c.width / (double)c.height;
+        // each FP64 value as a double-float pair: hi its FP32 rounding, lo that of the remainder
+        auto split3 = [](const double* v, float3& hi, float3& lo) {
+            hi = make_float3((float)v[0], (float)v[1], (float)v[2]);
+            lo = make_float3((float)(v[0] - (double)hi.x), (float)(v[1] - (double)hi.y), (float)(v[2] - (double)hi.z));
+        };
+        split3(f, r->cam.fwd_hi, r->cam.fwd_lo);
+        split3(rt, r->cam.right_hi, r->cam.right_lo);
+        split3(up, r->cam.up_hi, r->cam.up_lo);
+        const double th = std::tan((double)c.vfov_deg * M_PI / 180.0 / 2.0), aspect = (double)c.width / (double)c.height;
+        r->cam.th_hi = (float)th;
+        r->cam.th_lo = (float)(th - (double)r->cam.th_hi);
+        r->cam.aspect_hi = (float)aspect;
+        r->cam.aspect_lo = (float)(aspect - (double)r->cam.aspect_hi);
         r->cam.w = c.width;
         r->cam.h = c.height;
     }

@@ -22,10 +22,12 @@ namespace gspd {
 constexpr float kPi = 3.14159265358979323846f;
 constexpr int kSlotsPerPath = 32;
 
+// The camera with its FP64 basis, tan(vfov / 2) and aspect ratio each split into double-float
+// hi + lo parts (about 48 of their 53 bits).
 struct CamDev {
     float3 eye;
-    double3 fwd, right, up;
-    double th, aspect;
+    float3 fwd_hi, fwd_lo, right_hi, right_lo, up_hi, up_lo;
+    float th_hi, th_lo, aspect_hi, aspect_lo;
     int32_t w, h;
 };
 
@@ -362,14 +364,29 @@ k_eye_emit(CamDev C, PassDev P, PathQ Q, EyeOut O, uint32_t* __restrict__ qn, un
     const int px = (int)(p % C.w), py = (int)(p / C.w);
     Rng rng = rng_seed(P.seed, P.scene_id, 0u, pass_index(P), (uint64_t)p);
     const float u0 = rng_next(rng), u1 = rng_next(rng);
-    // primary ray in FP64 (once per pixel), rounded once
-    const double sx = (((double)px + u0) / (double)C.w * 2.0 - 1.0) * C.th * C.aspect;
-    const double sy = (1.0 - ((double)py + u1) / (double)C.h * 2.0) * C.th;
-    const double dx = C.fwd.x + C.right.x * sx + C.up.x * sy, dy = C.fwd.y + C.right.y * sx + C.up.y * sy,
-                 dz = C.fwd.z + C.right.z * sx + C.up.z * sy;
-    const double il = rsqrt(dx * dx + dy * dy + dz * dz);
+    // primary ray d = fwd + right sx + up sy, sx = ((px + u0) / w 2 - 1) tan(vfov/2) aspect,
+    // sy = (1 - (py + u1) / h 2) tan(vfov/2), normalised: in double-float arithmetic (FP64 runs
+    // at a small fraction of the FP32 rate here) and rounded once, the FP32 rounding of the exact
+    // direction up to near-ties
+    const DF th{C.th_hi, C.th_lo};
+    DF sx = df_div_f(two_sum_df((float)px, u0), (float)C.w);
+    sx = df_mul(df_add(DF{2.0f * sx.hi, 2.0f * sx.lo}, DF{-1.0f, 0.0f}), th);
+    sx = df_mul(sx, DF{C.aspect_hi, C.aspect_lo});
+    DF sy = df_div_f(two_sum_df((float)py, u1), (float)C.h);
+    sy = df_mul(df_add(DF{1.0f, 0.0f}, DF{-2.0f * sy.hi, -2.0f * sy.lo}), th);
+    const auto comp = [&](float fh, float fl, float rh, float rl, float uh, float ul) {
+        return df_add(df_add(DF{fh, fl}, df_mul(DF{rh, rl}, sx)), df_mul(DF{uh, ul}, sy));
+    };
+    const DF dx = comp(C.fwd_hi.x, C.fwd_lo.x, C.right_hi.x, C.right_lo.x, C.up_hi.x, C.up_lo.x);
+    const DF dy = comp(C.fwd_hi.y, C.fwd_lo.y, C.right_hi.y, C.right_lo.y, C.up_hi.y, C.up_lo.y);
+    const DF dz = comp(C.fwd_hi.z, C.fwd_lo.z, C.right_hi.z, C.right_lo.z, C.up_hi.z, C.up_lo.z);
+    const DF il = df_rsqrt(df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz)));
+    const auto out = [&](DF v) {
+        const DF c = df_mul(v, il);
+        return __fadd_rn(c.hi, c.lo);
+    };
     Q.ray[2 * p] = make_float4(C.eye.x, C.eye.y, C.eye.z, 0.0f);
-    Q.ray[2 * p + 1] = make_float4((float)(dx * il), (float)(dy * il), (float)(dz * il), __int_as_float(0x7f800000));
+    Q.ray[2 * p + 1] = make_float4(out(dx), out(dy), out(dz), __int_as_float(0x7f800000));
     Q.w[p] = make_float4(1.0f, 1.0f, 1.0f, __int_as_float((int32_t)p));
     Q.rng[p] = make_int4(rng.s[0], rng.s[1], rng.s[2], rng.s[3]);
     Q.meta[p] = 0;
@@ -429,10 +446,17 @@ __device__ __forceinline__ void emit_photon(const EmitDev& E, Rng& rng, float3& 
                  e2 = f3(__ldg(E.geo + 5 * j + 2)), n = f3(__ldg(E.geo + 5 * j + 3));
     phi = f3(__ldg(E.geo + 5 * j + 4));
     const float u1 = rng_next(rng), u2 = rng_next(rng);
-    // point on the triangle in FP64 (once per path), rounded once
-    const double su = sqrt((double)u1), b1 = su * (1.0 - (double)u2), b2 = su * (double)u2;
-    o = make_float3((float)(v0.x + e1.x * b1 + e2.x * b2), (float)(v0.y + e1.y * b1 + e2.y * b2),
-                    (float)(v0.z + e1.z * b1 + e2.z * b2));
+    // point on the triangle v0 + e1 b1 + e2 b2, b1 = sqrt(u1) (1 - u2), b2 = sqrt(u1) u2, in
+    // double-float arithmetic (FP64 runs at a small fraction of the FP32 rate here) and rounded
+    // once: the FP32 rounding of the exact point up to near-ties
+    float th, tl;
+    two_sum(1.0f, -u2, th, tl);  // 1 - u2 exactly
+    const DF su = df_sqrt(u1), b1 = df_mul(su, DF{th, tl}), b2 = df_mul_f(su, u2);
+    const auto coord = [&](float v, float a, float b) {
+        const DF c = df_add(df_add(DF{v, 0.0f}, df_mul_f(b1, a)), df_mul_f(b2, b));
+        return __fadd_rn(c.hi, c.lo);
+    };
+    o = make_float3(coord(v0.x, e1.x, e2.x), coord(v0.y, e1.y, e2.y), coord(v0.z, e1.z, e2.z));
     const float u3 = rng_next(rng), u4 = rng_next(rng);
     d = cosine_dir(n, u3, u4);
 }
