@@ -588,6 +588,8 @@ k_photon_shade(DevScene S, PassDev P, DepositDev D, PathQ cur, PathQ nxt, uint32
 // next item as soon as its path ends (WarpQueue, counter *ctr), so the long specular eye paths,
 // which start first, run beside the bulk of the photon work instead of after it. Eye entries
 // have depth <= max_eye, photon entries depth < max_photon (the host launches accordingly).
+// Once nothing is left to take, a path left alone in its warp has its walks done by all lanes
+// (coop_walk).
 // STACK: walk the child-pair layout with a stack (StackWalk) instead of the hit/miss links.
 // COUNT: add the work of the launch to P.work (the instantiation used only while counting, so
 // that the counters take no registers in the others).
