@@ -36,7 +36,7 @@ k_trace(DevScene S, const float4* __restrict__ rays, int64_t n, const uint32_t* 
     Trav st;
     st.node = -1;
     st.slot = -1;
-    WarpQueue wq;
+    WarpQueue<> wq;
     wq.init((int32_t)n);  // ray indices fit in 31 bits (the entry point rejects larger batches)
     int32_t ray = -1;
     int32_t pend = -1;  // leaf word of a postponed leaf, -1 = none
@@ -89,7 +89,7 @@ k_trace_stack(DevScene S, const float4* __restrict__ rays, int64_t n, int32_t* _
               int2* __restrict__ rlist, float refine_factor) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    WarpQueue wq;
+    WarpQueue<> wq;
     wq.init((int32_t)n);
     Trav st;
     st.slot = -1;

@@ -17,12 +17,17 @@ constexpr int kTraceThreads = 128;
 #ifndef GSP_TRACE_MIN_BLOCKS
 #define GSP_TRACE_MIN_BLOCKS 9
 #endif
+#ifndef GSP_PATH_CHUNK
+#define GSP_PATH_CHUNK 32
+#endif
 #ifndef GSP_PATH_MIN_BLOCKS
 #define GSP_PATH_MIN_BLOCKS 8
 #endif
 constexpr int kTraceChunk = GSP_TRACE_CHUNK;           // rays a warp takes from the global counter at once
 constexpr int kTraceInner = GSP_TRACE_INNER;           // traversal steps between refills
 constexpr int kTraceLeafBatch = GSP_TRACE_LEAF_BATCH;  // pending leaves that trigger a warp-wide leaf test
+constexpr int kPathChunk = GSP_PATH_CHUNK;  // paths a warp of the path kernels takes at once (a block's
+                                            // grid share is 128 paths: every warp of a short launch gets some)
 
 // Persistent grid size of the closest-hit kernel: SMs x resident blocks per SM.
 int gsp_trace_grid(int device);

@@ -13,12 +13,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Work distribution of a persistent kernel over items [0, n). A warp takes kTraceChunk
-// consecutive items at a time and hands them to its lanes as they become free, so a lane whose
-// item has finished starts the next one without waiting for the rest of the warp. Each warp's
-// first chunk is static (an empty or short launch costs no atomics); later chunks come from a
-// counter that the caller has zeroed and that counts past the static chunks. All fields are
-// warp-uniform.
+// Work distribution of a persistent kernel over items [0, n). A warp takes CHUNK consecutive
+// items at a time and hands them to its lanes as they become free, so a lane whose item has
+// finished starts the next one without waiting for the rest of the warp. Each warp's first chunk
+// is static (an empty or short launch costs no atomics); later chunks come from a counter that
+// the caller has zeroed and that counts past the static chunks. All fields are warp-uniform.
+template <int CHUNK = kTraceChunk>
 struct WarpQueue {
     int32_t n, static_end, qbase, qend;
     bool done;
@@ -26,9 +26,9 @@ struct WarpQueue {
     __device__ __forceinline__ void init(int32_t n_) {
         n = n_;
         const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-        static_end = (int32_t)min(warps * kTraceChunk, (int64_t)n);
-        qbase = (int32_t)min(((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kTraceChunk, (int64_t)n);
-        qend = min(qbase + kTraceChunk, n);
+        static_end = (int32_t)min(warps * CHUNK, (int64_t)n);
+        qbase = (int32_t)min(((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * CHUNK, (int64_t)n);
+        qend = min(qbase + CHUNK, n);
         done = false;
     }
 
@@ -42,10 +42,10 @@ struct WarpQueue {
         while (m) {
             if (qbase >= qend) {
                 CounterT b = 0;
-                if (static_end < n && (threadIdx.x & 31) == 0) b = atomicAdd(ctr, (CounterT)kTraceChunk);
+                if (static_end < n && (threadIdx.x & 31) == 0) b = atomicAdd(ctr, (CounterT)CHUNK);
                 b = __shfl_sync(0xffffffffu, b, 0);
                 qbase = (int32_t)min((int64_t)static_end + (int64_t)b, (int64_t)n);
-                qend = min(qbase + kTraceChunk, n);
+                qend = min(qbase + CHUNK, n);
                 if (qbase >= n) {
                     done = true;
                     break;

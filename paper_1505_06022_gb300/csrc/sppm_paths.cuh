@@ -600,7 +600,7 @@ k_paths(DevScene S, PassDev P, PathQ qe, EyeOut O, const uint32_t* __restrict__ 
     const int32_t cap = trav_cap(S);
     const int32_t ne = ne_ptr ? (int32_t)*ne_ptr : 0;
     const int32_t nph = np_ptr ? (int32_t)*np_ptr : 0;
-    WarpQueue wq;
+    WarpQueue<kPathChunk> wq;
     wq.init(ne + nph);
     Trav st;
     st.node = -1;
@@ -849,7 +849,7 @@ template <bool STACK, bool SHADE, bool COUNT>
 __global__ void __launch_bounds__(kTraceThreads, GSP_PATH_MIN_BLOCKS)
 k_photon_regen(DevScene S, EmitDev E, PassDev P, DepositDev D, RegenDev R, uint32_t* __restrict__ ctr) {
     const int32_t cap = trav_cap(S);
-    WarpQueue wq;
+    WarpQueue<kPathChunk> wq;
     wq.init((int32_t)P.np);
     Trav st;
     st.node = -1;
