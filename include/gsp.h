@@ -304,8 +304,9 @@ gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
  * in double-float arithmetic, as the persistent kernel's hits always do; > 0 = only hits whose
  * estimated FP32 error amplification exceeds it take an FP64 distance (trades hit-distance
  * accuracy for time).
- * gather_lanes: lanes that share one hit point's exact range query (1, 4, 8 or 16; default 8;
- * 0 = keep); changes only the order in which a pixel sums its photons.
+ * gather_lanes: lanes that share one hit point's exact range query (1, 4, 8 or 16; 0 = keep);
+ * the default at creation is 16 for images under 65,536 pixels and 8 from there on. Changes only
+ * the order in which a pixel sums its photons.
  * traversal: GSP_TRAVERSAL_MTBVH (default) or GSP_TRAVERSAL_STACK for the persistent path kernel
  * (0 = keep); the closest hits, hence the results, are the same. The stack needs a tree less
  * than 64 levels deep (GSP_ERR_INVALID_ARG otherwise). */

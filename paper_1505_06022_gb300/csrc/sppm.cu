@@ -104,7 +104,7 @@ struct gsp_sppm {
     unsigned long long* work = nullptr;  // work counters (kWorkCounts), see gsp_sppm_count_work
     bool count_work = false;
     // tuning
-    int32_t gather_lanes = 8;  // lanes per hit point in the exact gather
+    int32_t gather_lanes = 8;  // lanes per hit point in the exact gather (set at creation)
     int32_t traversal = GSP_TRAVERSAL_MTBVH;  // of the path kernel
     int64_t qcap = 0;
     int32_t eye_steps = 0;      // eye wavefront steps before the persistent path kernel
@@ -344,6 +344,9 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         A(&r->ecount, r->T);
     }
     r->qcap = std::max(r->npix, P.photon_mode == GSP_FULL_PATH ? r->np : (int64_t)0);
+    // gather lanes per hit point: a small image's gather has too few hit points to fill the GPU
+    // with 8 lanes each (a 64x64 pass: 0.183 against 0.200 ms with 16)
+    r->gather_lanes = r->npix < kGatherWideBelow ? 16 : 8;
     r->eye_steps = 0;     // no wavefront steps: the persistent path kernel (per-lane refill)
     r->photon_steps = 0;  // traces every bounce; a step costs a closest-hit launch over the whole
                           // queue plus a shade launch, and waits for its slowest ray

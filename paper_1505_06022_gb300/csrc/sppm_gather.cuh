@@ -271,6 +271,8 @@ constexpr uint32_t kHeavyPerLane = GSP_HEAVY_PER_LANE;
 // gather 67-71 us against 57 + 11 us), and in a batch of many smaller images its extra launches
 // cost more than they save.
 constexpr int64_t kHeavyMinPixels = 512 * 512;
+// Images below this many pixels gather with 16 lanes per hit point by default, larger ones with 8.
+constexpr int64_t kGatherWideBelow = 256 * 256;
 
 // Exact range query + progressive update, a group of L lanes per hit point. The group visits
 // every cell overlapping the box x +- R (any number per axis, so the cell may be smaller than the
