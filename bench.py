@@ -599,7 +599,7 @@ def bench_grad(args, ctx, dev, stream, rl):
     probe.close()
     params = dict(params, cell_h=float(choice["cell_h"]))
     fwd, bwd = [], []
-    for rep in range(3):
+    for rep in range(7):  # medians of 6 timed repetitions (the first warms up)
         r = gsp.Renderer(s, params)
         r.tune(choice["eye_steps"], choice["photon_steps"], 0.0, choice["gather_lanes"], choice["traversal"])
         r.enable_grad(passes)

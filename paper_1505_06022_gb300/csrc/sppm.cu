@@ -119,6 +119,7 @@ struct gsp_sppm {
     int32_t* smat = nullptr;                 // alias as hw
     double* gacc = nullptr;            // [nmat * 3 + 3]
     uint32_t *hp_order = nullptr, *hp_bstart = nullptr, *hp_scratch = nullptr;
+    float4* hp_rec = nullptr;  // hit points in grid order for the adjoint gather (3 float4 each)
     int64_t hp_T = 0;
     int64_t passes = 0;
     std::vector<void*> allocs;
@@ -669,6 +670,10 @@ static gsp_status gather_half(gsp_sppm* r, const PassDev& P, cudaStream_t st) {
     return GSP_OK;
 }
 
+#ifndef GSP_ADJ_LANES
+#define GSP_ADJ_LANES 8
+#endif
+
 static gsp_status check_grad_room(gsp_sppm* r, int64_t npasses) {
     if (r->grad && r->passes + npasses > r->grad_max_passes) {
         gsp_set_last_error("gsp_sppm_pass: more passes than gsp_sppm_enable_grad reserved radius history for");
@@ -842,6 +847,7 @@ gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
     A(&r->hp_order, r->npix);
     A(&r->hp_bstart, r->hp_T + 1);
     A(&r->hp_scratch, gsp_grid_scratch_words(r->npix, r->hp_T));
+    A(&r->hp_rec, 3 * r->npix);
     if (e != cudaSuccess) {
         gsp_set_last_error(cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
@@ -906,8 +912,10 @@ gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad
         A.d_total = r->counters;
         A.badj = r->badj;
         A.work = r->count_work ? r->work : nullptr;
+        A.hp_rec = r->hp_rec;
         if (A.work) k_work_add<<<1, 1, 0, st>>>(A.work + kWorkDeposits, r->counters);
-        k_adj_photons<8><<<grid * 8, 128, 0, st>>>(A);
+        k_adj_hp_records<<<blocks(r->npix, 256), 256, 0, st>>>(A, r->npix, r->hp_rec);
+        k_adj_photons<GSP_ADJ_LANES><<<grid * GSP_ADJ_LANES, 128, 0, st>>>(A);
         k_adj_pixels<<<grid, 256, 0, st>>>(r->hx, r->hw, A.rhist, r->shist + (size_t)i * r->npix, d_dloss_dimg,
                                            r->npix, r->gacc, nmat);
         k_adj_paths<<<grid, 128, 0, st>>>(r->slots, r->pcount, r->smat, r->badj, r->scene->d_mats, r->np, r->gacc,

@@ -392,6 +392,7 @@ struct AdjDev {
     const float* __restrict__ g;        // dLoss/dL [npix][3]
     const uint32_t* __restrict__ hp_order;   // hit-point grid: pixel at each sorted position
     const uint32_t* __restrict__ hp_bstart;
+    const float4* __restrict__ hp_rec;  // per sorted position (k_adj_hp_records): {x, bits}, {n, R}, {B term, 0}
     uint32_t hp_mask;
     float inv_hp;                       // 1 / hit-point cell size
     float rmax;                         // largest gather radius (r0)
@@ -402,6 +403,24 @@ struct AdjDev {
     float4* __restrict__ badj;          // per slot: B_k, the weight of Phi_k in the loss
     unsigned long long* work;           // work counters, or null
 };
+
+// The hit points in the order of the hit-point grid, three float4 each: {x, material bits},
+// {normal, R}, {g * f / R^2, 0} (g = dLoss/dL of the pixel, f = its w rho / pi, R its radius in
+// this pass), so that the photon-centric gather reads a bucket's hit points one after another
+// instead of through the order array, with the loss term already formed (the same operations as
+// forming it per photon).
+__global__ void __launch_bounds__(256) k_adj_hp_records(AdjDev A, int64_t npix, float4* __restrict__ rec) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= npix) return;
+    const uint32_t p = A.hp_order[j];
+    const float R = A.rhist[p];
+    const float3 gp = make_float3(A.g[3 * p], A.g[3 * p + 1], A.g[3 * p + 2]);
+    const float3 w = mul3(gp, f3(A.hf[p])) * (1.0f / (R * R));
+    const float4 n = A.hn[p];
+    rec[3 * j] = A.hx[p];
+    rec[3 * j + 1] = make_float4(n.x, n.y, n.z, R);
+    rec[3 * j + 2] = make_float4(w.x, w.y, w.z, 0.0f);
+}
 
 // Photon-centric adjoint gather. For deposit k the hit points that gathered it in the forward
 // pass (same acceptance test, same radii) give B_k = sum_p g_p (w rho / pi)_p / R_p^2, the weight
@@ -432,17 +451,14 @@ __global__ void __launch_bounds__(128) k_adj_photons(AdjDev A) {
                     const uint32_t e = __ldg(A.hp_bstart + b + 1);
                     for (uint32_t j = __ldg(A.hp_bstart + b) + gl; j < e; j += L) {
                         ++scanned;
-                        const uint32_t p = __ldg(A.hp_order + j);
-                        const float4 hxp = __ldg(A.hx + p);
+                        const float4 hxp = __ldg(A.hp_rec + 3 * (size_t)j);
                         if (__float_as_int(hxp.w) < 0) continue;
                         if (cell_of(hxp.x, A.inv_hp) != ix || cell_of(hxp.y, A.inv_hp) != iy ||
                             cell_of(hxp.z, A.inv_hp) != iz)
                             continue;
-                        const float R = __ldg(A.rhist + p);
-                        if (!photon_accept(xk, f3(hxp), R, dir, f3(__ldg(A.hn + p)))) continue;
-                        const float3 gp =
-                            make_float3(__ldg(A.g + 3 * p), __ldg(A.g + 3 * p + 1), __ldg(A.g + 3 * p + 2));
-                        B = B + mul3(gp, f3(__ldg(A.hf + p))) * (1.0f / (R * R));
+                        const float4 nr = __ldg(A.hp_rec + 3 * (size_t)j + 1);
+                        if (!photon_accept(xk, f3(hxp), nr.w, dir, f3(nr))) continue;
+                        B = B + f3(__ldg(A.hp_rec + 3 * (size_t)j + 2));
                     }
                 }
 #pragma unroll
