@@ -13,7 +13,7 @@
 //
 // Device layout (all library-owned, sized at creation):
 //   pixel state   st0[p] = {tau.rgb, N}, st1[p] = {direct.rgb, R}          32 B / pixel
-//   trace sets    two (both made at creation in exact mode), each:
+//   trace sets    two (both made at creation), each:
 //     hit points  hx[p] = {x.xyz, material or -1}, hn[p] = {n_s.xyz, 0},
 //                 hf[p] = {w * albedo / pi, 0}, hd[p] = {direct.rgb, 0}     64 B / pixel
 //     photons     slot s: {x.xyz, id}, {flux.rgb, octahedral direction}    32 B / deposit
@@ -21,7 +21,7 @@
 //     queues      eye and photon wavefront queues, two of each (ping-pong), their lengths,
 //                 the path kernel's work counter, the wavefront steps' trace counters
 //   exact grid    bucket-sorted SoA copies spos[], spay[] + bucket starts bstart[T+1]
-//   stochastic    entry[T] = min(random depth bits << 32 | slot), ecount[T]
+//   stochastic    entry[T] = min(random depth bits << 32 | slot), ecount[T], one table per trace set
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -80,6 +80,8 @@ struct gsp_sppm {
         uint32_t* qctr = nullptr;  // [16]: eye queue lengths 4..6, photon 8..10, path-kernel work 12, regen 13
         unsigned long long* tctr = nullptr;  // closest-hit counters of the wavefront steps
         int2* rlist = nullptr;               // their FP64 refinement list (qcap entries)
+        unsigned long long* entry = nullptr;  // stochastic hashing: the pass's table (T entries)
+        uint32_t* ecount = nullptr;
     } tb[2];
     int cur = 0;
     float4 *hx = nullptr, *hn = nullptr, *hf = nullptr, *hd = nullptr;
@@ -156,6 +158,8 @@ void use_buf(gsp_sppm* r, int j) {
     r->qctr = r->tb[j].qctr;
     r->tctr = r->tb[j].tctr;
     r->rlist = r->tb[j].rlist;
+    r->entry = r->tb[j].entry;
+    r->ecount = r->tb[j].ecount;
 }
 
 // The path queues and counters of trace set j.
@@ -341,8 +345,8 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         // the heavy-query split pays on large images; on small ones its extra launch costs more
         if (r->npix >= kHeavyMinPixels) A(&r->heavy, r->npix);
     } else {
-        A(&r->entry, r->T);
-        A(&r->ecount, r->T);
+        A(&r->tb[0].entry, r->T);  // one table per trace set, so that passes overlap
+        A(&r->tb[0].ecount, r->T);
     }
     r->qcap = std::max(r->npix, P.photon_mode == GSP_FULL_PATH ? r->np : (int64_t)0);
     // gather lanes per hit point: a small image's gather has too few hit points to fill the GPU
@@ -371,9 +375,9 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
         if (e == cudaSuccess) e = cudaMemset(r->rd, 0, r->np * sizeof(float4));
         if (e == cudaSuccess) e = cudaMemset(r->rphi, 0, r->np * sizeof(float4));
     }
-    // exact mode traces several passes into both trace sets: the second one is made now, so
-    // that no pass allocates
-    if (e == cudaSuccess && P.hash_mode == GSP_EXACT) {
+    // several passes are traced into both trace sets: the second one is made now, so that no
+    // pass allocates
+    if (e == cudaSuccess) {
         const gsp_status se = ensure_second_buffer(r);
         if (se != GSP_OK) {
             gsp_sppm_destroy(r);
@@ -701,7 +705,9 @@ static gsp_status sppm_one_pass(gsp_sppm* r, cudaStream_t st, bool graph = false
 // The second set of trace buffers, the tracing streams and their events (at creation in exact
 // mode, else on first use).
 static gsp_status ensure_second_buffer(gsp_sppm* r) {
-    if (r->tb[1].hx && r->tb[1].qctr && (!r->grad || r->tb[1].hw)) return GSP_OK;
+    if (r->tb[1].hx && r->tb[1].qctr && (!r->grad || r->tb[1].hw) &&
+        (r->P.hash_mode != GSP_STOCHASTIC || r->tb[1].entry))
+        return GSP_OK;
     cudaError_t e = cudaSuccess;
     auto A = [&](auto** p, int64_t n) {
         if (e == cudaSuccess && !*p) e = alloc(r, p, n);
@@ -715,6 +721,10 @@ static gsp_status ensure_second_buffer(gsp_sppm* r) {
     if (r->grad) {
         A(&r->tb[1].hw, r->npix);
         A(&r->tb[1].smat, r->slot_cap);
+    }
+    if (r->P.hash_mode == GSP_STOCHASTIC) {
+        A(&r->tb[1].entry, r->T);
+        A(&r->tb[1].ecount, r->T);
     }
     if (!r->tb[1].qctr) alloc_trace_queues(r, 1, A);
     for (cudaStream_t& t : r->tstream)
@@ -803,7 +813,7 @@ gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream) {
     (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
     gsp_status s = check_grad_room(r, npasses);
     if (s != GSP_OK) return s;
-    if (npasses >= 2 && r->P.hash_mode == GSP_EXACT) return passes_overlapped(r, npasses, (cudaStream_t)stream);
+    if (npasses >= 2) return passes_overlapped(r, npasses, (cudaStream_t)stream);
     for (int32_t i = 0; i < npasses; ++i) {
         s = sppm_one_pass(r, (cudaStream_t)stream);
         if (s != GSP_OK) return s;
@@ -1377,9 +1387,9 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     Cand pick{r->eye_steps, r->photon_steps, r->P.cell_h, r->gather_lanes, r->traversal};
     // Each candidate starts from a fresh state (radii r0), runs one untimed pass and times
     // trial_passes more, so every candidate sees the same radii. Several passes are timed the
-    // way gsp_sppm_pass runs them (overlapped in exact mode), which changes which settings win:
+    // way gsp_sppm_pass runs them (overlapped), which changes which settings win:
     // the overlap hides the path kernel's tail.
-    const bool overlap = trial_passes >= 2 && r->P.hash_mode == GSP_EXACT;
+    const bool overlap = trial_passes >= 2;
     if (overlap) e = ensure_second_buffer(t);
     auto trial = [&](const Cand& c) {
         if (ce != cudaSuccess || e != GSP_OK) return;

@@ -80,13 +80,14 @@ def test_exact_gather_counts_do_not_depend_on_cell_size(ctx):
         np.testing.assert_allclose(st["tau"], states[0]["tau"], rtol=1e-5, atol=1e-7 * states[0]["tau"].max())
 
 
-@pytest.mark.parametrize("photon_mode", [0, 1])
-def test_overlapped_passes_equal_single_passes(ctx, photon_mode):
+@pytest.mark.parametrize("photon_mode,hash_mode", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_overlapped_passes_equal_single_passes(ctx, photon_mode, hash_mode):
     """Several passes per call trace pass i + 1 while pass i is gathered (two streams, two sets of
-    trace buffers); the result is bit-identical to one pass per call."""
+    trace buffers, and with stochastic hashing two tables); the result is bit-identical to one
+    pass per call."""
     sc = I.full_scene(seed=9, width=80, height=64, plane_quads=40, sphere_n=8)
     s = gsp.Scene(ctx, sc)
-    params = gsp.sppm_params(sc, 30000, seed=7, r0_frac=0.01, photon_mode=photon_mode)
+    params = gsp.sppm_params(sc, 30000, seed=7, r0_frac=0.01, photon_mode=photon_mode, hash_mode=hash_mode)
     a = gsp.Renderer(s, params)
     a.run(5)
     b = gsp.Renderer(s, params)
