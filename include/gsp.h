@@ -22,11 +22,10 @@
  *    exceeds its step limit, an overflowing buffer) in a device status word; the next
  *    gsp_sppm_sync()/gsp_context_sync() returns the first such error.
  *  - Memory the library allocates itself (scene, BVH, SPPM state) lives in device memory of
- *    the context's device, sized at creation (a renderer in exact mode makes both of its trace
- *    sets then). A few buffers are made on first use and kept: the second trace set of a
- *    renderer in stochastic mode when a gradient replay or a two-pass batch graph needs it,
- *    the per-stream buffers of host-buffer tracing, a batch's job tables; each entry point says
- *    so. Nothing is allocated between the launches of a pass.
+ *    the context's device, sized at creation (a renderer makes both of its trace sets then). A
+ *    few buffers are made on first use and kept: the per-stream buffers of host-buffer tracing,
+ *    a batch's job tables; each entry point says so. Nothing is allocated between the launches
+ *    of a pass.
  *  - Passes, batches and gradients use the handles' own extra streams internally; they are
  *    ordered after earlier work on `stream`, and later work on `stream` is ordered after them.
  */
@@ -289,10 +288,10 @@ void gsp_sppm_destroy(gsp_sppm* r);
 /* Runs `npasses` SPPM iterations on `stream`: eye pass (first non-specular hit per pixel,
  * emission seen directly), photon pass, hash-grid deposit, range query with the progressive
  * update N' = N + alpha M, R' = R sqrt((N + alpha M) / (N + M)), tau' = (tau + Phi) R'^2/R^2.
- * With npasses >= 2 in exact mode, the passes are traced on two streams of the renderer's own,
- * alternating between two sets of trace buffers and queues (both allocated by gsp_sppm_create in
- * exact mode; nothing is allocated during a pass): pass i + 1 is traced while the last paths of
- * pass i are still being traced and while pass i is deposited and gathered on `stream`; the
+ * With npasses >= 2, the passes are traced on two streams of the renderer's own, alternating
+ * between two sets of trace buffers and queues (with stochastic hashing, two tables; all made by
+ * gsp_sppm_create, nothing is allocated during a pass): pass i + 1 is traced while the last paths
+ * of pass i are still being traced and while pass i is deposited and gathered on `stream`; the
  * result equals npasses single-pass calls bit for bit. */
 gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream);
 
