@@ -28,6 +28,12 @@
  *    of a pass.
  *  - Passes, batches and gradients use the handles' own extra streams internally; they are
  *    ordered after earlier work on `stream`, and later work on `stream` is ordered after them.
+ *  - A CUDA error that earlier work left pending on the calling thread (the runtime's last error,
+ *    which the library shares with every user of the same CUDA runtime) makes a call that launches
+ *    device work return GSP_ERR_CUDA before it does anything, with gsp_last_error_message() naming
+ *    the call and the error; it is neither discarded nor reported later as a failure of the call's
+ *    own launches. A failing call consumes the error it reports, so the next call starts clean
+ *    (a sticky error, one that ends the context, fails every later call).
  */
 #ifndef GSP_H_
 #define GSP_H_

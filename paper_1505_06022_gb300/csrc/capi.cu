@@ -16,6 +16,18 @@ thread_local std::string g_last_error;
 
 void gsp_set_last_error(const std::string& msg) { g_last_error = msg; }
 
+gsp_status gsp_cuda_fail(cudaError_t e) {
+    gsp_set_last_error(cudaGetErrorString(e));
+    (void)cudaGetLastError();  // reported here; a sticky error stays and fails every later call
+    return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+}
+
+gsp_status gsp_pending_error(const char* who, cudaError_t e) {
+    gsp_set_last_error(std::string(who) + ": a CUDA error was pending before the call (left by earlier CUDA work "
+                       "on this thread): " + cudaGetErrorString(e));
+    return GSP_ERR_CUDA;
+}
+
 namespace gspd {
 
 // Closest-hit kernel (Fig. 3), persistent. A warp takes chunks of kTraceChunk consecutive rays
@@ -256,9 +268,9 @@ gsp_status gsp_context_create(int32_t device, gsp_context** out) {
     cudaError_t e = cudaMalloc(&c->d_status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
     if (e != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(e));
+        cudaFree(c->d_status);
         delete c;
-        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+        return gsp_cuda_fail(e);
     }
     *out = c;
     return GSP_OK;
@@ -411,9 +423,8 @@ gsp_status gsp_scene_upload(gsp_context* ctx, const float* verts, int64_t nv, co
     if (e == cudaSuccess) e = cudaMemcpy(s->d_nlo, nlo.data(), nt * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_mats, mt.data(), 2 * nmat * sizeof(float4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(e));
         gsp_scene_destroy(s);
-        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+        return gsp_cuda_fail(e);
     }
     *out = s;
     return GSP_OK;
@@ -438,7 +449,7 @@ gsp_status gsp_scene_set_materials(gsp_scene* s, const gsp_material* mats, int32
         mt[2 * m + 1] = float4{mats[m].emission[0], mats[m].emission[1], mats[m].emission[2], mats[m].ior};
     }
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_scene_set_materials");
     GSP_CUDA_TRY(cudaMemcpy(s->d_mats, mt.data(), mt.size() * sizeof(float4), cudaMemcpyHostToDevice));
     return GSP_OK;
 }
@@ -468,10 +479,12 @@ gsp_status gsp_scene_set_attributes(gsp_scene* s, const float* normals, const fl
                 gsp_set_last_error("gsp_scene_set_attributes: remove the scene's textures before its texture coordinates");
                 return GSP_ERR_BAD_STATE;
             }
-    if (s->ctx) GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
-    (void)cudaGetLastError();
-    cudaFree(s->d_attr);
-    s->d_attr = nullptr;
+    if (s->ctx) {  // a host-only scene has no device copy and makes no CUDA call
+        GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+        GSP_NO_PENDING_ERROR("gsp_scene_set_attributes");
+        cudaFree(s->d_attr);
+        s->d_attr = nullptr;
+    }
     s->has_texcoords = false;
     if (!normals && !texcoords) return GSP_OK;
     s->has_texcoords = texcoords != nullptr;
@@ -525,7 +538,7 @@ gsp_status gsp_scene_set_texture(gsp_scene* s, int32_t material, const float* rg
     }
     if (!s->ctx) return GSP_OK;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_scene_set_texture");
     cudaFree(s->d_texels);
     cudaFree(s->d_mtex);
     s->d_texels = nullptr;
@@ -599,7 +612,7 @@ gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, i
     if (((uintptr_t)d_rays & 15) || ((uintptr_t)d_uv & 7)) return GSP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
-    (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
+    GSP_NO_PENDING_ERROR("gsp_trace_closest_hit");
     if (n > s->rlist_cap) {  // refine list sized for the largest batch seen (worst case: every ray)
         GSP_CUDA_TRY(cudaStreamSynchronize(st));
         cudaFree(s->d_rlist);
@@ -661,7 +674,7 @@ gsp_status gsp_trace_closest_hit_host(gsp_scene* s, const float* h_rays, int64_t
     if (n == 0) return GSP_OK;
     if (!h_rays || !h_tri || !h_t || n > INT32_MAX) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_trace_closest_hit_host");
     // page-locked host memory that the device can address directly (NULL if it cannot)
     auto mapped = [](const void* p) -> const void* {
         cudaPointerAttributes a{};
@@ -747,7 +760,7 @@ gsp_status gsp_trace_closest_hit_stack(gsp_scene* s, const float* d_rays, int64_
     if (((uintptr_t)d_rays & 15) || ((uintptr_t)d_uv & 7)) return GSP_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
-    (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
+    GSP_NO_PENDING_ERROR("gsp_trace_closest_hit_stack");
     if (n > s->rlist_cap) {  // refine list sized for the largest batch seen (worst case: every ray)
         GSP_CUDA_TRY(cudaStreamSynchronize(st));
         cudaFree(s->d_rlist);
@@ -772,7 +785,7 @@ gsp_status gsp_rng_fill(gsp_context* ctx, uint64_t seed, uint32_t scene, uint32_
     if (!ctx || n < 0 || ndraw < 0 || (n > 0 && (!d_ids || !d_out))) return GSP_ERR_INVALID_ARG;
     if (n == 0 || ndraw == 0) return GSP_OK;
     GSP_CUDA_TRY(cudaSetDevice(ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_rng_fill");
     const int64_t nb = std::min<int64_t>((n + 255) / 256, 65535);
     gspd::k_rng_fill<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(seed, scene, domain, pass, d_ids, n, ndraw, d_out);
     GSP_CUDA_TRY(cudaGetLastError());

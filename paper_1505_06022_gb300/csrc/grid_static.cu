@@ -54,8 +54,10 @@ void* driver_fn(const char* name) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
     if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
+        q != cudaDriverEntryPointSuccess) {
+        (void)cudaGetLastError();  // the query's own failure: not left for the next call to report
         return nullptr;
+    }
     return p;
 }
 
@@ -83,14 +85,7 @@ extern "C" gsp_status gsp_hash_grid_build_static(const float* d_pos, int64_t n, 
                            ", table_size = " + std::to_string(table_size) + ")");
         return GSP_ERR_INVALID_ARG;
     }
-    // An error left pending by the caller's earlier CUDA work would otherwise be reported as this
-    // call's failure after the launches: report it now, before touching anything.
-    const cudaError_t pending = cudaGetLastError();
-    if (pending != cudaSuccess) {
-        gsp_set_last_error(std::string("gsp_hash_grid_build_static: a CUDA error was pending before the call: ") +
-                           cudaGetErrorString(pending));
-        return GSP_ERR_CUDA;
-    }
+    GSP_NO_PENDING_ERROR("gsp_hash_grid_build_static");
     const cudaStream_t st = (cudaStream_t)stream;
     int dev = 0;
     GSP_CUDA_TRY(cudaGetDevice(&dev));

@@ -106,13 +106,27 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+void gsp_set_last_error(const std::string& msg);
+
+// Reports a CUDA failure of the library's own work: sets the message, consumes the runtime's
+// last error (so that the next call does not see it as left over by the caller) and maps it to
+// GSP_ERR_OOM or GSP_ERR_CUDA.
+gsp_status gsp_cuda_fail(cudaError_t e);
+
+// An error that the caller's earlier CUDA work left pending on this thread (the runtime's last
+// error, shared with every user of the same CUDA runtime): reported as GSP_ERR_CUDA before the call
+// touches anything, rather than discarded or returned later as a failure of the call's own launches.
+// The library's failure paths consume the errors they report, so a pending error is never its own.
+gsp_status gsp_pending_error(const char* who, cudaError_t e);
+
 #define GSP_CUDA_TRY(expr)                                   \
     do {                                                     \
         cudaError_t e_ = (expr);                             \
-        if (e_ != cudaSuccess) {                             \
-            gsp_set_last_error(cudaGetErrorString(e_));      \
-            return e_ == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA; \
-        }                                                    \
+        if (e_ != cudaSuccess) return gsp_cuda_fail(e_);     \
     } while (0)
 
-void gsp_set_last_error(const std::string& msg);
+#define GSP_NO_PENDING_ERROR(who)                                        \
+    do {                                                                 \
+        const cudaError_t p_ = cudaGetLastError();                       \
+        if (p_ != cudaSuccess) return gsp_pending_error((who), p_);      \
+    } while (0)

@@ -252,7 +252,7 @@ extern "C" gsp_status gsp_build_bvh_device(gsp_scene* s, int32_t link_sets, int3
     const int64_t nt = s->nt;
     if (nt < 1 || nt > (int64_t(1) << 28)) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_build_bvh_device");
     NvtxRange nvtx("gsp: device LBVH build + threading");
     const int n = (int)nt;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -297,8 +297,9 @@ extern "C" gsp_status gsp_build_bvh_device(gsp_scene* s, int32_t link_sets, int3
     A(&d_depth, 1);
     auto fail = [&](cudaError_t ce) {
         for (void* p : tmp) cudaFree(p);
+        const gsp_status st = gsp_cuda_fail(ce);
         gsp_set_last_error(std::string("gsp_build_bvh_device: ") + cudaGetErrorString(ce));
-        return ce == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+        return st;
     };
     if (e != cudaSuccess) return fail(e);
 

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(512) k_read_stream(const uint4* __restrict__ p
 extern "C" gsp_status gsp_measure_read_bandwidth(gsp_context* ctx, int64_t bytes, int32_t reps, double* gbps) {
     if (!ctx || !gbps || bytes < 16 * 1024 || (bytes & 15) || reps < 1) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(ctx->device));
+    GSP_NO_PENDING_ERROR("gsp_measure_read_bandwidth");
     int sms = 0;
     GSP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
     uint4* buf = nullptr;
@@ -64,8 +65,9 @@ extern "C" gsp_status gsp_measure_read_bandwidth(gsp_context* ctx, int64_t bytes
     cudaFree(buf);
     cudaFree(sink);
     if (e != cudaSuccess) {
+        const gsp_status st = gsp_cuda_fail(e);
         gsp_set_last_error(std::string("gsp_measure_read_bandwidth: ") + cudaGetErrorString(e));
-        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+        return st;
     }
     *gbps = (double)bytes * (double)reps / ((double)ms * 1e-3) / 1e9;
     return GSP_OK;

@@ -199,7 +199,7 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     *out = nullptr;
     if (!s->ctx || !s->has_cam) return GSP_ERR_INVALID_ARG;
     if (!s->built) return GSP_ERR_NOT_BUILT;
-    (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
+    GSP_NO_PENDING_ERROR("gsp_sppm_create");
     gsp_sppm_params P = *params;
     if (P.photons_per_pass <= 0 || P.photons_per_pass > (int64_t(1) << 27)) return GSP_ERR_INVALID_ARG;
     if (!(P.alpha > 0.0f && P.alpha <= 1.0f) || !(P.r0 > 0.0f) || !(P.rr_continue > 0.0f && P.rr_continue <= 1.0f) ||
@@ -386,10 +386,9 @@ gsp_status gsp_sppm_create(gsp_scene* s, const gsp_sppm_params* params, gsp_sppm
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(e));
         free_all(r);
         delete r;
-        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
+        return gsp_cuda_fail(e);
     }
     *out = r;
     return GSP_OK;
@@ -731,10 +730,7 @@ static gsp_status ensure_second_buffer(gsp_sppm* r) {
         if (e == cudaSuccess && !t) e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
     for (cudaEvent_t* ev : {&r->ev_start, &r->ev_traced[0], &r->ev_traced[1], &r->ev_free[0], &r->ev_free[1]})
         if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(e));
-        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
-    }
+    if (e != cudaSuccess) return gsp_cuda_fail(e);
     use_buf(r, r->cur);
     return GSP_OK;
 }
@@ -810,7 +806,7 @@ gsp_status gsp_sppm_count_work(gsp_sppm* r, int32_t on, uint64_t* h_counts) {
 gsp_status gsp_sppm_pass(gsp_sppm* r, int32_t npasses, void* stream) {
     if (!r || npasses < 0) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
-    (void)cudaGetLastError();  // drop a stale error left by an unrelated earlier runtime call
+    GSP_NO_PENDING_ERROR("gsp_sppm_pass");
     gsp_status s = check_grad_room(r, npasses);
     if (s != GSP_OK) return s;
     if (npasses >= 2) return passes_overlapped(r, npasses, (cudaStream_t)stream);
@@ -858,10 +854,7 @@ gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
     A(&r->hp_bstart, r->hp_T + 1);
     A(&r->hp_scratch, gsp_grid_scratch_words(r->npix, r->hp_T));
     A(&r->hp_rec, 3 * r->npix);
-    if (e != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(e));
-        return e == cudaErrorMemoryAllocation ? GSP_ERR_OOM : GSP_ERR_CUDA;
-    }
+    if (e != cudaSuccess) return gsp_cuda_fail(e);
     r->grad = true;
     r->grad_max_passes = max_passes;
     r->emit_mat = em;
@@ -872,10 +865,9 @@ gsp_status gsp_sppm_enable_grad(gsp_sppm* r, int32_t max_passes) {
 gsp_status gsp_render_grad(gsp_sppm* r, const float* d_dloss_dimg, float* d_grad_albedo, float* d_grad_emission,
                            void* stream) {
     if (!r || !d_dloss_dimg || !d_grad_albedo || !d_grad_emission) return GSP_ERR_INVALID_ARG;
-    (void)cudaGetLastError();
     if (!r->grad || r->passes < 1) return GSP_ERR_BAD_STATE;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_render_grad");
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t nmat = r->scene->nmat;
     GSP_CUDA_TRY(cudaMemsetAsync(r->gacc, 0, ((size_t)kMaxGradMats * 3 + 3) * sizeof(double), st));
@@ -1107,10 +1099,7 @@ static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st, int K, cuda
     if (ce == cudaSuccess && e == GSP_OK)
         ce = cudaMemcpy(b->d_jobs + base, jobs.data(), jobs.size() * sizeof(PathJob), cudaMemcpyHostToDevice);
     if (e != GSP_OK) return e;
-    if (ce != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(ce));
-        return GSP_ERR_CUDA;
-    }
+    if (ce != cudaSuccess) return gsp_cuda_fail(ce);
     return GSP_OK;
 }
 
@@ -1133,10 +1122,7 @@ static gsp_status batch_capture(gsp_batch* b, cudaStream_t st) {
     if (ce == cudaSuccess && e == GSP_OK) ce = cudaGraphInstantiate(&b->exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != GSP_OK) return e;
-    if (ce != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(ce));
-        return GSP_ERR_CUDA;
-    }
+    if (ce != cudaSuccess) return gsp_cuda_fail(ce);
     return GSP_OK;
 }
 
@@ -1185,9 +1171,8 @@ gsp_status gsp_batch_create(gsp_sppm* const* renderers, int32_t n, gsp_batch** o
     }
     (void)gsp_trace_grid(dev);  // fill the launch-size cache outside any capture
     if (e != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(e));
         batch_free(b);
-        return GSP_ERR_CUDA;
+        return gsp_cuda_fail(e);
     }
     *out = b;
     return GSP_OK;
@@ -1212,7 +1197,7 @@ void gsp_batch_destroy(gsp_batch* b) {
 gsp_status gsp_batch_pass(gsp_batch* b, int32_t npasses, void* stream) {
     if (!b || npasses < 0) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(b->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_batch_pass");
     cudaStream_t st = (cudaStream_t)stream;
     for (gsp_sppm* r : b->rs) {
         if (r->grad && r->passes + npasses > r->grad_max_passes) return GSP_ERR_OVERFLOW;
@@ -1255,7 +1240,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
     for (gsp_sppm* r : b->rs)
         if (r->passes != 0 || r->grad || r->count_work) return GSP_ERR_BAD_STATE;
     GSP_CUDA_TRY(cudaSetDevice(b->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_batch_autotune");
     cudaStream_t st = b->cap;
     cudaEvent_t a = nullptr, z = nullptr;
     cudaError_t ce = cudaEventCreate(&a);
@@ -1346,10 +1331,7 @@ gsp_status gsp_batch_autotune(gsp_batch* b, int32_t trial_passes, gsp_tune_resul
     if (z) cudaEventDestroy(z);
     apply(pick);  // captured again at the next gsp_batch_pass
     if (e != GSP_OK) return e;
-    if (ce != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(ce));
-        return GSP_ERR_CUDA;
-    }
+    if (ce != cudaSuccess) return gsp_cuda_fail(ce);
     if (out) {
         out->eye_steps = pick.es;
         out->photon_steps = pick.ps;
@@ -1371,7 +1353,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
         return GSP_ERR_BAD_STATE;
     }
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_sppm_autotune");
     gsp_sppm* t = nullptr;
     gsp_sppm_params P = r->P;
     gsp_status e = gsp_sppm_create(r->scene, &P, &t);
@@ -1444,10 +1426,7 @@ gsp_status gsp_sppm_autotune(gsp_sppm* r, int32_t trial_passes, gsp_tune_result*
     if (z) cudaEventDestroy(z);
     gsp_sppm_destroy(t);
     if (e != GSP_OK) return e;
-    if (ce != cudaSuccess) {
-        gsp_set_last_error(cudaGetErrorString(ce));
-        return GSP_ERR_CUDA;
-    }
+    if (ce != cudaSuccess) return gsp_cuda_fail(ce);
     r->eye_steps = pick.es;
     r->photon_steps = pick.ps;
     r->gather_lanes = pick.gl;
@@ -1477,7 +1456,13 @@ static const char kCkMagic[8] = {'G', 'S', 'P', 'P', 'M', 'C', 'K', '1'};
 
 static bool ck_write(FILE* f, const void* d_src, size_t bytes, std::vector<char>& buf) {
     buf.resize(bytes);
-    if (bytes && cudaMemcpy(buf.data(), d_src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    if (bytes) {
+        const cudaError_t e = cudaMemcpy(buf.data(), d_src, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            (void)gsp_cuda_fail(e);  // message and last error; the call reports GSP_ERR_IO
+            return false;
+        }
+    }
     return fwrite(buf.data(), 1, bytes, f) == bytes;
 }
 
@@ -1584,7 +1569,7 @@ gsp_status gsp_sppm_load(gsp_sppm* r, const char* path) {
 gsp_status gsp_sppm_image(gsp_sppm* r, float* d_rgb, void* stream) {
     if (!r || !d_rgb) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_sppm_image");
     const float inv_p = r->passes > 0 ? 1.0f / (float)r->passes : 0.0f;
     const double ne_host = (double)r->passes * (double)r->np;
     k_image<<<blocks(r->npix, 256), 256, 0, (cudaStream_t)stream>>>(
@@ -1597,7 +1582,7 @@ gsp_status gsp_sppm_state(gsp_sppm* r, float* d_N, float* d_R, float* d_tau, flo
                           double* h_counts, void* stream) {
     if (!r) return GSP_ERR_INVALID_ARG;
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_sppm_state");
     cudaStream_t st = (cudaStream_t)stream;
     if (d_N || d_R || d_tau || d_direct) {
         k_state<<<blocks(r->npix, 256), 256, 0, st>>>(r->st0, r->st1, r->npix, d_N, d_R, d_tau, d_direct);
@@ -1625,6 +1610,7 @@ gsp_status gsp_sppm_set_state(gsp_sppm* r, const float* d_N, const float* d_R, c
         return GSP_ERR_BAD_STATE;
     }
     GSP_CUDA_TRY(cudaSetDevice(r->scene->ctx->device));
+    GSP_NO_PENDING_ERROR("gsp_sppm_set_state");
     // every value is checked before any is taken (a radius above r0 would make a gather visit
     // cells without bound): counters[11] counts the pixels out of range
     const cudaStream_t st = (cudaStream_t)stream;
@@ -1646,18 +1632,19 @@ gsp_status gsp_sppm_set_state(gsp_sppm* r, const float* d_N, const float* d_R, c
 
 int64_t gsp_sppm_last_deposits(gsp_sppm* r, uint32_t* h_ids, int64_t capacity) {
     if (!r) return GSP_ERR_INVALID_ARG;
-    if (cudaSetDevice(r->scene->ctx->device) != cudaSuccess) return GSP_ERR_CUDA;
-    if (cudaDeviceSynchronize() != cudaSuccess) return GSP_ERR_CUDA;
+    cudaError_t ce = cudaSetDevice(r->scene->ctx->device);
+    if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
     uint32_t total = 0;
-    if (cudaMemcpy(&total, r->counters, sizeof total, cudaMemcpyDeviceToHost) != cudaSuccess) return GSP_ERR_CUDA;
+    if (ce == cudaSuccess) ce = cudaMemcpy(&total, r->counters, sizeof total, cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return gsp_cuda_fail(ce);
     if (!h_ids) return (int64_t)total;
     if (capacity < (int64_t)total) return GSP_ERR_INVALID_ARG;
     // ids of every deposit: walk the per-path counts on the host
     std::vector<uint32_t> cnt(r->np);
     std::vector<float4> rec(2 * (size_t)r->slot_cap);
-    if (cudaMemcpy(cnt.data(), r->pcount, r->np * sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(rec.data(), r->slots, rec.size() * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return GSP_ERR_CUDA;
+    ce = cudaMemcpy(cnt.data(), r->pcount, r->np * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = cudaMemcpy(rec.data(), r->slots, rec.size() * sizeof(float4), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return gsp_cuda_fail(ce);
     int64_t k = 0;
     for (int64_t pth = 0; pth < r->np; ++pth)
         for (uint32_t i = 0; i < cnt[pth]; ++i) {
@@ -1719,7 +1706,7 @@ gsp_status gsp_hash_grid_build(gsp_context* ctx, const float* d_pos, int64_t n, 
     gsp_status a = grid_args_ok(d_pos, n, cell_h, table_size, d_order, d_bstart);
     if (a != GSP_OK) return a;
     GSP_CUDA_TRY(cudaSetDevice(ctx->device));
-    (void)cudaGetLastError();
+    GSP_NO_PENDING_ERROR("gsp_hash_grid_build");
     const int64_t words = gsp_grid_scratch_words(n, table_size);
     if (words > ctx->grid_words) {  // grow the context's scratch (first use or a larger build)
         GSP_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
