@@ -248,6 +248,18 @@ gsp_status gsp_build_bvh_device(gsp_scene* scene, int32_t link_sets, int32_t max
 gsp_status gsp_trace_closest_hit(gsp_scene* scene, const float* d_rays, int64_t n, int32_t* d_tri,
                                  float* d_t, float* d_uv, void* stream);
 
+/* Per-launch timing of the closest-hit kernel, for measuring it against its roofline (Fig. 3's
+ * traversal alone). gsp_trace_time_launches(scene, n) makes n pairs of CUDA events (timing
+ * enabled; any earlier pairs are destroyed; n = 0 just frees them, n <= 2^20); each of the next n
+ * gsp_trace_closest_hit calls on the scene records one pair on its stream, immediately before and
+ * after its traversal kernel, so the counter reset and the re-evaluation of flagged hits beside it
+ * stay outside. The timed calls allocate nothing. gsp_trace_launch_times waits for the recorded
+ * launches, writes the first min(count, capacity) durations in milliseconds to h_ms (host floats),
+ * stores the number recorded in *count and starts recording again from the first pair.
+ * GSP_ERR_INVALID_ARG on a host-only scene, n < 0 or n > 2^20. */
+gsp_status gsp_trace_time_launches(gsp_scene* scene, int64_t n);
+gsp_status gsp_trace_launch_times(gsp_scene* scene, float* h_ms, int64_t capacity, int64_t* count);
+
 /* The same closest-hit query on HOST buffers (h_rays [n][8], h_tri [n], h_t [n], h_uv [n][2] or
  * NULL), synchronous. Page-locked buffers the device can address (cudaHostAlloc /
  * cudaHostRegister, e.g. pinned torch tensors; h_rays 16-byte aligned): the traversal reads the

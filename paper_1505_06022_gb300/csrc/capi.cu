@@ -192,13 +192,17 @@ int gsp_trace_grid(int device) {
 
 // One closest-hit call on device buffers: counters zeroed, k_trace, FP64 refinement of the
 // flagged hits. ctr (2 u64) and rlist (n entries) belong to this call's stream.
+// With e0 and e1 (gsp_trace_time_launches), the two events bracket the k_trace launch alone.
 static void launch_trace(const gsp_scene* s, const float4* rays, int64_t n, int32_t* tri, float* t, float2* uv,
-                         unsigned long long* ctr, int2* rlist, cudaStream_t st) {
+                         unsigned long long* ctr, int2* rlist, cudaStream_t st, cudaEvent_t e0 = nullptr,
+                         cudaEvent_t e1 = nullptr) {
     NvtxRange nvtx("gsp: closest hit");
     const gspd::DevScene S = gsp_dev_scene(s);
     gspd::k_zero_u64x2<<<1, 1, 0, st>>>(ctr);
     const int grid = gsp_trace_grid(s->ctx->device);
+    if (e0) cudaEventRecord(e0, st);
     gspd::k_trace<<<grid, kTraceThreads, 0, st>>>(S, rays, n, nullptr, tri, t, uv, ctr, rlist, GSP_REFINE_FACTOR, 0);
+    if (e1) cudaEventRecord(e1, st);
     gspd::k_refine<<<std::max(1, grid / 2), 256, 0, st>>>(S, rays, rlist, ctr, t, uv);
 }
 
@@ -294,6 +298,13 @@ gsp_status gsp_context_sync(gsp_context* ctx) {
     return st;
 }
 
+static void trace_events_free(gsp_scene* s) {
+    for (cudaEvent_t e : s->tev)
+        if (e) cudaEventDestroy(e);
+    s->tev.clear();
+    s->tev_used = 0;
+}
+
 static void host_lanes_free(gsp_scene* s) {
     for (auto& L : s->lanes) {
         if (L.st) cudaStreamDestroy(L.st);
@@ -327,6 +338,7 @@ void gsp_scene_destroy(gsp_scene* s) {
     if (s->ctx) {
         cudaSetDevice(s->ctx->device);
         scene_free_bvh(s);
+        trace_events_free(s);
         cudaFree(s->d_shade);
         cudaFree(s->d_nlo);
         cudaFree(s->d_mats);
@@ -621,8 +633,43 @@ gsp_status gsp_trace_closest_hit(gsp_scene* s, const float* d_rays, int64_t n, i
         GSP_CUDA_TRY(cudaMalloc(&s->d_rlist, (size_t)n * sizeof(int2)));
         s->rlist_cap = n;
     }
-    launch_trace(s, (const float4*)d_rays, n, d_tri, d_t, (float2*)d_uv, s->d_counter, s->d_rlist, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (2 * s->tev_used < (int64_t)s->tev.size()) {
+        e0 = s->tev[2 * s->tev_used];
+        e1 = s->tev[2 * s->tev_used + 1];
+        ++s->tev_used;
+    }
+    launch_trace(s, (const float4*)d_rays, n, d_tri, d_t, (float2*)d_uv, s->d_counter, s->d_rlist, st, e0, e1);
     GSP_CUDA_TRY(cudaGetLastError());
+    return GSP_OK;
+}
+
+gsp_status gsp_trace_time_launches(gsp_scene* s, int64_t n) {
+    if (!s || !s->ctx || n < 0 || n > (int64_t(1) << 20)) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    GSP_NO_PENDING_ERROR("gsp_trace_time_launches");
+    trace_events_free(s);
+    s->tev.assign((size_t)(2 * n), nullptr);
+    for (cudaEvent_t& e : s->tev) {
+        const cudaError_t ce = cudaEventCreate(&e);
+        if (ce != cudaSuccess) {
+            trace_events_free(s);
+            return gsp_cuda_fail(ce);
+        }
+    }
+    return GSP_OK;
+}
+
+gsp_status gsp_trace_launch_times(gsp_scene* s, float* h_ms, int64_t capacity, int64_t* count) {
+    if (!s || !s->ctx || capacity < 0 || (capacity > 0 && !h_ms) || !count) return GSP_ERR_INVALID_ARG;
+    GSP_CUDA_TRY(cudaSetDevice(s->ctx->device));
+    const int64_t m = s->tev_used;
+    for (int64_t i = 0; i < std::min(m, capacity); ++i) {
+        GSP_CUDA_TRY(cudaEventSynchronize(s->tev[2 * i + 1]));
+        GSP_CUDA_TRY(cudaEventElapsedTime(&h_ms[i], s->tev[2 * i], s->tev[2 * i + 1]));
+    }
+    *count = m;
+    s->tev_used = 0;
     return GSP_OK;
 }
 

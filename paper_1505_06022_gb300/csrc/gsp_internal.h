@@ -92,6 +92,10 @@ struct gsp_scene {
         void* h_out = nullptr;
     } lanes[kHostLanes];
     int64_t lane_cap = 0;  // rays per chunk the lanes were allocated for
+    // per-launch timing of k_trace in gsp_trace_closest_hit (gsp_trace_time_launches): event
+    // pairs made up front, the first `tev_used` of them recorded
+    std::vector<cudaEvent_t> tev;
+    int64_t tev_used = 0;
 };
 
 // Installs a BVH built elsewhere (host copies + device arrays the scene takes ownership of),

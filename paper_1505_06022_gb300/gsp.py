@@ -41,7 +41,7 @@ ABI = ["gsp_status_string", "gsp_last_error_message", "gsp_context_create", "gsp
        "gsp_scene_set_materials", "gsp_batch_create", "gsp_batch_destroy", "gsp_batch_pass",
        "gsp_sppm_autotune", "gsp_sppm_save", "gsp_sppm_load", "gsp_batch_autotune", "gsp_batch_tune",
        "gsp_scene_set_attributes", "gsp_scene_set_texture", "gsp_measure_read_bandwidth", "gsp_sppm_count_work",
-       "gsp_sppm_set_state"]
+       "gsp_sppm_set_state", "gsp_trace_time_launches", "gsp_trace_launch_times"]
 GRID_STATIC_MAX_POINTS = 524288
 GRID_STATIC_MAX_TABLE = 16777216
 
@@ -115,6 +115,8 @@ def lib():
             L.gsp_scene_set_attributes.argtypes = [P, P, P]
             L.gsp_scene_set_texture.argtypes = [P, I32, P, I32, I32]
             L.gsp_trace_closest_hit.argtypes = [P, P, I64, P, P, P, P]
+            L.gsp_trace_time_launches.argtypes = [P, I64]
+            L.gsp_trace_launch_times.argtypes = [P, P, I64, C.POINTER(I64)]
             L.gsp_trace_closest_hit_stack.argtypes = [P, P, I64, P, P, P, P]
             L.gsp_trace_closest_hit_host.argtypes = [P, P, I64, P, P, P]
             L.gsp_bvh_host_walk.argtypes = [P, P, I64, P, P, P, P]
@@ -319,6 +321,20 @@ def gsp_trace_closest_hit(scene, rays, tri, t, uv=None, stream=None):
     rc = lib().gsp_trace_closest_hit(scene, _dev(rays, F32, 8 * n, "rays"), n, _dev(tri, I32, n, "tri"),
                                      _dev(t, F32, n, "t"), _dev(uv, F32, 2 * n, "uv"), _stream(stream))
     _check("gsp_trace_closest_hit", rc)
+
+
+def gsp_trace_time_launches(scene, n):
+    """The next n gsp_trace_closest_hit calls on `scene` record their traversal kernel's duration."""
+    _check("gsp_trace_time_launches", lib().gsp_trace_time_launches(scene, int(n)))
+
+
+def gsp_trace_launch_times(scene, capacity):
+    """Durations (ms, numpy float32) of the traversal kernels recorded since gsp_trace_time_launches."""
+    out = np.zeros(max(0, int(capacity)), np.float32)
+    cnt = C.c_int64()
+    _check("gsp_trace_launch_times",
+           lib().gsp_trace_launch_times(scene, out.ctypes.data if len(out) else None, len(out), C.byref(cnt)))
+    return out[:min(cnt.value, len(out))]
 
 
 def gsp_trace_closest_hit_stack(scene, rays, tri, t, uv=None, stream=None):

@@ -197,3 +197,13 @@ def test_shading_data_argument_checks_on_a_host_scene():
     gsp.gsp_scene_set_texture(s.h, 3, None)
     gsp.gsp_scene_set_attributes(s.h, None, None)
     s.close()
+
+
+def test_launch_timing_needs_a_device_scene():
+    """gsp_trace_time_launches / gsp_trace_launch_times refuse a host-only scene (it has no device
+    traversal to time) with GSP_ERR_INVALID_ARG, before any CUDA call."""
+    s = gsp.Scene(None, I.cornell_box(width=8, height=8))
+    for call in (lambda: gsp.gsp_trace_time_launches(s.h, 4), lambda: gsp.gsp_trace_launch_times(s.h, 4)):
+        with pytest.raises(gsp.GspError) as e:
+            call()
+        assert e.value.code == -1

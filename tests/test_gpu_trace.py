@@ -202,3 +202,33 @@ def test_warp_walk_of_a_lone_last_ray(ctx):
     assert np.array_equal(t_one.view(np.int32), t_all.view(np.int32))
     ids, tt, _, _, nd = O.Mesh(sc.verts, sc.tris).closest_hit(sub)
     parity_hits(tri_one, t_one, ids, tt, nd)
+
+
+def test_launch_timing_records_the_traversal_kernel(ctx):
+    """gsp_trace_time_launches: the next n calls record their traversal kernel's duration, the
+    results do not change, a read restarts the recording, and n = 0 turns it off."""
+    sc = I.traversal_sphere(n=24, seed=3)
+    rays = torch.from_numpy(I.traversal_rays(64, 32, n_random=4000, seed=52)).cuda()
+    s = gsp.Scene(ctx, sc)
+    n = rays.shape[0]
+    ref = [torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.float32, device="cuda")]
+    gsp.gsp_trace_closest_hit(s.h, rays, *ref)
+    gsp.gsp_trace_time_launches(s.h, 3)
+    outs = []
+    for _ in range(5):  # two more calls than pairs: they are not timed
+        o = [torch.empty_like(ref[0]), torch.empty_like(ref[1])]
+        gsp.gsp_trace_closest_hit(s.h, rays, *o)
+        outs.append(o)
+    ms = gsp.gsp_trace_launch_times(s.h, 8)
+    assert len(ms) == 3 and np.all(ms > 0) and np.all(ms < 1000)
+    for o in outs:
+        assert torch.equal(o[0], ref[0]) and torch.equal(o[1].view(torch.int32), ref[1].view(torch.int32))
+    assert len(gsp.gsp_trace_launch_times(s.h, 8)) == 0  # nothing recorded since the read
+    gsp.gsp_trace_closest_hit(s.h, rays, *outs[0])
+    assert len(gsp.gsp_trace_launch_times(s.h, 8)) == 1  # recording restarted from the first pair
+    gsp.gsp_trace_time_launches(s.h, 0)
+    gsp.gsp_trace_closest_hit(s.h, rays, *outs[0])
+    assert len(gsp.gsp_trace_launch_times(s.h, 8)) == 0
+    with pytest.raises(gsp.GspError):
+        gsp.gsp_trace_time_launches(s.h, -1)
+    ctx.sync()
