@@ -295,7 +295,16 @@ extern "C" gsp_status gsp_build_bvh_device(gsp_scene* s, int32_t link_sets, int3
     A(&box, nn);
     A(&arrived, std::max<int64_t>(1, n - 1));
     A(&d_depth, 1);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // build and threading times
+    auto drop_events = [&]() {
+        for (cudaEvent_t& x : ev)
+            if (x) {
+                cudaEventDestroy(x);
+                x = nullptr;
+            }
+    };
     auto fail = [&](cudaError_t ce) {
+        drop_events();
         for (void* p : tmp) cudaFree(p);
         const gsp_status st = gsp_cuda_fail(ce);
         gsp_set_last_error(std::string("gsp_build_bvh_device: ") + cudaGetErrorString(ce));
@@ -303,8 +312,9 @@ extern "C" gsp_status gsp_build_bvh_device(gsp_scene* s, int32_t link_sets, int3
     };
     if (e != cudaSuccess) return fail(e);
 
-    cudaEvent_t ev[3];
-    for (auto& x : ev) cudaEventCreate(&x);
+    for (cudaEvent_t& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    if (e != cudaSuccess) return fail(e);
     const uint32_t nn32 = (uint32_t)nt;
     e = cudaMemcpy(d_verts, s->verts.data(), 3 * s->nv * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_tris, s->tris.data(), 3 * nt * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -352,7 +362,7 @@ extern "C" gsp_status gsp_build_bvh_device(gsp_scene* s, int32_t link_sets, int3
     float build_ms = 0, thread_ms = 0;
     cudaEventElapsedTime(&build_ms, ev[0], ev[1]);
     cudaEventElapsedTime(&thread_ms, ev[1], ev[2]);
-    for (auto& x : ev) cudaEventDestroy(x);
+    drop_events();
     int32_t depth = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&depth, d_depth, sizeof depth, cudaMemcpyDeviceToHost);
     // host copies (host walk, export), as the host build keeps them
