@@ -566,7 +566,7 @@ static gsp_status paths_front(gsp_sppm* r, const PassDev& P, const EyeOut& O, co
     J.np_ptr = ph_left ? r->qctr + 8 + bp % 3 : nullptr;
     J.first_chunk = 0;
     const int64_t items = (eye_left ? r->npix : 0) + (ph_left ? r->np : 0);
-    J.nchunks = (int32_t)((items + kTraceChunk - 1) / kTraceChunk);
+    J.nchunks = (int32_t)((items + kMultiChunk - 1) / kMultiChunk);
     return GSP_OK;
 }
 
@@ -577,7 +577,7 @@ static gsp_status stage_paths(gsp_sppm* r, const PassDev& P, const EyeOut& O, co
     if (e != GSP_OK) return e;
     if (J.nchunks > 0) {
         const bool stack = r->traversal == GSP_TRAVERSAL_STACK;
-        const unsigned grid = (unsigned)path_grid((int64_t)J.nchunks * kTraceChunk, r->scene->ctx->device, stack, J.S.attr != nullptr);
+        const unsigned grid = (unsigned)path_grid((int64_t)J.nchunks * kMultiChunk, r->scene->ctx->device, stack, J.S.attr != nullptr);
         if (stack)
             J.S.attr ? k_paths<true, true, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12)
                      : k_paths<true, false, false><<<grid, kTraceThreads, 0, st>>>(J.S, P, J.qe, O, J.ne_ptr, J.qp, D, J.np_ptr, r->qctr + 12);
@@ -1064,7 +1064,7 @@ static gsp_status batch_capture_fused(gsp_batch* b, cudaStream_t st, int K, cuda
         const PathJob* jt = b->d_jobs + base + (size_t)k * n;
         if (ce == cudaSuccess && total[k] > 0) {
             ce = cudaMemsetAsync(ctr, 0, sizeof(uint32_t), ps);
-            const unsigned grid = (unsigned)path_grid((int64_t)total[k] * kTraceChunk, b->device, stack, shade, true);
+            const unsigned grid = (unsigned)path_grid((int64_t)total[k] * kMultiChunk, b->device, stack, shade, true);
             if (ce == cudaSuccess) {
                 if (stack)
                     shade ? k_paths_multi<true, true><<<grid, kTraceThreads, 0, ps>>>(jt, n, total[k], ctr)

@@ -16,10 +16,14 @@
 #ifndef GSP_PATH_MULTI_MIN_BLOCKS  // the multi-scene path kernel: 70 registers without spills
 #define GSP_PATH_MULTI_MIN_BLOCKS 7
 #endif
+#ifndef GSP_MULTI_CHUNK  // items (eye or photon paths) of one job that a warp takes at once
+#define GSP_MULTI_CHUNK 64
+#endif
 
 namespace gspd {
 
 constexpr float kPi = 3.14159265358979323846f;
+constexpr int kMultiChunk = GSP_MULTI_CHUNK;  // a job's chunk in the multi-scene path kernel
 constexpr int kSlotsPerPath = 32;
 
 // The camera with its FP64 basis, tan(vfov / 2) and aspect ratio each split into double-float
@@ -715,8 +719,8 @@ struct MultiQueue {
         job = lo;
         const PathJob& J = jobs[lo];
         const int32_t items = (J.ne_ptr ? (int32_t)*J.ne_ptr : 0) + (J.np_ptr ? (int32_t)*J.np_ptr : 0);
-        pos = (c - J.first_chunk) * kTraceChunk;
-        pend = min(pos + kTraceChunk, items);
+        pos = (c - J.first_chunk) * kMultiChunk;
+        pend = min(pos + kMultiChunk, items);
         return pos < pend;
     }
 
